@@ -1,0 +1,178 @@
+/*
+ * apfc.h - C ABI of the GB300 library for the semi-implicit time step of the
+ * amplitude expansion of the phase-field crystal model (APFC).
+ *
+ * Method: Praetorius, Salvalaglio, Voigt, "An efficient numerical framework
+ * for the amplitude expansion of the phase-field crystal model",
+ * arXiv:1902.09761.
+ *
+ *   Model (Sec. II, Eqs. energyamplitude, amplitudetime, gs), standard
+ *   parameters (dB, Bx, t, v) = (2 a1, a0, a3, 4 a2 / 3):
+ *     d eta_j/dt = -|k_j|^2 [ (dB + Bx G_j^2) eta_j + N_j(eta) ],
+ *     G_j = Laplacian + 2i k_j . grad.
+ *   Space: uniform periodic grid, second-order central differences
+ *   (G_h = L_h + 2i k_j . D_h), replacing the paper's P1 finite elements.
+ *   Time (Alg. 1, one nonlinear iterate, nonlinear term explicit): per
+ *   amplitude the split block system of Eq. linear_system2 with M = I,
+ *     [ I             -G_h              ] [zeta]   [ 0                      ]
+ *     [ kap Bx G_h    (1/dt + kap dB) I ] [eta ] = [ eta^n/dt - kap N(eta^n) ]
+ *   solved by a Krylov method right-preconditioned with the factorised
+ *   Schur-complement preconditioner of Eq. preconditioner (Sec. II.B), whose
+ *   diffusion solves are Chebyshev polynomials of a stencil.
+ *
+ * Every entry point returns an apfc_status and never aborts.  Errors are
+ * sticky on a context: after a failure, apfc_last_error() describes it and
+ * calls that advance the state refuse to run until apfc_set_amplitudes()
+ * resets the context.
+ *
+ * Buffers: complex numbers are interleaved (re, im) doubles (complex128).
+ * "where" says whether a caller pointer is host (APFC_HOST) or device
+ * (APFC_DEVICE) memory.  The caller owns every buffer it passes; the library
+ * copies in or out and keeps no caller pointer.  Device copies run on the
+ * context's stream; every call that takes "where" returns after its copies
+ * have completed.
+ *
+ * Field layout: amplitude arrays are [J][nz][ny][nx] (x fastest).  Block
+ * vectors (the unknowns (zeta_j, eta_j) of the block system) are
+ * [J][2][nz][ny][nx]: for amplitude j first the zeta-part, then the eta-part.
+ *
+ * Threading: one context per stream; calls on one context must not overlap.
+ */
+#ifndef APFC_H
+#define APFC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct apfc_ctx apfc_ctx;
+
+typedef enum {
+  APFC_OK = 0,
+  APFC_EINVAL = 1,  /* bad argument; nothing was changed                          */
+  APFC_ENOMEM = 2,  /* device or host allocation failed                           */
+  APFC_ECUDA = 3,   /* a CUDA call failed; see apfc_last_error                    */
+  APFC_ENOCONV = 4, /* Krylov solve hit max_iter; the best iterate is kept        */
+  APFC_ENAN = 5,    /* a residual norm became NaN/Inf (e.g. NaN amplitudes)       */
+  APFC_ESTATE = 6   /* context is in a failed state or has no amplitudes yet      */
+} apfc_status;
+
+enum { APFC_HOST = 0, APFC_DEVICE = 1 };
+
+/* Lattices.  HEX2D: triangular lattice, J = 3, dim = 2, k_1 + k_2 + k_3 = 0,
+ * nonlinear term in the closed form of Sec. II.  BCC3D / CUSTOM: the nonlinear
+ * term is generated from k by keeping the resonant (zero-sum) wavevector
+ * combinations of the cell-averaged density powers <n^3>, <n^4>, with
+ * n = sum_j (eta_j e^{i k_j.r} + c.c.) (Eq. density). */
+enum { APFC_LATTICE_CUSTOM = 0, APFC_LATTICE_HEX2D = 1, APFC_LATTICE_BCC3D = 2 };
+
+enum { APFC_FP64 = 0,         /* fields, Krylov iterates and reductions in FP64 */
+       APFC_FP32_REFINED = 1  /* FP32 Krylov inside FP64 iterative refinement   */ };
+enum { APFC_BICGSTAB = 0 };
+enum { APFC_TAU_FOLD = 0,     /* preconditioner uses 1/tau = 1/dt + kap dB      */
+       APFC_TAU_PLAIN = 1     /* preconditioner uses tau = dt                    */ };
+
+#define APFC_MAX_J 8
+
+typedef struct {
+  int lattice;               /* APFC_LATTICE_*                                   */
+  int dim;                   /* 2 or 3                                           */
+  int J;                     /* number of amplitudes, 1..APFC_MAX_J              */
+  double k[APFC_MAX_J][3];   /* reciprocal vectors k_j (x, y, z); z ignored in 2D */
+} apfc_lattice;
+
+typedef struct { double dB, Bx, t, v; } apfc_params;
+
+typedef struct {
+  int n[3];                  /* grid points (nx, ny, nz); nz = 1 in 2D; each >= 3 */
+  double h[3];               /* spacings (hx, hy, hz) > 0                          */
+} apfc_grid;
+
+typedef struct {
+  int precision;             /* APFC_FP64 or APFC_FP32_REFINED                     */
+  int krylov;                /* APFC_BICGSTAB                                       */
+  int max_iter;              /* cap on Krylov iterations per solve (per refinement) */
+  int cheb_degree;           /* applications of D per diffusion solve in P^{-1}, 0..16 */
+  int tau_mode;              /* APFC_TAU_FOLD or APFC_TAU_PLAIN                     */
+  int max_refine;            /* cap on FP64 refinement sweeps (FP32_REFINED)        */
+  int check_every;           /* Krylov iterations between convergence checks        */
+  int reserved;
+  double tol;                /* stop at ||b - A x||_2 <= tol ||b||_2 (block norm, per amplitude) */
+  double tol_inner;          /* relative tolerance of each FP32 inner solve         */
+} apfc_opts;
+
+typedef struct {
+  long long steps;           /* steps taken since apfc_set_amplitudes             */
+  long long iters_total;     /* Krylov iterations summed over steps and amplitudes */
+  int iters_last;            /* max over amplitudes of iterations in the last step */
+  int refine_last;           /* refinement sweeps in the last step (FP32_REFINED)  */
+  double resid_last;         /* max over amplitudes of ||b-Ax||/||b|| after the last step */
+} apfc_stats_t;
+
+/* Fill *o with defaults: FP64, BiCGStab, tol 1e-10, max_iter 500,
+ * cheb_degree 3, tau fold, max_refine 10, tol_inner 1e-4, check_every 4. */
+apfc_status apfc_default_opts(apfc_opts* o);
+
+/* Relaxed-solid amplitude phi of a uniform crystal (eta_j = phi for all j):
+ * the larger root of the uniform stationarity condition.  HEX2D:
+ * phi = (t + sqrt(t^2 - 15 v dB)) / (15 v).  BCC3D: phi = (2t + sqrt(4t^2 -
+ * 45 v dB)) / (45 v).  EINVAL for CUSTOM or when the root is not real. */
+apfc_status apfc_uniform_amplitude(const apfc_lattice* lat, const apfc_params* p, double* phi);
+
+/* Create a context (Sec. II model on the given grid).  Validates arguments,
+ * builds per-amplitude stencil coefficients and the nonlinear-term table, and
+ * allocates all device memory it needs (the context owns it).  stream: a
+ * cudaStream_t (NULL = legacy default stream) used for every launch.  opts may
+ * be NULL (defaults).  Amplitudes start unset (apfc_step returns ESTATE). */
+apfc_status apfc_init(apfc_ctx** ctx, const apfc_lattice* lat, const apfc_params* p,
+                      const apfc_grid* g, const apfc_opts* opts, void* stream);
+
+/* Replace the solver options (precision, tolerances, degree). */
+apfc_status apfc_set_opts(apfc_ctx* ctx, const apfc_opts* opts);
+
+/* Copy amplitudes eta in ([J][nz][ny][nx] complex128) and set zeta = G_h eta
+ * (the auxiliary field of Sec. II.A).  Clears a sticky error and the stats. */
+apfc_status apfc_set_amplitudes(apfc_ctx* ctx, const void* eta, int where);
+
+/* Copy the current amplitudes eta (or the auxiliary field zeta) out. */
+apfc_status apfc_get_amplitudes(apfc_ctx* ctx, void* eta, int where);
+apfc_status apfc_get_zeta(apfc_ctx* ctx, void* zeta, int where);
+
+/* Advance n steps of size dt (Alg. 1 with one nonlinear iterate): explicit
+ * nonlinear right-hand side from eta^n for all amplitudes, then one
+ * preconditioned Krylov solve per amplitude from the initial guess
+ * (zeta^n, eta^n).  Returns after the last step; ENOCONV / ENAN if a solve
+ * failed (the state then holds the last iterate). */
+apfc_status apfc_step(apfc_ctx* ctx, double dt, int n);
+
+/* Discrete free energy (Eq. energyamplitude with the gradient term scaled so
+ * that its Wirtinger derivative is the flow's Bx G_h^2 eta_j):
+ *   F = h^d sum_points [ dB/2 A^2 + t-, v-terms of the bulk polynomial
+ *                        + Bx sum_j |G_h eta_j|^2 ],  in FP64. */
+apfc_status apfc_energy(apfc_ctx* ctx, double* F);
+
+apfc_status apfc_stats(const apfc_ctx* ctx, apfc_stats_t* out);
+const char* apfc_last_error(const apfc_ctx* ctx);
+void apfc_destroy(apfc_ctx* ctx);
+
+/* ---- operator-level entry points (FP64; same kernels as the step) ---------- */
+
+/* y = A_j x for every amplitude (block operator of Eq. linear_system2, M = I);
+ * x, y: block vectors [J][2][pts] complex128. */
+apfc_status apfc_apply_operator(apfc_ctx* ctx, double dt, const void* x, void* y, int where);
+
+/* x = P_j^{-1} b for every amplitude: the four-step application of the
+ * preconditioner of Eq. preconditioner (Sec. II.B) with M = I and the
+ * diffusion solves D^{-1} replaced by cheb_degree-application Chebyshev
+ * polynomials on D's spectral interval; step 4 uses the sign that inverts the
+ * displayed factorisation.  b, x: block vectors [J][2][pts]. */
+apfc_status apfc_apply_preconditioner(apfc_ctx* ctx, double dt, const void* b, void* x, int where);
+
+/* rhs_j = eta_j/dt - |k_j|^2 N_j(eta) for every amplitude (the explicit
+ * nonlinear right-hand side); eta, rhs: [J][pts] complex128. */
+apfc_status apfc_nonlinear_rhs(apfc_ctx* ctx, double dt, const void* eta, void* rhs, int where);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* APFC_H */

@@ -1,0 +1,301 @@
+"""Thin ctypes binding of libapfc (the C ABI declared in include/apfc.h).
+
+Argument marshalling only: every step of the time integration runs in the
+CUDA library.  The binding refuses to run when the library is missing; there
+is no CPU fallback.
+
+Buffers may be numpy arrays (host memory, ``APFC_HOST``) or torch CUDA
+tensors (device memory, ``APFC_DEVICE``), complex128 and C-contiguous.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libapfc.so")
+
+APFC_OK, APFC_EINVAL, APFC_ENOMEM, APFC_ECUDA, APFC_ENOCONV, APFC_ENAN, APFC_ESTATE = range(7)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENAN", 6: "ESTATE"}
+APFC_HOST, APFC_DEVICE = 0, 1
+APFC_LATTICE_CUSTOM, APFC_LATTICE_HEX2D, APFC_LATTICE_BCC3D = 0, 1, 2
+APFC_FP64, APFC_FP32_REFINED = 0, 1
+APFC_BICGSTAB = 0
+APFC_TAU_FOLD, APFC_TAU_PLAIN = 0, 1
+APFC_MAX_J = 8
+
+
+class ApfcError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"apfc status {STATUS_NAMES.get(status, status)}: {msg}")
+
+
+class Lattice(C.Structure):
+    _fields_ = [("lattice", C.c_int), ("dim", C.c_int), ("J", C.c_int), ("k", (C.c_double * 3) * APFC_MAX_J)]
+
+
+class Params(C.Structure):
+    _fields_ = [("dB", C.c_double), ("Bx", C.c_double), ("t", C.c_double), ("v", C.c_double)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("n", C.c_int * 3), ("h", C.c_double * 3)]
+
+
+class Opts(C.Structure):
+    _fields_ = [
+        ("precision", C.c_int),
+        ("krylov", C.c_int),
+        ("max_iter", C.c_int),
+        ("cheb_degree", C.c_int),
+        ("tau_mode", C.c_int),
+        ("max_refine", C.c_int),
+        ("check_every", C.c_int),
+        ("reserved", C.c_int),
+        ("tol", C.c_double),
+        ("tol_inner", C.c_double),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("steps", C.c_longlong),
+        ("iters_total", C.c_longlong),
+        ("iters_last", C.c_int),
+        ("refine_last", C.c_int),
+        ("resid_last", C.c_double),
+    ]
+
+
+EXPORTS = {
+    "apfc_default_opts": (C.c_int, [C.POINTER(Opts)]),
+    "apfc_uniform_amplitude": (C.c_int, [C.POINTER(Lattice), C.POINTER(Params), C.POINTER(C.c_double)]),
+    "apfc_init": (
+        C.c_int,
+        [C.POINTER(C.c_void_p), C.POINTER(Lattice), C.POINTER(Params), C.POINTER(Grid), C.POINTER(Opts), C.c_void_p],
+    ),
+    "apfc_set_opts": (C.c_int, [C.c_void_p, C.POINTER(Opts)]),
+    "apfc_set_amplitudes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "apfc_get_amplitudes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "apfc_get_zeta": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "apfc_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
+    "apfc_energy": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "apfc_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
+    "apfc_last_error": (C.c_char_p, [C.c_void_p]),
+    "apfc_destroy": (None, [C.c_void_p]),
+    "apfc_apply_operator": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_int]),
+    "apfc_apply_preconditioner": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_int]),
+    "apfc_nonlinear_rhs": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_int]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libapfc.so (built by ``paper_1902_09761_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libapfc.so is not built ({path}); run __graft_entry__.build() first")
+    lib = C.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------------------
+# Plain wrappers with the C names
+# ---------------------------------------------------------------------------
+
+
+def make_lattice(k, kind: int) -> Lattice:
+    k = np.asarray(k, dtype=float)
+    L = Lattice()
+    L.lattice = kind
+    L.J, L.dim = k.shape
+    for j in range(L.J):
+        for d in range(L.dim):
+            L.k[j][d] = float(k[j, d])
+    return L
+
+
+def make_params(dB, Bx, t, v) -> Params:
+    return Params(dB, Bx, t, v)
+
+
+def make_grid(shape, h) -> Grid:
+    """shape in array order ((ny, nx) or (nz, ny, nx)); h in (x, y[, z]) order."""
+    dim = len(shape)
+    g = Grid()
+    for d in range(3):
+        g.n[d] = int(shape[dim - 1 - d]) if d < dim else 1
+        g.h[d] = float(h[d]) if d < dim else 1.0
+    return g
+
+
+def apfc_default_opts(**kw) -> Opts:
+    o = Opts()
+    _check(load().apfc_default_opts(C.byref(o)))
+    for key, val in kw.items():
+        setattr(o, key, val)
+    return o
+
+
+def apfc_uniform_amplitude(lattice: Lattice, params: Params) -> float:
+    phi = C.c_double()
+    _check(load().apfc_uniform_amplitude(C.byref(lattice), C.byref(params), C.byref(phi)))
+    return phi.value
+
+
+def _check(status, ctx=None):
+    if status != APFC_OK:
+        msg = load().apfc_last_error(ctx).decode() if ctx else ""
+        raise ApfcError(status, msg)
+
+
+def _ptr(buf, writable=False):
+    """(pointer, where, keepalive) of a numpy array or torch tensor of complex128."""
+    if isinstance(buf, np.ndarray):
+        if buf.dtype != np.complex128 or not buf.flags["C_CONTIGUOUS"]:
+            raise TypeError("numpy buffers must be C-contiguous complex128")
+        if writable and not buf.flags["WRITEABLE"]:
+            raise TypeError("output buffer is read-only")
+        return buf.ctypes.data_as(C.c_void_p), APFC_HOST, buf
+    import torch  # device buffers only
+
+    if not isinstance(buf, torch.Tensor):
+        raise TypeError("buffer must be a numpy array or a torch tensor")
+    if buf.dtype != torch.complex128 or not buf.is_contiguous():
+        raise TypeError("torch buffers must be contiguous complex128")
+    if buf.is_cuda:
+        return C.c_void_p(buf.data_ptr()), APFC_DEVICE, buf
+    if writable:
+        raise TypeError("host output must be a numpy array")
+    arr = buf.numpy()
+    return arr.ctypes.data_as(C.c_void_p), APFC_HOST, arr
+
+
+class Context:
+    """One APFC simulation on one CUDA stream (owns the library context)."""
+
+    def __init__(self, k, kind, params, shape, h, opts: Opts | None = None, stream=None):
+        lib = load()
+        self.shape = tuple(int(s) for s in shape)
+        self.k = np.asarray(k, dtype=float)
+        self.J, self.dim = self.k.shape
+        self.lattice = make_lattice(self.k, kind)
+        self.params = params if isinstance(params, Params) else make_params(*params)
+        self.grid = make_grid(self.shape, h)
+        self.opts = opts if opts is not None else apfc_default_opts()
+        handle = C.c_void_p()
+        st = lib.apfc_init(
+            C.byref(handle), C.byref(self.lattice), C.byref(self.params), C.byref(self.grid), C.byref(self.opts),
+            C.c_void_p(stream) if stream else None,
+        )
+        _check(st)
+        self._h = handle
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            load().apfc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- state -------------------------------------------------------------
+    @property
+    def amp_shape(self):
+        return (self.J,) + self.shape
+
+    @property
+    def block_shape(self):
+        return (self.J, 2) + self.shape
+
+    def set_opts(self, opts: Opts):
+        _check(load().apfc_set_opts(self._h, C.byref(opts)), self._h)
+        self.opts = opts
+
+    def set_amplitudes(self, eta):
+        p, where, keep = _ptr(eta)
+        _check(load().apfc_set_amplitudes(self._h, p, where), self._h)
+
+    def get_amplitudes(self, out=None):
+        out = np.empty(self.amp_shape, np.complex128) if out is None else out
+        p, where, keep = _ptr(out, True)
+        _check(load().apfc_get_amplitudes(self._h, p, where), self._h)
+        return out
+
+    def get_zeta(self, out=None):
+        out = np.empty(self.amp_shape, np.complex128) if out is None else out
+        p, where, keep = _ptr(out, True)
+        _check(load().apfc_get_zeta(self._h, p, where), self._h)
+        return out
+
+    def step(self, dt: float, n: int = 1):
+        _check(load().apfc_step(self._h, float(dt), int(n)), self._h)
+
+    def try_step(self, dt: float, n: int = 1) -> int:
+        """apfc_step returning the raw status instead of raising."""
+        return load().apfc_step(self._h, float(dt), int(n))
+
+    def energy(self) -> float:
+        F = C.c_double()
+        _check(load().apfc_energy(self._h, C.byref(F)), self._h)
+        return F.value
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().apfc_stats(self._h, C.byref(s)), self._h)
+        return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+    def last_error(self) -> str:
+        return load().apfc_last_error(self._h).decode()
+
+    # -- operator-level entry points --------------------------------------
+    def _binary(self, fn, dt, x, shape, out):
+        out = np.empty(shape, np.complex128) if out is None else out
+        px, wx, kx = _ptr(x)
+        py, wy, ky = _ptr(out, True)
+        if wx != wy:
+            raise TypeError("input and output must both be host or both be device buffers")
+        _check(fn(self._h, float(dt), px, py, wx), self._h)
+        return out
+
+    def apply_operator(self, dt, x, out=None):
+        return self._binary(load().apfc_apply_operator, dt, x, self.block_shape, out)
+
+    def apply_preconditioner(self, dt, b, out=None):
+        return self._binary(load().apfc_apply_preconditioner, dt, b, self.block_shape, out)
+
+    def nonlinear_rhs(self, dt, eta, out=None):
+        return self._binary(load().apfc_nonlinear_rhs, dt, eta, self.amp_shape, out)
+
+
+def apfc_init(k, kind, params, shape, h, opts=None, stream=None) -> Context:
+    return Context(k, kind, params, shape, h, opts, stream)
+
+
+def apfc_step(ctx: Context, dt: float, n: int = 1):
+    ctx.step(dt, n)
+
+
+def apfc_energy(ctx: Context) -> float:
+    return ctx.energy()

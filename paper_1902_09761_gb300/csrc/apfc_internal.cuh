@@ -1,0 +1,169 @@
+// Internal declarations shared by the CUDA translation units of libapfc.
+//
+// Notation follows arXiv:1902.09761, Sec. II: amplitudes eta_j, auxiliary
+// fields zeta_j = G_j eta_j, G_h = L_h + 2i k_j . D_h on a periodic grid.
+//
+// Storage: a "field" is [J][pts] complex; a "block vector" is [J][2][pts]
+// complex (zeta-part, then eta-part, per amplitude).  A FieldRef addresses
+// amplitude j of a field or of one part of a block vector through a stride.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "apfc.h"
+
+namespace apfc {
+
+constexpr int kMaxJ = APFC_MAX_J;
+constexpr int kMaxCheb = 16;     // Chebyshev applications per diffusion solve
+constexpr int kMaxTerms = 96;    // derivative / energy monomials of table lattices
+constexpr int kDotBlocks = 304;  // partial-sum blocks per amplitude (2 x 152 SMs)
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Complex helpers (interleaved double2 / float2)
+// ---------------------------------------------------------------------------
+template <typename T> struct CT;
+template <> struct CT<double> { using c = double2; };
+template <> struct CT<float> { using c = float2; };
+template <typename T> using cplx = typename CT<T>::c;
+
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> mkc(T re, T im) {
+  cplx<T> r;
+  r.x = re;
+  r.y = im;
+  return r;
+}
+
+template <typename T>
+struct FieldRef {
+  cplx<T>* p;
+  long long ld;  // elements between amplitude j and j+1
+  __device__ __forceinline__ cplx<T>* at(int j) const { return p + (long long)j * ld; }
+};
+template <typename T>
+struct CFieldRef {
+  const cplx<T>* p;
+  long long ld;
+  __device__ __forceinline__ const cplx<T>* at(int j) const { return p + (long long)j * ld; }
+};
+
+// ---------------------------------------------------------------------------
+// Operator coefficients (rebuilt when dt changes)
+// ---------------------------------------------------------------------------
+struct OpCoef {
+  int J, dim, nx, ny, nz;
+  long long pts;            // nx * ny * nz
+  double ih2[3];            // 1/h_d^2
+  double c0;                // -2 sum_d 1/h_d^2 (centre weight of L_h)
+  double kh[kMaxJ][3];      // k_{j,d} / h_d: 2i k_d D_d u = i (k_d/h_d)(u+ - u-)
+  double kap[kMaxJ];        // |k_j|^2
+  double kt[kMaxJ];         // |k_j|^2 Bx: coefficient of G_h in the (2,1) block
+  double a[kMaxJ];          // 1/dt + |k_j|^2 dB: the (2,2) block
+  double inv_dt;
+  double sD[kMaxJ];         // D = sD I + mu (-L_h), sD = 1/sqrt(tau~)
+  double mu[kMaxJ];         //                       mu = sqrt(kt)
+  double inv_mu[kMaxJ];
+  double inv_theta[kMaxJ];  // Chebyshev: 1/theta, theta = centre of D's interval
+};
+
+// Chebyshev recurrence weights for one application (per amplitude):
+// d_{k+1} = c1 d_k + c2 r_{k+1}.
+struct ChebStep {
+  double c1[kMaxJ];
+  double c2[kMaxJ];
+};
+
+// Nonlinear term N_j.  hex = 1: closed form of the triangular lattice.
+// Otherwise N_j = sum_{terms of j} coef * prod_f mode(f) with
+// mode(f) = eta_{f>>1} if (f & 1) == 0 else conj(eta_{f>>1}).
+struct NonlinTable {
+  int hex;
+  double t, v;
+  int start[kMaxJ + 1];
+  double coef[kMaxTerms];
+  int nf[kMaxTerms];
+  int f[kMaxTerms][3];
+};
+
+// Bulk energy density beyond dB/2 A^2 for table lattices: sum_e ecoef Re(prod).
+struct EnergyTable {
+  int hex;
+  double dB, t, v;
+  int ne;
+  double coef[kMaxTerms];
+  int nf[kMaxTerms];
+  int f[kMaxTerms][4];
+};
+
+// Per-amplitude Krylov scalars, resident on the device.
+struct KScal {
+  double2 rho, alpha, omega, beta;
+  double bnorm2, rnorm2, tol2, tolrel2;
+  int active, iters, status, max_iter;
+};
+
+enum KStatus { KS_RUNNING = 0, KS_CONVERGED = 1, KS_NOCONV = 2, KS_BREAKDOWN = 3, KS_NAN = 4 };
+enum KOp { OP_INIT = 0, OP_ALPHA = 1, OP_SNORM = 2, OP_OMEGA = 3, OP_RHO = 4, OP_NORMS = 5 };
+
+// Up to three (u, v) pairs of block vectors for conj(u).v per amplitude.
+template <typename T>
+struct DotPairs {
+  const cplx<T>* u[3];
+  const cplx<T>* v[3];
+};
+
+// ---------------------------------------------------------------------------
+// kernels.cu
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_apply_A(const cplx<T>* x, cplx<T>* y, const OpCoef& c, const KScal* act, cudaStream_t s);
+template <typename T>
+void launch_residual(const cplx<T>* b, const cplx<T>* x, cplx<T>* r, cplx<T>* rhat, const OpCoef& c,
+                     cudaStream_t s);
+template <typename T>
+void launch_pc_rhs(const cplx<T>* beta, FieldRef<T> f, const OpCoef& c, const KScal* act, cudaStream_t s);
+template <typename T>
+void launch_cheb_zero(CFieldRef<T> f, FieldRef<T> X, const OpCoef& c, const KScal* act, cudaStream_t s);
+template <typename T>
+void launch_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
+                       const OpCoef& c, const KScal* act, cudaStream_t s);
+template <typename T>
+void launch_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
+                       const OpCoef& c, const KScal* act, cudaStream_t s);
+template <typename T>
+void launch_pc_final(const cplx<T>* beta, CFieldRef<T> b2p, cplx<T>* chi, const OpCoef& c, const KScal* act,
+                     cudaStream_t s);
+template <typename T>
+void launch_p_update(const cplx<T>* r, cplx<T>* p, const cplx<T>* v, const OpCoef& c, const KScal* k,
+                     cudaStream_t s);
+template <typename T>
+void launch_s_update(cplx<T>* r, const cplx<T>* v, cplx<T>* u, const cplx<T>* p, const OpCoef& c, const KScal* k,
+                     cudaStream_t s);
+template <typename T>
+void launch_r_update(cplx<T>* r, const cplx<T>* t, cplx<T>* u, const OpCoef& c, const KScal* k, cudaStream_t s);
+template <typename T>
+void launch_add_to(const cplx<T>* d, double2* x, const OpCoef& c, cudaStream_t s);
+
+void launch_rhs(const double2* x, double2* b, const OpCoef& c, const NonlinTable& nt, cudaStream_t s);
+void launch_zeta(double2* x, const OpCoef& c, cudaStream_t s);
+void launch_residual_refine(const double2* b, const double2* x, float2* r32, double* partials, const OpCoef& c,
+                            cudaStream_t s);
+void launch_energy(const double2* x, double* partials, double* out, const OpCoef& c, const EnergyTable& et,
+                   double Bx, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// reduce.cu
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_dots(int npair, const DotPairs<T>& pr, void* partials, const OpCoef& c, const KScal* act,
+                 cudaStream_t s);
+template <typename T>
+void launch_finalize(int npair, const void* partials, KScal* k, int op, int J, cudaStream_t s);
+// partials in FP64 double2 layout regardless of T (for the fused FP64 residual)
+void launch_finalize64(int npair, const void* partials, KScal* k, int op, int J, cudaStream_t s);
+
+}  // namespace apfc

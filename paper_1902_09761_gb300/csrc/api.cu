@@ -1,0 +1,797 @@
+// C ABI of libapfc: context, validation, nonlinear-term tables, the Krylov
+// driver and the time step (arXiv:1902.09761, Alg. 1 with one nonlinear
+// iterate and the nonlinear term explicit; Sec. II.B for the solver).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "apfc_internal.cuh"
+
+using namespace apfc;
+
+namespace {
+
+template <typename T>
+struct Work {
+  static constexpr int kBlocks = 8;  // r, rhat, p, v, u, t, z, bb
+  static constexpr int kFields = 5;  // f, b2p, R, Da, Db
+  cplx<T>* blk[kBlocks] = {};
+  cplx<T>* fld[kFields] = {};
+  void* partials = nullptr;  // [J][3][kDotBlocks] x 16 bytes
+  KScal* ks = nullptr;       // device
+  KScal* ks_host = nullptr;  // pinned
+  bool ready = false;
+};
+
+}  // namespace
+
+struct apfc_ctx {
+  apfc_lattice lat;
+  apfc_params par;
+  apfc_grid grid;
+  apfc_opts opts;
+  cudaStream_t stream = nullptr;
+  int J = 0, dim = 0;
+  long long pts = 0;
+  NonlinTable nt;
+  EnergyTable et;
+  double2* x64 = nullptr;  // state block vector (zeta, eta) per amplitude
+  double2* b64 = nullptr;  // right-hand side block (0, rhs)
+  double* epart = nullptr;
+  double* eout = nullptr;
+  double* eout_host = nullptr;
+  Work<double> w64;
+  Work<float> w32;
+  KScal* ks64 = nullptr;       // refinement norms (device)
+  KScal* ks64_host = nullptr;  // pinned
+  void* part64 = nullptr;      // refinement partials
+  bool has_state = false;
+  bool failed = false;
+  std::string err;
+  apfc_stats_t stats{};
+  OpCoef coef{};
+  double coef_dt = -1.0;
+};
+
+namespace {
+
+apfc_status fail(apfc_ctx* c, apfc_status s, const std::string& msg) {
+  if (c) {
+    c->err = msg;
+    if (s == APFC_ECUDA || s == APFC_ENAN || s == APFC_ENOMEM) c->failed = true;
+  }
+  return s;
+}
+
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? APFC_ENOMEM : APFC_ECUDA,            \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+  } while (0)
+
+template <typename T>
+size_t block_bytes(const apfc_ctx* c) {
+  return sizeof(cplx<T>) * 2ull * (size_t)c->J * (size_t)c->pts;
+}
+template <typename T>
+size_t field_bytes(const apfc_ctx* c) {
+  return sizeof(cplx<T>) * (size_t)c->J * (size_t)c->pts;
+}
+
+template <typename T>
+apfc_status alloc_work(apfc_ctx* ctx, Work<T>& w) {
+  if (w.ready) return APFC_OK;
+  for (auto& b : w.blk) CK(cudaMalloc(&b, block_bytes<T>(ctx)));
+  for (auto& f : w.fld) CK(cudaMalloc(&f, field_bytes<T>(ctx)));
+  CK(cudaMalloc(&w.partials, 16ull * 3 * kDotBlocks * ctx->J));
+  CK(cudaMalloc(&w.ks, sizeof(KScal) * ctx->J));
+  CK(cudaMallocHost(&w.ks_host, sizeof(KScal) * ctx->J));
+  std::memset(w.ks_host, 0, sizeof(KScal) * ctx->J);
+  CK(cudaMemsetAsync(w.blk[7], 0, block_bytes<T>(ctx), ctx->stream));
+  w.ready = true;
+  return APFC_OK;
+}
+
+template <typename T>
+void free_work(Work<T>& w) {
+  for (auto& b : w.blk) cudaFree(b), b = nullptr;
+  for (auto& f : w.fld) cudaFree(f), f = nullptr;
+  cudaFree(w.partials);
+  cudaFree(w.ks);
+  if (w.ks_host) cudaFreeHost(w.ks_host);
+  w.partials = nullptr;
+  w.ks = nullptr;
+  w.ks_host = nullptr;
+  w.ready = false;
+}
+
+// ---------------------------------------------------------------------------
+// Nonlinear-term tables from the resonance rule: <n^p> keeps the ordered
+// p-tuples of signed modes (j, s) whose wavevectors s k_j sum to zero.
+// ---------------------------------------------------------------------------
+struct Mode {
+  int j, s;
+  bool operator<(const Mode& o) const { return j != o.j ? j < o.j : s < o.s; }
+  bool operator==(const Mode& o) const { return j == o.j && s == o.s; }
+};
+
+void enumerate(const apfc_lattice& L, int p, std::map<std::vector<Mode>, int>& out) {
+  const int nm = 2 * L.J;
+  std::vector<int> idx(p, 0);
+  while (true) {
+    double v[3] = {0, 0, 0};
+    for (int q = 0; q < p; ++q) {
+      const int j = idx[q] >> 1, s = (idx[q] & 1) ? -1 : 1;
+      for (int d = 0; d < L.dim; ++d) v[d] += s * L.k[j][d];
+    }
+    bool zero = true;
+    for (int d = 0; d < L.dim; ++d) zero = zero && std::fabs(v[d]) < 1e-9;
+    if (zero) {
+      std::vector<Mode> m;
+      for (int q = 0; q < p; ++q) m.push_back(Mode{idx[q] >> 1, (idx[q] & 1) ? -1 : 1});
+      std::sort(m.begin(), m.end());
+      out[m] += 1;
+    }
+    int q = p - 1;
+    while (q >= 0 && ++idx[q] == nm) idx[q--] = 0;
+    if (q < 0) break;
+  }
+}
+
+inline int code_of(const Mode& m) { return 2 * m.j + (m.s < 0 ? 1 : 0); }
+
+bool build_tables(const apfc_lattice& L, const apfc_params& P, NonlinTable& nt, EnergyTable& et, std::string& err) {
+  std::memset(&nt, 0, sizeof(nt));
+  std::memset(&et, 0, sizeof(et));
+  nt.t = et.t = P.t;
+  nt.v = et.v = P.v;
+  et.dB = P.dB;
+  nt.hex = et.hex = (L.lattice == APFC_LATTICE_HEX2D) ? 1 : 0;
+  if (nt.hex) return true;
+  std::map<std::vector<Mode>, int> m3, m4;
+  enumerate(L, 3, m3);
+  enumerate(L, 4, m4);
+  const double c3 = -P.t / 3.0, c4 = 0.25 * P.v;
+  int n = 0;
+  for (int j = 0; j < L.J; ++j) {
+    nt.start[j] = n;
+    for (int pass = 0; pass < 2; ++pass) {
+      const auto& tab = pass == 0 ? m3 : m4;
+      const double cp = pass == 0 ? c3 : c4;
+      for (const auto& kv : tab) {
+        const Mode target{j, -1};
+        const int cnt = (int)std::count(kv.first.begin(), kv.first.end(), target);
+        if (cnt == 0) continue;
+        if (n >= kMaxTerms) {
+          err = "nonlinear table too large for this lattice";
+          return false;
+        }
+        std::vector<Mode> rest = kv.first;
+        rest.erase(std::find(rest.begin(), rest.end(), target));
+        nt.coef[n] = cp * kv.second * cnt;
+        nt.nf[n] = (int)rest.size();
+        for (size_t q = 0; q < rest.size(); ++q) nt.f[n][q] = code_of(rest[q]);
+        ++n;
+      }
+    }
+  }
+  nt.start[L.J] = n;
+  int ne = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const auto& tab = pass == 0 ? m3 : m4;
+    const double cp = pass == 0 ? c3 : c4;
+    for (const auto& kv : tab) {
+      if (ne >= kMaxTerms) {
+        err = "energy table too large for this lattice";
+        return false;
+      }
+      et.coef[ne] = cp * kv.second;
+      et.nf[ne] = (int)kv.first.size();
+      for (size_t q = 0; q < kv.first.size(); ++q) et.f[ne][q] = code_of(kv.first[q]);
+      ++ne;
+    }
+  }
+  et.ne = ne;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Operator coefficients for a time step dt
+// ---------------------------------------------------------------------------
+bool build_coef(apfc_ctx* c, double dt, std::string& err) {
+  if (!(dt > 0.0) || !std::isfinite(dt)) {
+    err = "dt must be positive and finite";
+    return false;
+  }
+  if (c->coef_dt == dt) return true;
+  OpCoef& o = c->coef;
+  std::memset(&o, 0, sizeof(o));
+  o.J = c->J;
+  o.dim = c->dim;
+  o.nx = c->grid.n[0];
+  o.ny = c->grid.n[1];
+  o.nz = c->dim == 3 ? c->grid.n[2] : 1;
+  o.pts = c->pts;
+  double lapmax = 0.0;
+  for (int d = 0; d < c->dim; ++d) {
+    const double h = c->grid.h[d];
+    o.ih2[d] = 1.0 / (h * h);
+    o.c0 -= 2.0 / (h * h);
+    lapmax += 4.0 / (h * h);
+  }
+  o.inv_dt = 1.0 / dt;
+  for (int j = 0; j < c->J; ++j) {
+    double kap = 0.0;
+    for (int d = 0; d < c->dim; ++d) {
+      o.kh[j][d] = c->lat.k[j][d] / c->grid.h[d];
+      kap += c->lat.k[j][d] * c->lat.k[j][d];
+    }
+    o.kap[j] = kap;
+    o.kt[j] = kap * c->par.Bx;
+    o.a[j] = 1.0 / dt + kap * c->par.dB;
+    const double inv_tau = 1.0 / dt + (c->opts.tau_mode == APFC_TAU_FOLD ? kap * c->par.dB : 0.0);
+    if (!(o.a[j] > 0.0) || !(inv_tau > 0.0) || !(o.kt[j] > 0.0)) {
+      err = "need 1/dt + |k_j|^2 dB > 0 and |k_j|^2 Bx > 0";
+      return false;
+    }
+    o.sD[j] = std::sqrt(inv_tau);
+    o.mu[j] = std::sqrt(o.kt[j]);
+    o.inv_mu[j] = 1.0 / o.mu[j];
+    const double lmin = o.sD[j], lmax = o.sD[j] + o.mu[j] * lapmax;
+    o.inv_theta[j] = 2.0 / (lmax + lmin);
+  }
+  c->coef_dt = dt;
+  return true;
+}
+
+// Chebyshev recurrence weights (Saad, Sec. 12.3) for application k of D.
+std::vector<ChebStep> cheb_weights(const apfc_ctx* c) {
+  const int m = c->opts.cheb_degree;
+  std::vector<ChebStep> w(std::max(m, 1));
+  double lapmax = 0.0;
+  for (int d = 0; d < c->dim; ++d) lapmax += 4.0 / (c->grid.h[d] * c->grid.h[d]);
+  for (int j = 0; j < c->J; ++j) {
+    const double lmin = c->coef.sD[j], lmax = c->coef.sD[j] + c->coef.mu[j] * lapmax;
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    for (int k = 0; k < m; ++k) {
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      w[k].c1[j] = rn * rho;
+      w[k].c2[j] = 2.0 * rn / delta;
+      rho = rn;
+    }
+  }
+  return w;
+}
+
+// chi = P^{-1} beta (four steps of Sec. II.B, M = I).
+template <typename T>
+void apply_pinv(apfc_ctx* ctx, Work<T>& w, const cplx<T>* beta, cplx<T>* chi, const KScal* act,
+                const std::vector<ChebStep>& cw) {
+  const OpCoef& c = ctx->coef;
+  const long long P = c.pts;
+  FieldRef<T> f{w.fld[0], P}, b2p{w.fld[1], P}, R{w.fld[2], P};
+  FieldRef<T> D[2] = {{w.fld[3], P}, {w.fld[4], P}};
+  FieldRef<T> chi2{chi + P, 2 * P};
+  const int m = ctx->opts.cheb_degree;
+  auto cheb = [&](CFieldRef<T> src, FieldRef<T> X) {
+    if (m == 0) {
+      launch_cheb_zero<T>(src, X, c, act, ctx->stream);
+      return;
+    }
+    launch_cheb_first<T>(src, X, R, D[0], cw[0], m == 1, c, act, ctx->stream);
+    int cur = 0;
+    for (int k = 1; k < m; ++k) {
+      launch_cheb_sweep<T>(CFieldRef<T>{D[cur].p, P}, X, R, D[1 - cur], cw[k], k == m - 1, c, act, ctx->stream);
+      cur = 1 - cur;
+    }
+  };
+  launch_pc_rhs<T>(beta, f, c, act, ctx->stream);
+  cheb(CFieldRef<T>{f.p, P}, b2p);
+  cheb(CFieldRef<T>{b2p.p, P}, chi2);
+  launch_pc_final<T>(beta, CFieldRef<T>{b2p.p, P}, chi, c, act, ctx->stream);
+}
+
+template <typename T>
+apfc_status sync_scalars(apfc_ctx* ctx, Work<T>& w) {
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(w.ks_host, w.ks, sizeof(KScal) * ctx->J, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return APFC_OK;
+}
+
+// Right-preconditioned BiCGStab on A_j x = b for all amplitudes at once.
+// The iterate is kept as x = x0 + P^{-1} u, so P^{-1} is applied to the
+// search directions only inside A P^{-1} and once at the end.
+// T = double: b FP64, x0 = x64 (state), restarts from the true residual.
+// T = float : b FP32, x0 = 0, the correction P^{-1} u is added to x64.
+// Returns the worst per-amplitude KStatus; iterations in *iters (max over j).
+template <typename T>
+apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, double tol, int max_iter, int* iters,
+                   int* worst) {
+  const OpCoef& c = ctx->coef;
+  cudaStream_t s = ctx->stream;
+  cplx<T>*r = w.blk[0], *rhat = w.blk[1], *p = w.blk[2], *v = w.blk[3], *u = w.blk[4], *t = w.blk[5], *z = w.blk[6];
+  const auto cw = cheb_weights(ctx);
+  const size_t bb = block_bytes<T>(ctx);
+  const bool fp64 = sizeof(T) == 8;
+  const int attempts = fp64 ? 4 : 1;
+  std::vector<int> it_sum(ctx->J, 0);
+  *worst = KS_CONVERGED;
+  for (int attempt = 0;; ++attempt) {
+    // init: r = b - A x0, rhat = r, p = v = u = 0
+    for (int j = 0; j < ctx->J; ++j) {
+      w.ks_host[j].tolrel2 = tol * tol;
+      w.ks_host[j].max_iter = max_iter;
+    }
+    CK(cudaMemcpyAsync(w.ks, w.ks_host, sizeof(KScal) * ctx->J, cudaMemcpyHostToDevice, s));
+    if (fp64) {
+      launch_residual<T>(b, reinterpret_cast<const cplx<T>*>(x64), r, rhat, c, s);
+    } else {
+      CK(cudaMemcpyAsync(r, b, bb, cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(rhat, b, bb, cudaMemcpyDeviceToDevice, s));
+    }
+    CK(cudaMemsetAsync(p, 0, bb, s));
+    CK(cudaMemsetAsync(v, 0, bb, s));
+    CK(cudaMemsetAsync(u, 0, bb, s));
+    {
+      DotPairs<T> d{{r, b, nullptr}, {r, b, nullptr}};
+      launch_dots<T>(2, d, w.partials, c, nullptr, s);
+      launch_finalize<T>(2, w.partials, w.ks, OP_INIT, ctx->J, s);
+    }
+    apfc_status st = sync_scalars(ctx, w);
+    if (st != APFC_OK) return st;
+    bool any = false;
+    *worst = KS_CONVERGED;
+    for (int j = 0; j < ctx->J; ++j) {
+      any = any || w.ks_host[j].active;
+      *worst = std::max(*worst, w.ks_host[j].status == KS_RUNNING ? KS_CONVERGED : w.ks_host[j].status);
+    }
+    if (*worst == KS_NAN) break;
+    if (!any) break;  // every amplitude meets tol with its true residual
+    if (attempt == attempts) {
+      *worst = KS_NOCONV;
+      break;
+    }
+    // iterate
+    const int every = std::max(1, ctx->opts.check_every);
+    long long launched = 0;  // host-side cap: every amplitude stops at max_iter on the device
+    while (true) {
+      if (launched > (long long)max_iter + every) {
+        *worst = KS_NOCONV;
+        return fail(ctx, APFC_ENOCONV, "Krylov iteration cap exceeded on the host");
+      }
+      launched += every;
+      for (int q = 0; q < every; ++q) {
+        launch_p_update<T>(r, p, v, c, w.ks, s);
+        apply_pinv<T>(ctx, w, p, z, w.ks, cw);
+        launch_apply_A<T>(z, v, c, w.ks, s);
+        {
+          DotPairs<T> d{{rhat, nullptr, nullptr}, {v, nullptr, nullptr}};
+          launch_dots<T>(1, d, w.partials, c, w.ks, s);
+          launch_finalize<T>(1, w.partials, w.ks, OP_ALPHA, ctx->J, s);
+        }
+        launch_s_update<T>(r, v, u, p, c, w.ks, s);
+        {
+          DotPairs<T> d{{r, nullptr, nullptr}, {r, nullptr, nullptr}};
+          launch_dots<T>(1, d, w.partials, c, w.ks, s);
+          launch_finalize<T>(1, w.partials, w.ks, OP_SNORM, ctx->J, s);
+        }
+        apply_pinv<T>(ctx, w, r, z, w.ks, cw);
+        launch_apply_A<T>(z, t, c, w.ks, s);
+        {
+          DotPairs<T> d{{t, t, nullptr}, {r, t, nullptr}};
+          launch_dots<T>(2, d, w.partials, c, w.ks, s);
+          launch_finalize<T>(2, w.partials, w.ks, OP_OMEGA, ctx->J, s);
+        }
+        launch_r_update<T>(r, t, u, c, w.ks, s);
+        {
+          DotPairs<T> d{{rhat, r, nullptr}, {r, r, nullptr}};
+          launch_dots<T>(2, d, w.partials, c, w.ks, s);
+          launch_finalize<T>(2, w.partials, w.ks, OP_RHO, ctx->J, s);
+        }
+      }
+      st = sync_scalars(ctx, w);
+      if (st != APFC_OK) return st;
+      bool run = false;
+      for (int j = 0; j < ctx->J; ++j) run = run || w.ks_host[j].active;
+      if (!run) break;
+    }
+    // x += P^{-1} u
+    apply_pinv<T>(ctx, w, u, z, nullptr, cw);
+    launch_add_to<T>(z, x64, c, s);
+    *worst = KS_CONVERGED;
+    for (int j = 0; j < ctx->J; ++j) {
+      it_sum[j] += w.ks_host[j].iters;
+      *worst = std::max(*worst, w.ks_host[j].status == KS_RUNNING ? KS_CONVERGED : w.ks_host[j].status);
+    }
+    if (!fp64) break;
+    if (*worst == KS_NAN) break;
+  }
+  *iters = 0;
+  for (int j = 0; j < ctx->J; ++j) *iters = std::max(*iters, it_sum[j]);
+  CK(cudaGetLastError());
+  return APFC_OK;
+}
+
+double max_rel_resid(const KScal* k, int J) {
+  double r = 0.0;
+  for (int j = 0; j < J; ++j) {
+    const double b = k[j].bnorm2 > 0 ? k[j].bnorm2 : 1.0;
+    r = std::max(r, std::sqrt(k[j].rnorm2 / b));
+  }
+  return r;
+}
+
+apfc_status status_of(apfc_ctx* ctx, int worst) {
+  if (worst == KS_NAN) return fail(ctx, APFC_ENAN, "residual norm is not finite (NaN/Inf in the state?)");
+  if (worst == KS_NOCONV || worst == KS_BREAKDOWN)
+    return fail(ctx, APFC_ENOCONV, "Krylov solve did not reach the tolerance within max_iter");
+  return APFC_OK;
+}
+
+// One step in FP64.
+apfc_status step_fp64(apfc_ctx* ctx) {
+  apfc_status st = alloc_work<double>(ctx, ctx->w64);
+  if (st != APFC_OK) return st;
+  launch_rhs(ctx->x64, ctx->b64, ctx->coef, ctx->nt, ctx->stream);
+  int iters = 0, worst = 0;
+  st = krylov<double>(ctx, ctx->w64, ctx->b64, ctx->x64, ctx->opts.tol, ctx->opts.max_iter, &iters, &worst);
+  if (st != APFC_OK) return st;
+  ctx->stats.iters_last = iters;
+  ctx->stats.iters_total += iters;
+  ctx->stats.refine_last = 0;
+  ctx->stats.resid_last = max_rel_resid(ctx->w64.ks_host, ctx->J);
+  return status_of(ctx, worst);
+}
+
+// One step with FP32 Krylov inside FP64 iterative refinement.
+apfc_status step_refined(apfc_ctx* ctx) {
+  apfc_status st = alloc_work<float>(ctx, ctx->w32);
+  if (st != APFC_OK) return st;
+  cudaStream_t s = ctx->stream;
+  launch_rhs(ctx->x64, ctx->b64, ctx->coef, ctx->nt, s);
+  float2* r32 = ctx->w32.blk[7];
+  int total_it = 0, worst = KS_CONVERGED, sweep = 0;
+  const double tol2 = ctx->opts.tol * ctx->opts.tol;
+  for (;; ++sweep) {
+    launch_residual_refine(ctx->b64, ctx->x64, r32, reinterpret_cast<double*>(ctx->part64), ctx->coef, s);
+    launch_finalize64(2, ctx->part64, ctx->ks64, OP_NORMS, ctx->J, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->ks64_host, ctx->ks64, sizeof(KScal) * ctx->J, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    bool done = true, bad = false;
+    for (int j = 0; j < ctx->J; ++j) {
+      const KScal& k = ctx->ks64_host[j];
+      if (!std::isfinite(k.rnorm2) || !std::isfinite(k.bnorm2)) bad = true;
+      if (k.rnorm2 > tol2 * k.bnorm2) done = false;
+    }
+    if (bad) {
+      worst = KS_NAN;
+      break;
+    }
+    if (done) {
+      worst = KS_CONVERGED;
+      break;
+    }
+    if (sweep >= ctx->opts.max_refine) {
+      worst = KS_NOCONV;
+      break;
+    }
+    int it = 0, w = 0;
+    st = krylov<float>(ctx, ctx->w32, r32, ctx->x64, ctx->opts.tol_inner, ctx->opts.max_iter, &it, &w);
+    if (st != APFC_OK) return st;
+    total_it += it;
+    if (w == KS_NAN) {
+      worst = KS_NAN;
+      break;
+    }
+  }
+  ctx->stats.iters_last = total_it;
+  ctx->stats.iters_total += total_it;
+  ctx->stats.refine_last = sweep;
+  ctx->stats.resid_last = max_rel_resid(ctx->ks64_host, ctx->J);
+  return status_of(ctx, worst);
+}
+
+bool valid_opts(const apfc_opts& o, std::string& e) {
+  if (o.precision != APFC_FP64 && o.precision != APFC_FP32_REFINED) e = "precision";
+  else if (o.krylov != APFC_BICGSTAB) e = "krylov";
+  else if (o.max_iter < 1) e = "max_iter";
+  else if (o.cheb_degree < 0 || o.cheb_degree > kMaxCheb) e = "cheb_degree";
+  else if (o.tau_mode != APFC_TAU_FOLD && o.tau_mode != APFC_TAU_PLAIN) e = "tau_mode";
+  else if (o.max_refine < 0) e = "max_refine";
+  else if (o.check_every < 1) e = "check_every";
+  else if (!(o.tol > 0.0) || !(o.tol_inner > 0.0) || !(o.tol_inner < 1.0)) e = "tol";
+  else return true;
+  e = "invalid option: " + e;
+  return false;
+}
+
+apfc_status copy_in_block(apfc_ctx* ctx, double2* dst_dev, const void* src, int where) {
+  const cudaMemcpyKind k = where == APFC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(dst_dev, src, sizeof(double2) * 2ull * ctx->J * ctx->pts, k, ctx->stream));
+  return APFC_OK;
+}
+apfc_status copy_out_block(apfc_ctx* ctx, void* dst, const double2* src_dev, int where) {
+  const cudaMemcpyKind k = where == APFC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(dst, src_dev, sizeof(double2) * 2ull * ctx->J * ctx->pts, k, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return APFC_OK;
+}
+
+// Copy one part (0 = zeta, 1 = eta) of the state block to/from [J][pts].
+apfc_status copy_part(apfc_ctx* ctx, void* plain, int where, int part, bool to_state) {
+  const size_t row = sizeof(double2) * (size_t)ctx->pts;
+  double2* base = ctx->x64 + (size_t)part * ctx->pts;
+  cudaMemcpyKind k;
+  if (to_state)
+    k = where == APFC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  else
+    k = where == APFC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  if (to_state)
+    CK(cudaMemcpy2DAsync(base, 2 * row, plain, row, row, ctx->J, k, ctx->stream));
+  else
+    CK(cudaMemcpy2DAsync(plain, row, base, 2 * row, row, ctx->J, k, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return APFC_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+apfc_status apfc_default_opts(apfc_opts* o) {
+  if (!o) return APFC_EINVAL;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = APFC_FP64;
+  o->krylov = APFC_BICGSTAB;
+  o->max_iter = 500;
+  o->cheb_degree = 3;
+  o->tau_mode = APFC_TAU_FOLD;
+  o->max_refine = 10;
+  o->check_every = 4;
+  o->tol = 1e-10;
+  o->tol_inner = 1e-4;
+  return APFC_OK;
+}
+
+apfc_status apfc_uniform_amplitude(const apfc_lattice* lat, const apfc_params* p, double* phi) {
+  if (!lat || !p || !phi) return APFC_EINVAL;
+  double disc, val;
+  if (lat->lattice == APFC_LATTICE_HEX2D) {
+    disc = p->t * p->t - 15.0 * p->v * p->dB;
+    if (!(disc >= 0.0) || !(p->v > 0.0)) return APFC_EINVAL;
+    val = (p->t + std::sqrt(disc)) / (15.0 * p->v);
+  } else if (lat->lattice == APFC_LATTICE_BCC3D) {
+    disc = 4.0 * p->t * p->t - 45.0 * p->v * p->dB;
+    if (!(disc >= 0.0) || !(p->v > 0.0)) return APFC_EINVAL;
+    val = (2.0 * p->t + std::sqrt(disc)) / (45.0 * p->v);
+  } else {
+    return APFC_EINVAL;
+  }
+  *phi = val;
+  return APFC_OK;
+}
+
+apfc_status apfc_init(apfc_ctx** out, const apfc_lattice* lat, const apfc_params* p, const apfc_grid* g,
+                      const apfc_opts* opts, void* stream) {
+  if (!out || !lat || !p || !g) return APFC_EINVAL;
+  *out = nullptr;
+  if (lat->dim != 2 && lat->dim != 3) return APFC_EINVAL;
+  if (lat->J < 1 || lat->J > kMaxJ) return APFC_EINVAL;
+  if (lat->lattice != APFC_LATTICE_CUSTOM && lat->lattice != APFC_LATTICE_HEX2D && lat->lattice != APFC_LATTICE_BCC3D)
+    return APFC_EINVAL;
+  for (int j = 0; j < lat->J; ++j)
+    for (int d = 0; d < lat->dim; ++d)
+      if (!std::isfinite(lat->k[j][d])) return APFC_EINVAL;
+  if (lat->lattice == APFC_LATTICE_HEX2D) {
+    if (lat->J != 3 || lat->dim != 2) return APFC_EINVAL;
+    for (int d = 0; d < 2; ++d)
+      if (std::fabs(lat->k[0][d] + lat->k[1][d] + lat->k[2][d]) > 1e-12) return APFC_EINVAL;
+  }
+  if (lat->lattice == APFC_LATTICE_BCC3D && (lat->J != 6 || lat->dim != 3)) return APFC_EINVAL;
+  if (!std::isfinite(p->dB) || !std::isfinite(p->t) || !std::isfinite(p->v) || !(p->Bx > 0.0)) return APFC_EINVAL;
+  for (int d = 0; d < lat->dim; ++d)
+    if (g->n[d] < 3 || !(g->h[d] > 0.0) || !std::isfinite(g->h[d])) return APFC_EINVAL;
+  if (lat->dim == 2 && g->n[2] != 1) return APFC_EINVAL;
+  apfc_opts o;
+  apfc_default_opts(&o);
+  if (opts) o = *opts;
+  std::string e;
+  if (!valid_opts(o, e)) return APFC_EINVAL;
+
+  apfc_ctx* ctx = new (std::nothrow) apfc_ctx();
+  if (!ctx) return APFC_ENOMEM;
+  ctx->lat = *lat;
+  ctx->par = *p;
+  ctx->grid = *g;
+  if (lat->dim == 2) ctx->grid.n[2] = 1, ctx->grid.h[2] = 1.0;
+  ctx->opts = o;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  ctx->J = lat->J;
+  ctx->dim = lat->dim;
+  ctx->pts = (long long)g->n[0] * g->n[1] * (lat->dim == 3 ? g->n[2] : 1);
+  if (!build_tables(*lat, *p, ctx->nt, ctx->et, e)) {
+    delete ctx;
+    return APFC_EINVAL;
+  }
+  auto cleanup = [&](apfc_status s) {
+    apfc_destroy(ctx);
+    return s;
+  };
+  const size_t blk = sizeof(double2) * 2ull * ctx->J * ctx->pts;
+  if (cudaMalloc(&ctx->x64, blk) != cudaSuccess) return cleanup(APFC_ENOMEM);
+  if (cudaMalloc(&ctx->b64, blk) != cudaSuccess) return cleanup(APFC_ENOMEM);
+  if (cudaMalloc(&ctx->epart, sizeof(double) * kDotBlocks) != cudaSuccess) return cleanup(APFC_ENOMEM);
+  if (cudaMalloc(&ctx->eout, sizeof(double)) != cudaSuccess) return cleanup(APFC_ENOMEM);
+  if (cudaMallocHost(&ctx->eout_host, sizeof(double)) != cudaSuccess) return cleanup(APFC_ENOMEM);
+  if (cudaMalloc(&ctx->ks64, sizeof(KScal) * ctx->J) != cudaSuccess) return cleanup(APFC_ENOMEM);
+  if (cudaMallocHost(&ctx->ks64_host, sizeof(KScal) * ctx->J) != cudaSuccess) return cleanup(APFC_ENOMEM);
+  if (cudaMalloc(&ctx->part64, 16ull * 3 * kDotBlocks * ctx->J) != cudaSuccess) return cleanup(APFC_ENOMEM);
+  if (cudaMemsetAsync(ctx->b64, 0, blk, ctx->stream) != cudaSuccess) return cleanup(APFC_ECUDA);
+  if (cudaMemsetAsync(ctx->ks64, 0, sizeof(KScal) * ctx->J, ctx->stream) != cudaSuccess) return cleanup(APFC_ECUDA);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cleanup(APFC_ECUDA);
+  *out = ctx;
+  return APFC_OK;
+}
+
+apfc_status apfc_set_opts(apfc_ctx* ctx, const apfc_opts* opts) {
+  if (!ctx || !opts) return APFC_EINVAL;
+  std::string e;
+  if (!valid_opts(*opts, e)) return fail(ctx, APFC_EINVAL, e);
+  ctx->opts = *opts;
+  ctx->coef_dt = -1.0;  // tau_mode may have changed
+  return APFC_OK;
+}
+
+apfc_status apfc_set_amplitudes(apfc_ctx* ctx, const void* eta, int where) {
+  if (!ctx || !eta || (where != APFC_HOST && where != APFC_DEVICE)) return APFC_EINVAL;
+  ctx->failed = false;
+  ctx->err.clear();
+  apfc_status st = copy_part(ctx, const_cast<void*>(eta), where, 1, true);
+  if (st != APFC_OK) return st;
+  std::string e;
+  if (ctx->coef_dt < 0 && !build_coef(ctx, 1.0, e)) return fail(ctx, APFC_EINVAL, e);
+  launch_zeta(ctx->x64, ctx->coef, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->has_state = true;
+  std::memset(&ctx->stats, 0, sizeof(ctx->stats));
+  return APFC_OK;
+}
+
+apfc_status apfc_get_amplitudes(apfc_ctx* ctx, void* eta, int where) {
+  if (!ctx || !eta || (where != APFC_HOST && where != APFC_DEVICE)) return APFC_EINVAL;
+  if (!ctx->has_state) return fail(ctx, APFC_ESTATE, "no amplitudes set");
+  return copy_part(ctx, eta, where, 1, false);
+}
+
+apfc_status apfc_get_zeta(apfc_ctx* ctx, void* zeta, int where) {
+  if (!ctx || !zeta || (where != APFC_HOST && where != APFC_DEVICE)) return APFC_EINVAL;
+  if (!ctx->has_state) return fail(ctx, APFC_ESTATE, "no amplitudes set");
+  return copy_part(ctx, zeta, where, 0, false);
+}
+
+apfc_status apfc_step(apfc_ctx* ctx, double dt, int n) {
+  if (!ctx || n < 0) return APFC_EINVAL;
+  if (ctx->failed) return APFC_ESTATE;
+  if (!ctx->has_state) return fail(ctx, APFC_ESTATE, "no amplitudes set");
+  std::string e;
+  if (!build_coef(ctx, dt, e)) return fail(ctx, APFC_EINVAL, e);
+  for (int i = 0; i < n; ++i) {
+    apfc_status st = ctx->opts.precision == APFC_FP64 ? step_fp64(ctx) : step_refined(ctx);
+    if (st != APFC_OK) return st;
+    ctx->stats.steps += 1;
+  }
+  return APFC_OK;
+}
+
+apfc_status apfc_energy(apfc_ctx* ctx, double* F) {
+  if (!ctx || !F) return APFC_EINVAL;
+  if (!ctx->has_state) return fail(ctx, APFC_ESTATE, "no amplitudes set");
+  launch_energy(ctx->x64, ctx->epart, ctx->eout, ctx->coef, ctx->et, ctx->par.Bx, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->eout_host, ctx->eout, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  double vol = 1.0;
+  for (int d = 0; d < ctx->dim; ++d) vol *= ctx->grid.h[d];
+  *F = vol * ctx->eout_host[0];
+  return APFC_OK;
+}
+
+apfc_status apfc_stats(const apfc_ctx* ctx, apfc_stats_t* out) {
+  if (!ctx || !out) return APFC_EINVAL;
+  *out = ctx->stats;
+  return APFC_OK;
+}
+
+const char* apfc_last_error(const apfc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void apfc_destroy(apfc_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  cudaFree(ctx->x64);
+  cudaFree(ctx->b64);
+  cudaFree(ctx->epart);
+  cudaFree(ctx->eout);
+  if (ctx->eout_host) cudaFreeHost(ctx->eout_host);
+  cudaFree(ctx->ks64);
+  if (ctx->ks64_host) cudaFreeHost(ctx->ks64_host);
+  cudaFree(ctx->part64);
+  free_work(ctx->w64);
+  free_work(ctx->w32);
+  delete ctx;
+}
+
+apfc_status apfc_apply_operator(apfc_ctx* ctx, double dt, const void* x, void* y, int where) {
+  if (!ctx || !x || !y || (where != APFC_HOST && where != APFC_DEVICE)) return APFC_EINVAL;
+  std::string e;
+  if (!build_coef(ctx, dt, e)) return fail(ctx, APFC_EINVAL, e);
+  apfc_status st = alloc_work<double>(ctx, ctx->w64);
+  if (st != APFC_OK) return st;
+  double2* in = ctx->w64.blk[0];
+  double2* outb = ctx->w64.blk[1];
+  if (where == APFC_DEVICE) {
+    in = const_cast<double2*>(static_cast<const double2*>(x));
+    outb = static_cast<double2*>(y);
+  } else if ((st = copy_in_block(ctx, in, x, where)) != APFC_OK) {
+    return st;
+  }
+  launch_apply_A<double>(in, outb, ctx->coef, nullptr, ctx->stream);
+  CK(cudaGetLastError());
+  if (where == APFC_HOST) return copy_out_block(ctx, y, outb, where);
+  CK(cudaStreamSynchronize(ctx->stream));
+  return APFC_OK;
+}
+
+apfc_status apfc_apply_preconditioner(apfc_ctx* ctx, double dt, const void* b, void* x, int where) {
+  if (!ctx || !b || !x || (where != APFC_HOST && where != APFC_DEVICE)) return APFC_EINVAL;
+  std::string e;
+  if (!build_coef(ctx, dt, e)) return fail(ctx, APFC_EINVAL, e);
+  apfc_status st = alloc_work<double>(ctx, ctx->w64);
+  if (st != APFC_OK) return st;
+  double2* in = ctx->w64.blk[0];
+  double2* outb = ctx->w64.blk[1];
+  if (where == APFC_DEVICE) {
+    in = const_cast<double2*>(static_cast<const double2*>(b));
+    outb = static_cast<double2*>(x);
+  } else if ((st = copy_in_block(ctx, in, b, where)) != APFC_OK) {
+    return st;
+  }
+  apply_pinv<double>(ctx, ctx->w64, in, outb, nullptr, cheb_weights(ctx));
+  CK(cudaGetLastError());
+  if (where == APFC_HOST) return copy_out_block(ctx, x, outb, where);
+  CK(cudaStreamSynchronize(ctx->stream));
+  return APFC_OK;
+}
+
+apfc_status apfc_nonlinear_rhs(apfc_ctx* ctx, double dt, const void* eta, void* rhs, int where) {
+  if (!ctx || !eta || !rhs || (where != APFC_HOST && where != APFC_DEVICE)) return APFC_EINVAL;
+  std::string e;
+  if (!build_coef(ctx, dt, e)) return fail(ctx, APFC_EINVAL, e);
+  apfc_status st = alloc_work<double>(ctx, ctx->w64);
+  if (st != APFC_OK) return st;
+  // stage eta into the eta-parts of a scratch block, compute, copy the eta-parts out
+  double2* in = ctx->w64.blk[0];
+  double2* outb = ctx->w64.blk[1];
+  const size_t row = sizeof(double2) * (size_t)ctx->pts;
+  const cudaMemcpyKind kin = where == APFC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const cudaMemcpyKind kout = where == APFC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpy2DAsync(in + ctx->pts, 2 * row, eta, row, row, ctx->J, kin, ctx->stream));
+  launch_rhs(in, outb, ctx->coef, ctx->nt, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpy2DAsync(rhs, row, outb + ctx->pts, 2 * row, row, ctx->J, kout, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return APFC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,535 @@
+// Stencil and pointwise kernels of the APFC step (arXiv:1902.09761, Sec. II).
+//
+// All operators are constant-coefficient periodic stencils:
+//   L_h u  = sum_d (u(+e_d) - 2u + u(-e_d)) / h_d^2
+//   G_h u  = L_h u + 2i sum_d k_d (u(+e_d) - u(-e_d)) / (2 h_d)
+//   A_j (zeta, eta) = (zeta - G_h eta, kt G_h zeta + a eta)       (Eq. linear_system2, M = I)
+//   D u    = sD u - mu L_h u                                      (diffusion part of Eq. preconditioner)
+#include "apfc_internal.cuh"
+
+namespace apfc {
+
+namespace {
+
+struct Nb {
+  long long c, xp, xm, yp, ym, zp, zm;
+};
+
+__device__ __forceinline__ Nb neighbours(long long p, const OpCoef& c) {
+  Nb n;
+  n.c = p;
+  const long long nx = c.nx, ny = c.ny, plane = nx * ny;
+  const long long z = p / plane;
+  const long long rem = p - z * plane;
+  const long long y = rem / nx;
+  const long long x = rem - y * nx;
+  n.xp = (x + 1 == nx) ? p - x : p + 1;
+  n.xm = (x == 0) ? p + nx - 1 : p - 1;
+  n.yp = (y + 1 == ny) ? p - y * nx : p + nx;
+  n.ym = (y == 0) ? p + (ny - 1) * nx : p - nx;
+  if (c.dim == 3) {
+    n.zp = (z + 1 == c.nz) ? p - z * plane : p + plane;
+    n.zm = (z == 0) ? p + (long long)(c.nz - 1) * plane : p - plane;
+  } else {
+    n.zp = n.zm = p;
+  }
+  return n;
+}
+
+// G_h u at one point.
+template <typename T>
+__device__ __forceinline__ cplx<T> opG(const cplx<T>* __restrict__ u, const Nb& n, const OpCoef& c, int j) {
+  const cplx<T> uc = u[n.c];
+  T re = (T)c.c0 * uc.x, im = (T)c.c0 * uc.y;
+  {
+    const cplx<T> a = u[n.xp], b = u[n.xm];
+    const T s = (T)c.ih2[0], k = (T)c.kh[j][0];
+    re += s * (a.x + b.x) - k * (a.y - b.y);
+    im += s * (a.y + b.y) + k * (a.x - b.x);
+  }
+  {
+    const cplx<T> a = u[n.yp], b = u[n.ym];
+    const T s = (T)c.ih2[1], k = (T)c.kh[j][1];
+    re += s * (a.x + b.x) - k * (a.y - b.y);
+    im += s * (a.y + b.y) + k * (a.x - b.x);
+  }
+  if (c.dim == 3) {
+    const cplx<T> a = u[n.zp], b = u[n.zm];
+    const T s = (T)c.ih2[2], k = (T)c.kh[j][2];
+    re += s * (a.x + b.x) - k * (a.y - b.y);
+    im += s * (a.y + b.y) + k * (a.x - b.x);
+  }
+  return mkc<T>(re, im);
+}
+
+// D u = sD u - mu L_h u at one point.
+template <typename T>
+__device__ __forceinline__ cplx<T> opD(const cplx<T>* __restrict__ u, const Nb& n, const OpCoef& c, int j) {
+  const cplx<T> uc = u[n.c];
+  T re = (T)c.c0 * uc.x, im = (T)c.c0 * uc.y;
+  {
+    const cplx<T> a = u[n.xp], b = u[n.xm];
+    re += (T)c.ih2[0] * (a.x + b.x);
+    im += (T)c.ih2[0] * (a.y + b.y);
+  }
+  {
+    const cplx<T> a = u[n.yp], b = u[n.ym];
+    re += (T)c.ih2[1] * (a.x + b.x);
+    im += (T)c.ih2[1] * (a.y + b.y);
+  }
+  if (c.dim == 3) {
+    const cplx<T> a = u[n.zp], b = u[n.zm];
+    re += (T)c.ih2[2] * (a.x + b.x);
+    im += (T)c.ih2[2] * (a.y + b.y);
+  }
+  const T sD = (T)c.sD[j], mu = (T)c.mu[j];
+  return mkc<T>(sD * uc.x - mu * re, sD * uc.y - mu * im);
+}
+
+template <typename T>
+__device__ __forceinline__ cplx<T> cmul(double2 s, cplx<T> v) {
+  const T a = (T)s.x, b = (T)s.y;
+  return mkc<T>(a * v.x - b * v.y, a * v.y + b * v.x);
+}
+
+__device__ __forceinline__ bool skip(const KScal* act, int j) { return act != nullptr && act[j].active == 0; }
+
+#define APFC_POINT_INDEX                                                  \
+  const int j = blockIdx.y;                                               \
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; \
+  if (p >= c.pts) return;
+
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_apply_A(const cplx<T>* __restrict__ x, cplx<T>* __restrict__ y, OpCoef c, const KScal* act) {
+  if (skip(act, blockIdx.y)) return;
+  APFC_POINT_INDEX
+  const cplx<T>* z = x + 2LL * j * c.pts;
+  const cplx<T>* e = z + c.pts;
+  const Nb n = neighbours(p, c);
+  const cplx<T> gz = opG<T>(z, n, c, j), ge = opG<T>(e, n, c, j);
+  const cplx<T> zc = z[p], ec = e[p];
+  cplx<T>* y1 = y + 2LL * j * c.pts;
+  const T kt = (T)c.kt[j], a = (T)c.a[j];
+  y1[p] = mkc<T>(zc.x - ge.x, zc.y - ge.y);
+  y1[c.pts + p] = mkc<T>(kt * gz.x + a * ec.x, kt * gz.y + a * ec.y);
+}
+
+template <typename T>
+__global__ void k_residual(const cplx<T>* __restrict__ b, const cplx<T>* __restrict__ x, cplx<T>* __restrict__ r,
+                           cplx<T>* __restrict__ rhat, OpCoef c) {
+  APFC_POINT_INDEX
+  const long long o = 2LL * j * c.pts;
+  const cplx<T>* z = x + o;
+  const cplx<T>* e = z + c.pts;
+  const Nb n = neighbours(p, c);
+  const cplx<T> gz = opG<T>(z, n, c, j), ge = opG<T>(e, n, c, j);
+  const cplx<T> zc = z[p], ec = e[p];
+  const cplx<T> b1 = b[o + p], b2 = b[o + c.pts + p];
+  const T kt = (T)c.kt[j], a = (T)c.a[j];
+  const cplx<T> r1 = mkc<T>(b1.x - (zc.x - ge.x), b1.y - (zc.y - ge.y));
+  const cplx<T> r2 = mkc<T>(b2.x - (kt * gz.x + a * ec.x), b2.y - (kt * gz.y + a * ec.y));
+  r[o + p] = r1;
+  r[o + c.pts + p] = r2;
+  rhat[o + p] = r1;
+  rhat[o + c.pts + p] = r2;
+}
+
+// Step 2 right-hand side of P^{-1}: f = beta2 - kt G_h beta1 (beta1' = beta1 since M = I).
+template <typename T>
+__global__ void k_pc_rhs(const cplx<T>* __restrict__ beta, FieldRef<T> f, OpCoef c, const KScal* act) {
+  if (skip(act, blockIdx.y)) return;
+  APFC_POINT_INDEX
+  const cplx<T>* b1 = beta + 2LL * j * c.pts;
+  const cplx<T> b2 = b1[c.pts + p];
+  const Nb n = neighbours(p, c);
+  const cplx<T> g = opG<T>(b1, n, c, j);
+  const T kt = (T)c.kt[j];
+  f.at(j)[p] = mkc<T>(b2.x - kt * g.x, b2.y - kt * g.y);
+}
+
+// Chebyshev with zero applications of D: X = f / theta.
+template <typename T>
+__global__ void k_cheb_zero(CFieldRef<T> f, FieldRef<T> X, OpCoef c, const KScal* act) {
+  if (skip(act, blockIdx.y)) return;
+  APFC_POINT_INDEX
+  const T it = (T)c.inv_theta[j];
+  const cplx<T> v = f.at(j)[p];
+  X.at(j)[p] = mkc<T>(it * v.x, it * v.y);
+}
+
+// First Chebyshev application: d0 = f/theta, x1 = d0, r1 = f - D d0, d1 = c1 d0 + c2 r1.
+// last: write x_final = x1 + d1 only.
+template <typename T>
+__global__ void k_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, ChebStep w, int last,
+                             OpCoef c, const KScal* act) {
+  if (skip(act, blockIdx.y)) return;
+  APFC_POINT_INDEX
+  const cplx<T>* fj = f.at(j);
+  const Nb n = neighbours(p, c);
+  const T it = (T)c.inv_theta[j];
+  const cplx<T> Df = opD<T>(fj, n, c, j);
+  const cplx<T> fc = fj[p];
+  const cplx<T> d0 = mkc<T>(it * fc.x, it * fc.y);
+  const cplx<T> r1 = mkc<T>(fc.x - it * Df.x, fc.y - it * Df.y);
+  const T c1 = (T)w.c1[j], c2 = (T)w.c2[j];
+  const cplx<T> d1 = mkc<T>(c1 * d0.x + c2 * r1.x, c1 * d0.y + c2 * r1.y);
+  if (last) {
+    X.at(j)[p] = mkc<T>(d0.x + d1.x, d0.y + d1.y);
+  } else {
+    X.at(j)[p] = d0;
+    R.at(j)[p] = r1;
+    Dn.at(j)[p] = d1;
+  }
+}
+
+// Later application: x += d; r -= D d; d' = c1 d + c2 r.  last: write x + d' only.
+template <typename T>
+__global__ void k_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, ChebStep w, int last,
+                             OpCoef c, const KScal* act) {
+  if (skip(act, blockIdx.y)) return;
+  APFC_POINT_INDEX
+  const cplx<T>* dj = Dd.at(j);
+  const Nb n = neighbours(p, c);
+  const cplx<T> DD = opD<T>(dj, n, c, j);
+  const cplx<T> d = dj[p];
+  const cplx<T> x = X.at(j)[p];
+  const cplx<T> r = R.at(j)[p];
+  const cplx<T> xn = mkc<T>(x.x + d.x, x.y + d.y);
+  const cplx<T> rn = mkc<T>(r.x - DD.x, r.y - DD.y);
+  const T c1 = (T)w.c1[j], c2 = (T)w.c2[j];
+  const cplx<T> dn = mkc<T>(c1 * d.x + c2 * rn.x, c1 * d.y + c2 * rn.y);
+  if (last) {
+    X.at(j)[p] = mkc<T>(xn.x + dn.x, xn.y + dn.y);
+  } else {
+    X.at(j)[p] = xn;
+    R.at(j)[p] = rn;
+    Dn.at(j)[p] = dn;
+  }
+}
+
+// Step 4 of P^{-1}: chi1 = beta1 + (beta2' - sD chi2) / mu; chi2 is already in place.
+template <typename T>
+__global__ void k_pc_final(const cplx<T>* __restrict__ beta, CFieldRef<T> b2p, cplx<T>* __restrict__ chi, OpCoef c,
+                           const KScal* act) {
+  if (skip(act, blockIdx.y)) return;
+  APFC_POINT_INDEX
+  const long long o = 2LL * j * c.pts;
+  const cplx<T> b1 = beta[o + p];
+  const cplx<T> bp = b2p.at(j)[p];
+  const cplx<T> x2 = chi[o + c.pts + p];
+  const T sD = (T)c.sD[j], im = (T)c.inv_mu[j];
+  chi[o + p] = mkc<T>(b1.x + im * (bp.x - sD * x2.x), b1.y + im * (bp.y - sD * x2.y));
+}
+
+// BiCGStab updates on block vectors (scalars from the device KScal array).
+template <typename T>
+__global__ void k_p_update(const cplx<T>* __restrict__ r, cplx<T>* __restrict__ p_, const cplx<T>* __restrict__ v,
+                           OpCoef c, const KScal* k) {
+  const int j = blockIdx.y;
+  if (!k[j].active) return;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * c.pts) return;
+  const long long q = 2LL * j * c.pts + i;
+  const double2 beta = k[j].beta, omega = k[j].omega;
+  const cplx<T> pv = p_[q], vv = v[q], rv = r[q];
+  const cplx<T> w = cmul<T>(omega, vv);
+  const cplx<T> t = mkc<T>(pv.x - w.x, pv.y - w.y);
+  const cplx<T> bt = cmul<T>(beta, t);
+  p_[q] = mkc<T>(rv.x + bt.x, rv.y + bt.y);
+}
+
+// s = r - alpha v (in place in r); u += alpha p.
+template <typename T>
+__global__ void k_s_update(cplx<T>* __restrict__ r, const cplx<T>* __restrict__ v, cplx<T>* __restrict__ u,
+                           const cplx<T>* __restrict__ p_, OpCoef c, const KScal* k) {
+  const int j = blockIdx.y;
+  if (!k[j].active) return;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * c.pts) return;
+  const long long q = 2LL * j * c.pts + i;
+  const double2 al = k[j].alpha;
+  const cplx<T> av = cmul<T>(al, v[q]), ap = cmul<T>(al, p_[q]);
+  const cplx<T> rv = r[q], uv = u[q];
+  r[q] = mkc<T>(rv.x - av.x, rv.y - av.y);
+  u[q] = mkc<T>(uv.x + ap.x, uv.y + ap.y);
+}
+
+// u += omega s; r = s - omega t (s held in r).
+template <typename T>
+__global__ void k_r_update(cplx<T>* __restrict__ r, const cplx<T>* __restrict__ t, cplx<T>* __restrict__ u, OpCoef c,
+                           const KScal* k) {
+  const int j = blockIdx.y;
+  if (!k[j].active) return;
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * c.pts) return;
+  const long long q = 2LL * j * c.pts + i;
+  const double2 om = k[j].omega;
+  const cplx<T> s = r[q];
+  const cplx<T> os = cmul<T>(om, s), ot = cmul<T>(om, t[q]);
+  const cplx<T> uv = u[q];
+  u[q] = mkc<T>(uv.x + os.x, uv.y + os.y);
+  r[q] = mkc<T>(s.x - ot.x, s.y - ot.y);
+}
+
+template <typename T>
+__global__ void k_add_to(const cplx<T>* __restrict__ d, double2* __restrict__ x, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const cplx<T> dv = d[i];
+  double2 xv = x[i];
+  xv.x += (double)dv.x;
+  xv.y += (double)dv.y;
+  x[i] = xv;
+}
+
+// ---------------------------------------------------------------------------
+// Explicit nonlinear right-hand side: b_eta,j = eta_j/dt - |k_j|^2 N_j(eta).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double2 cm(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+__global__ void k_rhs(const double2* __restrict__ x, double2* __restrict__ b, OpCoef c, NonlinTable nt) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= c.pts) return;
+  double2 eta[kMaxJ];
+  double A2 = 0.0;
+  for (int j = 0; j < c.J; ++j) {
+    eta[j] = x[(2LL * j + 1) * c.pts + p];
+    A2 += eta[j].x * eta[j].x + eta[j].y * eta[j].y;
+  }
+  A2 *= 2.0;
+  for (int j = 0; j < c.J; ++j) {
+    double2 N;
+    if (nt.hex) {
+      // N_j = 3v (A^2 - |eta_j|^2) eta_j - 2t conj(eta_k eta_l)
+      const int k1 = (j + 1) % 3, k2 = (j + 2) % 3;
+      const double m2 = eta[j].x * eta[j].x + eta[j].y * eta[j].y;
+      const double s = 3.0 * nt.v * (A2 - m2);
+      const double2 pr = cconj(cm(eta[k1], eta[k2]));
+      N = make_double2(s * eta[j].x - 2.0 * nt.t * pr.x, s * eta[j].y - 2.0 * nt.t * pr.y);
+    } else {
+      N = make_double2(0.0, 0.0);
+      for (int q = nt.start[j]; q < nt.start[j + 1]; ++q) {
+        double2 prod = make_double2(nt.coef[q], 0.0);
+        for (int f = 0; f < nt.nf[q]; ++f) {
+          const int code = nt.f[q][f];
+          const double2 m = (code & 1) ? cconj(eta[code >> 1]) : eta[code >> 1];
+          prod = cm(prod, m);
+        }
+        N.x += prod.x;
+        N.y += prod.y;
+      }
+    }
+    const double kap = c.kap[j];
+    b[(2LL * j + 1) * c.pts + p] = make_double2(eta[j].x * c.inv_dt - kap * N.x, eta[j].y * c.inv_dt - kap * N.y);
+  }
+}
+
+// zeta-part of the state = G_h (eta-part)
+__global__ void k_zeta(double2* __restrict__ x, OpCoef c) {
+  APFC_POINT_INDEX
+  const double2* e = x + (2LL * j + 1) * c.pts;
+  const Nb n = neighbours(p, c);
+  x[2LL * j * c.pts + p] = opG<double>(e, n, c, j);
+}
+
+// ---------------------------------------------------------------------------
+// Block sums in FP64
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+  __shared__ double sh[NV][kThreads / 32];
+#pragma unroll
+  for (int i = 0; i < NV; ++i)
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+#pragma unroll
+    for (int i = 0; i < NV; ++i) sh[i][w] = v[i];
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      v[i] = (l < kThreads / 32) ? sh[i][l] : 0.0;
+      for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+  }
+}
+
+// FP64 outer residual of the refinement: r = b - A x (x, b FP64), written as FP32;
+// partials: ||r||^2 and ||b||^2 per amplitude (double2 layout [J][2][kDotBlocks]).
+__global__ void k_residual_refine(const double2* __restrict__ b, const double2* __restrict__ x, float2* __restrict__ r32,
+                                  double2* __restrict__ partials, OpCoef c) {
+  const int j = blockIdx.y;
+  const long long o = 2LL * j * c.pts;
+  const double2* z = x + o;
+  const double2* e = z + c.pts;
+  const double kt = c.kt[j], a = c.a[j];
+  double acc[2] = {0.0, 0.0};
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < c.pts;
+       p += (long long)gridDim.x * blockDim.x) {
+    const Nb n = neighbours(p, c);
+    const double2 gz = opG<double>(z, n, c, j), ge = opG<double>(e, n, c, j);
+    const double2 zc = z[p], ec = e[p];
+    const double2 b1 = b[o + p], b2 = b[o + c.pts + p];
+    const double r1x = b1.x - (zc.x - ge.x), r1y = b1.y - (zc.y - ge.y);
+    const double r2x = b2.x - (kt * gz.x + a * ec.x), r2y = b2.y - (kt * gz.y + a * ec.y);
+    r32[o + p] = make_float2((float)r1x, (float)r1y);
+    r32[o + c.pts + p] = make_float2((float)r2x, (float)r2y);
+    acc[0] += r1x * r1x + r1y * r1y + r2x * r2x + r2y * r2y;
+    acc[1] += b1.x * b1.x + b1.y * b1.y + b2.x * b2.x + b2.y * b2.y;
+  }
+  block_sum<2>(acc);
+  if (threadIdx.x == 0) {
+    partials[(j * 3 + 0) * kDotBlocks + blockIdx.x] = make_double2(acc[0], 0.0);
+    partials[(j * 3 + 1) * kDotBlocks + blockIdx.x] = make_double2(acc[1], 0.0);
+  }
+}
+
+// Energy density summed per block.
+__global__ void k_energy(const double2* __restrict__ x, double* __restrict__ partials, OpCoef c, EnergyTable et,
+                         double Bx) {
+  double acc[1] = {0.0};
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < c.pts;
+       p += (long long)gridDim.x * blockDim.x) {
+    const Nb n = neighbours(p, c);
+    double2 eta[kMaxJ];
+    double S2 = 0.0, S4 = 0.0, grad = 0.0;
+    for (int j = 0; j < c.J; ++j) {
+      const double2* e = x + (2LL * j + 1) * c.pts;
+      eta[j] = e[p];
+      const double m2 = eta[j].x * eta[j].x + eta[j].y * eta[j].y;
+      S2 += m2;
+      S4 += m2 * m2;
+      const double2 g = opG<double>(e, n, c, j);
+      grad += g.x * g.x + g.y * g.y;
+    }
+    const double A2 = 2.0 * S2;
+    double f = 0.5 * et.dB * A2;
+    if (et.hex) {
+      const double2 cub = cm(cm(eta[0], eta[1]), eta[2]);
+      f += 0.75 * et.v * A2 * A2 - 1.5 * et.v * S4 - 4.0 * et.t * cub.x;
+    } else {
+      for (int q = 0; q < et.ne; ++q) {
+        double2 prod = make_double2(et.coef[q], 0.0);
+        for (int ff = 0; ff < et.nf[q]; ++ff) {
+          const int code = et.f[q][ff];
+          prod = cm(prod, (code & 1) ? cconj(eta[code >> 1]) : eta[code >> 1]);
+        }
+        f += prod.x;
+      }
+    }
+    acc[0] += f + Bx * grad;
+  }
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partials, int n, double* __restrict__ out) {
+  double acc[1] = {0.0};
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc[0] += partials[i];
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) out[0] = acc[0];
+}
+
+inline dim3 grid_pts(const OpCoef& c, long long n) {
+  return dim3((unsigned)((n + kThreads - 1) / kThreads), (unsigned)c.J);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launch wrappers
+// ---------------------------------------------------------------------------
+template <typename T>
+void launch_apply_A(const cplx<T>* x, cplx<T>* y, const OpCoef& c, const KScal* act, cudaStream_t s) {
+  k_apply_A<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(x, y, c, act);
+}
+template <typename T>
+void launch_residual(const cplx<T>* b, const cplx<T>* x, cplx<T>* r, cplx<T>* rhat, const OpCoef& c, cudaStream_t s) {
+  k_residual<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(b, x, r, rhat, c);
+}
+template <typename T>
+void launch_pc_rhs(const cplx<T>* beta, FieldRef<T> f, const OpCoef& c, const KScal* act, cudaStream_t s) {
+  k_pc_rhs<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(beta, f, c, act);
+}
+template <typename T>
+void launch_cheb_zero(CFieldRef<T> f, FieldRef<T> X, const OpCoef& c, const KScal* act, cudaStream_t s) {
+  k_cheb_zero<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(f, X, c, act);
+}
+template <typename T>
+void launch_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
+                       const OpCoef& c, const KScal* act, cudaStream_t s) {
+  k_cheb_first<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(f, X, R, Dn, w, last, c, act);
+}
+template <typename T>
+void launch_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
+                       const OpCoef& c, const KScal* act, cudaStream_t s) {
+  k_cheb_sweep<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(Dd, X, R, Dn, w, last, c, act);
+}
+template <typename T>
+void launch_pc_final(const cplx<T>* beta, CFieldRef<T> b2p, cplx<T>* chi, const OpCoef& c, const KScal* act,
+                     cudaStream_t s) {
+  k_pc_final<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(beta, b2p, chi, c, act);
+}
+template <typename T>
+void launch_p_update(const cplx<T>* r, cplx<T>* p, const cplx<T>* v, const OpCoef& c, const KScal* k, cudaStream_t s) {
+  k_p_update<T><<<grid_pts(c, 2 * c.pts), kThreads, 0, s>>>(r, p, v, c, k);
+}
+template <typename T>
+void launch_s_update(cplx<T>* r, const cplx<T>* v, cplx<T>* u, const cplx<T>* p, const OpCoef& c, const KScal* k,
+                     cudaStream_t s) {
+  k_s_update<T><<<grid_pts(c, 2 * c.pts), kThreads, 0, s>>>(r, v, u, p, c, k);
+}
+template <typename T>
+void launch_r_update(cplx<T>* r, const cplx<T>* t, cplx<T>* u, const OpCoef& c, const KScal* k, cudaStream_t s) {
+  k_r_update<T><<<grid_pts(c, 2 * c.pts), kThreads, 0, s>>>(r, t, u, c, k);
+}
+template <typename T>
+void launch_add_to(const cplx<T>* d, double2* x, const OpCoef& c, cudaStream_t s) {
+  const long long n = 2LL * c.J * c.pts;
+  k_add_to<T><<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(d, x, n);
+}
+
+void launch_rhs(const double2* x, double2* b, const OpCoef& c, const NonlinTable& nt, cudaStream_t s) {
+  k_rhs<<<(unsigned)((c.pts + kThreads - 1) / kThreads), kThreads, 0, s>>>(x, b, c, nt);
+}
+void launch_zeta(double2* x, const OpCoef& c, cudaStream_t s) {
+  k_zeta<<<grid_pts(c, c.pts), kThreads, 0, s>>>(x, c);
+}
+void launch_residual_refine(const double2* b, const double2* x, float2* r32, double* partials, const OpCoef& c,
+                            cudaStream_t s) {
+  k_residual_refine<<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(b, x, r32, reinterpret_cast<double2*>(partials), c);
+}
+void launch_energy(const double2* x, double* partials, double* out, const OpCoef& c, const EnergyTable& et, double Bx,
+                   cudaStream_t s) {
+  k_energy<<<kDotBlocks, kThreads, 0, s>>>(x, partials, c, et, Bx);
+  k_sum_partials<<<1, kThreads, 0, s>>>(partials, kDotBlocks, out);
+}
+
+#define APFC_INST(T)                                                                                                 \
+  template void launch_apply_A<T>(const cplx<T>*, cplx<T>*, const OpCoef&, const KScal*, cudaStream_t);             \
+  template void launch_residual<T>(const cplx<T>*, const cplx<T>*, cplx<T>*, cplx<T>*, const OpCoef&,               \
+                                   cudaStream_t);                                                                   \
+  template void launch_pc_rhs<T>(const cplx<T>*, FieldRef<T>, const OpCoef&, const KScal*, cudaStream_t);           \
+  template void launch_cheb_zero<T>(CFieldRef<T>, FieldRef<T>, const OpCoef&, const KScal*, cudaStream_t);          \
+  template void launch_cheb_first<T>(CFieldRef<T>, FieldRef<T>, FieldRef<T>, FieldRef<T>, const ChebStep&, int,     \
+                                     const OpCoef&, const KScal*, cudaStream_t);                                    \
+  template void launch_cheb_sweep<T>(CFieldRef<T>, FieldRef<T>, FieldRef<T>, FieldRef<T>, const ChebStep&, int,     \
+                                     const OpCoef&, const KScal*, cudaStream_t);                                    \
+  template void launch_pc_final<T>(const cplx<T>*, CFieldRef<T>, cplx<T>*, const OpCoef&, const KScal*,             \
+                                   cudaStream_t);                                                                   \
+  template void launch_p_update<T>(const cplx<T>*, cplx<T>*, const cplx<T>*, const OpCoef&, const KScal*,           \
+                                   cudaStream_t);                                                                   \
+  template void launch_s_update<T>(cplx<T>*, const cplx<T>*, cplx<T>*, const cplx<T>*, const OpCoef&, const KScal*, \
+                                   cudaStream_t);                                                                   \
+  template void launch_r_update<T>(cplx<T>*, const cplx<T>*, cplx<T>*, const OpCoef&, const KScal*, cudaStream_t);  \
+  template void launch_add_to<T>(const cplx<T>*, double2*, const OpCoef&, cudaStream_t);
+
+APFC_INST(double)
+APFC_INST(float)
+
+}  // namespace apfc

@@ -1,0 +1,219 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Tolerances: operator-level results are FP64 stencils whose only difference
+from the oracle is the summation order, so they must agree to ~1e-13
+relative.  Time steps solve the block system to a relative residual tol;
+the error of eta is then at most cond(S_j) * tol with cond(S_j) < 20 on these
+grids (S_j's symbol spans [1/dt + dB, 1/dt + dB + Bx max g^2]), so parity
+runs use tol = 1e-13 and must match the oracle to relative L2 <= 1e-10 per
+step and per amplitude.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1902_09761_gb300 import apfc as A
+from paper_1902_09761_gb300 import inputs
+
+from gpu_common import H2, H3, P, context, ensure_built, rel_l2, rel_l2_per_amp
+
+pytestmark = pytest.mark.gpu
+
+CASES = [("hex", (16, 16), H2), ("hex", (98, 130), (0.9, 1.3)), ("bcc", (8, 10, 12), (1.1, 0.9, 1.2))]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    return ensure_built()
+
+
+def _max_rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("kind,shape,h", CASES)
+def test_block_operator_parity(kind, shape, h):
+    ctx, L = context(kind, shape, h)
+    x = inputs.random_amplitudes(2 * L.J, shape, seed=1, scale=1.0).reshape((L.J, 2) + shape)
+    dt = 0.8
+    y = ctx.apply_operator(dt, x)
+    for j in range(L.J):
+        y1, y2 = O.apply_A(x[j, 0], x[j, 1], L.k[j], dt, P, h)
+        assert _max_rel(y[j, 0], y1) < 1e-13
+        assert _max_rel(y[j, 1], y2) < 1e-13
+
+
+@pytest.mark.parametrize("kind,shape,h", CASES)
+@pytest.mark.parametrize("m", [0, 1, 3, 6])
+@pytest.mark.parametrize("tau", ["fold", "plain"])
+def test_preconditioner_parity(kind, shape, h, m, tau):
+    ctx, L = context(kind, shape, h, cheb_degree=m, tau_mode=A.APFC_TAU_FOLD if tau == "fold" else A.APFC_TAU_PLAIN)
+    b = inputs.random_amplitudes(2 * L.J, shape, seed=2, scale=1.0).reshape((L.J, 2) + shape)
+    dt = 1.0
+    x = ctx.apply_preconditioner(dt, b)
+    for j in range(L.J):
+        c1, c2 = O.apply_Pinv(b[j, 0], b[j, 1], L.k[j], dt, P, h, m, tau)
+        assert _max_rel(x[j, 0], c1) < 1e-12
+        assert _max_rel(x[j, 1], c2) < 1e-12
+
+
+@pytest.mark.parametrize("kind,shape,h", CASES)
+def test_nonlinear_rhs_and_energy_parity(kind, shape, h):
+    ctx, L = context(kind, shape, h)
+    eta = inputs.random_amplitudes(L.J, shape, seed=3, scale=0.3)
+    rhs = ctx.nonlinear_rhs(0.7, eta)
+    assert _max_rel(rhs, O.rhs(eta, 0.7, P, L)) < 1e-14
+    ctx.set_amplitudes(eta)
+    assert ctx.energy() == pytest.approx(O.energy(eta, P, L, h), rel=1e-12)
+    assert _max_rel(ctx.get_zeta(), O.zeta_of(eta, L, h)) < 1e-13
+    assert np.array_equal(ctx.get_amplitudes(), eta)
+
+
+def _trajectory_parity(kind, eta0, shape, h, nsteps, dt=1.0, bound=1e-10, **opts):
+    ctx, L = context(kind, shape, h, **opts)
+    ctx.set_amplitudes(eta0)
+    eta_o = eta0.copy()
+    worst = 0.0
+    for m in range(nsteps):
+        ctx.step(dt, 1)
+        eta_o, zeta_o = O.step(eta_o, dt, P, L, h)
+        eg, zg = ctx.get_amplitudes(), ctx.get_zeta()
+        e1 = max(rel_l2_per_amp(eg, eta_o))
+        e2 = max(rel_l2_per_amp(zg, zeta_o))
+        worst = max(worst, e1, e2)
+        assert e1 <= bound, (m, e1)
+        assert e2 <= bound, (m, e2)
+    return worst, ctx.stats()
+
+
+def test_step_parity_grain_128_fp64():
+    # 2D hexagonal, 128x128, grain R=30 rotated 5 deg in liquid, dt=1, 20 steps.
+    eta0 = inputs.hex_grain_128(O.uniform_solid_hex(P))
+    worst, st = _trajectory_parity("hex", eta0, (128, 128), H2, 20, tol=1e-13)
+    print(f"fp64 grain-128 worst rel L2 {worst:.3e}, iters last {st['iters_last']}")
+    assert st["steps"] == 20 and st["resid_last"] <= 1e-13
+
+
+def test_step_parity_grain_128_fp32_refined():
+    eta0 = inputs.hex_grain_128(O.uniform_solid_hex(P))
+    worst, st = _trajectory_parity(
+        "hex", eta0, (128, 128), H2, 20, tol=1e-13, precision=A.APFC_FP32_REFINED, tol_inner=1e-4
+    )
+    print(f"fp32-refined grain-128 worst rel L2 {worst:.3e}, refine sweeps {st['refine_last']}")
+    assert st["resid_last"] <= 1e-13
+
+
+@pytest.mark.parametrize("prec", [A.APFC_FP64, A.APFC_FP32_REFINED])
+@pytest.mark.parametrize("kind,shape,h", CASES[1:])
+def test_step_parity_ragged(kind, shape, h, prec):
+    L = O.hex_lattice() if kind == "hex" else O.bcc_lattice()
+    eta0 = inputs.random_amplitudes(L.J, shape, seed=4, scale=0.1)
+    _trajectory_parity(kind, eta0, shape, h, 3, dt=0.5, tol=1e-13, precision=prec)
+
+
+def test_fourier_mode_decay():
+    # t = v = 0: one step multiplies the grid mode w by 1/(1 + dt (dB + Bx lam^2)), G_h w = lam w.
+    p = O.Params(dB=P.dB, Bx=P.Bx, t=0.0, v=0.0)
+    shape, h, dt = (16, 32), H2, 1.0
+    ctx, L = context("hex", shape, h, p=p, tol=1e-14)
+    x, y = inputs.grid_coords(shape, h)
+    for mode in [(0, 0), (1, 0), (3, -2), (16, 8), (-5, 8)]:
+        q = (2 * np.pi * mode[0] / (32 * h[0]), 2 * np.pi * mode[1] / (16 * h[1]))
+        w = np.exp(1j * (q[0] * x + q[1] * y))
+        eta = np.stack([w, 2 * w, -w])
+        ctx.set_amplitudes(eta)
+        ctx.step(dt, 1)
+        got = ctx.get_amplitudes()
+        for j in range(3):
+            lam = (O.apply_G(w, L.k[j], h) / w).mean().real
+            fac = 1.0 / (1.0 + dt * (p.dB + p.Bx * lam**2))
+            assert rel_l2(got[j], fac * eta[j]) < 1e-12
+
+
+@pytest.mark.parametrize("prec", [A.APFC_FP64, A.APFC_FP32_REFINED])
+def test_uniform_solid_and_liquid_are_fixed_points(prec):
+    phi = O.uniform_solid_hex(P)
+    ctx, L = context("hex", (32, 32), H2, precision=prec)
+    eta = np.full((3, 32, 32), phi, dtype=complex)
+    ctx.set_amplitudes(eta)
+    ctx.step(1.0, 3)
+    assert np.max(np.abs(ctx.get_amplitudes() - phi)) < 1e-15
+    ctx.set_amplitudes(np.zeros_like(eta))
+    ctx.step(1.0, 2)
+    assert np.all(ctx.get_amplitudes() == 0)
+
+
+def test_bcc_uniform_solid_fixed_point():
+    phi = O.uniform_solid_bcc(P)
+    ctx, L = context("bcc", (6, 6, 6), H3)
+    ctx.set_amplitudes(np.full((6, 6, 6, 6), phi, dtype=complex))
+    ctx.step(1.0, 2)
+    assert np.max(np.abs(ctx.get_amplitudes() - phi)) < 1e-15
+
+
+def test_energy_decreases_on_gpu():
+    eta0 = inputs.hex_grain_128(O.uniform_solid_hex(P))
+    ctx, L = context("hex", (128, 128), H2)
+    ctx.set_amplitudes(eta0)
+    F = [ctx.energy()]
+    for _ in range(10):
+        ctx.step(1.0, 1)
+        F.append(ctx.energy())
+    assert all(b <= a + 1e-12 * abs(a) for a, b in zip(F, F[1:]))
+    assert F[0] == pytest.approx(O.energy(eta0, P, L, H2), rel=1e-12)
+
+
+def test_failure_paths_return_status_codes():
+    ctx, L = context("hex", (16, 16), H2)
+    assert ctx.try_step(1.0, 1) == A.APFC_ESTATE  # no amplitudes yet
+    eta = inputs.random_amplitudes(3, (16, 16), seed=5, scale=0.2)
+    ctx.set_amplitudes(eta)
+    assert ctx.try_step(0.0, 1) == A.APFC_EINVAL
+    assert ctx.try_step(-1.0, 1) == A.APFC_EINVAL
+    # a max_iter that is too low gives ENOCONV (never a hang)
+    o = A.apfc_default_opts(max_iter=1, tol=1e-14)
+    ctx.set_opts(o)
+    assert ctx.try_step(1.0, 1) == A.APFC_ENOCONV
+    # NaN in the amplitudes is caught by the residual norms
+    ctx.set_opts(A.apfc_default_opts())
+    bad = eta.copy()
+    bad[1, 3, 4] = np.nan
+    ctx.set_amplitudes(bad)
+    assert ctx.try_step(1.0, 1) == A.APFC_ENAN
+    assert ctx.try_step(1.0, 1) == A.APFC_ESTATE  # sticky until new amplitudes
+    ctx.set_amplitudes(eta)
+    assert ctx.try_step(1.0, 1) == A.APFC_OK
+
+
+def test_device_pointer_path():
+    torch = pytest.importorskip("torch")
+    shape = (24, 20)
+    ctx, L = context("hex", shape, H2, tol=1e-13)
+    eta = inputs.random_amplitudes(3, shape, seed=6, scale=0.2)
+    ctx.set_amplitudes(torch.from_numpy(eta).cuda())
+    out = torch.empty((3,) + shape, dtype=torch.complex128, device="cuda")
+    ctx.step(1.0, 1)
+    ctx.get_amplitudes(out)
+    ref, _ = O.step(eta, 1.0, P, L, H2)
+    assert rel_l2(out.cpu().numpy(), ref) < 1e-10
+    x = torch.from_numpy(inputs.random_amplitudes(6, shape, seed=7).reshape(3, 2, *shape)).cuda()
+    y = torch.empty_like(x)
+    ctx.apply_operator(1.0, x, y)
+    assert np.allclose(y.cpu().numpy(), ctx.apply_operator(1.0, x.cpu().numpy()), rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("prec", [A.APFC_FP64, A.APFC_FP32_REFINED])
+def test_full_size_voronoi_4096_one_step(prec):
+    # The benchmark workload (4096^2, 16 Voronoi grains) at the benchmark tolerance 1e-10:
+    # error vs the oracle stays within cond(S) * tol.
+    phi = O.uniform_solid_hex(P)
+    eta0 = inputs.hex_voronoi(phi)
+    ctx, L = context("hex", (4096, 4096), H2, tol=1e-10, precision=prec)
+    ctx.set_amplitudes(eta0)
+    ctx.step(1.0, 1)
+    got = ctx.get_amplitudes()
+    ref, _ = O.step(eta0, 1.0, P, L, H2)
+    errs = rel_l2_per_amp(got, ref)
+    print(f"4096^2 precision {prec}: rel L2 per amplitude {errs}, stats {ctx.stats()}")
+    assert max(errs) < 2e-9
+    assert ctx.stats()["resid_last"] <= 1e-10
