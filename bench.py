@@ -1,0 +1,413 @@
+#!/usr/bin/env python
+"""Throughput of the semi-implicit APFC amplitude step on GB300.
+
+Workload: 2D hexagonal APFC (J = 3), 4096 x 4096 periodic grid, h = pi/2,
+16 Voronoi grains (rotations uniform in [-10, 10] deg, seed 1), noise 1e-3,
+dB = 0.02, Bx = 0.98, t = 0.5, v = 1/3, dt = 1.  Every Krylov solve stops at
+relative residual 1e-10 ("fixed residual").  One benchmark step = one time
+step of the whole hot path (explicit nonlinear right-hand side, J block solves,
+state update).  The state (805 MB in FP64) is larger than L2, so no flush is
+needed between steps.
+
+Reported: amplitude DOF-steps/s (DOF = one complex eta_j at one grid point) of
+the FP32-Krylov + FP64-refinement path (the headline) and of the plain FP64
+path, the roofline of the dominant kernel measured live with CUDA events on
+the library's stream, the end-to-end rate through the C ABI with host
+buffers, and the FP64 oracle timed on the host cores as a CPU baseline.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "amplitude DOF-steps/s at fixed residual; stencil HBM GB/s vs peak; FP32-refined vs FP64"
+UNIT = "DOF-steps/s"
+PARAMS = (0.02, 0.98, 0.5, 1.0 / 3.0)  # dB, Bx, t, v
+H = np.pi / 2
+TOL = 1e-10
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=4096, help="grid points per side")
+    ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--timed-kernel", default="cheb_sweep_f32")
+    ap.add_argument("--cheb", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(n, steps_note=None):
+    cfg = {
+        "workload": f"hex2d-{n}x{n}-voronoi16",
+        "lattice": "triangular, J=3",
+        "grid": [n, n],
+        "h": "pi/2",
+        "dt": 1.0,
+        "params": {"dB": PARAMS[0], "Bx": PARAMS[1], "t": PARAMS[2], "v": PARAMS[3]},
+        "tol": TOL,
+        "krylov": "right-preconditioned BiCGStab, Schur-complement preconditioner",
+        "l2": "inputs larger than L2 (FP64 state 805 MB per 4096^2 replica); no flush",
+    }
+    if steps_note:
+        cfg["note"] = steps_note
+    return cfg
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1902_09761_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[kernel]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return float(e["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms during the timed region."""
+
+    FIELDS = (
+        "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+        "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+    )
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL,
+            )
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.file.name)
+        return {
+            "sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons),
+            "samples": len(sm),
+        }
+
+
+def init_dist(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allmax(world, value, device=None):
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# Reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+
+def oracle_rate(n, steps, warmup=0):
+    """Time the oracle's step on an n x n sample of the workload; DOF-steps/s."""
+    import oracle as O
+    from paper_1902_09761_gb300 import inputs
+
+    P = O.params_from_paper(0.98, 0.01, 0.25, 0.5)
+    L = O.hex_lattice()
+    eta = inputs.hex_voronoi(O.uniform_solid_hex(P), n=n)
+    for _ in range(warmup):
+        eta, _ = O.step(eta, 1.0, P, L, (H, H))
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        eta, _ = O.step(eta, 1.0, P, L, (H, H))
+    dt = time.perf_counter() - t0
+    return 3.0 * n * n * steps / dt, dt
+
+
+def run_reference(args):
+    world, rank, local = init_dist(args)
+    if rank != 0:
+        return
+    n_sample = min(args.n, 2048)
+    rate, secs = oracle_rate(n_sample, args.steps, args.warmup)
+    sample = (
+        f"oracle FP64 step (numpy, exact FFT Schur solve) on a {n_sample}x{n_sample} sample of the workload, "
+        f"{args.steps} timed steps after {args.warmup} warm-up"
+    )
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": rate,
+        "unit": UNIT,
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / max(args.steps, 1),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": workload_config(args.n, f"timed on a {n_sample}^2 sample"),
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = init_dist(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1902_09761_gb300 import apfc as A
+    from paper_1902_09761_gb300 import inputs
+
+    A.load()
+    n = args.n
+    J = 3
+    k = inputs.hex_vectors()
+    lat = A.make_lattice(k, A.APFC_LATTICE_HEX2D)
+    prm = A.make_params(*PARAMS)
+    phi = A.apfc_uniform_amplitude(lat, prm)
+    eta0 = inputs.hex_voronoi(phi, n=n, seed=1 + rank)
+    dof = J * n * n
+    stream = torch.cuda.current_stream(dev)
+
+    opts = A.apfc_default_opts(precision=A.APFC_FP32_REFINED, tol=TOL, cheb_degree=args.cheb)
+    ctx = A.Context(k, A.APFC_LATTICE_HEX2D, prm, (n, n), (H, H), opts, stream=stream.cuda_stream)
+    eta_dev = torch.from_numpy(eta0).to(dev)
+
+    def timed_steps(nsteps, sampler=None, timed_kernel=None):
+        ctx.set_amplitudes(eta_dev)
+        ctx.step(1.0, args.warmup)
+        if timed_kernel is not None:
+            ctx.profile_start(timed_kernel)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        if sampler:
+            sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(1.0, nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        clocks = sampler.stop() if sampler else None
+        barrier(world)
+        ms = e0.elapsed_time(e1)
+        return allmax(world, ms, dev), clocks
+
+    # --- headline: FP32 Krylov + FP64 refinement --------------------------------
+    sampler = ClockSampler(local)
+    ms, clocks = timed_steps(args.steps, sampler, args.timed_kernel)
+    st = ctx.stats()
+    prof = ctx.profile_read(args.timed_kernel)
+    ctx.profile_stop()
+    value = world * dof * args.steps / (ms * 1e-3)
+
+    peak, peak_src = measured_peaks()
+    avg_ms = prof["ms"] / max(prof["launches"], 1)
+    bytes_per_launch = prof["bytes"] / max(prof["launches"], 1)
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else None
+    traffic = ncu_traffic(args.timed_kernel, f"hex2d-{n}")
+
+    # --- plain FP64 path at the same final residual ------------------------------
+    ctx.set_opts(A.apfc_default_opts(precision=A.APFC_FP64, tol=TOL, cheb_degree=args.cheb))
+    ms64, _ = timed_steps(args.fp64_steps)
+    st64 = ctx.stats()
+    value64 = world * dof * args.fp64_steps / (ms64 * 1e-3)
+
+    # --- end to end through the C ABI with pinned host buffers -------------------
+    ctx.set_opts(opts)
+    h_in = torch.from_numpy(eta0).pin_memory()
+    h_out = torch.empty(eta0.shape, dtype=torch.complex128).pin_memory()
+    h_out_np = h_out.numpy()
+    ctx.set_amplitudes(h_in)
+    ctx.step(1.0, 1)
+    ctx.get_amplitudes(h_out_np)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ctx.set_amplitudes(h_in)  # host -> device copy of the step's input
+        ctx.step(1.0, 1)
+        ctx.get_amplitudes(h_out_np)  # device -> host copy of the step's result
+    torch.cuda.synchronize(dev)
+    e2e_s = allmax(world, time.perf_counter() - t0, dev)
+    barrier(world)
+    e2e = world * dof * args.e2e_steps / e2e_s
+    bytes_step = eta0.nbytes
+
+    # --- CPU baseline: the oracle on this host's cores (rank 0, N = 1 only) -----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, secs = oracle_rate(n, 1)
+        cpu = {
+            "value": rate,
+            "unit": UNIT,
+            "cores": 1,
+            "kind": "oracle",
+            "sample": f"one oracle FP64 step (numpy, exact FFT Schur solve) of the full {n}x{n} workload, "
+            f"{secs:.1f} s; numpy FFT and elementwise ops run on one thread",
+        }
+
+    ctx.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 Krylov + f64 refinement",
+        "data": "synthetic",
+        "config": dict(workload_config(n), parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
+        "iters_per_step_last": st["iters_last"],
+        "refine_sweeps_last": st["refine_last"],
+        "resid_last": st["resid_last"],
+        "fp64": {
+            "value": value64,
+            "unit": UNIT,
+            "ms_per_step": ms64 / args.fp64_steps,
+            "steps": args.fp64_steps,
+            "iters_last": st64["iters_last"],
+            "resid_last": st64["resid_last"],
+        },
+        "speedup_fp32_refined_vs_fp64": value / value64,
+        "roofline": {
+            "bound": "hbm",
+            "kernel": args.timed_kernel,
+            "achieved": achieved,
+            "peak": peak,
+            "peak_source": peak_src,
+            "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic,
+            "algorithmic_bytes_per_launch": bytes_per_launch,
+            "avg_launch_ms": avg_ms,
+            "launches": prof["launches"],
+        },
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step},
+        "gpu_launches": prof["all_launches"],
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

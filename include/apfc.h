@@ -172,6 +172,27 @@ apfc_status apfc_apply_preconditioner(apfc_ctx* ctx, double dt, const void* b, v
  * nonlinear right-hand side); eta, rhs: [J][pts] complex128. */
 apfc_status apfc_nonlinear_rhs(apfc_ctx* ctx, double dt, const void* eta, void* rhs, int where);
 
+/* ---- measurement (tracing) ------------------------------------------------
+ * Kernel ids run 0..apfc_kernel_count()-1 (FP64 variants, then FP32 ones);
+ * apfc_kernel_name(id) names them.  Measurement is process-wide and serves
+ * one context at a time.
+ *
+ * apfc_profile_start(ctx, timed_id): zeroes the counters.  From then on every
+ * kernel adds the algorithmic bytes it moves (its whole-field reads and
+ * writes, counted once per active amplitude) to a device counter of its id,
+ * the host counts launches per id, and each launch of kernel timed_id
+ * (-1: none) is bracketed by CUDA events recorded on the context stream.
+ * apfc_profile_read(ctx, id, ...): synchronises the stream; returns since the
+ * start the summed event time of id in ms (0 unless id == timed_id), its
+ * launches, its algorithmic bytes, and the launches of all library kernels.
+ * Null output pointers are skipped.  apfc_profile_stop(ctx) ends it. */
+int apfc_kernel_count(void);
+const char* apfc_kernel_name(int id);
+apfc_status apfc_profile_start(apfc_ctx* ctx, int timed_id);
+apfc_status apfc_profile_read(apfc_ctx* ctx, int id, double* ms, long long* launches, double* bytes,
+                              long long* all_launches);
+apfc_status apfc_profile_stop(apfc_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

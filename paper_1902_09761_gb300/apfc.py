@@ -89,6 +89,15 @@ EXPORTS = {
     "apfc_apply_operator": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_int]),
     "apfc_apply_preconditioner": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_int]),
     "apfc_nonlinear_rhs": (C.c_int, [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_int]),
+    "apfc_kernel_count": (C.c_int, []),
+    "apfc_kernel_name": (C.c_char_p, [C.c_int]),
+    "apfc_profile_start": (C.c_int, [C.c_void_p, C.c_int]),
+    "apfc_profile_read": (
+        C.c_int,
+        [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+         C.POINTER(C.c_longlong)],
+    ),
+    "apfc_profile_stop": (C.c_int, [C.c_void_p]),
 }
 
 _lib = None
@@ -269,6 +278,20 @@ class Context:
     def last_error(self) -> str:
         return load().apfc_last_error(self._h).decode()
 
+    # -- measurement -------------------------------------------------------
+    def profile_start(self, timed: str | int | None = None):
+        tid = -1 if timed is None else (timed if isinstance(timed, int) else kernel_ids()[timed])
+        _check(load().apfc_profile_start(self._h, tid), self._h)
+
+    def profile_read(self, kernel: str | int) -> dict:
+        kid = kernel if isinstance(kernel, int) else kernel_ids()[kernel]
+        ms, n, b, tot = C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong()
+        _check(load().apfc_profile_read(self._h, kid, C.byref(ms), C.byref(n), C.byref(b), C.byref(tot)), self._h)
+        return {"ms": ms.value, "launches": n.value, "bytes": b.value, "all_launches": tot.value}
+
+    def profile_stop(self):
+        _check(load().apfc_profile_stop(self._h), self._h)
+
     # -- operator-level entry points --------------------------------------
     def _binary(self, fn, dt, x, shape, out):
         out = np.empty(shape, np.complex128) if out is None else out
@@ -287,6 +310,12 @@ class Context:
 
     def nonlinear_rhs(self, dt, eta, out=None):
         return self._binary(load().apfc_nonlinear_rhs, dt, eta, self.amp_shape, out)
+
+
+def kernel_ids() -> dict:
+    """{name: id} of the library's kernels (apfc_kernel_name)."""
+    lib = load()
+    return {lib.apfc_kernel_name(i).decode(): i for i in range(lib.apfc_kernel_count())}
 
 
 def apfc_init(k, kind, params, shape, h, opts=None, stream=None) -> Context:

@@ -68,7 +68,53 @@ struct OpCoef {
   double mu[kMaxJ];         //                       mu = sqrt(kt)
   double inv_mu[kMaxJ];
   double inv_theta[kMaxJ];  // Chebyshev: 1/theta, theta = centre of D's interval
+  unsigned long long* prof; // device byte counters per kernel id (nullptr: not measuring)
 };
+
+// ---------------------------------------------------------------------------
+// Measurement: every kernel adds the algorithmic bytes it moves (whole-field
+// reads and writes, once per active amplitude) to prof[id]; the launch
+// wrappers count launches and bracket one selected kernel id with events.
+// FP32 variants use id + KID_COUNT.
+// ---------------------------------------------------------------------------
+enum KernelId {
+  KID_APPLY_A = 0,
+  KID_RESIDUAL,
+  KID_PC_RHS,
+  KID_CHEB_ZERO,
+  KID_CHEB_FIRST,
+  KID_CHEB_SWEEP,
+  KID_PC_FINAL,
+  KID_P_UPDATE,
+  KID_S_UPDATE,
+  KID_R_UPDATE,
+  KID_ADD_TO,
+  KID_DOTS,
+  KID_FINALIZE,
+  KID_RHS,
+  KID_ZETA,
+  KID_RESID_REFINE,
+  KID_ENERGY,
+  KID_COUNT
+};
+template <typename T>
+__host__ __device__ constexpr int kid_of(int k) {
+  return k + (sizeof(T) == 4 ? KID_COUNT : 0);
+}
+
+// Host side (api.cu): called by every launch wrapper around its launch.
+void prof_launch_begin(int kid, cudaStream_t s);
+void prof_launch_end(int kid, cudaStream_t s);
+struct ProfScope {
+  int kid;
+  cudaStream_t s;
+  ProfScope(int k, cudaStream_t st) : kid(k), s(st) { prof_launch_begin(kid, s); }
+  ~ProfScope() { prof_launch_end(kid, s); }
+};
+
+__device__ __forceinline__ void prof_add(const OpCoef& c, int kid, unsigned long long bytes) {
+  if (c.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(c.prof + kid, bytes);
+}
 
 // Chebyshev recurrence weights for one application (per amplitude):
 // d_{k+1} = c1 d_k + c2 r_{k+1}.

@@ -30,6 +30,49 @@ struct Work {
 
 }  // namespace
 
+// Process-wide measurement state (see apfc_profile_start in apfc.h).
+namespace apfc {
+struct Profiler {
+  bool on = false;
+  int timed = -1;
+  cudaStream_t stream = nullptr;
+  std::vector<cudaEvent_t> ev;  // begin/end pairs of the timed kernel
+  size_t used = 0;
+  long long launches[2 * KID_COUNT] = {};
+  long long all = 0;
+  unsigned long long* dev = nullptr;  // device byte counters [2 * KID_COUNT]
+  bool failed = false;
+};
+static Profiler g_prof;
+
+void prof_launch_begin(int kid, cudaStream_t s) {
+  if (!g_prof.on) return;
+  g_prof.launches[kid] += 1;
+  g_prof.all += 1;
+  if (kid != g_prof.timed || g_prof.failed) return;
+  if (g_prof.used + 2 > g_prof.ev.size()) {
+    if (g_prof.ev.size() > 2000000) {
+      g_prof.failed = true;
+      return;
+    }
+    for (int i = 0; i < 2; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        g_prof.failed = true;
+        return;
+      }
+      g_prof.ev.push_back(e);
+    }
+  }
+  cudaEventRecord(g_prof.ev[g_prof.used], s);
+}
+void prof_launch_end(int kid, cudaStream_t s) {
+  if (!g_prof.on || kid != g_prof.timed || g_prof.failed) return;
+  cudaEventRecord(g_prof.ev[g_prof.used + 1], s);
+  g_prof.used += 2;
+}
+}  // namespace apfc
+
 struct apfc_ctx {
   apfc_lattice lat;
   apfc_params par;
@@ -212,7 +255,9 @@ bool build_coef(apfc_ctx* c, double dt, std::string& err) {
   }
   if (c->coef_dt == dt) return true;
   OpCoef& o = c->coef;
+  unsigned long long* prof = o.prof;
   std::memset(&o, 0, sizeof(o));
+  o.prof = prof;
   o.J = c->J;
   o.dim = c->dim;
   o.nx = c->grid.n[0];
@@ -730,6 +775,66 @@ void apfc_destroy(apfc_ctx* ctx) {
   free_work(ctx->w64);
   free_work(ctx->w32);
   delete ctx;
+}
+
+static const char* kKernelNames[KID_COUNT] = {
+    "apply_A", "residual", "pc_rhs", "cheb_zero", "cheb_first", "cheb_sweep", "pc_final", "p_update", "s_update",
+    "r_update", "add_to", "dots", "finalize", "rhs", "zeta", "residual_refine", "energy"};
+
+int apfc_kernel_count(void) { return 2 * KID_COUNT; }
+
+const char* apfc_kernel_name(int id) {
+  static std::string names[2 * KID_COUNT];
+  if (id < 0 || id >= 2 * KID_COUNT) return "";
+  if (names[id].empty()) names[id] = std::string(kKernelNames[id % KID_COUNT]) + (id < KID_COUNT ? "_f64" : "_f32");
+  return names[id].c_str();
+}
+
+apfc_status apfc_profile_start(apfc_ctx* ctx, int timed_id) {
+  if (!ctx || timed_id < -1 || timed_id >= 2 * KID_COUNT) return APFC_EINVAL;
+  if (g_prof.on && g_prof.stream != ctx->stream) return fail(ctx, APFC_EINVAL, "measurement already running");
+  if (!g_prof.dev) CK(cudaMalloc(&g_prof.dev, sizeof(unsigned long long) * 2 * KID_COUNT));
+  CK(cudaMemsetAsync(g_prof.dev, 0, sizeof(unsigned long long) * 2 * KID_COUNT, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  g_prof.on = true;
+  g_prof.timed = timed_id;
+  g_prof.stream = ctx->stream;
+  g_prof.used = 0;
+  g_prof.failed = false;
+  std::memset(g_prof.launches, 0, sizeof(g_prof.launches));
+  g_prof.all = 0;
+  ctx->coef.prof = g_prof.dev;
+  return APFC_OK;
+}
+
+apfc_status apfc_profile_read(apfc_ctx* ctx, int id, double* ms, long long* launches, double* bytes,
+                              long long* all_launches) {
+  if (!ctx || id < 0 || id >= 2 * KID_COUNT) return APFC_EINVAL;
+  if (!g_prof.dev) return fail(ctx, APFC_ESTATE, "measurement was never started");
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (g_prof.failed) return fail(ctx, APFC_ENOMEM, "event pool exhausted");
+  double total = 0.0;
+  if (id == g_prof.timed) {
+    for (size_t i = 0; i + 1 < g_prof.used; i += 2) {
+      float t = 0.f;
+      CK(cudaEventElapsedTime(&t, g_prof.ev[i], g_prof.ev[i + 1]));
+      total += t;
+    }
+  }
+  unsigned long long b[2 * KID_COUNT];
+  CK(cudaMemcpy(b, g_prof.dev, sizeof(b), cudaMemcpyDeviceToHost));
+  if (ms) *ms = total;
+  if (launches) *launches = g_prof.launches[id];
+  if (bytes) *bytes = (double)b[id];
+  if (all_launches) *all_launches = g_prof.all;
+  return APFC_OK;
+}
+
+apfc_status apfc_profile_stop(apfc_ctx* ctx) {
+  if (!ctx) return APFC_EINVAL;
+  g_prof.on = false;
+  ctx->coef.prof = nullptr;
+  return APFC_OK;
 }
 
 apfc_status apfc_apply_operator(apfc_ctx* ctx, double dt, const void* x, void* y, int where) {

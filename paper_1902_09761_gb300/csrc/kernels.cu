@@ -103,6 +103,7 @@ __device__ __forceinline__ bool skip(const KScal* act, int j) { return act != nu
 template <typename T>
 __global__ void k_apply_A(const cplx<T>* __restrict__ x, cplx<T>* __restrict__ y, OpCoef c, const KScal* act) {
   if (skip(act, blockIdx.y)) return;
+  prof_add(c, kid_of<T>(KID_APPLY_A), 4ull * (unsigned long long)c.pts * sizeof(cplx<T>));
   APFC_POINT_INDEX
   const cplx<T>* z = x + 2LL * j * c.pts;
   const cplx<T>* e = z + c.pts;
@@ -118,6 +119,7 @@ __global__ void k_apply_A(const cplx<T>* __restrict__ x, cplx<T>* __restrict__ y
 template <typename T>
 __global__ void k_residual(const cplx<T>* __restrict__ b, const cplx<T>* __restrict__ x, cplx<T>* __restrict__ r,
                            cplx<T>* __restrict__ rhat, OpCoef c) {
+  prof_add(c, kid_of<T>(KID_RESIDUAL), 8ull * (unsigned long long)c.pts * sizeof(cplx<T>));
   APFC_POINT_INDEX
   const long long o = 2LL * j * c.pts;
   const cplx<T>* z = x + o;
@@ -139,6 +141,7 @@ __global__ void k_residual(const cplx<T>* __restrict__ b, const cplx<T>* __restr
 template <typename T>
 __global__ void k_pc_rhs(const cplx<T>* __restrict__ beta, FieldRef<T> f, OpCoef c, const KScal* act) {
   if (skip(act, blockIdx.y)) return;
+  prof_add(c, kid_of<T>(KID_PC_RHS), 3ull * (unsigned long long)c.pts * sizeof(cplx<T>));
   APFC_POINT_INDEX
   const cplx<T>* b1 = beta + 2LL * j * c.pts;
   const cplx<T> b2 = b1[c.pts + p];
@@ -152,6 +155,7 @@ __global__ void k_pc_rhs(const cplx<T>* __restrict__ beta, FieldRef<T> f, OpCoef
 template <typename T>
 __global__ void k_cheb_zero(CFieldRef<T> f, FieldRef<T> X, OpCoef c, const KScal* act) {
   if (skip(act, blockIdx.y)) return;
+  prof_add(c, kid_of<T>(KID_CHEB_ZERO), 2ull * (unsigned long long)c.pts * sizeof(cplx<T>));
   APFC_POINT_INDEX
   const T it = (T)c.inv_theta[j];
   const cplx<T> v = f.at(j)[p];
@@ -164,8 +168,10 @@ template <typename T>
 __global__ void k_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, ChebStep w, int last,
                              OpCoef c, const KScal* act) {
   if (skip(act, blockIdx.y)) return;
+  prof_add(c, kid_of<T>(KID_CHEB_FIRST), (last ? 2ull : 4ull) * (unsigned long long)c.pts * sizeof(cplx<T>));
   APFC_POINT_INDEX
   const cplx<T>* fj = f.at(j);
+
   const Nb n = neighbours(p, c);
   const T it = (T)c.inv_theta[j];
   const cplx<T> Df = opD<T>(fj, n, c, j);
@@ -188,6 +194,7 @@ template <typename T>
 __global__ void k_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, ChebStep w, int last,
                              OpCoef c, const KScal* act) {
   if (skip(act, blockIdx.y)) return;
+  prof_add(c, kid_of<T>(KID_CHEB_SWEEP), (last ? 4ull : 6ull) * (unsigned long long)c.pts * sizeof(cplx<T>));
   APFC_POINT_INDEX
   const cplx<T>* dj = Dd.at(j);
   const Nb n = neighbours(p, c);
@@ -213,6 +220,7 @@ template <typename T>
 __global__ void k_pc_final(const cplx<T>* __restrict__ beta, CFieldRef<T> b2p, cplx<T>* __restrict__ chi, OpCoef c,
                            const KScal* act) {
   if (skip(act, blockIdx.y)) return;
+  prof_add(c, kid_of<T>(KID_PC_FINAL), 4ull * (unsigned long long)c.pts * sizeof(cplx<T>));
   APFC_POINT_INDEX
   const long long o = 2LL * j * c.pts;
   const cplx<T> b1 = beta[o + p];
@@ -228,6 +236,7 @@ __global__ void k_p_update(const cplx<T>* __restrict__ r, cplx<T>* __restrict__ 
                            OpCoef c, const KScal* k) {
   const int j = blockIdx.y;
   if (!k[j].active) return;
+  prof_add(c, kid_of<T>(KID_P_UPDATE), 8ull * (unsigned long long)c.pts * sizeof(cplx<T>));
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * c.pts) return;
   const long long q = 2LL * j * c.pts + i;
@@ -245,6 +254,7 @@ __global__ void k_s_update(cplx<T>* __restrict__ r, const cplx<T>* __restrict__ 
                            const cplx<T>* __restrict__ p_, OpCoef c, const KScal* k) {
   const int j = blockIdx.y;
   if (!k[j].active) return;
+  prof_add(c, kid_of<T>(KID_S_UPDATE), 12ull * (unsigned long long)c.pts * sizeof(cplx<T>));
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * c.pts) return;
   const long long q = 2LL * j * c.pts + i;
@@ -261,6 +271,7 @@ __global__ void k_r_update(cplx<T>* __restrict__ r, const cplx<T>* __restrict__ 
                            const KScal* k) {
   const int j = blockIdx.y;
   if (!k[j].active) return;
+  prof_add(c, kid_of<T>(KID_R_UPDATE), 10ull * (unsigned long long)c.pts * sizeof(cplx<T>));
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 2 * c.pts) return;
   const long long q = 2LL * j * c.pts + i;
@@ -273,7 +284,8 @@ __global__ void k_r_update(cplx<T>* __restrict__ r, const cplx<T>* __restrict__ 
 }
 
 template <typename T>
-__global__ void k_add_to(const cplx<T>* __restrict__ d, double2* __restrict__ x, long long n) {
+__global__ void k_add_to(const cplx<T>* __restrict__ d, double2* __restrict__ x, long long n, OpCoef c) {
+  prof_add(c, kid_of<T>(KID_ADD_TO), (unsigned long long)n * (sizeof(cplx<T>) + 2 * sizeof(double2)));
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const cplx<T> dv = d[i];
@@ -292,6 +304,7 @@ __device__ __forceinline__ double2 cm(double2 a, double2 b) {
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 
 __global__ void k_rhs(const double2* __restrict__ x, double2* __restrict__ b, OpCoef c, NonlinTable nt) {
+  prof_add(c, KID_RHS, 2ull * c.J * (unsigned long long)c.pts * sizeof(double2));
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= c.pts) return;
   double2 eta[kMaxJ];
@@ -330,6 +343,7 @@ __global__ void k_rhs(const double2* __restrict__ x, double2* __restrict__ b, Op
 
 // zeta-part of the state = G_h (eta-part)
 __global__ void k_zeta(double2* __restrict__ x, OpCoef c) {
+  prof_add(c, KID_ZETA, 2ull * (unsigned long long)c.pts * sizeof(double2));
   APFC_POINT_INDEX
   const double2* e = x + (2LL * j + 1) * c.pts;
   const Nb n = neighbours(p, c);
@@ -364,6 +378,7 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
 __global__ void k_residual_refine(const double2* __restrict__ b, const double2* __restrict__ x, float2* __restrict__ r32,
                                   double2* __restrict__ partials, OpCoef c) {
   const int j = blockIdx.y;
+  prof_add(c, KID_RESID_REFINE, (unsigned long long)c.pts * (4 * sizeof(double2) + 2 * sizeof(float2)));
   const long long o = 2LL * j * c.pts;
   const double2* z = x + o;
   const double2* e = z + c.pts;
@@ -392,6 +407,7 @@ __global__ void k_residual_refine(const double2* __restrict__ b, const double2* 
 // Energy density summed per block.
 __global__ void k_energy(const double2* __restrict__ x, double* __restrict__ partials, OpCoef c, EnergyTable et,
                          double Bx) {
+  prof_add(c, KID_ENERGY, (unsigned long long)c.J * c.pts * sizeof(double2));
   double acc[1] = {0.0};
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < c.pts;
        p += (long long)gridDim.x * blockDim.x) {
@@ -446,66 +462,81 @@ inline dim3 grid_pts(const OpCoef& c, long long n) {
 // ---------------------------------------------------------------------------
 template <typename T>
 void launch_apply_A(const cplx<T>* x, cplx<T>* y, const OpCoef& c, const KScal* act, cudaStream_t s) {
+  ProfScope ps_(kid_of<T>(KID_APPLY_A), s);
   k_apply_A<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(x, y, c, act);
 }
 template <typename T>
 void launch_residual(const cplx<T>* b, const cplx<T>* x, cplx<T>* r, cplx<T>* rhat, const OpCoef& c, cudaStream_t s) {
+  ProfScope ps_(kid_of<T>(KID_RESIDUAL), s);
   k_residual<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(b, x, r, rhat, c);
 }
 template <typename T>
 void launch_pc_rhs(const cplx<T>* beta, FieldRef<T> f, const OpCoef& c, const KScal* act, cudaStream_t s) {
+  ProfScope ps_(kid_of<T>(KID_PC_RHS), s);
   k_pc_rhs<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(beta, f, c, act);
 }
 template <typename T>
 void launch_cheb_zero(CFieldRef<T> f, FieldRef<T> X, const OpCoef& c, const KScal* act, cudaStream_t s) {
+  ProfScope ps_(kid_of<T>(KID_CHEB_ZERO), s);
   k_cheb_zero<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(f, X, c, act);
 }
 template <typename T>
 void launch_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
                        const OpCoef& c, const KScal* act, cudaStream_t s) {
+  ProfScope ps_(kid_of<T>(KID_CHEB_FIRST), s);
   k_cheb_first<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(f, X, R, Dn, w, last, c, act);
 }
 template <typename T>
 void launch_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
                        const OpCoef& c, const KScal* act, cudaStream_t s) {
+  ProfScope ps_(kid_of<T>(KID_CHEB_SWEEP), s);
   k_cheb_sweep<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(Dd, X, R, Dn, w, last, c, act);
 }
 template <typename T>
 void launch_pc_final(const cplx<T>* beta, CFieldRef<T> b2p, cplx<T>* chi, const OpCoef& c, const KScal* act,
                      cudaStream_t s) {
+  ProfScope ps_(kid_of<T>(KID_PC_FINAL), s);
   k_pc_final<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(beta, b2p, chi, c, act);
 }
 template <typename T>
 void launch_p_update(const cplx<T>* r, cplx<T>* p, const cplx<T>* v, const OpCoef& c, const KScal* k, cudaStream_t s) {
+  ProfScope ps_(kid_of<T>(KID_P_UPDATE), s);
   k_p_update<T><<<grid_pts(c, 2 * c.pts), kThreads, 0, s>>>(r, p, v, c, k);
 }
 template <typename T>
 void launch_s_update(cplx<T>* r, const cplx<T>* v, cplx<T>* u, const cplx<T>* p, const OpCoef& c, const KScal* k,
                      cudaStream_t s) {
+  ProfScope ps_(kid_of<T>(KID_S_UPDATE), s);
   k_s_update<T><<<grid_pts(c, 2 * c.pts), kThreads, 0, s>>>(r, v, u, p, c, k);
 }
 template <typename T>
 void launch_r_update(cplx<T>* r, const cplx<T>* t, cplx<T>* u, const OpCoef& c, const KScal* k, cudaStream_t s) {
+  ProfScope ps_(kid_of<T>(KID_R_UPDATE), s);
   k_r_update<T><<<grid_pts(c, 2 * c.pts), kThreads, 0, s>>>(r, t, u, c, k);
 }
 template <typename T>
 void launch_add_to(const cplx<T>* d, double2* x, const OpCoef& c, cudaStream_t s) {
   const long long n = 2LL * c.J * c.pts;
-  k_add_to<T><<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(d, x, n);
+  ProfScope ps_(kid_of<T>(KID_ADD_TO), s);
+  k_add_to<T><<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(d, x, n, c);
 }
 
 void launch_rhs(const double2* x, double2* b, const OpCoef& c, const NonlinTable& nt, cudaStream_t s) {
+  ProfScope ps_(KID_RHS, s);
   k_rhs<<<(unsigned)((c.pts + kThreads - 1) / kThreads), kThreads, 0, s>>>(x, b, c, nt);
 }
 void launch_zeta(double2* x, const OpCoef& c, cudaStream_t s) {
+  ProfScope ps_(KID_ZETA, s);
   k_zeta<<<grid_pts(c, c.pts), kThreads, 0, s>>>(x, c);
 }
 void launch_residual_refine(const double2* b, const double2* x, float2* r32, double* partials, const OpCoef& c,
                             cudaStream_t s) {
+  ProfScope ps_(KID_RESID_REFINE, s);
   k_residual_refine<<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(b, x, r32, reinterpret_cast<double2*>(partials), c);
 }
 void launch_energy(const double2* x, double* partials, double* out, const OpCoef& c, const EnergyTable& et, double Bx,
                    cudaStream_t s) {
+  ProfScope ps_(KID_ENERGY, s);
   k_energy<<<kDotBlocks, kThreads, 0, s>>>(x, partials, c, et, Bx);
   k_sum_partials<<<1, kThreads, 0, s>>>(partials, kDotBlocks, out);
 }

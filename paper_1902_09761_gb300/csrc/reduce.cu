@@ -113,6 +113,18 @@ __global__ void k_dots(DotPairs<T> pr, void* partials, OpCoef c, const KScal* ac
   const int j = blockIdx.y;
   if (act != nullptr && act[j].active == 0) return;
   const long long n = 2LL * c.pts, o = 2LL * j * c.pts;
+  if (c.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0) {
+    // count each distinct array once
+    const void* seen[2 * NP];
+    int ns = 0;
+    for (int q = 0; q < 2 * NP; ++q) {
+      const void* ptr = q < NP ? (const void*)pr.u[q] : (const void*)pr.v[q - NP];
+      bool dup = false;
+      for (int r = 0; r < ns; ++r) dup = dup || seen[r] == ptr;
+      if (!dup) seen[ns++] = ptr;
+    }
+    atomicAdd(c.prof + kid_of<T>(KID_DOTS), (unsigned long long)ns * n * sizeof(cplx<T>));
+  }
   Acc<T> acc[NP];
 #pragma unroll
   for (int q = 0; q < NP; ++q) acc[q].zero();
@@ -250,6 +262,7 @@ __global__ void k_finalize(const void* partials, KScal* ks, int op) {
 template <typename T>
 void launch_dots(int npair, const DotPairs<T>& pr, void* partials, const OpCoef& c, const KScal* act, cudaStream_t s) {
   const dim3 g(kDotBlocks, c.J);
+  ProfScope ps_(kid_of<T>(KID_DOTS), s);
   if (npair == 1)
     k_dots<T, 1><<<g, kThreads, 0, s>>>(pr, partials, c, act);
   else if (npair == 2)
@@ -260,6 +273,7 @@ void launch_dots(int npair, const DotPairs<T>& pr, void* partials, const OpCoef&
 
 template <typename T>
 void launch_finalize(int npair, const void* partials, KScal* k, int op, int J, cudaStream_t s) {
+  ProfScope ps_(kid_of<T>(KID_FINALIZE), s);
   if (npair == 1)
     k_finalize<T, 1><<<J, kThreads, 0, s>>>(partials, k, op);
   else if (npair == 2)

@@ -67,19 +67,17 @@ def grain_state(k, phi, shape, h, centres, thetas_rad, owner, background=None) -
     k = np.asarray(k, dtype=float)
     J, dim = k.shape
     coords = grid_coords(shape, h)
-    eta = np.zeros((J,) + tuple(shape), dtype=np.complex128)
-    if background is not None:
-        eta[:] = background
-    for g, (c, th) in enumerate(zip(centres, thetas_rad)):
-        mask = owner == g
-        if not mask.any():
-            continue
-        dk = delta_k(k, th)
-        for j in range(J):
-            ph = np.zeros(shape)
-            for d in range(dim):
-                ph = ph + dk[j, d] * (coords[d] - c[d])
-            eta[j][mask] = phi * np.exp(1j * ph[mask])
+    centres = np.asarray(centres, dtype=float).reshape(len(thetas_rad), dim)
+    dk = np.stack([delta_k(k, th) for th in thetas_rad])  # (G, J, dim)
+    inside = owner >= 0
+    g = np.where(inside, owner, 0)
+    eta = np.empty((J,) + tuple(shape), dtype=np.complex128)
+    for j in range(J):
+        ph = np.zeros(shape)
+        for d in range(dim):
+            ph += dk[g, j, d] * (coords[d] - centres[g, d])
+        val = phi * np.exp(1j * ph)
+        eta[j] = np.where(inside, val, 0.0 if background is None else background)
     return eta
 
 
