@@ -54,7 +54,8 @@ typedef enum {
   APFC_ECUDA = 3,   /* a CUDA call failed; see apfc_last_error                    */
   APFC_ENOCONV = 4, /* Krylov solve hit max_iter; the best iterate is kept        */
   APFC_ENAN = 5,    /* a residual norm became NaN/Inf (e.g. NaN amplitudes)       */
-  APFC_ESTATE = 6   /* context is in a failed state or has no amplitudes yet      */
+  APFC_ESTATE = 6,  /* context is in a failed state or has no amplitudes yet      */
+  APFC_ETOOBIG = 7  /* problem exceeds the fixed scratch of the no-allocation entry point */
 } apfc_status;
 
 enum { APFC_HOST = 0, APFC_DEVICE = 1 };
@@ -171,6 +172,38 @@ apfc_status apfc_apply_preconditioner(apfc_ctx* ctx, double dt, const void* b, v
 /* rhs_j = eta_j/dt - |k_j|^2 N_j(eta) for every amplitude (the explicit
  * nonlinear right-hand side); eta, rhs: [J][pts] complex128. */
 apfc_status apfc_nonlinear_rhs(apfc_ctx* ctx, double dt, const void* eta, void* rhs, int where);
+
+/* ---- preconditioner apply without allocation ----------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * may not allocate device memory where they apply the preconditioner (a
+ * framework that owns the allocator, a latency-critical path where cudaMalloc
+ * would synchronise the device, a plugin handed buffers and a stream only).
+ *
+ * x = P_j^{-1} b for every amplitude, computed exactly as apfc_apply_preconditioner
+ * computes it (same kernels, same Chebyshev polynomial of degree cheb_degree,
+ * same tau_mode), but with no context: the caller passes lattice, parameters,
+ * grid, dt, and DEVICE buffers b and x (block vectors [J][2][pts] complex128,
+ * not aliased).  The five intermediate fields live in one file-scope device
+ * array of 5 * APFC_STATIC_MAX_DOF complex128 (20 MB) that every GPU which
+ * loads the library holds until the process exits; the call performs no
+ * cudaMalloc/cudaFree and calls no allocating library routine.
+ *
+ * Limits and behaviour:
+ *  - J * nx * ny * nz must be <= APFC_STATIC_MAX_DOF, else APFC_ETOOBIG
+ *    (nothing is launched); other bad arguments give APFC_EINVAL.
+ *  - The first call on a device resolves the array's device address with
+ *    cudaGetSymbolAddress (with that device current); make that first call
+ *    before any stream capture.  stream must belong to the current device.
+ *  - Work is enqueued on stream (NULL = legacy default stream) and the call
+ *    returns without waiting; x is ready when the stream reaches that point.
+ *  - Every call shares the one array and it keeps the last call's contents;
+ *    no intermediate needs to start at zero (each is written in full before it
+ *    is read).  Calls that overlap on the GPU (different streams, or threads)
+ *    race on the array and give wrong results: serialise them. */
+#define APFC_STATIC_MAX_DOF 262144
+apfc_status apfc_apply_preconditioner_static(const apfc_lattice* lat, const apfc_params* p, const apfc_grid* g,
+                                             int cheb_degree, int tau_mode, double dt, const void* b, void* x,
+                                             void* stream);
 
 /* ---- measurement (tracing) ------------------------------------------------
  * Kernel ids run 0..apfc_kernel_count()-1 (FP64 variants, then FP32 ones);

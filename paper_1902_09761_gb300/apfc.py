@@ -17,8 +17,9 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libapfc.so")
 
-APFC_OK, APFC_EINVAL, APFC_ENOMEM, APFC_ECUDA, APFC_ENOCONV, APFC_ENAN, APFC_ESTATE = range(7)
-STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENAN", 6: "ESTATE"}
+APFC_OK, APFC_EINVAL, APFC_ENOMEM, APFC_ECUDA, APFC_ENOCONV, APFC_ENAN, APFC_ESTATE, APFC_ETOOBIG = range(8)
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENAN", 6: "ESTATE", 7: "ETOOBIG"}
+APFC_STATIC_MAX_DOF = 262144
 APFC_HOST, APFC_DEVICE = 0, 1
 APFC_LATTICE_CUSTOM, APFC_LATTICE_HEX2D, APFC_LATTICE_BCC3D = 0, 1, 2
 APFC_FP64, APFC_FP32_REFINED = 0, 1
@@ -98,6 +99,11 @@ EXPORTS = {
          C.POINTER(C.c_longlong)],
     ),
     "apfc_profile_stop": (C.c_int, [C.c_void_p]),
+    "apfc_apply_preconditioner_static": (
+        C.c_int,
+        [C.POINTER(Lattice), C.POINTER(Params), C.POINTER(Grid), C.c_int, C.c_int, C.c_double, C.c_void_p,
+         C.c_void_p, C.c_void_p],
+    ),
 }
 
 _lib = None
@@ -310,6 +316,15 @@ class Context:
 
     def nonlinear_rhs(self, dt, eta, out=None):
         return self._binary(load().apfc_nonlinear_rhs, dt, eta, self.amp_shape, out)
+
+
+def apfc_apply_preconditioner_static(lattice: Lattice, params: Params, grid: Grid, cheb_degree: int, tau_mode: int,
+                                     dt: float, b_ptr: int, x_ptr: int, stream: int | None = None) -> int:
+    """Preconditioner apply without any device allocation (device pointers; returns the status)."""
+    return load().apfc_apply_preconditioner_static(
+        C.byref(lattice), C.byref(params), C.byref(grid), int(cheb_degree), int(tau_mode), float(dt),
+        C.c_void_p(b_ptr), C.c_void_p(x_ptr), C.c_void_p(stream) if stream else None,
+    )
 
 
 def kernel_ids() -> dict:
