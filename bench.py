@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--n", type=int, default=4096, help="grid points per side")
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--e2e-steps", type=int, default=4)
-    ap.add_argument("--timed-kernel", default="cheb_sweep_f32")
+    ap.add_argument("--timed-kernel", default="fused_apinv_f32")
     ap.add_argument("--cheb", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()

@@ -97,7 +97,8 @@ typedef struct {
   int tau_mode;              /* APFC_TAU_FOLD or APFC_TAU_PLAIN                     */
   int max_refine;            /* cap on FP64 refinement sweeps (FP32_REFINED)        */
   int check_every;           /* Krylov iterations between convergence checks        */
-  int reserved;
+  int fused;                 /* 1: fused row-streaming A P^{-1} kernels on 2D grids (default);
+                                0: one kernel per stencil pass                         */
   double tol;                /* stop at ||b - A x||_2 <= tol ||b||_2 (block norm, per amplitude) */
   double tol_inner;          /* relative tolerance of each FP32 inner solve         */
 } apfc_opts;
@@ -111,7 +112,7 @@ typedef struct {
 } apfc_stats_t;
 
 /* Fill *o with defaults: FP64, BiCGStab, tol 1e-10, max_iter 500,
- * cheb_degree 3, tau fold, max_refine 10, tol_inner 1e-4, check_every 4. */
+ * cheb_degree 3, tau fold, max_refine 10, tol_inner 1e-4, check_every 4, fused 1. */
 apfc_status apfc_default_opts(apfc_opts* o);
 
 /* Relaxed-solid amplitude phi of a uniform crystal (eta_j = phi for all j):

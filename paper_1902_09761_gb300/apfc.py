@@ -55,7 +55,7 @@ class Opts(C.Structure):
         ("tau_mode", C.c_int),
         ("max_refine", C.c_int),
         ("check_every", C.c_int),
-        ("reserved", C.c_int),
+        ("fused", C.c_int),
         ("tol", C.c_double),
         ("tol_inner", C.c_double),
     ]

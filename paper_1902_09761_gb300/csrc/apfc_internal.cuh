@@ -95,6 +95,9 @@ enum KernelId {
   KID_ZETA,
   KID_RESID_REFINE,
   KID_ENERGY,
+  KID_FUSED_APINV,
+  KID_FUSED_PINV,
+  KID_BICG_UPDATE,
   KID_COUNT
 };
 template <typename T>
@@ -153,7 +156,7 @@ struct KScal {
 };
 
 enum KStatus { KS_RUNNING = 0, KS_CONVERGED = 1, KS_NOCONV = 2, KS_BREAKDOWN = 3, KS_NAN = 4 };
-enum KOp { OP_INIT = 0, OP_ALPHA = 1, OP_SNORM = 2, OP_OMEGA = 3, OP_RHO = 4, OP_NORMS = 5 };
+enum KOp { OP_INIT = 0, OP_ALPHA = 1, OP_SNORM = 2, OP_OMEGA = 3, OP_RHO = 4, OP_NORMS = 5, OP_OMEGA3 = 6 };
 
 // Up to three (u, v) pairs of block vectors for conj(u).v per amplitude.
 template <typename T>
@@ -202,13 +205,44 @@ void launch_energy(const double2* x, double* partials, double* out, const OpCoef
                    double Bx, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
+// fused2d.cu: row-streaming fused P^{-1} / A P^{-1} for 2D grids, Chebyshev
+// degree m in 1..fused2d_max_degree(); each returns false when it cannot run.
+// Dot partials use layout [J][3][npart], npart = fused2d_npart(c, m, Ly).
+// ---------------------------------------------------------------------------
+int fused2d_max_degree(int elem_bytes);
+int fused2d_npart(const OpCoef& c, int m, int Ly, int elem_bytes);  // elem_bytes = sizeof(complex)
+// p_new = r + beta (p_old - omega v_old); v_new = A P^{-1} p_new; partial (rhat, v_new)
+template <typename T>
+bool launch_fused_v(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* p_old,
+                    const cplx<T>* v_old, cplx<T>* p_new, cplx<T>* v_new, const cplx<T>* rhat, const KScal* act,
+                    void* partials, cudaStream_t s);
+// t = A P^{-1} (r - alpha v); partials (t, s), (t, t), (s, s)
+template <typename T>
+bool launch_fused_t(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
+                    cplx<T>* t_out, const KScal* act, void* partials, cudaStream_t s);
+// x64 += P^{-1} u
+template <typename T>
+bool launch_fused_pinv_add(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* u, double2* x64,
+                           cudaStream_t s);
+// x = P^{-1} b
+template <typename T>
+bool launch_fused_pinv_store(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* b, cplx<T>* x,
+                             cudaStream_t s);
+// s = r - alpha v; u += alpha p + omega s; r = s - omega t; partials (rhat, r), (r, r) in [J][3][kDotBlocks]
+template <typename T>
+void launch_bicg_update(cplx<T>* r, const cplx<T>* v, const cplx<T>* p, cplx<T>* u, const cplx<T>* t,
+                        const cplx<T>* rhat, const KScal* ks, void* partials, const OpCoef& c, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
 // reduce.cu
 // ---------------------------------------------------------------------------
 template <typename T>
 void launch_dots(int npair, const DotPairs<T>& pr, void* partials, const OpCoef& c, const KScal* act,
                  cudaStream_t s);
+// npart: partial-sum slots per (amplitude, pair); layout [J][3][npart].
 template <typename T>
-void launch_finalize(int npair, const void* partials, KScal* k, int op, int J, cudaStream_t s);
+void launch_finalize(int npair, const void* partials, KScal* k, int op, int J, cudaStream_t s,
+                     int npart = kDotBlocks);
 // partials in FP64 double2 layout regardless of T (for the fused FP64 residual)
 void launch_finalize64(int npair, const void* partials, KScal* k, int op, int J, cudaStream_t s);
 

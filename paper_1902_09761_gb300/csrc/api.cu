@@ -16,13 +16,16 @@ using namespace apfc;
 
 namespace {
 
+constexpr int kFusedRows = 256;  // rows per block segment of the fused 2D pipeline
+
 template <typename T>
 struct Work {
-  static constexpr int kBlocks = 8;  // r, rhat, p, v, u, t, z, bb
+  static constexpr int kBlocks = 10;  // r, rhat, p, v, u, t, z, bb, p', v' (ping-pong p and v)
   static constexpr int kFields = 5;  // f, b2p, R, Da, Db
   cplx<T>* blk[kBlocks] = {};
   cplx<T>* fld[kFields] = {};
-  void* partials = nullptr;  // [J][3][kDotBlocks] x 16 bytes
+  void* partials = nullptr;  // [J][3][npart] x 16 bytes, npart <= npart_cap
+  int npart_cap = 0;
   KScal* ks = nullptr;       // device
   KScal* ks_host = nullptr;  // pinned
   bool ready = false;
@@ -133,7 +136,19 @@ apfc_status alloc_work(apfc_ctx* ctx, Work<T>& w) {
   if (w.ready) return APFC_OK;
   for (auto& b : w.blk) CK(cudaMalloc(&b, block_bytes<T>(ctx)));
   for (auto& f : w.fld) CK(cudaMalloc(&f, field_bytes<T>(ctx)));
-  CK(cudaMalloc(&w.partials, 16ull * 3 * kDotBlocks * ctx->J));
+  // partial-sum slots: the unfused reductions use kDotBlocks; the fused pipeline one per block
+  int cap = kDotBlocks;
+  if (ctx->dim == 2) {
+    OpCoef g{};
+    g.nx = ctx->grid.n[0];
+    g.ny = ctx->grid.n[1];
+    g.nz = 1;
+    g.pts = ctx->pts;
+    for (int m = 1; m <= fused2d_max_degree((int)sizeof(cplx<T>)); ++m)
+      cap = std::max(cap, fused2d_npart(g, m, kFusedRows, (int)sizeof(cplx<T>)));
+  }
+  w.npart_cap = cap;
+  CK(cudaMalloc(&w.partials, 16ull * 3 * cap * ctx->J));
   CK(cudaMalloc(&w.ks, sizeof(KScal) * ctx->J));
   CK(cudaMallocHost(&w.ks_host, sizeof(KScal) * ctx->J));
   std::memset(w.ks_host, 0, sizeof(KScal) * ctx->J);
@@ -344,6 +359,11 @@ void apply_pinv(apfc_ctx* ctx, Work<T>& w, const cplx<T>* beta, cplx<T>* chi, co
   launch_pc_final<T>(beta, CFieldRef<T>{b2p.p, P}, chi, c, act, ctx->stream);
 }
 
+bool use_fused(const apfc_ctx* ctx, int elem_bytes) {
+  return ctx->dim == 2 && ctx->opts.fused != 0 && ctx->opts.cheb_degree >= 1 &&
+         ctx->opts.cheb_degree <= fused2d_max_degree(elem_bytes);
+}
+
 template <typename T>
 apfc_status sync_scalars(apfc_ctx* ctx, Work<T>& w) {
   CK(cudaGetLastError());
@@ -407,6 +427,12 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
     }
     // iterate
     const int every = std::max(1, ctx->opts.check_every);
+    const bool fused = use_fused(ctx, (int)sizeof(cplx<T>));
+    const int m = ctx->opts.cheb_degree;
+    const int npart = fused ? fused2d_npart(c, m, kFusedRows, (int)sizeof(cplx<T>)) : kDotBlocks;
+    cplx<T>* pp[2] = {p, w.blk[8]};
+    cplx<T>* vv[2] = {v, w.blk[9]};
+    int cur = 0;
     long long launched = 0;  // host-side cap: every amplitude stops at max_iter on the device
     while (true) {
       if (launched > (long long)max_iter + every) {
@@ -415,6 +441,20 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
       }
       launched += every;
       for (int q = 0; q < every; ++q) {
+        if (fused) {
+          // v' = A P^{-1} p' with p' = r + beta (p - omega v); alpha = rho / (rhat, v')
+          launch_fused_v<T>(m, kFusedRows, c, cw.data(), r, pp[cur], vv[cur], pp[1 - cur], vv[1 - cur], rhat, w.ks,
+                            w.partials, s);
+          launch_finalize<T>(1, w.partials, w.ks, OP_ALPHA, ctx->J, s, npart);
+          // t = A P^{-1} s, s = r - alpha v'; omega = (t, s) / (t, t)
+          launch_fused_t<T>(m, kFusedRows, c, cw.data(), r, vv[1 - cur], t, w.ks, w.partials, s);
+          launch_finalize<T>(3, w.partials, w.ks, OP_OMEGA3, ctx->J, s, npart);
+          // u += alpha p' + omega s; r = s - omega t; rho' = (rhat, r)
+          launch_bicg_update<T>(r, vv[1 - cur], pp[1 - cur], u, t, rhat, w.ks, w.partials, c, s);
+          launch_finalize<T>(2, w.partials, w.ks, OP_RHO, ctx->J, s, kDotBlocks);
+          cur = 1 - cur;
+          continue;
+        }
         launch_p_update<T>(r, p, v, c, w.ks, s);
         apply_pinv<T>(ctx, w, p, z, w.ks, cw);
         launch_apply_A<T>(z, v, c, w.ks, s);
@@ -450,8 +490,10 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
       if (!run) break;
     }
     // x += P^{-1} u
-    apply_pinv<T>(ctx, w, u, z, nullptr, cw);
-    launch_add_to<T>(z, x64, c, s);
+    if (!fused || !launch_fused_pinv_add<T>(m, kFusedRows, c, cw.data(), u, x64, s)) {
+      apply_pinv<T>(ctx, w, u, z, nullptr, cw);
+      launch_add_to<T>(z, x64, c, s);
+    }
     *worst = KS_CONVERGED;
     for (int j = 0; j < ctx->J; ++j) {
       it_sum[j] += w.ks_host[j].iters;
@@ -554,6 +596,7 @@ bool valid_opts(const apfc_opts& o, std::string& e) {
   else if (o.tau_mode != APFC_TAU_FOLD && o.tau_mode != APFC_TAU_PLAIN) e = "tau_mode";
   else if (o.max_refine < 0) e = "max_refine";
   else if (o.check_every < 1) e = "check_every";
+  else if (o.fused != 0 && o.fused != 1) e = "fused";
   else if (!(o.tol > 0.0) || !(o.tol_inner > 0.0) || !(o.tol_inner < 1.0)) e = "tol";
   else return true;
   e = "invalid option: " + e;
@@ -606,6 +649,7 @@ apfc_status apfc_default_opts(apfc_opts* o) {
   o->check_every = 4;
   o->tol = 1e-10;
   o->tol_inner = 1e-4;
+  o->fused = 1;
   return APFC_OK;
 }
 
@@ -779,7 +823,8 @@ void apfc_destroy(apfc_ctx* ctx) {
 
 static const char* kKernelNames[KID_COUNT] = {
     "apply_A", "residual", "pc_rhs", "cheb_zero", "cheb_first", "cheb_sweep", "pc_final", "p_update", "s_update",
-    "r_update", "add_to", "dots", "finalize", "rhs", "zeta", "residual_refine", "energy"};
+    "r_update", "add_to", "dots", "finalize", "rhs", "zeta", "residual_refine", "energy", "fused_apinv",
+    "fused_pinv", "bicg_update"};
 
 int apfc_kernel_count(void) { return 2 * KID_COUNT; }
 
@@ -872,7 +917,11 @@ apfc_status apfc_apply_preconditioner(apfc_ctx* ctx, double dt, const void* b, v
   } else if ((st = copy_in_block(ctx, in, b, where)) != APFC_OK) {
     return st;
   }
-  apply_pinv<double>(ctx, ctx->w64, in, outb, nullptr, cheb_weights(ctx));
+  const auto cw = cheb_weights(ctx);
+  if (!use_fused(ctx, (int)sizeof(double2)) ||
+      !launch_fused_pinv_store<double>(ctx->opts.cheb_degree, kFusedRows, ctx->coef, cw.data(), in, outb,
+                                       ctx->stream))
+    apply_pinv<double>(ctx, ctx->w64, in, outb, nullptr, cw);
   CK(cudaGetLastError());
   if (where == APFC_HOST) return copy_out_block(ctx, x, outb, where);
   CK(cudaStreamSynchronize(ctx->stream));

@@ -1,0 +1,786 @@
+// Row-streaming fused application of P^{-1} (and of A P^{-1}) on 2D grids.
+//
+// The preconditioner of Sec. II.B (Eq. preconditioner, M = I) applied to
+// beta = (beta1, beta2), followed optionally by the block operator of
+// Eq. linear_system2, is a chain of radius-1 stencil stages:
+//
+//   stage 1         f     = beta2 - kt G_h beta1                 (step 2 right side)
+//   stages 2..M+1   Chebyshev solve D beta2' = f, M applications of D
+//   stages M+2..2M+1 Chebyshev solve D chi2 = beta2', M applications;
+//                   the last also forms chi1 = beta1 + (beta2' - sD chi2)/mu (step 4)
+//   stage 2M+2      y = A (chi1, chi2) = (chi1 - G_h chi2, kt G_h chi1 + a chi2)
+//
+// with D = sD I - mu L_h and the Chebyshev recurrence of Saad, Sec. 12.3
+// (x += d; r -= D d; d = c1 d + c2 r).  One thread block owns a strip of
+// NT columns (NT - 2S of them valid, S = number of stages) and a segment of
+// rows, and streams down the rows: at local time rho, stage s works on local
+// row rho - 2s.  Every stage keeps the row it produced in a 4-row shared-memory
+// ring (for the x- and y-neighbours of the next stage); values a later stage
+// needs at the same point (Chebyshev x and r, beta2, beta2') travel in register
+// delay lines.  Lag 2 per stage lets all stages of one time step run without a
+// barrier between them: one __syncthreads per row.  Each input row is read from
+// HBM once (plus the x halo), each output row written once.
+//
+// Loaders form the input on the fly from Krylov vectors; epilogues store the
+// result and accumulate inner products for the BiCGStab scalars.
+#include "acc.cuh"
+#include "apfc_internal.cuh"
+
+#include <type_traits>
+
+namespace apfc {
+
+namespace {
+
+// Columns per block: FP32 pipelines use 128 (three blocks fit per SM), FP64 256.
+template <typename T>
+__host__ __device__ constexpr int pipe_nt() {
+  return sizeof(T) == 4 ? 128 : 256;
+}
+
+// Complex helpers.  FP32 complex values use the packed f32x2 instructions of
+// sm_100-class GPUs (one instruction for both components).
+__device__ __forceinline__ unsigned long long pk(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 upk(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)));
+  return upk(r);
+}
+__device__ __forceinline__ float2 csub(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk(a)), "l"(pk(b)));
+  return upk(r);
+}
+__device__ __forceinline__ float2 cscale(float s, float2 a) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk(make_float2(s, s))), "l"(pk(a)));
+  return upk(r);
+}
+__device__ __forceinline__ float2 caxpy(float s, float2 a, float2 b) {  // s a + b
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pk(make_float2(s, s))), "l"(pk(a)), "l"(pk(b)));
+  return upk(r);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 cscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__device__ __forceinline__ double2 caxpy(double s, double2 a, double2 b) {
+  return make_double2(fma(s, a.x, b.x), fma(s, a.y, b.y));
+}
+template <typename C>
+__device__ __forceinline__ C cmulz(C z, C a) {  // complex z a
+  C r;
+  r.x = z.x * a.x - z.y * a.y;
+  r.y = z.x * a.y + z.y * a.x;
+  return r;
+}
+template <typename C>
+__device__ __forceinline__ C add_i(C a, C b) {  // a + i b
+  C r;
+  r.x = a.x - b.y;
+  r.y = a.y + b.x;
+  return r;
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> to_c(double2 z) {
+  return mkc<T>((T)z.x, (T)z.y);
+}
+
+template <int I, int N, typename F>
+__device__ __forceinline__ void static_for_rev(F&& f) {
+  if constexpr (I >= N) {
+    f(std::integral_constant<int, I>{});
+    static_for_rev<I - 1, N>(f);
+  }
+}
+
+// Per-amplitude coefficients in the field precision.
+template <typename T>
+struct JCoef {
+  T c0, ihx, ihy, khx, khy, kt, a, sD, mu, inv_mu, it;
+};
+
+template <typename T>
+__device__ __forceinline__ JCoef<T> jcoef(const OpCoef& c, int j) {
+  JCoef<T> q;
+  q.c0 = (T)c.c0;
+  q.ihx = (T)c.ih2[0];
+  q.ihy = (T)c.ih2[1];
+  q.khx = (T)c.kh[j][0];
+  q.khy = (T)c.kh[j][1];
+  q.kt = (T)c.kt[j];
+  q.a = (T)c.a[j];
+  q.sD = (T)c.sD[j];
+  q.mu = (T)c.mu[j];
+  q.inv_mu = (T)c.inv_mu[j];
+  q.it = (T)c.inv_theta[j];
+  return q;
+}
+
+// 5-point neighbourhood of one point of a ring quantity.
+template <typename T>
+struct Nbh {
+  cplx<T> c, l, r, u, d;  // centre, x-1, x+1, y-1, y+1
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> lap(const Nbh<T>& n, const JCoef<T>& q) {
+  return caxpy(q.ihy, cadd(n.u, n.d), caxpy(q.ihx, cadd(n.l, n.r), cscale(q.c0, n.c)));
+}
+// G_h = L_h + i (k_x/h_x)(u(x+1) - u(x-1)) + i (k_y/h_y)(u(y+1) - u(y-1))
+template <typename T>
+__device__ __forceinline__ cplx<T> opG(const Nbh<T>& n, const JCoef<T>& q) {
+  const cplx<T> adv = caxpy(q.khy, csub(n.d, n.u), cscale(q.khx, csub(n.r, n.l)));
+  return add_i(lap(n, q), adv);
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> opD(const Nbh<T>& n, const JCoef<T>& q) {
+  return caxpy(-q.mu, lap(n, q), cscale(q.sD, n.c));
+}
+
+struct PipeGeom {
+  int nx, ny, Ly, wv, nstrips, nsegs, npart;
+  long long pts;
+};
+
+// ---------------------------------------------------------------------------
+// Loaders and epilogues.  Each names the global arrays ("raw values") it needs
+// at a point; the kernel fetches them (asynchronously, PF rows ahead, when
+// PF > 0) and hands them back to form():
+//   loader raw "in": the input row          -> (beta1, beta2)
+//   loader raw "re": re-forming beta1 for step 4 of P^{-1}, 2(2M+1) rows later
+//   epilogue raw   : operands of the output stage (stored result, dot products)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct LoadPlain {
+  static constexpr int NIN = 2, NRE = 1;
+  const cplx<T>* b;
+  long long pts;
+  long long off;
+  __device__ void setup(int j, const KScal*) { off = 2LL * j * pts; }
+  __device__ const cplx<T>* in(int i) const { return b + off + i * pts; }
+  __device__ const cplx<T>* re(int) const { return b + off; }
+  __device__ void form_in(const cplx<T>* raw, int st, long long, bool, cplx<T>& b1, cplx<T>& b2) const {
+    b1 = raw[0];
+    b2 = raw[st];
+  }
+  __device__ cplx<T> form_re(const cplx<T>* raw, int) const { return raw[0]; }
+};
+
+// p = r + beta (p_old - omega v_old), written to p_new at the points this block owns.
+template <typename T>
+struct LoadP {
+  static constexpr int NIN = 6, NRE = 3;
+  const cplx<T>* r;
+  const cplx<T>* po;
+  const cplx<T>* vo;
+  cplx<T>* pn;
+  long long pts;
+  cplx<T> beta, omega;
+  long long off;
+  __device__ void setup(int j, const KScal* k) {
+    beta = to_c<T>(k[j].beta);
+    omega = to_c<T>(k[j].omega);
+    off = 2LL * j * pts;
+  }
+  // raw order: r1, r2, po1, po2, vo1, vo2
+  __device__ const cplx<T>* in(int i) const {
+    const cplx<T>* base = i < 2 ? r : (i < 4 ? po : vo);
+    return base + off + (i & 1) * pts;
+  }
+  __device__ const cplx<T>* re(int i) const { return (i == 0 ? r : (i == 1 ? po : vo)) + off; }
+  __device__ __forceinline__ cplx<T> form(cplx<T> rr, cplx<T> pp, cplx<T> vv) const {
+    return cadd(rr, cmulz(beta, csub(pp, cmulz(omega, vv))));
+  }
+  __device__ void form_in(const cplx<T>* raw, int st, long long p, bool own, cplx<T>& b1, cplx<T>& b2) const {
+    b1 = form(raw[0], raw[2 * st], raw[4 * st]);
+    b2 = form(raw[st], raw[3 * st], raw[5 * st]);
+    if (own) {
+      pn[off + p] = b1;
+      pn[off + pts + p] = b2;
+    }
+  }
+  __device__ cplx<T> form_re(const cplx<T>* raw, int st) const { return form(raw[0], raw[st], raw[2 * st]); }
+};
+
+// s = r - alpha v.
+template <typename T>
+struct LoadS {
+  static constexpr int NIN = 4, NRE = 2;
+  const cplx<T>* r;
+  const cplx<T>* v;
+  long long pts;
+  cplx<T> alpha;
+  long long off;
+  __device__ void setup(int j, const KScal* k) {
+    alpha = to_c<T>(k[j].alpha);
+    off = 2LL * j * pts;
+  }
+  // raw order: r1, r2, v1, v2
+  __device__ const cplx<T>* in(int i) const { return (i < 2 ? r : v) + off + (i & 1) * pts; }
+  __device__ const cplx<T>* re(int i) const { return (i == 0 ? r : v) + off; }
+  __device__ void form_in(const cplx<T>* raw, int st, long long, bool, cplx<T>& b1, cplx<T>& b2) const {
+    b1 = csub(raw[0], cmulz(alpha, raw[2 * st]));
+    b2 = csub(raw[st], cmulz(alpha, raw[3 * st]));
+  }
+  __device__ cplx<T> form_re(const cplx<T>* raw, int st) const { return csub(raw[0], cmulz(alpha, raw[st])); }
+};
+
+template <typename T>
+struct EpStore {  // out = y
+  static constexpr int NDOT = 0, NEP = 0;
+  cplx<T>* out;
+  long long pts;
+  long long off;
+  Acc<T> acc[1];
+  __device__ void setup(int j, const KScal*) { off = 2LL * j * pts; }
+  __device__ const cplx<T>* ep(int) const { return nullptr; }
+  __device__ void put(const cplx<T>*, int, long long p, cplx<T> y1, cplx<T> y2) {
+    out[off + p] = y1;
+    out[off + pts + p] = y2;
+  }
+};
+
+template <typename T>
+struct EpAddX {  // x64 += y (the Krylov correction P^{-1} u)
+  static constexpr int NDOT = 0, NEP = 0;
+  double2* x;
+  long long pts;
+  long long off;
+  Acc<T> acc[1];
+  __device__ void setup(int j, const KScal*) { off = 2LL * j * pts; }
+  __device__ const cplx<T>* ep(int) const { return nullptr; }
+  __device__ void put(const cplx<T>*, int, long long p, cplx<T> y1, cplx<T> y2) {
+    double2 a = x[off + p], b = x[off + pts + p];
+    a.x += (double)y1.x;
+    a.y += (double)y1.y;
+    b.x += (double)y2.x;
+    b.y += (double)y2.y;
+    x[off + p] = a;
+    x[off + pts + p] = b;
+  }
+};
+
+template <typename T>
+struct EpV {  // v = y; (rhat, v)
+  static constexpr int NDOT = 1, NEP = 2;
+  cplx<T>* v;
+  const cplx<T>* rhat;
+  long long pts;
+  long long off;
+  Acc<T> acc[1];
+  __device__ void setup(int j, const KScal*) { off = 2LL * j * pts; }
+  __device__ const cplx<T>* ep(int i) const { return rhat + off + i * pts; }
+  __device__ void put(const cplx<T>* raw, int st, long long p, cplx<T> y1, cplx<T> y2) {
+    v[off + p] = y1;
+    v[off + pts + p] = y2;
+    acc[0].add_run(raw[0], y1);
+    acc[0].add_run(raw[st], y2);
+  }
+};
+
+template <typename T>
+struct EpT {  // t = y; (t, s), (t, t), (s, s) with s = r - alpha v
+  static constexpr int NDOT = 3, NEP = 4;
+  cplx<T>* t;
+  const cplx<T>* r;
+  const cplx<T>* v;
+  long long pts;
+  long long off;
+  cplx<T> alpha;
+  Acc<T> acc[3];
+  __device__ void setup(int j, const KScal* k) {
+    off = 2LL * j * pts;
+    alpha = to_c<T>(k[j].alpha);
+  }
+  // raw order: r1, r2, v1, v2
+  __device__ const cplx<T>* ep(int i) const { return (i < 2 ? r : v) + off + (i & 1) * pts; }
+  __device__ void one(long long q, cplx<T> y, cplx<T> rr, cplx<T> vv) {
+    const cplx<T> s = csub(rr, cmulz(alpha, vv));
+    t[q] = y;
+    acc[0].add_run(y, s);
+    acc[1].add_run(y, y);
+    acc[2].add_run(s, s);
+  }
+  __device__ void put(const cplx<T>* raw, int st, long long p, cplx<T> y1, cplx<T> y2) {
+    one(off + p, y1, raw[0], raw[2 * st]);
+    one(off + pts + p, y2, raw[st], raw[3 * st]);
+  }
+};
+
+// ---- asynchronous global -> shared copies (one element per thread) --------
+template <typename T>
+__device__ __forceinline__ void cp_async(cplx<T>* dst, const cplx<T>* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(cplx<T>) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// ---------------------------------------------------------------------------
+// The pipeline kernel.  M = Chebyshev applications per diffusion solve;
+// PF = rows of look-ahead of the asynchronous fetches (0: fetch when needed).
+// ---------------------------------------------------------------------------
+// Chebyshev weights of all applications: c1[k][j], c2[k][j].
+struct ChebAll {
+  double c1[kMaxCheb][kMaxJ];
+  double c2[kMaxCheb][kMaxJ];
+};
+
+template <int N>
+__host__ __device__ constexpr int pow2_at_least() {
+  int p = 1;
+  while (p < N) p *= 2;
+  return p;
+}
+
+template <typename T, int M, bool WITH_A, int PF, class LD, class EP>
+struct PipeShape {
+  static constexpr int S = 2 * M + 1 + (WITH_A ? 1 : 0);  // stencil stages = halo radius
+  static constexpr int NRING = 2 * M + 1 + (WITH_A ? 2 : 0);
+  static constexpr int QB = M + 1;                          // ring of beta2' (deep: read again by step 4)
+  static constexpr int DB = pow2_at_least<2 * M + 1>() < 4 ? 4 : pow2_at_least<2 * M + 1>();
+  static constexpr int SCHI = 2 * M + 1;  // stage forming chi1 (step 4)
+  static constexpr int SEP = S;           // stage calling the epilogue
+  static constexpr int NRAW = LD::NIN + LD::NRE + EP::NEP;
+  static constexpr int NSLOT = PF > 0 ? PF + 1 : 0;
+  static constexpr int NT = pipe_nt<T>();
+  static constexpr size_t ring_elems = (size_t)((NRING - 1) * 4 + DB) * NT;
+  static constexpr size_t smem = sizeof(cplx<T>) * (ring_elems + (size_t)NSLOT * NRAW * NT);
+  // element offset of ring q
+  __host__ __device__ static constexpr int off(int qi) { return (qi <= QB ? qi * 4 : QB * 4 + DB + (qi - QB - 1) * 4) * NT; }
+  __host__ __device__ static constexpr int depth(int qi) { return qi == QB ? DB : 4; }
+};
+
+template <typename T>
+__device__ __forceinline__ Nbh<T> fetch_d(const cplx<T>* ring, int mask, int row, int t) {
+  constexpr int NT = pipe_nt<T>();
+  const int sc = row & mask, su = (row - 1) & mask, sd = (row + 1) & mask;
+  const int tl = t > 0 ? t - 1 : t, tr = t < NT - 1 ? t + 1 : t;
+  Nbh<T> n;
+  n.c = ring[sc * NT + t];
+  n.l = ring[sc * NT + tl];
+  n.r = ring[sc * NT + tr];
+  n.u = ring[su * NT + t];
+  n.d = ring[sd * NT + t];
+  return n;
+}
+
+__device__ __forceinline__ int wrap_inc(int y, int n) { return y + 1 == n ? 0 : y + 1; }
+
+template <typename T, int M, bool WITH_A, int PF, class LD, class EP>
+__global__ void __launch_bounds__(pipe_nt<T>()) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g, LD ld, EP ep,
+                                                         const KScal* act, void* partials, int kid,
+                                                         unsigned long long bytes_per_amp) {
+  using SH = PipeShape<T, M, WITH_A, PF, LD, EP>;
+  constexpr int NT = SH::NT;
+  constexpr int S = SH::S;
+  constexpr int NRAW = SH::NRAW;
+  constexpr int OIN = 0, ORE = LD::NIN, OEP = LD::NIN + LD::NRE;  // raw offsets inside a slot
+  extern __shared__ unsigned char smem_raw[];
+  cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
+  cplx<T>* stage_buf = sm + SH::ring_elems;
+
+  const int j = blockIdx.z;
+  if (act != nullptr && act[j].active == 0) return;
+  const int t = threadIdx.x;
+  const JCoef<T> q = jcoef<T>(c, j);
+  T c1[M], c2[M];
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    c1[k] = (T)cw.c1[k][j];
+    c2[k] = (T)cw.c2[k][j];
+  }
+  ld.setup(j, act);
+  ep.setup(j, act);
+#pragma unroll
+  for (int k = 0; k < EP::NDOT; ++k) ep.acc[k].zero();
+  if (c.prof != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && t == 0) atomicAdd(c.prof + kid, bytes_per_amp);
+
+  // zero the rings (garbage in invalid halo columns must stay finite)
+  for (int i = t; i < (int)SH::ring_elems; i += NT) sm[i] = mkc<T>((T)0, (T)0);
+
+  const int x_first = blockIdx.x * g.wv - S;  // global column of thread 0 (unwrapped)
+  int gx = (x_first + t) % g.nx;
+  if (gx < 0) gx += g.nx;
+  const int xo = blockIdx.x * g.wv + (t - S);  // output column of this thread
+  const bool col_own = (t >= S) && (t < NT - S) && (xo < g.nx);
+  const int y0 = blockIdx.y * g.Ly;
+  const int rows_in = g.Ly + 2 * S;  // local rows 0 .. rows_in-1 = global y0-S ..
+  const int steps = g.Ly + 3 * S;
+
+  auto grow = [&](int lr) {  // only for initialising the incremental row trackers
+    int y = (y0 - S + lr) % g.ny;
+    return y < 0 ? y + g.ny : y;
+  };
+  auto row_own = [&](int lr) { return lr >= S && lr < S + g.Ly && (y0 + lr - S) < g.ny; };
+  auto valid_at = [&](int s, int lr) { return lr >= s && lr < rows_in - s; };
+  auto need_ep = [&](int lr) { return valid_at(SH::SEP, lr) && col_own && row_own(lr); };
+  auto ptg = [&](int gy) { return (long long)gy * g.nx + gx; };
+
+  // global rows of the points touched at this step, advanced by one row per step
+  int gy_in = grow(0), gy_chi = grow(-2 * SH::SCHI), gy_ep = grow(-2 * SH::SEP);
+  // rows of the next fetch, starting with the prologue's local time 0
+  int fy_in = grow(0), fy_re = grow(-2 * SH::SCHI), fy_ep = grow(-2 * SH::SEP);
+
+  // asynchronous fetch of everything local time tf will consume (rows fy_*)
+  auto issue = [&](int tf) {
+    if constexpr (PF > 0) {
+      cplx<T>* slot = stage_buf + (size_t)(tf % SH::NSLOT) * NRAW * NT + t;
+      if (tf < rows_in) {
+        const long long p = ptg(fy_in);
+#pragma unroll
+        for (int i = 0; i < LD::NIN; ++i) cp_async<T>(slot + (OIN + i) * NT, ld.in(i) + p);
+      }
+      if (valid_at(SH::SCHI, tf - 2 * SH::SCHI)) {
+        const long long p = ptg(fy_re);
+#pragma unroll
+        for (int i = 0; i < LD::NRE; ++i) cp_async<T>(slot + (ORE + i) * NT, ld.re(i) + p);
+      }
+      if constexpr (EP::NEP > 0) {
+        if (need_ep(tf - 2 * SH::SEP)) {
+          const long long p = ptg(fy_ep);
+#pragma unroll
+          for (int i = 0; i < EP::NEP; ++i) cp_async<T>(slot + (OEP + i) * NT, ep.ep(i) + p);
+        }
+      }
+      cp_commit();
+      fy_in = wrap_inc(fy_in, g.ny);
+      fy_re = wrap_inc(fy_re, g.ny);
+      fy_ep = wrap_inc(fy_ep, g.ny);
+    }
+  };
+
+  // register delay lines: beta2 (2 steps) and the Chebyshev x, r of every stage (2 steps)
+  cplx<T> b2dl[2];
+  cplx<T> XD[2 * M + 2][2], RD[2 * M + 2][2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) b2dl[k] = mkc<T>((T)0, (T)0);
+#pragma unroll
+  for (int s = 0; s < 2 * M + 2; ++s)
+#pragma unroll
+    for (int k = 0; k < 2; ++k) XD[s][k] = RD[s][k] = mkc<T>((T)0, (T)0);
+
+  auto ring = [&](int qi) { return sm + SH::off(qi); };
+
+  if constexpr (PF > 0) {
+#pragma unroll
+    for (int tf = 0; tf < PF; ++tf) issue(tf);
+  }
+  __syncthreads();
+
+#pragma unroll(sizeof(T) == 4 ? 2 : 1)
+  for (int rho = 0; rho < steps; ++rho) {
+    const cplx<T>* raw = nullptr;
+    int st = 1;
+    if constexpr (PF > 0) {
+      issue(rho + PF);
+      cp_wait<PF>();
+      raw = stage_buf + (size_t)(rho % SH::NSLOT) * NRAW * NT + t;
+      st = NT;
+    }
+    Nbh<T> nb[S + 2];
+    // phase B: compute and write this step's rows, latest stage first
+    static_for_rev<S, 1>([&](auto sc) {
+      constexpr int s = decltype(sc)::value;
+      const int lr = rho - 2 * s;
+      const bool valid = valid_at(s, lr);
+      if (valid) {
+        if constexpr (WITH_A && s == S) {
+          nb[S] = fetch_d<T>(ring(2 * M + 1), 3, lr, t);
+          nb[S + 1] = fetch_d<T>(ring(2 * M + 2), 3, lr, t);
+        } else {
+          nb[s] = fetch_d<T>(ring(s - 1), SH::depth(s - 1) - 1, lr, t);
+        }
+      }
+      if constexpr (s == 1) {
+        // f = beta2 - kt G beta1
+        if (valid) {
+          const cplx<T> gb = opG<T>(nb[1], q);
+          ring(1)[(lr & 3) * NT + t] = csub(b2dl[1], cscale(q.kt, gb));
+        }
+      } else if constexpr (s <= 2 * M + 1) {
+        // Chebyshev application k of solve 1 (s <= M+1) or solve 2
+        constexpr bool solve1 = s <= M + 1;
+        constexpr int k = solve1 ? s - 2 : s - M - 2;
+        constexpr bool last = (k == M - 1);
+        cplx<T> X, R, dn;
+        if (valid) {
+          const Nbh<T>& n = nb[s];
+          const cplx<T> Dd = opD<T>(n, q);
+          if constexpr (k == 0) {
+            const cplx<T> d0 = cscale(q.it, n.c);
+            X = d0;
+            R = csub(n.c, cscale(q.it, Dd));
+            dn = caxpy(c1[0], d0, cscale(c2[0], R));
+          } else {
+            X = cadd(XD[s - 1][1], n.c);
+            R = csub(RD[s - 1][1], Dd);
+            dn = caxpy(c1[k], n.c, cscale(c2[k], R));
+          }
+          if constexpr (!last) {
+            ring(s)[(lr & 3) * NT + t] = dn;
+          } else if constexpr (solve1) {
+            ring(s)[(lr & (SH::DB - 1)) * NT + t] = cadd(X, dn);  // beta2'
+          } else {
+            const cplx<T> chi2 = cadd(X, dn);
+            const long long p = ptg(gy_chi);
+            cplx<T> b1;
+            if constexpr (PF > 0) {
+              b1 = ld.form_re(raw + ORE * st, st);
+            } else {
+              cplx<T> rr[LD::NRE];
+#pragma unroll
+              for (int i = 0; i < LD::NRE; ++i) rr[i] = ld.re(i)[p];
+              b1 = ld.form_re(rr, 1);
+            }
+            const cplx<T> b2p = ring(SH::QB)[(lr & (SH::DB - 1)) * NT + t];
+            const cplx<T> chi1 = cadd(b1, cscale(q.inv_mu, csub(b2p, cscale(q.sD, chi2))));
+            if constexpr (WITH_A) {
+              ring(s)[(lr & 3) * NT + t] = chi1;
+              ring(s + 1)[(lr & 3) * NT + t] = chi2;
+            } else {
+              if (col_own && row_own(lr)) ep.put(raw + OEP * st, st, p, chi1, chi2);
+            }
+          }
+        }
+        if constexpr (!last) {
+          XD[s][1] = XD[s][0];
+          XD[s][0] = X;
+          RD[s][1] = RD[s][0];
+          RD[s][0] = R;
+        }
+      } else {
+        // y = A (chi1, chi2)
+        if (valid && col_own && row_own(lr)) {
+          const Nbh<T>& n1 = nb[S];
+          const Nbh<T>& n2 = nb[S + 1];
+          const cplx<T> g1 = opG<T>(n1, q), g2 = opG<T>(n2, q);
+          const cplx<T> y1 = csub(n1.c, g2);
+          const cplx<T> y2 = caxpy(q.kt, g1, cscale(q.a, n2.c));
+          const long long p = ptg(gy_ep);
+          if constexpr (PF > 0) {
+            ep.put(raw + OEP * st, st, p, y1, y2);
+          } else {
+            cplx<T> er[EP::NEP > 0 ? EP::NEP : 1];
+#pragma unroll
+            for (int i = 0; i < EP::NEP; ++i) er[i] = ep.ep(i)[p];
+            ep.put(er, 1, p, y1, y2);
+          }
+        }
+      }
+    });
+    // stage 0: input row rho
+    {
+      cplx<T> b1 = mkc<T>((T)0, (T)0), b2 = b1;
+      if (rho < rows_in) {
+        const long long p = ptg(gy_in);
+        if constexpr (PF > 0) {
+          ld.form_in(raw + OIN * st, st, p, col_own && row_own(rho), b1, b2);
+        } else {
+          cplx<T> ri[LD::NIN];
+#pragma unroll
+          for (int i = 0; i < LD::NIN; ++i) ri[i] = ld.in(i)[p];
+          ld.form_in(ri, 1, p, col_own && row_own(rho), b1, b2);
+        }
+        ring(0)[(rho & 3) * NT + t] = b1;
+      }
+      b2dl[1] = b2dl[0];
+      b2dl[0] = b2;
+    }
+    if constexpr (EP::NDOT > 0) {
+      if ((rho & 7) == 7) {
+#pragma unroll
+        for (int k = 0; k < EP::NDOT; ++k) ep.acc[k].flush();
+      }
+    }
+    gy_in = wrap_inc(gy_in, g.ny);
+    gy_chi = wrap_inc(gy_chi, g.ny);
+    gy_ep = wrap_inc(gy_ep, g.ny);
+    __syncthreads();
+  }
+  if constexpr (PF > 0) cp_wait<0>();
+
+  if constexpr (EP::NDOT > 0) {
+    const int blk = blockIdx.y * g.nstrips + blockIdx.x;
+#pragma unroll
+    for (int k = 0; k < EP::NDOT; ++k) {
+      ep.acc[k].flush();
+      block_reduce<T, NT>(ep.acc[k]);
+      if (t == 0) ep.acc[k].store(partials, (long long)(j * 3 + k) * g.npart + blk);
+    }
+  }
+}
+
+PipeGeom geom(const OpCoef& c, int S, int Ly, int NT) {
+  PipeGeom g;
+  g.nx = c.nx;
+  g.ny = c.ny;
+  g.Ly = Ly < c.ny ? Ly : c.ny;
+  g.wv = NT - 2 * S;
+  g.nstrips = (c.nx + g.wv - 1) / g.wv;
+  g.nsegs = (c.ny + g.Ly - 1) / g.Ly;
+  g.npart = g.nstrips * g.nsegs;
+  g.pts = c.pts;
+  return g;
+}
+
+// Look-ahead rows: FP32 fields prefetch 2 rows; FP64 pipelines (limited by
+// FP64 arithmetic, and by shared memory for their 16-byte rings) fetch on use.
+template <typename T>
+constexpr int prefetch_rows() {
+  return sizeof(T) == 4 ? 2 : 0;
+}
+
+template <typename T, int M, bool WITH_A, class LD, class EP>
+void launch_pipe(const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const KScal* act, void* partials,
+                 cudaStream_t s, int kid, int fields) {
+  constexpr int PF = prefetch_rows<T>();
+  using SH = PipeShape<T, M, WITH_A, PF, LD, EP>;
+  constexpr int NT = SH::NT;
+  const PipeGeom g = geom(c, SH::S, Ly, NT);
+  constexpr size_t sm = SH::smem;
+  auto kern = k_pipe2d<T, M, WITH_A, PF, LD, EP>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr_set = true;
+  }
+  ProfScope ps_(kid, s);
+  ChebAll ca;
+  for (int k = 0; k < kMaxCheb; ++k)
+    for (int i = 0; i < kMaxJ; ++i) {
+      ca.c1[k][i] = k < M ? w[k].c1[i] : 0.0;
+      ca.c2[k][i] = k < M ? w[k].c2[i] : 0.0;
+    }
+  const unsigned long long bytes = (unsigned long long)fields * (unsigned long long)g.pts * sizeof(cplx<T>);
+  kern<<<dim3(g.nstrips, g.nsegs, c.J), NT, sm, s>>>(c, ca, g, ld, ep, act, partials, kid, bytes);
+}
+
+template <typename T, bool WITH_A, class LD, class EP>
+bool dispatch(int m, const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const KScal* act, void* partials,
+              cudaStream_t s, int kid, int fields) {
+  switch (m) {
+    case 1: launch_pipe<T, 1, WITH_A>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+    case 2: launch_pipe<T, 2, WITH_A>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+    case 3: launch_pipe<T, 3, WITH_A>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+    case 4: launch_pipe<T, 4, WITH_A>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+    default: return false;
+  }
+}
+
+// BiCGStab vector update: s = r - alpha v; u += alpha p + omega s; r = s - omega t;
+// partials of (rhat, r) and (r, r).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_bicg_update(cplx<T>* __restrict__ r, const cplx<T>* __restrict__ v,
+                                                          const cplx<T>* __restrict__ p, cplx<T>* __restrict__ u,
+                                                          const cplx<T>* __restrict__ t,
+                                                          const cplx<T>* __restrict__ rhat, const KScal* ks,
+                                                          long long pts, void* partials, OpCoef c) {
+  const int j = blockIdx.y;
+  if (ks[j].active == 0) return;
+  prof_add(c, kid_of<T>(KID_BICG_UPDATE), 16ull * (unsigned long long)pts * sizeof(cplx<T>));
+  const cplx<T> al = to_c<T>(ks[j].alpha), om = to_c<T>(ks[j].omega);
+  const long long n = 2 * pts, o = 2LL * j * pts;
+  Acc<T> a0, a1;
+  a0.zero();
+  a1.zero();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long q = o + i;
+    const cplx<T> s = csub(r[q], cmulz(al, v[q]));
+    u[q] = cadd(u[q], cadd(cmulz(al, p[q]), cmulz(om, s)));
+    const cplx<T> rn = csub(s, cmulz(om, t[q]));
+    r[q] = rn;
+    a0.add(rhat[q], rn);
+    a1.add(rn, rn);
+  }
+  block_reduce<T>(a0);
+  if (threadIdx.x == 0) a0.store(partials, (long long)(j * 3 + 0) * kDotBlocks + blockIdx.x);
+  block_reduce<T>(a1);
+  if (threadIdx.x == 0) a1.store(partials, (long long)(j * 3 + 1) * kDotBlocks + blockIdx.x);
+}
+
+}  // namespace
+
+int fused2d_max_degree(int elem_bytes) { return elem_bytes == 8 ? 4 : 4; }
+
+int fused2d_npart(const OpCoef& c, int m, int Ly, int elem_bytes) {
+  return geom(c, 2 * m + 2, Ly, elem_bytes == 8 ? pipe_nt<float>() : pipe_nt<double>()).npart;
+}
+
+template <typename T>
+bool launch_fused_v(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* p_old,
+                    const cplx<T>* v_old, cplx<T>* p_new, cplx<T>* v_new, const cplx<T>* rhat, const KScal* act,
+                    void* partials, cudaStream_t s) {
+  LoadP<T> ld{r, p_old, v_old, p_new, c.pts};
+  EpV<T> ep{v_new, rhat, c.pts};
+  // reads r, p_old, v_old, rhat (2 fields each); writes p_new, v_new
+  return dispatch<T, true>(m, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV), 12);
+}
+
+template <typename T>
+bool launch_fused_t(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
+                    cplx<T>* t_out, const KScal* act, void* partials, cudaStream_t s) {
+  LoadS<T> ld{r, v, c.pts};
+  EpT<T> ep{t_out, r, v, c.pts};
+  // reads r, v; writes t
+  return dispatch<T, true>(m, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV), 6);
+}
+
+template <typename T>
+bool launch_fused_pinv_add(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* u, double2* x64,
+                           cudaStream_t s) {
+  LoadPlain<T> ld{u, c.pts};
+  EpAddX<T> ep{x64, c.pts};
+  // reads u (2 fields); reads and writes the FP64 block x (2 FP64 fields each way)
+  const int f = 2 + 4 * (int)(sizeof(double2) / sizeof(cplx<T>));
+  return dispatch<T, false>(m, c, w, Ly, ld, ep, nullptr, nullptr, s, kid_of<T>(KID_FUSED_PINV), f);
+}
+
+template <typename T>
+bool launch_fused_pinv_store(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* b, cplx<T>* x,
+                             cudaStream_t s) {
+  LoadPlain<T> ld{b, c.pts};
+  EpStore<T> ep{x, c.pts};
+  return dispatch<T, false>(m, c, w, Ly, ld, ep, nullptr, nullptr, s, kid_of<T>(KID_FUSED_PINV), 4);
+}
+
+template <typename T>
+void launch_bicg_update(cplx<T>* r, const cplx<T>* v, const cplx<T>* p, cplx<T>* u, const cplx<T>* t,
+                        const cplx<T>* rhat, const KScal* ks, void* partials, const OpCoef& c, cudaStream_t s) {
+  ProfScope ps_(kid_of<T>(KID_BICG_UPDATE), s);
+  k_bicg_update<T><<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(r, v, p, u, t, rhat, ks, c.pts, partials, c);
+}
+
+#define APFC_FUSED_INST(T)                                                                                         \
+  template bool launch_fused_v<T>(int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*,        \
+                                  const cplx<T>*, cplx<T>*, cplx<T>*, const cplx<T>*, const KScal*, void*,         \
+                                  cudaStream_t);                                                                   \
+  template bool launch_fused_t<T>(int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*,        \
+                                  cplx<T>*, const KScal*, void*, cudaStream_t);                                    \
+  template bool launch_fused_pinv_add<T>(int, int, const OpCoef&, const ChebStep*, const cplx<T>*, double2*,       \
+                                         cudaStream_t);                                                            \
+  template bool launch_fused_pinv_store<T>(int, int, const OpCoef&, const ChebStep*, const cplx<T>*, cplx<T>*,     \
+                                           cudaStream_t);                                                          \
+  template void launch_bicg_update<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, cplx<T>*, const cplx<T>*,          \
+                                      const cplx<T>*, const KScal*, void*, const OpCoef&, cudaStream_t);
+
+APFC_FUSED_INST(double)
+APFC_FUSED_INST(float)
+
+}  // namespace apfc

@@ -6,107 +6,12 @@
 // Neumaier-compensated summation (each partial is a (sum, compensation) pair)
 // through the thread, block and final stages; the fixed reduction tree makes
 // every result deterministic.
+#include "acc.cuh"
 #include "apfc_internal.cuh"
 
 namespace apfc {
 
 namespace {
-
-// ---- compensated FP32 pair arithmetic ------------------------------------
-struct CF {
-  float s, c;
-};
-__device__ __forceinline__ void cf_add(CF& a, float x) {
-  const float t = a.s + x;
-  if (fabsf(a.s) >= fabsf(x))
-    a.c += (a.s - t) + x;
-  else
-    a.c += (x - t) + a.s;
-  a.s = t;
-}
-__device__ __forceinline__ void cf_merge(CF& a, const CF& b) {
-  cf_add(a, b.s);
-  a.c += b.c;
-}
-
-template <typename T>
-struct Acc;
-
-template <>
-struct Acc<double> {
-  double re, im;
-  __device__ __forceinline__ void zero() { re = im = 0.0; }
-  __device__ __forceinline__ void add(double2 u, double2 v) {
-    re += u.x * v.x + u.y * v.y;
-    im += u.x * v.y - u.y * v.x;
-  }
-  __device__ __forceinline__ void shfl_merge(int o) {
-    re += __shfl_xor_sync(0xffffffffu, re, o);
-    im += __shfl_xor_sync(0xffffffffu, im, o);
-  }
-  __device__ __forceinline__ void merge(const Acc& b) {
-    re += b.re;
-    im += b.im;
-  }
-  __device__ __forceinline__ void store(void* part, long long idx) const {
-    reinterpret_cast<double2*>(part)[idx] = make_double2(re, im);
-  }
-  __device__ __forceinline__ void load(const void* part, long long idx) {
-    const double2 v = reinterpret_cast<const double2*>(part)[idx];
-    re = v.x;
-    im = v.y;
-  }
-  __device__ __forceinline__ double2 value() const { return make_double2(re, im); }
-};
-
-template <>
-struct Acc<float> {
-  CF re, im;
-  __device__ __forceinline__ void zero() { re = CF{0.f, 0.f}; im = CF{0.f, 0.f}; }
-  __device__ __forceinline__ void add(float2 u, float2 v) {
-    cf_add(re, u.x * v.x + u.y * v.y);
-    cf_add(im, u.x * v.y - u.y * v.x);
-  }
-  __device__ __forceinline__ void shfl_merge(int o) {
-    CF r{__shfl_xor_sync(0xffffffffu, re.s, o), __shfl_xor_sync(0xffffffffu, re.c, o)};
-    CF i{__shfl_xor_sync(0xffffffffu, im.s, o), __shfl_xor_sync(0xffffffffu, im.c, o)};
-    cf_merge(re, r);
-    cf_merge(im, i);
-  }
-  __device__ __forceinline__ void merge(const Acc& b) {
-    cf_merge(re, b.re);
-    cf_merge(im, b.im);
-  }
-  __device__ __forceinline__ void store(void* part, long long idx) const {
-    reinterpret_cast<float4*>(part)[idx] = make_float4(re.s, re.c, im.s, im.c);
-  }
-  __device__ __forceinline__ void load(const void* part, long long idx) {
-    const float4 v = reinterpret_cast<const float4*>(part)[idx];
-    re = CF{v.x, v.y};
-    im = CF{v.z, v.w};
-  }
-  __device__ __forceinline__ double2 value() const {
-    return make_double2((double)re.s + (double)re.c, (double)im.s + (double)im.c);
-  }
-};
-
-// Reduce an accumulator over the block; thread 0 ends with the total.
-template <typename T>
-__device__ __forceinline__ void block_reduce(Acc<T>& a) {
-  __shared__ Acc<T> sh[kThreads / 32];
-  for (int o = 16; o > 0; o >>= 1) a.shfl_merge(o);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) sh[w] = a;
-  __syncthreads();
-  if (w == 0) {
-    if (l < kThreads / 32)
-      a = sh[l];
-    else
-      a.zero();
-    for (int o = 16; o > 0; o >>= 1) a.shfl_merge(o);
-  }
-  __syncthreads();
-}
 
 template <typename T, int NP>
 __global__ void k_dots(DotPairs<T> pr, void* partials, OpCoef c, const KScal* act) {
@@ -228,6 +133,20 @@ __device__ void scalar_update(KScal& k, int op, const double2* d) {
       }
       break;
     }
+    case OP_OMEGA3: {  // d0 = (t, s), d1 = (t, t), d2 = (s, s)
+      if (!finite2(d[0]) || !isfinite(d[1].x) || !isfinite(d[2].x)) {
+        k.status = KS_NAN;
+        k.active = 0;
+      } else if (d[2].x <= k.tol2) {
+        k.omega = make_double2(0.0, 0.0);  // s already meets tol: the update sets r = s
+      } else if (d[1].x == 0.0 || cabs2(d[0]) == 0.0) {
+        k.status = KS_BREAKDOWN;
+        k.active = 0;
+      } else {
+        k.omega = make_double2(d[0].x / d[1].x, d[0].y / d[1].x);
+      }
+      break;
+    }
     case OP_NORMS: {  // d0 = (r, r), d1 = (b, b): record only
       k.rnorm2 = d[0].x;
       k.bnorm2 = d[1].x;
@@ -237,7 +156,7 @@ __device__ void scalar_update(KScal& k, int op, const double2* d) {
 }
 
 template <typename T, int NP>
-__global__ void k_finalize(const void* partials, KScal* ks, int op) {
+__global__ void k_finalize(const void* partials, int npart, KScal* ks, int op) {
   const int j = blockIdx.x;
   KScal& k = ks[j];
   if (op != OP_INIT && op != OP_NORMS && k.active == 0) return;
@@ -246,9 +165,9 @@ __global__ void k_finalize(const void* partials, KScal* ks, int op) {
   for (int q = 0; q < NP; ++q) {
     Acc<T> a;
     a.zero();
-    for (int b = threadIdx.x; b < kDotBlocks; b += blockDim.x) {
+    for (int b = threadIdx.x; b < npart; b += blockDim.x) {
       Acc<T> t;
-      t.load(partials, (long long)(j * 3 + q) * kDotBlocks + b);
+      t.load(partials, (long long)(j * 3 + q) * npart + b);
       a.merge(t);
     }
     block_reduce<T>(a);
@@ -272,14 +191,14 @@ void launch_dots(int npair, const DotPairs<T>& pr, void* partials, const OpCoef&
 }
 
 template <typename T>
-void launch_finalize(int npair, const void* partials, KScal* k, int op, int J, cudaStream_t s) {
+void launch_finalize(int npair, const void* partials, KScal* k, int op, int J, cudaStream_t s, int npart) {
   ProfScope ps_(kid_of<T>(KID_FINALIZE), s);
   if (npair == 1)
-    k_finalize<T, 1><<<J, kThreads, 0, s>>>(partials, k, op);
+    k_finalize<T, 1><<<J, kThreads, 0, s>>>(partials, npart, k, op);
   else if (npair == 2)
-    k_finalize<T, 2><<<J, kThreads, 0, s>>>(partials, k, op);
+    k_finalize<T, 2><<<J, kThreads, 0, s>>>(partials, npart, k, op);
   else
-    k_finalize<T, 3><<<J, kThreads, 0, s>>>(partials, k, op);
+    k_finalize<T, 3><<<J, kThreads, 0, s>>>(partials, npart, k, op);
 }
 
 void launch_finalize64(int npair, const void* partials, KScal* k, int op, int J, cudaStream_t s) {
@@ -288,7 +207,7 @@ void launch_finalize64(int npair, const void* partials, KScal* k, int op, int J,
 
 template void launch_dots<double>(int, const DotPairs<double>&, void*, const OpCoef&, const KScal*, cudaStream_t);
 template void launch_dots<float>(int, const DotPairs<float>&, void*, const OpCoef&, const KScal*, cudaStream_t);
-template void launch_finalize<double>(int, const void*, KScal*, int, int, cudaStream_t);
-template void launch_finalize<float>(int, const void*, KScal*, int, int, cudaStream_t);
+template void launch_finalize<double>(int, const void*, KScal*, int, int, cudaStream_t, int);
+template void launch_finalize<float>(int, const void*, KScal*, int, int, cudaStream_t, int);
 
 }  // namespace apfc

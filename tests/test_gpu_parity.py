@@ -44,10 +44,14 @@ def test_block_operator_parity(kind, shape, h):
 
 
 @pytest.mark.parametrize("kind,shape,h", CASES)
-@pytest.mark.parametrize("m", [0, 1, 3, 6])
+@pytest.mark.parametrize("m", [0, 1, 2, 3, 4, 6])
 @pytest.mark.parametrize("tau", ["fold", "plain"])
-def test_preconditioner_parity(kind, shape, h, m, tau):
-    ctx, L = context(kind, shape, h, cheb_degree=m, tau_mode=A.APFC_TAU_FOLD if tau == "fold" else A.APFC_TAU_PLAIN)
+@pytest.mark.parametrize("fused", [0, 1])
+def test_preconditioner_parity(kind, shape, h, m, tau, fused):
+    # fused = 1 runs the row-streaming 2D pipeline for 1 <= m <= 4 (other cases take the per-pass kernels)
+    ctx, L = context(
+        kind, shape, h, cheb_degree=m, tau_mode=A.APFC_TAU_FOLD if tau == "fold" else A.APFC_TAU_PLAIN, fused=fused
+    )
     b = inputs.random_amplitudes(2 * L.J, shape, seed=2, scale=1.0).reshape((L.J, 2) + shape)
     dt = 1.0
     x = ctx.apply_preconditioner(dt, b)
@@ -86,10 +90,11 @@ def _trajectory_parity(kind, eta0, shape, h, nsteps, dt=1.0, bound=1e-10, **opts
     return worst, ctx.stats()
 
 
-def test_step_parity_grain_128_fp64():
+@pytest.mark.parametrize("fused", [1, 0])
+def test_step_parity_grain_128_fp64(fused):
     # 2D hexagonal, 128x128, grain R=30 rotated 5 deg in liquid, dt=1, 20 steps.
     eta0 = inputs.hex_grain_128(O.uniform_solid_hex(P))
-    worst, st = _trajectory_parity("hex", eta0, (128, 128), H2, 20, tol=1e-13)
+    worst, st = _trajectory_parity("hex", eta0, (128, 128), H2, 20, tol=1e-13, fused=fused)
     print(f"fp64 grain-128 worst rel L2 {worst:.3e}, iters last {st['iters_last']}")
     assert st["steps"] == 20 and st["resid_last"] <= 1e-13
 
@@ -104,11 +109,14 @@ def test_step_parity_grain_128_fp32_refined():
 
 
 @pytest.mark.parametrize("prec", [A.APFC_FP64, A.APFC_FP32_REFINED])
-@pytest.mark.parametrize("kind,shape,h", CASES[1:])
-def test_step_parity_ragged(kind, shape, h, prec):
+@pytest.mark.parametrize("kind,shape,h", CASES[1:] + [("hex", (300, 530), (1.2, 0.8))])
+@pytest.mark.parametrize("m", [1, 3, 4])
+def test_step_parity_ragged(kind, shape, h, prec, m):
+    # 530 columns span three 256-column strips of the fused pipeline with a ragged last one;
+    # 300 rows span two 256-row segments.
     L = O.hex_lattice() if kind == "hex" else O.bcc_lattice()
     eta0 = inputs.random_amplitudes(L.J, shape, seed=4, scale=0.1)
-    _trajectory_parity(kind, eta0, shape, h, 3, dt=0.5, tol=1e-13, precision=prec)
+    _trajectory_parity(kind, eta0, shape, h, 3, dt=0.5, tol=1e-13, precision=prec, cheb_degree=m)
 
 
 def test_fourier_mode_decay():
