@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--timed-kernel", default="fused_apinv_f32")
-    ap.add_argument("--cheb", type=int, default=3)
+    ap.add_argument("--cheb", type=int, default=1, help="Chebyshev applications per diffusion solve")
+    ap.add_argument("--tol-inner", type=float, default=1e-4, help="relative tolerance of each FP32 inner solve")
+    ap.add_argument("--breakdown-steps", type=int, default=3, help="steps of the per-kernel timing pass (0: off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -67,6 +69,8 @@ def workload_config(n, steps_note=None):
         "params": {"dB": PARAMS[0], "Bx": PARAMS[1], "t": PARAMS[2], "v": PARAMS[3]},
         "tol": TOL,
         "krylov": "right-preconditioned BiCGStab, Schur-complement preconditioner",
+        "cheb_degree": CHEB,
+        "tol_inner": TOL_INNER,
         "l2": "inputs larger than L2 (FP64 state 805 MB per 4096^2 replica); no flush",
     }
     if steps_note:
@@ -273,7 +277,9 @@ def run_ours(args):
     dof = J * n * n
     stream = torch.cuda.current_stream(dev)
 
-    opts = A.apfc_default_opts(precision=A.APFC_FP32_REFINED, tol=TOL, cheb_degree=args.cheb)
+    opts = A.apfc_default_opts(
+        precision=A.APFC_FP32_REFINED, tol=TOL, cheb_degree=args.cheb, tol_inner=args.tol_inner
+    )
     ctx = A.Context(k, A.APFC_LATTICE_HEX2D, prm, (n, n), (H, H), opts, stream=stream.cuda_stream)
     eta_dev = torch.from_numpy(eta0).to(dev)
 
@@ -310,6 +316,36 @@ def run_ours(args):
     bytes_per_launch = prof["bytes"] / max(prof["launches"], 1)
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else None
     traffic = ncu_traffic(args.timed_kernel, f"hex2d-{n}")
+
+    # --- per-kernel breakdown: every launch bracketed by events (separate pass) ----
+    breakdown = None
+    if args.breakdown_steps > 0:
+        ctx.set_amplitudes(eta_dev)
+        ctx.step(1.0, args.warmup)
+        ctx.profile_start("all")
+        torch.cuda.synchronize(dev)
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        ctx.step(1.0, args.breakdown_steps)
+        b1.record(stream)
+        torch.cuda.synchronize(dev)
+        wall = b0.elapsed_time(b1) / args.breakdown_steps
+        per = {}
+        for name in A.kernel_ids():
+            r = ctx.profile_read(name)
+            if r["launches"]:
+                per[name] = {
+                    "ms_per_step": r["ms"] / args.breakdown_steps,
+                    "launches_per_step": r["launches"] / args.breakdown_steps,
+                    "gbs": (r["bytes"] / (r["ms"] * 1e-3) / 1e9) if r["ms"] > 0 else None,
+                }
+        ctx.profile_stop()
+        breakdown = {
+            "ms_per_step_wall": wall,
+            "ms_per_step_kernels": sum(v["ms_per_step"] for v in per.values()),
+            "kernels": dict(sorted(per.items(), key=lambda kv: -kv[1]["ms_per_step"])),
+        }
 
     # --- plain FP64 path at the same final residual ------------------------------
     ctx.set_opts(A.apfc_default_opts(precision=A.APFC_FP64, tol=TOL, cheb_degree=args.cheb))
@@ -396,13 +432,20 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step},
         "gpu_launches": prof["all_launches"],
+        "breakdown": breakdown,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
 
 
+CHEB = 1
+TOL_INNER = 1e-4
+
+
 def main():
+    global CHEB, TOL_INNER
     args = parse()
+    CHEB, TOL_INNER = args.cheb, args.tol_inner
     if args.impl == "reference":
         run_reference(args)
     else:

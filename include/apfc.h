@@ -215,9 +215,10 @@ apfc_status apfc_apply_preconditioner_static(const apfc_lattice* lat, const apfc
  * kernel adds the algorithmic bytes it moves (its whole-field reads and
  * writes, counted once per active amplitude) to a device counter of its id,
  * the host counts launches per id, and each launch of kernel timed_id
- * (-1: none) is bracketed by CUDA events recorded on the context stream.
+ * (-1: none; -2: every kernel) is bracketed by CUDA events recorded on the
+ * context stream.
  * apfc_profile_read(ctx, id, ...): synchronises the stream; returns since the
- * start the summed event time of id in ms (0 unless id == timed_id), its
+ * start the summed event time of id in ms (0 unless id is timed), its
  * launches, its algorithmic bytes, and the launches of all library kernels.
  * Null output pointers are skipped.  apfc_profile_stop(ctx) ends it. */
 int apfc_kernel_count(void);

@@ -286,7 +286,11 @@ class Context:
 
     # -- measurement -------------------------------------------------------
     def profile_start(self, timed: str | int | None = None):
-        tid = -1 if timed is None else (timed if isinstance(timed, int) else kernel_ids()[timed])
+        """timed: a kernel name or id, None (no event timing) or "all" (every kernel)."""
+        if timed == "all":
+            tid = -2
+        else:
+            tid = -1 if timed is None else (timed if isinstance(timed, int) else kernel_ids()[timed])
         _check(load().apfc_profile_start(self._h, tid), self._h)
 
     def profile_read(self, kernel: str | int) -> dict:

@@ -20,6 +20,7 @@ constexpr int kMaxJ = APFC_MAX_J;
 constexpr int kMaxCheb = 16;     // Chebyshev applications per diffusion solve
 constexpr int kMaxTerms = 96;    // derivative / energy monomials of table lattices
 constexpr int kDotBlocks = 304;  // partial-sum blocks per amplitude (2 x 152 SMs)
+constexpr int kDotSlots = 6;     // inner products per amplitude that one reduction can carry
 constexpr int kThreads = 256;
 
 // ---------------------------------------------------------------------------
@@ -153,10 +154,12 @@ struct KScal {
   double2 rho, alpha, omega, beta;
   double bnorm2, rnorm2, tol2, tolrel2;
   int active, iters, status, max_iter;
+  int just_done;  // merged iteration: stopped in this iteration, its last update still pending
+  int pad;
 };
 
 enum KStatus { KS_RUNNING = 0, KS_CONVERGED = 1, KS_NOCONV = 2, KS_BREAKDOWN = 3, KS_NAN = 4 };
-enum KOp { OP_INIT = 0, OP_ALPHA = 1, OP_SNORM = 2, OP_OMEGA = 3, OP_RHO = 4, OP_NORMS = 5, OP_OMEGA3 = 6 };
+enum KOp { OP_INIT = 0, OP_ALPHA = 1, OP_SNORM = 2, OP_OMEGA = 3, OP_RHO = 4, OP_NORMS = 5, OP_OMEGA3 = 6, OP_RNORM = 7, OP_BNORM = 8, OP_OMEGA5 = 9 };
 
 // Up to three (u, v) pairs of block vectors for conj(u).v per amplitude.
 template <typename T>
@@ -201,13 +204,19 @@ void launch_rhs(const double2* x, double2* b, const OpCoef& c, const NonlinTable
 void launch_zeta(double2* x, const OpCoef& c, cudaStream_t s);
 void launch_residual_refine(const double2* b, const double2* x, float2* r32, double* partials, const OpCoef& c,
                             cudaStream_t s);
+// 2D only: FP64 residual with FP32 (and optional FP64) output
+void launch_residual_refine2d(const double2* b, const double2* x, float2* r32, double2* r64, double* partials,
+                              const OpCoef& c, cudaStream_t s);
+// new RHS and initial residual r0 = b - b_prev + r_prev (pointwise)
+void launch_rhs_resid(const double2* x, double2* b, const double2* b_prev, const double2* r_prev, float2* r32,
+                      double* partials, const OpCoef& c, const NonlinTable& nt, cudaStream_t s);
 void launch_energy(const double2* x, double* partials, double* out, const OpCoef& c, const EnergyTable& et,
                    double Bx, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // fused2d.cu: row-streaming fused P^{-1} / A P^{-1} for 2D grids, Chebyshev
 // degree m in 1..fused2d_max_degree(); each returns false when it cannot run.
-// Dot partials use layout [J][3][npart], npart = fused2d_npart(c, m, Ly).
+// Dot partials use layout [J][kDotSlots][npart], npart = fused2d_npart(c, m, Ly).
 // ---------------------------------------------------------------------------
 int fused2d_max_degree(int elem_bytes);
 int fused2d_npart(const OpCoef& c, int m, int Ly, int elem_bytes);  // elem_bytes = sizeof(complex)
@@ -228,7 +237,22 @@ bool launch_fused_pinv_add(int m, int Ly, const OpCoef& c, const ChebStep* w, co
 template <typename T>
 bool launch_fused_pinv_store(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* b, cplx<T>* x,
                              cudaStream_t s);
-// s = r - alpha v; u += alpha p + omega s; r = s - omega t; partials (rhat, r), (r, r) in [J][3][kDotBlocks]
+// Merged BiCGStab iteration (buffers of the previous iteration -> the next):
+// r' = r - alpha v - omega t, p' = r' + beta (p - omega v), u += alpha p + omega (r - alpha v)
+// (the last at owned points), v' = A P^{-1} p'; partial (rhat, v').
+template <typename T>
+bool launch_fused_merged_v(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
+                           const cplx<T>* t, const cplx<T>* p, cplx<T>* u, cplx<T>* r_new, cplx<T>* p_new,
+                           cplx<T>* v_new, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s);
+// t = A P^{-1} s, s = r - alpha v; partials (t, s), (t, t), (s, s), (rhat, s), (rhat, t)
+template <typename T>
+bool launch_fused_merged_t(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
+                           cplx<T>* t_out, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s);
+// the pending u += alpha p + omega (r - alpha v) of amplitudes that stopped in this iteration
+template <typename T>
+void launch_final_update(const cplx<T>* r, const cplx<T>* v, const cplx<T>* p, cplx<T>* u, const KScal* ks,
+                         const OpCoef& c, cudaStream_t s);
+// s = r - alpha v; u += alpha p + omega s; r = s - omega t; partials (rhat, r), (r, r) in [J][kDotSlots][kDotBlocks]
 template <typename T>
 void launch_bicg_update(cplx<T>* r, const cplx<T>* v, const cplx<T>* p, cplx<T>* u, const cplx<T>* t,
                         const cplx<T>* rhat, const KScal* ks, void* partials, const OpCoef& c, cudaStream_t s);
@@ -239,7 +263,7 @@ void launch_bicg_update(cplx<T>* r, const cplx<T>* v, const cplx<T>* p, cplx<T>*
 template <typename T>
 void launch_dots(int npair, const DotPairs<T>& pr, void* partials, const OpCoef& c, const KScal* act,
                  cudaStream_t s);
-// npart: partial-sum slots per (amplitude, pair); layout [J][3][npart].
+// npart: partial-sum slots per (amplitude, pair); layout [J][kDotSlots][npart].
 template <typename T>
 void launch_finalize(int npair, const void* partials, KScal* k, int op, int J, cudaStream_t s,
                      int npart = kDotBlocks);

@@ -20,11 +20,11 @@ constexpr int kFusedRows = 256;  // rows per block segment of the fused 2D pipel
 
 template <typename T>
 struct Work {
-  static constexpr int kBlocks = 10;  // r, rhat, p, v, u, t, z, bb, p', v' (ping-pong p and v)
+  static constexpr int kBlocks = 11;  // r, rhat, p, v, u, t, z, bb, p', v', r' (ping-pong r, p, v)
   static constexpr int kFields = 5;  // f, b2p, R, Da, Db
   cplx<T>* blk[kBlocks] = {};
   cplx<T>* fld[kFields] = {};
-  void* partials = nullptr;  // [J][3][npart] x 16 bytes, npart <= npart_cap
+  void* partials = nullptr;  // [J][kDotSlots][npart] x 16 bytes, npart <= npart_cap
   int npart_cap = 0;
   KScal* ks = nullptr;       // device
   KScal* ks_host = nullptr;  // pinned
@@ -39,7 +39,8 @@ struct Profiler {
   bool on = false;
   int timed = -1;
   cudaStream_t stream = nullptr;
-  std::vector<cudaEvent_t> ev;  // begin/end pairs of the timed kernel
+  std::vector<cudaEvent_t> ev;  // begin/end pairs of the timed kernel(s)
+  std::vector<int> ev_kid;      // kernel id of each pair
   size_t used = 0;
   long long launches[2 * KID_COUNT] = {};
   long long all = 0;
@@ -52,7 +53,7 @@ void prof_launch_begin(int kid, cudaStream_t s) {
   if (!g_prof.on) return;
   g_prof.launches[kid] += 1;
   g_prof.all += 1;
-  if (kid != g_prof.timed || g_prof.failed) return;
+  if ((kid != g_prof.timed && g_prof.timed != -2) || g_prof.failed) return;
   if (g_prof.used + 2 > g_prof.ev.size()) {
     if (g_prof.ev.size() > 2000000) {
       g_prof.failed = true;
@@ -66,11 +67,13 @@ void prof_launch_begin(int kid, cudaStream_t s) {
       }
       g_prof.ev.push_back(e);
     }
+    g_prof.ev_kid.resize(g_prof.ev.size() / 2);
   }
+  g_prof.ev_kid[g_prof.used / 2] = kid;
   cudaEventRecord(g_prof.ev[g_prof.used], s);
 }
 void prof_launch_end(int kid, cudaStream_t s) {
-  if (!g_prof.on || kid != g_prof.timed || g_prof.failed) return;
+  if (!g_prof.on || (kid != g_prof.timed && g_prof.timed != -2) || g_prof.failed) return;
   cudaEventRecord(g_prof.ev[g_prof.used + 1], s);
   g_prof.used += 2;
 }
@@ -88,6 +91,12 @@ struct apfc_ctx {
   EnergyTable et;
   double2* x64 = nullptr;  // state block vector (zeta, eta) per amplitude
   double2* b64 = nullptr;  // right-hand side block (0, rhs)
+  // FP32-refined path: previous step's RHS and final FP64 residual (r = b - A x),
+  // from which the next step's initial residual follows pointwise
+  double2* b64_prev = nullptr;
+  double2* r64_prev = nullptr;
+  bool have_prev = false;
+  double prev_dt = 0.0;
   double* epart = nullptr;
   double* eout = nullptr;
   double* eout_host = nullptr;
@@ -148,7 +157,7 @@ apfc_status alloc_work(apfc_ctx* ctx, Work<T>& w) {
       cap = std::max(cap, fused2d_npart(g, m, kFusedRows, (int)sizeof(cplx<T>)));
   }
   w.npart_cap = cap;
-  CK(cudaMalloc(&w.partials, 16ull * 3 * cap * ctx->J));
+  CK(cudaMalloc(&w.partials, 16ull * kDotSlots * cap * ctx->J));
   CK(cudaMalloc(&w.ks, sizeof(KScal) * ctx->J));
   CK(cudaMallocHost(&w.ks_host, sizeof(KScal) * ctx->J));
   std::memset(w.ks_host, 0, sizeof(KScal) * ctx->J);
@@ -406,6 +415,7 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
     CK(cudaMemsetAsync(p, 0, bb, s));
     CK(cudaMemsetAsync(v, 0, bb, s));
     CK(cudaMemsetAsync(u, 0, bb, s));
+    if (use_fused(ctx, (int)sizeof(cplx<T>))) CK(cudaMemsetAsync(t, 0, bb, s));
     {
       DotPairs<T> d{{r, b, nullptr}, {r, b, nullptr}};
       launch_dots<T>(2, d, w.partials, c, nullptr, s);
@@ -432,6 +442,7 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
     const int npart = fused ? fused2d_npart(c, m, kFusedRows, (int)sizeof(cplx<T>)) : kDotBlocks;
     cplx<T>* pp[2] = {p, w.blk[8]};
     cplx<T>* vv[2] = {v, w.blk[9]};
+    cplx<T>* rr[2] = {r, w.blk[10]};
     int cur = 0;
     long long launched = 0;  // host-side cap: every amplitude stops at max_iter on the device
     while (true) {
@@ -442,16 +453,17 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
       launched += every;
       for (int q = 0; q < every; ++q) {
         if (fused) {
-          // v' = A P^{-1} p' with p' = r + beta (p - omega v); alpha = rho / (rhat, v')
-          launch_fused_v<T>(m, kFusedRows, c, cw.data(), r, pp[cur], vv[cur], pp[1 - cur], vv[1 - cur], rhat, w.ks,
-                            w.partials, s);
-          launch_finalize<T>(1, w.partials, w.ks, OP_ALPHA, ctx->J, s, npart);
-          // t = A P^{-1} s, s = r - alpha v'; omega = (t, s) / (t, t)
-          launch_fused_t<T>(m, kFusedRows, c, cw.data(), r, vv[1 - cur], t, w.ks, w.partials, s);
-          launch_finalize<T>(3, w.partials, w.ks, OP_OMEGA3, ctx->J, s, npart);
-          // u += alpha p' + omega s; r = s - omega t; rho' = (rhat, r)
-          launch_bicg_update<T>(r, vv[1 - cur], pp[1 - cur], u, t, rhat, w.ks, w.partials, c, s);
-          launch_finalize<T>(2, w.partials, w.ks, OP_RHO, ctx->J, s, kDotBlocks);
+          // merged iteration: r' = r - alpha v - omega t, p' = r' + beta (p - omega v),
+          // u += alpha p + omega s (the previous iteration's update), v' = A P^{-1} p'
+          launch_fused_merged_v<T>(m, kFusedRows, c, cw.data(), rr[cur], vv[cur], t, pp[cur], u, rr[1 - cur],
+                                   pp[1 - cur], vv[1 - cur], rhat, w.ks, w.partials, s);
+          launch_finalize<T>(1, w.partials, w.ks, OP_ALPHA, ctx->J, s, npart);  // alpha = rho / (rhat, v')
+          // t = A P^{-1} s, s = r' - alpha v'; omega, rho', beta and ||r''||^2 from five inner products
+          launch_fused_merged_t<T>(m, kFusedRows, c, cw.data(), rr[1 - cur], vv[1 - cur], t, rhat, w.ks, w.partials,
+                                   s);
+          launch_finalize<T>(5, w.partials, w.ks, OP_OMEGA5, ctx->J, s, npart);
+          // amplitudes that stopped now still owe u += alpha p' + omega s
+          launch_final_update<T>(rr[1 - cur], vv[1 - cur], pp[1 - cur], u, w.ks, c, s);
           cur = 1 - cur;
           continue;
         }
@@ -526,6 +538,7 @@ apfc_status status_of(apfc_ctx* ctx, int worst) {
 
 // One step in FP64.
 apfc_status step_fp64(apfc_ctx* ctx) {
+  ctx->have_prev = false;
   apfc_status st = alloc_work<double>(ctx, ctx->w64);
   if (st != APFC_OK) return st;
   launch_rhs(ctx->x64, ctx->b64, ctx->coef, ctx->nt, ctx->stream);
@@ -544,13 +557,44 @@ apfc_status step_refined(apfc_ctx* ctx) {
   apfc_status st = alloc_work<float>(ctx, ctx->w32);
   if (st != APFC_OK) return st;
   cudaStream_t s = ctx->stream;
-  launch_rhs(ctx->x64, ctx->b64, ctx->coef, ctx->nt, s);
+  const size_t blk = sizeof(double2) * 2ull * ctx->J * ctx->pts;
+  const bool flat = ctx->dim == 2;  // the stencil-free initial residual and 2D residual kernel
+  if (flat && ctx->r64_prev == nullptr) {
+    CK(cudaMalloc(&ctx->b64_prev, blk));
+    CK(cudaMalloc(&ctx->r64_prev, blk));
+    CK(cudaMemsetAsync(ctx->b64_prev, 0, blk, s));
+    ctx->have_prev = false;
+  }
   float2* r32 = ctx->w32.blk[7];
+  double* part = reinterpret_cast<double*>(ctx->part64);
+  bool resid_ready = false;
+  if (flat && ctx->have_prev && ctx->prev_dt == ctx->coef_dt) {
+    // b_prev is the RHS the last residual was taken against; the new RHS goes to the other buffer
+    launch_rhs_resid(ctx->x64, ctx->b64_prev, ctx->b64, ctx->r64_prev, r32, part, ctx->coef, ctx->nt, s);
+    std::swap(ctx->b64, ctx->b64_prev);
+    resid_ready = true;
+  } else {
+    launch_rhs(ctx->x64, ctx->b64, ctx->coef, ctx->nt, s);
+  }
+  ctx->have_prev = false;
   int total_it = 0, worst = KS_CONVERGED, sweep = 0;
   const double tol2 = ctx->opts.tol * ctx->opts.tol;
   for (;; ++sweep) {
-    launch_residual_refine(ctx->b64, ctx->x64, r32, reinterpret_cast<double*>(ctx->part64), ctx->coef, s);
-    launch_finalize64(2, ctx->part64, ctx->ks64, OP_NORMS, ctx->J, s);
+    if (resid_ready) {
+      launch_finalize64(2, ctx->part64, ctx->ks64, OP_NORMS, ctx->J, s);  // ||r0||^2 and ||b||^2
+    } else if (flat) {
+      if (sweep == 0) {  // ||b||^2 once per step
+        DotPairs<double> d{{ctx->b64, nullptr, nullptr}, {ctx->b64, nullptr, nullptr}};
+        launch_dots<double>(1, d, ctx->part64, ctx->coef, nullptr, s);
+        launch_finalize64(1, ctx->part64, ctx->ks64, OP_BNORM, ctx->J, s);
+      }
+      launch_residual_refine2d(ctx->b64, ctx->x64, r32, ctx->r64_prev, part, ctx->coef, s);
+      launch_finalize64(1, ctx->part64, ctx->ks64, OP_RNORM, ctx->J, s);
+    } else {
+      launch_residual_refine(ctx->b64, ctx->x64, r32, part, ctx->coef, s);
+      launch_finalize64(2, ctx->part64, ctx->ks64, OP_NORMS, ctx->J, s);
+    }
+    resid_ready = false;
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(ctx->ks64_host, ctx->ks64, sizeof(KScal) * ctx->J, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -566,6 +610,10 @@ apfc_status step_refined(apfc_ctx* ctx) {
     }
     if (done) {
       worst = KS_CONVERGED;
+      // after at least one sweep the last check was a stencil residual that stored
+      // b - A x in r64_prev, which seeds the next step's initial residual
+      ctx->have_prev = flat && sweep > 0;
+      ctx->prev_dt = ctx->coef_dt;
       break;
     }
     if (sweep >= ctx->opts.max_refine) {
@@ -725,7 +773,7 @@ apfc_status apfc_init(apfc_ctx** out, const apfc_lattice* lat, const apfc_params
   if (cudaMallocHost(&ctx->eout_host, sizeof(double)) != cudaSuccess) return cleanup(APFC_ENOMEM);
   if (cudaMalloc(&ctx->ks64, sizeof(KScal) * ctx->J) != cudaSuccess) return cleanup(APFC_ENOMEM);
   if (cudaMallocHost(&ctx->ks64_host, sizeof(KScal) * ctx->J) != cudaSuccess) return cleanup(APFC_ENOMEM);
-  if (cudaMalloc(&ctx->part64, 16ull * 3 * kDotBlocks * ctx->J) != cudaSuccess) return cleanup(APFC_ENOMEM);
+  if (cudaMalloc(&ctx->part64, 16ull * kDotSlots * kDotBlocks * ctx->J) != cudaSuccess) return cleanup(APFC_ENOMEM);
   if (cudaMemsetAsync(ctx->b64, 0, blk, ctx->stream) != cudaSuccess) return cleanup(APFC_ECUDA);
   if (cudaMemsetAsync(ctx->ks64, 0, sizeof(KScal) * ctx->J, ctx->stream) != cudaSuccess) return cleanup(APFC_ECUDA);
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cleanup(APFC_ECUDA);
@@ -739,6 +787,7 @@ apfc_status apfc_set_opts(apfc_ctx* ctx, const apfc_opts* opts) {
   if (!valid_opts(*opts, e)) return fail(ctx, APFC_EINVAL, e);
   ctx->opts = *opts;
   ctx->coef_dt = -1.0;  // tau_mode may have changed
+  ctx->have_prev = false;
   return APFC_OK;
 }
 
@@ -746,6 +795,7 @@ apfc_status apfc_set_amplitudes(apfc_ctx* ctx, const void* eta, int where) {
   if (!ctx || !eta || (where != APFC_HOST && where != APFC_DEVICE)) return APFC_EINVAL;
   ctx->failed = false;
   ctx->err.clear();
+  ctx->have_prev = false;
   apfc_status st = copy_part(ctx, const_cast<void*>(eta), where, 1, true);
   if (st != APFC_OK) return st;
   std::string e;
@@ -810,6 +860,8 @@ void apfc_destroy(apfc_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   cudaFree(ctx->x64);
   cudaFree(ctx->b64);
+  cudaFree(ctx->b64_prev);
+  cudaFree(ctx->r64_prev);
   cudaFree(ctx->epart);
   cudaFree(ctx->eout);
   if (ctx->eout_host) cudaFreeHost(ctx->eout_host);
@@ -836,7 +888,7 @@ const char* apfc_kernel_name(int id) {
 }
 
 apfc_status apfc_profile_start(apfc_ctx* ctx, int timed_id) {
-  if (!ctx || timed_id < -1 || timed_id >= 2 * KID_COUNT) return APFC_EINVAL;
+  if (!ctx || timed_id < -2 || timed_id >= 2 * KID_COUNT) return APFC_EINVAL;
   if (g_prof.on && g_prof.stream != ctx->stream) return fail(ctx, APFC_EINVAL, "measurement already running");
   if (!g_prof.dev) CK(cudaMalloc(&g_prof.dev, sizeof(unsigned long long) * 2 * KID_COUNT));
   CK(cudaMemsetAsync(g_prof.dev, 0, sizeof(unsigned long long) * 2 * KID_COUNT, ctx->stream));
@@ -859,8 +911,9 @@ apfc_status apfc_profile_read(apfc_ctx* ctx, int id, double* ms, long long* laun
   CK(cudaStreamSynchronize(ctx->stream));
   if (g_prof.failed) return fail(ctx, APFC_ENOMEM, "event pool exhausted");
   double total = 0.0;
-  if (id == g_prof.timed) {
+  if (id == g_prof.timed || g_prof.timed == -2) {
     for (size_t i = 0; i + 1 < g_prof.used; i += 2) {
+      if (g_prof.ev_kid[i / 2] != id) continue;
       float t = 0.f;
       CK(cudaEventElapsedTime(&t, g_prof.ev[i], g_prof.ev[i + 1]));
       total += t;

@@ -235,6 +235,95 @@ struct LoadS {
   __device__ cplx<T> form_re(const cplx<T>* raw, int st) const { return csub(raw[0], cmulz(alpha, raw[st])); }
 };
 
+// Merged BiCGStab iteration loader: from the previous iteration's r, v, t, p form
+// r' = r - alpha v - omega t and p' = r' + beta (p - omega v); at owned points also
+// store r', p' and apply the previous iteration's update u += alpha p + omega (r - alpha v).
+template <typename T>
+struct LoadPR {
+  static constexpr int NIN = 10, NRE = 4;
+  const cplx<T>* r;
+  const cplx<T>* v;
+  const cplx<T>* t;
+  const cplx<T>* p;
+  cplx<T>* u;
+  cplx<T>* rn;
+  cplx<T>* pn;
+  long long pts;
+  cplx<T> al, om, be;
+  long long off;
+  __device__ void setup(int j, const KScal* k) {
+    al = to_c<T>(k[j].alpha);
+    om = to_c<T>(k[j].omega);
+    be = to_c<T>(k[j].beta);
+    off = 2LL * j * pts;
+  }
+  // raw order: r1 r2 v1 v2 t1 t2 p1 p2 u1 u2
+  __device__ const cplx<T>* in(int i) const {
+    const cplx<T>* base = i < 2 ? r : (i < 4 ? v : (i < 6 ? t : (i < 8 ? p : u)));
+    return base + off + (i & 1) * pts;
+  }
+  // raw order: r1 v1 t1 p1
+  __device__ const cplx<T>* re(int i) const { return (i == 0 ? r : (i == 1 ? v : (i == 2 ? t : p))) + off; }
+  __device__ __forceinline__ void form(cplx<T> rr, cplx<T> vv, cplx<T> tt, cplx<T> pp, cplx<T>& r2,
+                                       cplx<T>& p2) const {
+    r2 = csub(csub(rr, cmulz(al, vv)), cmulz(om, tt));
+    p2 = cadd(r2, cmulz(be, csub(pp, cmulz(om, vv))));
+  }
+  __device__ void form_in(const cplx<T>* raw, int st, long long pnt, bool own, cplx<T>& b1, cplx<T>& b2) const {
+    cplx<T> r1, r2;
+    form(raw[0], raw[2 * st], raw[4 * st], raw[6 * st], r1, b1);
+    form(raw[st], raw[3 * st], raw[5 * st], raw[7 * st], r2, b2);
+    if (own) {
+      rn[off + pnt] = r1;
+      rn[off + pts + pnt] = r2;
+      pn[off + pnt] = b1;
+      pn[off + pts + pnt] = b2;
+      // u += alpha p + omega (r - alpha v)
+      const cplx<T> s1 = csub(raw[0], cmulz(al, raw[2 * st])), s2 = csub(raw[st], cmulz(al, raw[3 * st]));
+      u[off + pnt] = cadd(raw[8 * st], cadd(cmulz(al, raw[6 * st]), cmulz(om, s1)));
+      u[off + pts + pnt] = cadd(raw[9 * st], cadd(cmulz(al, raw[7 * st]), cmulz(om, s2)));
+    }
+  }
+  __device__ cplx<T> form_re(const cplx<T>* raw, int st) const {
+    cplx<T> r1, p1;
+    form(raw[0], raw[st], raw[2 * st], raw[3 * st], r1, p1);
+    return p1;
+  }
+};
+
+// t = y with s = r - alpha v; (t, s), (t, t), (s, s), (rhat, s), (rhat, t).
+template <typename T>
+struct EpT5 {
+  static constexpr int NDOT = 5, NEP = 6;
+  cplx<T>* t;
+  const cplx<T>* r;
+  const cplx<T>* v;
+  const cplx<T>* rhat;
+  long long pts;
+  long long off;
+  cplx<T> alpha;
+  Acc<T> acc[5];
+  __device__ void setup(int j, const KScal* k) {
+    off = 2LL * j * pts;
+    alpha = to_c<T>(k[j].alpha);
+  }
+  // raw order: r1 r2 v1 v2 rhat1 rhat2
+  __device__ const cplx<T>* ep(int i) const { return (i < 2 ? r : (i < 4 ? v : rhat)) + off + (i & 1) * pts; }
+  __device__ void one(long long q, cplx<T> y, cplx<T> rr, cplx<T> vv, cplx<T> hh) {
+    const cplx<T> s = csub(rr, cmulz(alpha, vv));
+    t[q] = y;
+    acc[0].add_run(y, s);
+    acc[1].add_run(y, y);
+    acc[2].add_run(s, s);
+    acc[3].add_run(hh, s);
+    acc[4].add_run(hh, y);
+  }
+  __device__ void put(const cplx<T>* raw, int st, long long p, cplx<T> y1, cplx<T> y2) {
+    one(off + p, y1, raw[0], raw[2 * st], raw[4 * st]);
+    one(off + pts + p, y2, raw[st], raw[3 * st], raw[5 * st]);
+  }
+};
+
 template <typename T>
 struct EpStore {  // out = y
   static constexpr int NDOT = 0, NEP = 0;
@@ -478,6 +567,37 @@ __global__ void __launch_bounds__(pipe_nt<T>()) k_pipe2d(OpCoef c, ChebAll cw, P
 
   auto ring = [&](int qi) { return sm + SH::off(qi); };
 
+  // Own-column history of every stencil input (rows newest first): FP32 pipelines keep
+  // the y-neighbours in registers and read only the x-neighbours from shared memory.
+  constexpr bool HIST = sizeof(T) == 4;
+  cplx<T> H[HIST ? SH::NRING : 1][3];
+#pragma unroll
+  for (int qi = 0; qi < (HIST ? SH::NRING : 1); ++qi)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) H[qi][k] = mkc<T>((T)0, (T)0);
+  auto push = [&](int qi, cplx<T> v) {
+    if constexpr (HIST) {
+      H[qi][2] = H[qi][1];
+      H[qi][1] = H[qi][0];
+      H[qi][0] = v;
+    }
+  };
+  auto nbh = [&](int qi, int lr) {
+    if constexpr (HIST) {
+      const cplx<T>* rq = ring(qi);
+      const int sc = lr & (SH::depth(qi) - 1);
+      Nbh<T> n;
+      n.c = H[qi][1];
+      n.u = H[qi][2];
+      n.d = H[qi][0];
+      n.l = rq[sc * NT + (t > 0 ? t - 1 : t)];
+      n.r = rq[sc * NT + (t < NT - 1 ? t + 1 : t)];
+      return n;
+    } else {
+      return fetch_d<T>(ring(qi), SH::depth(qi) - 1, lr, t);
+    }
+  };
+
   if constexpr (PF > 0) {
 #pragma unroll
     for (int tf = 0; tf < PF; ++tf) issue(tf);
@@ -495,31 +615,35 @@ __global__ void __launch_bounds__(pipe_nt<T>()) k_pipe2d(OpCoef c, ChebAll cw, P
       st = NT;
     }
     Nbh<T> nb[S + 2];
-    // phase B: compute and write this step's rows, latest stage first
+    const cplx<T> zero = mkc<T>((T)0, (T)0);
+    // compute and write this step's rows, latest stage first
     static_for_rev<S, 1>([&](auto sc) {
       constexpr int s = decltype(sc)::value;
       const int lr = rho - 2 * s;
       const bool valid = valid_at(s, lr);
       if (valid) {
         if constexpr (WITH_A && s == S) {
-          nb[S] = fetch_d<T>(ring(2 * M + 1), 3, lr, t);
-          nb[S + 1] = fetch_d<T>(ring(2 * M + 2), 3, lr, t);
+          nb[S] = nbh(2 * M + 1, lr);
+          nb[S + 1] = nbh(2 * M + 2, lr);
         } else {
-          nb[s] = fetch_d<T>(ring(s - 1), SH::depth(s - 1) - 1, lr, t);
+          nb[s] = nbh(s - 1, lr);
         }
       }
       if constexpr (s == 1) {
         // f = beta2 - kt G beta1
+        cplx<T> f = zero;
         if (valid) {
           const cplx<T> gb = opG<T>(nb[1], q);
-          ring(1)[(lr & 3) * NT + t] = csub(b2dl[1], cscale(q.kt, gb));
+          f = csub(b2dl[1], cscale(q.kt, gb));
+          ring(1)[(lr & 3) * NT + t] = f;
         }
+        push(1, f);
       } else if constexpr (s <= 2 * M + 1) {
         // Chebyshev application k of solve 1 (s <= M+1) or solve 2
         constexpr bool solve1 = s <= M + 1;
         constexpr int k = solve1 ? s - 2 : s - M - 2;
         constexpr bool last = (k == M - 1);
-        cplx<T> X, R, dn;
+        cplx<T> X = zero, R = zero, dn = zero, out1 = zero, out2 = zero;
         if (valid) {
           const Nbh<T>& n = nb[s];
           const cplx<T> Dd = opD<T>(n, q);
@@ -534,9 +658,11 @@ __global__ void __launch_bounds__(pipe_nt<T>()) k_pipe2d(OpCoef c, ChebAll cw, P
             dn = caxpy(c1[k], n.c, cscale(c2[k], R));
           }
           if constexpr (!last) {
+            out1 = dn;
             ring(s)[(lr & 3) * NT + t] = dn;
           } else if constexpr (solve1) {
-            ring(s)[(lr & (SH::DB - 1)) * NT + t] = cadd(X, dn);  // beta2'
+            out1 = cadd(X, dn);  // beta2'
+            ring(s)[(lr & (SH::DB - 1)) * NT + t] = out1;
           } else {
             const cplx<T> chi2 = cadd(X, dn);
             const long long p = ptg(gy_chi);
@@ -552,6 +678,8 @@ __global__ void __launch_bounds__(pipe_nt<T>()) k_pipe2d(OpCoef c, ChebAll cw, P
             const cplx<T> b2p = ring(SH::QB)[(lr & (SH::DB - 1)) * NT + t];
             const cplx<T> chi1 = cadd(b1, cscale(q.inv_mu, csub(b2p, cscale(q.sD, chi2))));
             if constexpr (WITH_A) {
+              out1 = chi1;
+              out2 = chi2;
               ring(s)[(lr & 3) * NT + t] = chi1;
               ring(s + 1)[(lr & 3) * NT + t] = chi2;
             } else {
@@ -564,6 +692,12 @@ __global__ void __launch_bounds__(pipe_nt<T>()) k_pipe2d(OpCoef c, ChebAll cw, P
           XD[s][0] = X;
           RD[s][1] = RD[s][0];
           RD[s][0] = R;
+        }
+        if constexpr (!last || solve1) {
+          push(s, out1);
+        } else if constexpr (WITH_A) {
+          push(s, out1);
+          push(s + 1, out2);
         }
       } else {
         // y = A (chi1, chi2)
@@ -587,7 +721,7 @@ __global__ void __launch_bounds__(pipe_nt<T>()) k_pipe2d(OpCoef c, ChebAll cw, P
     });
     // stage 0: input row rho
     {
-      cplx<T> b1 = mkc<T>((T)0, (T)0), b2 = b1;
+      cplx<T> b1 = zero, b2 = zero;
       if (rho < rows_in) {
         const long long p = ptg(gy_in);
         if constexpr (PF > 0) {
@@ -600,6 +734,7 @@ __global__ void __launch_bounds__(pipe_nt<T>()) k_pipe2d(OpCoef c, ChebAll cw, P
         }
         ring(0)[(rho & 3) * NT + t] = b1;
       }
+      push(0, b1);
       b2dl[1] = b2dl[0];
       b2dl[0] = b2;
     }
@@ -622,7 +757,7 @@ __global__ void __launch_bounds__(pipe_nt<T>()) k_pipe2d(OpCoef c, ChebAll cw, P
     for (int k = 0; k < EP::NDOT; ++k) {
       ep.acc[k].flush();
       block_reduce<T, NT>(ep.acc[k]);
-      if (t == 0) ep.acc[k].store(partials, (long long)(j * 3 + k) * g.npart + blk);
+      if (t == 0) ep.acc[k].store(partials, (long long)(j * kDotSlots + k) * g.npart + blk);
     }
   }
 }
@@ -710,9 +845,9 @@ __global__ void __launch_bounds__(kThreads) k_bicg_update(cplx<T>* __restrict__ 
     a1.add(rn, rn);
   }
   block_reduce<T>(a0);
-  if (threadIdx.x == 0) a0.store(partials, (long long)(j * 3 + 0) * kDotBlocks + blockIdx.x);
+  if (threadIdx.x == 0) a0.store(partials, (long long)(j * kDotSlots + 0) * kDotBlocks + blockIdx.x);
   block_reduce<T>(a1);
-  if (threadIdx.x == 0) a1.store(partials, (long long)(j * 3 + 1) * kDotBlocks + blockIdx.x);
+  if (threadIdx.x == 0) a1.store(partials, (long long)(j * kDotSlots + 1) * kDotBlocks + blockIdx.x);
 }
 
 }  // namespace
@@ -761,6 +896,50 @@ bool launch_fused_pinv_store(int m, int Ly, const OpCoef& c, const ChebStep* w, 
 }
 
 template <typename T>
+bool launch_fused_merged_v(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
+                           const cplx<T>* t, const cplx<T>* p, cplx<T>* u, cplx<T>* r_new, cplx<T>* p_new,
+                           cplx<T>* v_new, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s) {
+  LoadPR<T> ld{r, v, t, p, u, r_new, p_new, c.pts};
+  EpV<T> ep{v_new, rhat, c.pts};
+  // reads r, v, t, p, u, rhat; writes r', p', u, v' (2 fields each)
+  return dispatch<T, true>(m, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV), 20);
+}
+
+template <typename T>
+bool launch_fused_merged_t(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
+                           cplx<T>* t_out, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s) {
+  LoadS<T> ld{r, v, c.pts};
+  EpT5<T> ep{t_out, r, v, rhat, c.pts};
+  // reads r, v, rhat; writes t
+  return dispatch<T, true>(m, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV), 8);
+}
+
+// u += alpha p + omega (r - alpha v) for amplitudes whose solve stopped in this iteration.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_final_update(const cplx<T>* __restrict__ r,
+                                                           const cplx<T>* __restrict__ v,
+                                                           const cplx<T>* __restrict__ p, cplx<T>* __restrict__ u,
+                                                           const KScal* ks, OpCoef c) {
+  const int j = blockIdx.y;
+  if (ks[j].just_done == 0) return;
+  prof_add(c, kid_of<T>(KID_BICG_UPDATE), 10ull * (unsigned long long)c.pts * sizeof(cplx<T>));
+  const cplx<T> al = to_c<T>(ks[j].alpha), om = to_c<T>(ks[j].omega);
+  const long long n = 2 * c.pts, o = 2LL * j * c.pts;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long q = o + i;
+    const cplx<T> s = csub(r[q], cmulz(al, v[q]));
+    u[q] = cadd(u[q], cadd(cmulz(al, p[q]), cmulz(om, s)));
+  }
+}
+
+template <typename T>
+void launch_final_update(const cplx<T>* r, const cplx<T>* v, const cplx<T>* p, cplx<T>* u, const KScal* ks,
+                         const OpCoef& c, cudaStream_t s) {
+  ProfScope ps_(kid_of<T>(KID_BICG_UPDATE), s);
+  k_final_update<T><<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(r, v, p, u, ks, c);
+}
+
+template <typename T>
 void launch_bicg_update(cplx<T>* r, const cplx<T>* v, const cplx<T>* p, cplx<T>* u, const cplx<T>* t,
                         const cplx<T>* rhat, const KScal* ks, void* partials, const OpCoef& c, cudaStream_t s) {
   ProfScope ps_(kid_of<T>(KID_BICG_UPDATE), s);
@@ -768,6 +947,13 @@ void launch_bicg_update(cplx<T>* r, const cplx<T>* v, const cplx<T>* p, cplx<T>*
 }
 
 #define APFC_FUSED_INST(T)                                                                                         \
+  template bool launch_fused_merged_v<T>(int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*, \
+                                         const cplx<T>*, const cplx<T>*, cplx<T>*, cplx<T>*, cplx<T>*, cplx<T>*,   \
+                                         const cplx<T>*, const KScal*, void*, cudaStream_t);                      \
+  template bool launch_fused_merged_t<T>(int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*, \
+                                         cplx<T>*, const cplx<T>*, const KScal*, void*, cudaStream_t);            \
+  template void launch_final_update<T>(const cplx<T>*, const cplx<T>*, const cplx<T>*, cplx<T>*, const KScal*,     \
+                                       const OpCoef&, cudaStream_t);                                              \
   template bool launch_fused_v<T>(int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*,        \
                                   const cplx<T>*, cplx<T>*, cplx<T>*, const cplx<T>*, const KScal*, void*,         \
                                   cudaStream_t);                                                                   \

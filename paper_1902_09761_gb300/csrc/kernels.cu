@@ -399,8 +399,138 @@ __global__ void k_residual_refine(const double2* __restrict__ b, const double2* 
   }
   block_sum<2>(acc);
   if (threadIdx.x == 0) {
-    partials[(j * 3 + 0) * kDotBlocks + blockIdx.x] = make_double2(acc[0], 0.0);
-    partials[(j * 3 + 1) * kDotBlocks + blockIdx.x] = make_double2(acc[1], 0.0);
+    partials[(j * kDotSlots + 0) * kDotBlocks + blockIdx.x] = make_double2(acc[0], 0.0);
+    partials[(j * kDotSlots + 1) * kDotBlocks + blockIdx.x] = make_double2(acc[1], 0.0);
+  }
+}
+
+// FP64 outer residual on 2D grids: r = b - A x with x, b FP64; writes r as FP32
+// (the inner solve's right-hand side) and, if r64 != nullptr, as FP64 (kept as
+// the previous residual of the next step).  32 x 8 point tiles, neighbours by
+// comparison (no division per point).  The partial ||r||^2 per amplitude is
+// accumulated from the FP32-rounded residual (it only decides convergence, where
+// a relative error of 1e-5 in the norm is immaterial); ||b||^2 is not
+// recomputed: b is fixed within a step.
+__global__ void __launch_bounds__(256) k_residual_refine2d(const double2* __restrict__ b,
+                                                           const double2* __restrict__ x, float2* __restrict__ r32,
+                                                           double2* __restrict__ r64, double2* __restrict__ partials,
+                                                           OpCoef c) {
+  const int j = blockIdx.y;
+  prof_add(c, KID_RESID_REFINE,
+           (unsigned long long)c.pts * (4 * sizeof(double2) + 2 * sizeof(float2) + (r64 ? 2 * sizeof(double2) : 0)));
+  const long long o = 2LL * j * c.pts;
+  const double2* z = x + o;
+  const double2* e = z + c.pts;
+  const double kt = c.kt[j], a = c.a[j];
+  const double c0 = c.c0, ihx = c.ih2[0], ihy = c.ih2[1], khx = c.kh[j][0], khy = c.kh[j][1];
+  const int nx = c.nx, ny = c.ny;
+  const int tx_count = (nx + 31) / 32, ntiles = tx_count * ((ny + 7) / 8);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float rr = 0.f;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int ty0 = tile / tx_count;
+    const int xx = (tile - ty0 * tx_count) * 32 + tx, yy = ty0 * 8 + ty;
+    if (xx >= nx || yy >= ny) continue;
+    const long long row = (long long)yy * nx;
+    const long long pc = row + xx;
+    const long long pl = row + (xx == 0 ? nx - 1 : xx - 1), pr = row + (xx + 1 == nx ? 0 : xx + 1);
+    const long long pu = (long long)(yy == 0 ? ny - 1 : yy - 1) * nx + xx;
+    const long long pd = (long long)(yy + 1 == ny ? 0 : yy + 1) * nx + xx;
+    // G_h u: 9 FP64 operations per component
+    auto G = [&](const double2* u) {
+      const double2 C = u[pc], L = u[pl], R = u[pr], U = u[pu], D = u[pd];
+      const double gx = fma(ihx, L.x + R.x, fma(ihy, U.x + D.x, fma(-khx, R.y - L.y, fma(-khy, D.y - U.y, c0 * C.x))));
+      const double gy = fma(ihx, L.y + R.y, fma(ihy, U.y + D.y, fma(khx, R.x - L.x, fma(khy, D.x - U.x, c0 * C.y))));
+      return make_double2(gx, gy);
+    };
+    const double2 gz = G(z), ge = G(e);
+    const double2 zc = z[pc], ec = e[pc];
+    const double2 b1 = b[o + pc], b2 = b[o + c.pts + pc];
+    const double r1x = (b1.x - zc.x) + ge.x, r1y = (b1.y - zc.y) + ge.y;
+    const double r2x = b2.x - fma(kt, gz.x, a * ec.x), r2y = b2.y - fma(kt, gz.y, a * ec.y);
+    const float2 f1 = make_float2((float)r1x, (float)r1y), f2 = make_float2((float)r2x, (float)r2y);
+    r32[o + pc] = f1;
+    r32[o + c.pts + pc] = f2;
+    if (r64 != nullptr) {
+      r64[o + pc] = make_double2(r1x, r1y);
+      r64[o + c.pts + pc] = make_double2(r2x, r2y);
+    }
+    rr = fmaf(f1.x, f1.x, fmaf(f1.y, f1.y, fmaf(f2.x, f2.x, fmaf(f2.y, f2.y, rr))));
+  }
+  double acc[1] = {(double)rr};
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) partials[(j * kDotSlots + 0) * kDotBlocks + blockIdx.x] = make_double2(acc[0], 0.0);
+}
+
+// New right-hand side plus the initial outer residual of the step without a
+// stencil: with the previous step's final residual r_prev = b_prev - A x0,
+// r0 = b - A x0 = b - b_prev + r_prev (exact algebra, pointwise in FP64).
+// Writes b (eta-parts), r0 as FP32, and partials ||r0||^2, ||b||^2.
+__global__ void __launch_bounds__(256) k_rhs_resid(const double2* __restrict__ x, double2* __restrict__ b,
+                                                   const double2* __restrict__ b_prev,
+                                                   const double2* __restrict__ r_prev, float2* __restrict__ r32,
+                                                   double2* __restrict__ partials, OpCoef c, NonlinTable nt) {
+  prof_add(c, KID_RHS, (unsigned long long)c.J * c.pts * (5 * sizeof(double2) + 2 * sizeof(float2)));
+  float accf[2 * kMaxJ];
+#pragma unroll
+  for (int i = 0; i < 2 * kMaxJ; ++i) accf[i] = 0.f;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < c.pts;
+       p += (long long)gridDim.x * blockDim.x) {
+    double2 eta[kMaxJ];
+    double A2 = 0.0;
+    for (int j = 0; j < c.J; ++j) {
+      eta[j] = x[(2LL * j + 1) * c.pts + p];
+      A2 += eta[j].x * eta[j].x + eta[j].y * eta[j].y;
+    }
+    A2 *= 2.0;
+    for (int j = 0; j < c.J; ++j) {
+      double2 N;
+      if (nt.hex) {
+        const int k1 = (j + 1) % 3, k2 = (j + 2) % 3;
+        const double m2 = eta[j].x * eta[j].x + eta[j].y * eta[j].y;
+        const double s = 3.0 * nt.v * (A2 - m2);
+        const double2 pr = cconj(cm(eta[k1], eta[k2]));
+        N = make_double2(s * eta[j].x - 2.0 * nt.t * pr.x, s * eta[j].y - 2.0 * nt.t * pr.y);
+      } else {
+        N = make_double2(0.0, 0.0);
+        for (int q = nt.start[j]; q < nt.start[j + 1]; ++q) {
+          double2 prod = make_double2(nt.coef[q], 0.0);
+          for (int f = 0; f < nt.nf[q]; ++f) {
+            const int code = nt.f[q][f];
+            prod = cm(prod, (code & 1) ? cconj(eta[code >> 1]) : eta[code >> 1]);
+          }
+          N.x += prod.x;
+          N.y += prod.y;
+        }
+      }
+      const double kap = c.kap[j];
+      const long long q1 = 2LL * j * c.pts + p, q2 = q1 + c.pts;
+      const double2 bn = make_double2(eta[j].x * c.inv_dt - kap * N.x, eta[j].y * c.inv_dt - kap * N.y);
+      b[q2] = bn;
+      const double2 bp = b_prev[q2], rp2 = r_prev[q2], rp1 = r_prev[q1];
+      const double r2x = (bn.x - bp.x) + rp2.x, r2y = (bn.y - bp.y) + rp2.y;
+      const float2 f1 = make_float2((float)rp1.x, (float)rp1.y), f2 = make_float2((float)r2x, (float)r2y);
+      r32[q1] = f1;
+      r32[q2] = f2;
+      // norms only decide convergence: accumulated from FP32-rounded values
+      const float2 fb = make_float2((float)bn.x, (float)bn.y);
+      accf[2 * j] = fmaf(f1.x, f1.x, fmaf(f1.y, f1.y, fmaf(f2.x, f2.x, fmaf(f2.y, f2.y, accf[2 * j]))));
+      accf[2 * j + 1] = fmaf(fb.x, fb.x, fmaf(fb.y, fb.y, accf[2 * j + 1]));
+    }
+  }
+  __shared__ double sh[2 * kMaxJ][kThreads / 32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  for (int i = 0; i < 2 * c.J; ++i) {
+    double v = (double)accf[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (l == 0) sh[i][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * c.J) {
+    double v = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) v += sh[threadIdx.x][k];
+    const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
+    partials[(j * kDotSlots + which) * kDotBlocks + blockIdx.x] = make_double2(v, 0.0);
   }
 }
 
@@ -533,6 +663,16 @@ void launch_residual_refine(const double2* b, const double2* x, float2* r32, dou
                             cudaStream_t s) {
   ProfScope ps_(KID_RESID_REFINE, s);
   k_residual_refine<<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(b, x, r32, reinterpret_cast<double2*>(partials), c);
+}
+void launch_residual_refine2d(const double2* b, const double2* x, float2* r32, double2* r64, double* partials,
+                              const OpCoef& c, cudaStream_t s) {
+  ProfScope ps_(KID_RESID_REFINE, s);
+  k_residual_refine2d<<<dim3(kDotBlocks, c.J), 256, 0, s>>>(b, x, r32, r64, reinterpret_cast<double2*>(partials), c);
+}
+void launch_rhs_resid(const double2* x, double2* b, const double2* b_prev, const double2* r_prev, float2* r32,
+                      double* partials, const OpCoef& c, const NonlinTable& nt, cudaStream_t s) {
+  ProfScope ps_(KID_RHS, s);
+  k_rhs_resid<<<kDotBlocks, kThreads, 0, s>>>(x, b, b_prev, r_prev, r32, reinterpret_cast<double2*>(partials), c, nt);
 }
 void launch_energy(const double2* x, double* partials, double* out, const OpCoef& c, const EnergyTable& et, double Bx,
                    cudaStream_t s) {

@@ -40,7 +40,7 @@ __global__ void k_dots(DotPairs<T> pr, void* partials, OpCoef c, const KScal* ac
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
     block_reduce<T>(acc[q]);
-    if (threadIdx.x == 0) acc[q].store(partials, (long long)(j * 3 + q) * kDotBlocks + blockIdx.x);
+    if (threadIdx.x == 0) acc[q].store(partials, (long long)(j * kDotSlots + q) * kDotBlocks + blockIdx.x);
   }
 }
 
@@ -63,10 +63,11 @@ __device__ void scalar_update(KScal& k, int op, const double2* d) {
       k.bnorm2 = d[1].x;
       k.tol2 = k.tolrel2 * (k.bnorm2 > 0.0 ? k.bnorm2 : k.rnorm2);
       k.rho = d[0];
-      k.alpha = make_double2(1.0, 0.0);
-      k.omega = make_double2(1.0, 0.0);
+      k.alpha = make_double2(0.0, 0.0);
+      k.omega = make_double2(0.0, 0.0);
       k.beta = make_double2(0.0, 0.0);
       k.iters = 0;
+      k.just_done = 0;
       if (!isfinite(k.rnorm2) || !isfinite(k.bnorm2)) {
         k.status = KS_NAN;
         k.active = 0;
@@ -147,6 +148,66 @@ __device__ void scalar_update(KScal& k, int op, const double2* d) {
       }
       break;
     }
+    case OP_BNORM: {  // d0 = (b, b)
+      k.bnorm2 = d[0].x;
+      break;
+    }
+    case OP_RNORM: {  // d0 = (r, r); ||b||^2 from an earlier OP_NORMS / OP_BNORM
+      k.rnorm2 = d[0].x;
+      break;
+    }
+    case OP_OMEGA5: {
+      // merged iteration: d0 = (t, s), d1 = (t, t), d2 = (s, s), d3 = (rhat, s), d4 = (rhat, t).
+      // omega = (t, s)/(t, t); by linearity r' = s - omega t has
+      // (rhat, r') = (rhat, s) - omega (rhat, t) and
+      // ||r'||^2 = (s, s) - 2 Re(omega conj(t, s)) + |omega|^2 (t, t).
+      k.just_done = 0;
+      bool fin = true;
+      for (int q = 0; q < 5; ++q) fin = fin && finite2(d[q]);
+      if (!fin) {
+        k.status = KS_NAN;
+        k.active = 0;
+        break;
+      }
+      k.iters += 1;
+      if (d[2].x <= k.tol2) {
+        k.omega = make_double2(0.0, 0.0);  // s already meets tol: r' = s
+        k.rnorm2 = d[2].x;
+        k.status = KS_CONVERGED;
+        k.active = 0;
+        k.just_done = 1;
+        break;
+      }
+      if (d[1].x == 0.0 || cabs2(d[0]) == 0.0) {
+        k.status = KS_BREAKDOWN;
+        k.active = 0;
+        k.just_done = 1;
+        break;
+      }
+      k.omega = make_double2(d[0].x / d[1].x, d[0].y / d[1].x);
+      const double2 oc = cmul2(k.omega, make_double2(d[0].x, -d[0].y));
+      double rn2 = d[2].x - 2.0 * oc.x + cabs2(k.omega) * d[1].x;
+      k.rnorm2 = rn2 > 0.0 ? rn2 : 0.0;
+      const double2 rho_new = make_double2(d[3].x - (k.omega.x * d[4].x - k.omega.y * d[4].y),
+                                           d[3].y - (k.omega.x * d[4].y + k.omega.y * d[4].x));
+      if (k.rnorm2 <= k.tol2) {
+        k.status = KS_CONVERGED;
+        k.active = 0;
+        k.just_done = 1;
+      } else if (k.iters >= k.max_iter) {
+        k.status = KS_NOCONV;
+        k.active = 0;
+        k.just_done = 1;
+      } else if (cabs2(rho_new) == 0.0) {
+        k.status = KS_BREAKDOWN;
+        k.active = 0;
+        k.just_done = 1;
+      } else {
+        k.beta = cmul2(cdiv(rho_new, k.rho), cdiv(k.alpha, k.omega));
+        k.rho = rho_new;
+      }
+      break;
+    }
     case OP_NORMS: {  // d0 = (r, r), d1 = (b, b): record only
       k.rnorm2 = d[0].x;
       k.bnorm2 = d[1].x;
@@ -159,15 +220,17 @@ template <typename T, int NP>
 __global__ void k_finalize(const void* partials, int npart, KScal* ks, int op) {
   const int j = blockIdx.x;
   KScal& k = ks[j];
-  if (op != OP_INIT && op != OP_NORMS && k.active == 0) return;
-  __shared__ double2 res[3];
+  // a pending final update was applied after the previous OP_OMEGA5: clear the flag
+  if (op == OP_ALPHA && threadIdx.x == 0) k.just_done = 0;
+  if (op != OP_INIT && op != OP_NORMS && op != OP_RNORM && op != OP_BNORM && k.active == 0) return;
+  __shared__ double2 res[kDotSlots];
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
     Acc<T> a;
     a.zero();
     for (int b = threadIdx.x; b < npart; b += blockDim.x) {
       Acc<T> t;
-      t.load(partials, (long long)(j * 3 + q) * npart + b);
+      t.load(partials, (long long)(j * kDotSlots + q) * npart + b);
       a.merge(t);
     }
     block_reduce<T>(a);
@@ -197,8 +260,10 @@ void launch_finalize(int npair, const void* partials, KScal* k, int op, int J, c
     k_finalize<T, 1><<<J, kThreads, 0, s>>>(partials, npart, k, op);
   else if (npair == 2)
     k_finalize<T, 2><<<J, kThreads, 0, s>>>(partials, npart, k, op);
-  else
+  else if (npair == 3)
     k_finalize<T, 3><<<J, kThreads, 0, s>>>(partials, npart, k, op);
+  else
+    k_finalize<T, 5><<<J, kThreads, 0, s>>>(partials, npart, k, op);
 }
 
 void launch_finalize64(int npair, const void* partials, KScal* k, int op, int J, cudaStream_t s) {
