@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--timed-kernel", default="fused_apinv_f32")
+    ap.add_argument("--tile", type=int, default=3)
+    ap.add_argument("--rows", type=int, default=0)
     ap.add_argument("--cheb", type=int, default=1, help="Chebyshev applications per diffusion solve")
     ap.add_argument("--tol-inner", type=float, default=1e-4, help="relative tolerance of each FP32 inner solve")
     ap.add_argument("--breakdown-steps", type=int, default=3, help="steps of the per-kernel timing pass (0: off)")
@@ -278,7 +280,8 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     opts = A.apfc_default_opts(
-        precision=A.APFC_FP32_REFINED, tol=TOL, cheb_degree=args.cheb, tol_inner=args.tol_inner
+        precision=A.APFC_FP32_REFINED, tol=TOL, cheb_degree=args.cheb, tol_inner=args.tol_inner, tile=args.tile,
+        tile_rows=args.rows,
     )
     ctx = A.Context(k, A.APFC_LATTICE_HEX2D, prm, (n, n), (H, H), opts, stream=stream.cuda_stream)
     eta_dev = torch.from_numpy(eta0).to(dev)
@@ -348,7 +351,7 @@ def run_ours(args):
         }
 
     # --- plain FP64 path at the same final residual ------------------------------
-    ctx.set_opts(A.apfc_default_opts(precision=A.APFC_FP64, tol=TOL, cheb_degree=args.cheb))
+    ctx.set_opts(A.apfc_default_opts(precision=A.APFC_FP64, tol=TOL, cheb_degree=args.cheb, tile_rows=args.rows))
     ms64, _ = timed_steps(args.fp64_steps)
     st64 = ctx.stats()
     value64 = world * dof * args.fp64_steps / (ms64 * 1e-3)

@@ -101,6 +101,9 @@ typedef struct {
                                 0: one kernel per stencil pass                         */
   double tol;                /* stop at ||b - A x||_2 <= tol ||b||_2 (block norm, per amplitude) */
   double tol_inner;          /* relative tolerance of each FP32 inner solve         */
+  int tile;                  /* fused 2D kernel variant 0..4 (columns per block and
+                                rows of look-ahead), default 3                     */
+  int tile_rows;             /* rows per block of the fused 2D kernels (0 = 128)   */
 } apfc_opts;
 
 typedef struct {
@@ -112,7 +115,8 @@ typedef struct {
 } apfc_stats_t;
 
 /* Fill *o with defaults: FP64, BiCGStab, tol 1e-10, max_iter 500,
- * cheb_degree 3, tau fold, max_refine 10, tol_inner 1e-4, check_every 4, fused 1. */
+ * cheb_degree 1, tau fold, max_refine 10, tol_inner 1e-4, check_every 4, fused 1,
+ * tile 3, tile_rows 0 (128). */
 apfc_status apfc_default_opts(apfc_opts* o);
 
 /* Relaxed-solid amplitude phi of a uniform crystal (eta_j = phi for all j):

@@ -58,6 +58,8 @@ class Opts(C.Structure):
         ("fused", C.c_int),
         ("tol", C.c_double),
         ("tol_inner", C.c_double),
+        ("tile", C.c_int),
+        ("tile_rows", C.c_int),
     ]
 
 

@@ -99,6 +99,7 @@ enum KernelId {
   KID_FUSED_APINV,
   KID_FUSED_PINV,
   KID_BICG_UPDATE,
+  KID_FUSED_APINV_T,
   KID_COUNT
 };
 template <typename T>
@@ -219,34 +220,35 @@ void launch_energy(const double2* x, double* partials, double* out, const OpCoef
 // Dot partials use layout [J][kDotSlots][npart], npart = fused2d_npart(c, m, Ly).
 // ---------------------------------------------------------------------------
 int fused2d_max_degree(int elem_bytes);
-int fused2d_npart(const OpCoef& c, int m, int Ly, int elem_bytes);  // elem_bytes = sizeof(complex)
+int fused2d_npart(const OpCoef& c, int m, int Ly, int elem_bytes, int tile);  // elem_bytes = sizeof(complex)
+int fused2d_tiles();  // number of tile variants
 // p_new = r + beta (p_old - omega v_old); v_new = A P^{-1} p_new; partial (rhat, v_new)
 template <typename T>
-bool launch_fused_v(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* p_old,
+bool launch_fused_v(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* p_old,
                     const cplx<T>* v_old, cplx<T>* p_new, cplx<T>* v_new, const cplx<T>* rhat, const KScal* act,
                     void* partials, cudaStream_t s);
 // t = A P^{-1} (r - alpha v); partials (t, s), (t, t), (s, s)
 template <typename T>
-bool launch_fused_t(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
+bool launch_fused_t(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
                     cplx<T>* t_out, const KScal* act, void* partials, cudaStream_t s);
 // x64 += P^{-1} u
 template <typename T>
-bool launch_fused_pinv_add(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* u, double2* x64,
+bool launch_fused_pinv_add(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* u, double2* x64,
                            cudaStream_t s);
 // x = P^{-1} b
 template <typename T>
-bool launch_fused_pinv_store(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* b, cplx<T>* x,
+bool launch_fused_pinv_store(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* b, cplx<T>* x,
                              cudaStream_t s);
 // Merged BiCGStab iteration (buffers of the previous iteration -> the next):
 // r' = r - alpha v - omega t, p' = r' + beta (p - omega v), u += alpha p + omega (r - alpha v)
 // (the last at owned points), v' = A P^{-1} p'; partial (rhat, v').
 template <typename T>
-bool launch_fused_merged_v(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
+bool launch_fused_merged_v(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
                            const cplx<T>* t, const cplx<T>* p, cplx<T>* u, cplx<T>* r_new, cplx<T>* p_new,
                            cplx<T>* v_new, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s);
 // t = A P^{-1} s, s = r - alpha v; partials (t, s), (t, t), (s, s), (rhat, s), (rhat, t)
 template <typename T>
-bool launch_fused_merged_t(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
+bool launch_fused_merged_t(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
                            cplx<T>* t_out, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s);
 // the pending u += alpha p + omega (r - alpha v) of amplitudes that stopped in this iteration
 template <typename T>

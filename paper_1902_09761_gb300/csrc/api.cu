@@ -16,7 +16,7 @@ using namespace apfc;
 
 namespace {
 
-constexpr int kFusedRows = 256;  // rows per block segment of the fused 2D pipeline
+constexpr int kFusedRows = 128;  // rows per block segment of the fused 2D pipeline
 
 template <typename T>
 struct Work {
@@ -154,7 +154,9 @@ apfc_status alloc_work(apfc_ctx* ctx, Work<T>& w) {
     g.nz = 1;
     g.pts = ctx->pts;
     for (int m = 1; m <= fused2d_max_degree((int)sizeof(cplx<T>)); ++m)
-      cap = std::max(cap, fused2d_npart(g, m, kFusedRows, (int)sizeof(cplx<T>)));
+      for (int tile = 0; tile < fused2d_tiles(); ++tile)
+        for (int rows : {32, 64, 128, 256, 512, 1024, ctx->opts.tile_rows})
+          if (rows > 0) cap = std::max(cap, fused2d_npart(g, m, rows, (int)sizeof(cplx<T>), tile));
   }
   w.npart_cap = cap;
   CK(cudaMalloc(&w.partials, 16ull * kDotSlots * cap * ctx->J));
@@ -368,6 +370,8 @@ void apply_pinv(apfc_ctx* ctx, Work<T>& w, const cplx<T>* beta, cplx<T>* chi, co
   launch_pc_final<T>(beta, CFieldRef<T>{b2p.p, P}, chi, c, act, ctx->stream);
 }
 
+int fused_rows(const apfc_ctx* ctx) { return ctx->opts.tile_rows > 0 ? ctx->opts.tile_rows : kFusedRows; }
+
 bool use_fused(const apfc_ctx* ctx, int elem_bytes) {
   return ctx->dim == 2 && ctx->opts.fused != 0 && ctx->opts.cheb_degree >= 1 &&
          ctx->opts.cheb_degree <= fused2d_max_degree(elem_bytes);
@@ -439,7 +443,8 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
     const int every = std::max(1, ctx->opts.check_every);
     const bool fused = use_fused(ctx, (int)sizeof(cplx<T>));
     const int m = ctx->opts.cheb_degree;
-    const int npart = fused ? fused2d_npart(c, m, kFusedRows, (int)sizeof(cplx<T>)) : kDotBlocks;
+    const int tile = ctx->opts.tile, rows = fused_rows(ctx);
+    const int npart = fused ? fused2d_npart(c, m, rows, (int)sizeof(cplx<T>), tile) : kDotBlocks;
     cplx<T>* pp[2] = {p, w.blk[8]};
     cplx<T>* vv[2] = {v, w.blk[9]};
     cplx<T>* rr[2] = {r, w.blk[10]};
@@ -455,11 +460,11 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
         if (fused) {
           // merged iteration: r' = r - alpha v - omega t, p' = r' + beta (p - omega v),
           // u += alpha p + omega s (the previous iteration's update), v' = A P^{-1} p'
-          launch_fused_merged_v<T>(m, kFusedRows, c, cw.data(), rr[cur], vv[cur], t, pp[cur], u, rr[1 - cur],
+          launch_fused_merged_v<T>(m, rows, tile, c, cw.data(), rr[cur], vv[cur], t, pp[cur], u, rr[1 - cur],
                                    pp[1 - cur], vv[1 - cur], rhat, w.ks, w.partials, s);
           launch_finalize<T>(1, w.partials, w.ks, OP_ALPHA, ctx->J, s, npart);  // alpha = rho / (rhat, v')
           // t = A P^{-1} s, s = r' - alpha v'; omega, rho', beta and ||r''||^2 from five inner products
-          launch_fused_merged_t<T>(m, kFusedRows, c, cw.data(), rr[1 - cur], vv[1 - cur], t, rhat, w.ks, w.partials,
+          launch_fused_merged_t<T>(m, rows, tile, c, cw.data(), rr[1 - cur], vv[1 - cur], t, rhat, w.ks, w.partials,
                                    s);
           launch_finalize<T>(5, w.partials, w.ks, OP_OMEGA5, ctx->J, s, npart);
           // amplitudes that stopped now still owe u += alpha p' + omega s
@@ -502,7 +507,7 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
       if (!run) break;
     }
     // x += P^{-1} u
-    if (!fused || !launch_fused_pinv_add<T>(m, kFusedRows, c, cw.data(), u, x64, s)) {
+    if (!fused || !launch_fused_pinv_add<T>(m, rows, tile, c, cw.data(), u, x64, s)) {
       apply_pinv<T>(ctx, w, u, z, nullptr, cw);
       launch_add_to<T>(z, x64, c, s);
     }
@@ -645,6 +650,8 @@ bool valid_opts(const apfc_opts& o, std::string& e) {
   else if (o.max_refine < 0) e = "max_refine";
   else if (o.check_every < 1) e = "check_every";
   else if (o.fused != 0 && o.fused != 1) e = "fused";
+  else if (o.tile < 0 || o.tile >= fused2d_tiles()) e = "tile";
+  else if (o.tile_rows < 0 || o.tile_rows > 65536) e = "tile_rows";
   else if (!(o.tol > 0.0) || !(o.tol_inner > 0.0) || !(o.tol_inner < 1.0)) e = "tol";
   else return true;
   e = "invalid option: " + e;
@@ -691,13 +698,15 @@ apfc_status apfc_default_opts(apfc_opts* o) {
   o->precision = APFC_FP64;
   o->krylov = APFC_BICGSTAB;
   o->max_iter = 500;
-  o->cheb_degree = 3;
+  o->cheb_degree = 1;
   o->tau_mode = APFC_TAU_FOLD;
   o->max_refine = 10;
   o->check_every = 4;
   o->tol = 1e-10;
   o->tol_inner = 1e-4;
   o->fused = 1;
+  o->tile = 3;
+  o->tile_rows = 0;
   return APFC_OK;
 }
 
@@ -876,7 +885,7 @@ void apfc_destroy(apfc_ctx* ctx) {
 static const char* kKernelNames[KID_COUNT] = {
     "apply_A", "residual", "pc_rhs", "cheb_zero", "cheb_first", "cheb_sweep", "pc_final", "p_update", "s_update",
     "r_update", "add_to", "dots", "finalize", "rhs", "zeta", "residual_refine", "energy", "fused_apinv",
-    "fused_pinv", "bicg_update"};
+    "fused_pinv", "bicg_update", "fused_apinv_t"};
 
 int apfc_kernel_count(void) { return 2 * KID_COUNT; }
 
@@ -972,7 +981,8 @@ apfc_status apfc_apply_preconditioner(apfc_ctx* ctx, double dt, const void* b, v
   }
   const auto cw = cheb_weights(ctx);
   if (!use_fused(ctx, (int)sizeof(double2)) ||
-      !launch_fused_pinv_store<double>(ctx->opts.cheb_degree, kFusedRows, ctx->coef, cw.data(), in, outb,
+      !launch_fused_pinv_store<double>(ctx->opts.cheb_degree, fused_rows(ctx), ctx->opts.tile, ctx->coef, cw.data(), in,
+                                       outb,
                                        ctx->stream))
     apply_pinv<double>(ctx, ctx->w64, in, outb, nullptr, cw);
   CK(cudaGetLastError());

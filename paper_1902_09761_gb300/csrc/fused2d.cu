@@ -32,11 +32,6 @@ namespace apfc {
 
 namespace {
 
-// Columns per block: FP32 pipelines use 128 (three blocks fit per SM), FP64 256.
-template <typename T>
-__host__ __device__ constexpr int pipe_nt() {
-  return sizeof(T) == 4 ? 128 : 256;
-}
 
 // Complex helpers.  FP32 complex values use the packed f32x2 instructions of
 // sm_100-class GPUs (one instruction for both components).
@@ -438,7 +433,7 @@ __host__ __device__ constexpr int pow2_at_least() {
   return p;
 }
 
-template <typename T, int M, bool WITH_A, int PF, class LD, class EP>
+template <typename T, int M, bool WITH_A, int PF, int NT_, class LD, class EP>
 struct PipeShape {
   static constexpr int S = 2 * M + 1 + (WITH_A ? 1 : 0);  // stencil stages = halo radius
   static constexpr int NRING = 2 * M + 1 + (WITH_A ? 2 : 0);
@@ -448,7 +443,7 @@ struct PipeShape {
   static constexpr int SEP = S;           // stage calling the epilogue
   static constexpr int NRAW = LD::NIN + LD::NRE + EP::NEP;
   static constexpr int NSLOT = PF > 0 ? PF + 1 : 0;
-  static constexpr int NT = pipe_nt<T>();
+  static constexpr int NT = NT_;
   static constexpr size_t ring_elems = (size_t)((NRING - 1) * 4 + DB) * NT;
   static constexpr size_t smem = sizeof(cplx<T>) * (ring_elems + (size_t)NSLOT * NRAW * NT);
   // element offset of ring q
@@ -456,9 +451,8 @@ struct PipeShape {
   __host__ __device__ static constexpr int depth(int qi) { return qi == QB ? DB : 4; }
 };
 
-template <typename T>
+template <typename T, int NT>
 __device__ __forceinline__ Nbh<T> fetch_d(const cplx<T>* ring, int mask, int row, int t) {
-  constexpr int NT = pipe_nt<T>();
   const int sc = row & mask, su = (row - 1) & mask, sd = (row + 1) & mask;
   const int tl = t > 0 ? t - 1 : t, tr = t < NT - 1 ? t + 1 : t;
   Nbh<T> n;
@@ -472,11 +466,10 @@ __device__ __forceinline__ Nbh<T> fetch_d(const cplx<T>* ring, int mask, int row
 
 __device__ __forceinline__ int wrap_inc(int y, int n) { return y + 1 == n ? 0 : y + 1; }
 
-template <typename T, int M, bool WITH_A, int PF, class LD, class EP>
-__global__ void __launch_bounds__(pipe_nt<T>()) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g, LD ld, EP ep,
-                                                         const KScal* act, void* partials, int kid,
-                                                         unsigned long long bytes_per_amp) {
-  using SH = PipeShape<T, M, WITH_A, PF, LD, EP>;
+template <typename T, int M, bool WITH_A, int PF, int NT_, class LD, class EP>
+__global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g, LD ld, EP ep, const KScal* act,
+                                                void* partials, int kid, unsigned long long bytes_per_amp) {
+  using SH = PipeShape<T, M, WITH_A, PF, NT_, LD, EP>;
   constexpr int NT = SH::NT;
   constexpr int S = SH::S;
   constexpr int NRAW = SH::NRAW;
@@ -594,7 +587,7 @@ __global__ void __launch_bounds__(pipe_nt<T>()) k_pipe2d(OpCoef c, ChebAll cw, P
       n.r = rq[sc * NT + (t < NT - 1 ? t + 1 : t)];
       return n;
     } else {
-      return fetch_d<T>(ring(qi), SH::depth(qi) - 1, lr, t);
+      return fetch_d<T, NT>(ring(qi), SH::depth(qi) - 1, lr, t);
     }
   };
 
@@ -775,22 +768,13 @@ PipeGeom geom(const OpCoef& c, int S, int Ly, int NT) {
   return g;
 }
 
-// Look-ahead rows: FP32 fields prefetch 2 rows; FP64 pipelines (limited by
-// FP64 arithmetic, and by shared memory for their 16-byte rings) fetch on use.
-template <typename T>
-constexpr int prefetch_rows() {
-  return sizeof(T) == 4 ? 2 : 0;
-}
-
-template <typename T, int M, bool WITH_A, class LD, class EP>
+template <typename T, int M, bool WITH_A, int PF, int NT, class LD, class EP>
 void launch_pipe(const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const KScal* act, void* partials,
                  cudaStream_t s, int kid, int fields) {
-  constexpr int PF = prefetch_rows<T>();
-  using SH = PipeShape<T, M, WITH_A, PF, LD, EP>;
-  constexpr int NT = SH::NT;
+  using SH = PipeShape<T, M, WITH_A, PF, NT, LD, EP>;
   const PipeGeom g = geom(c, SH::S, Ly, NT);
   constexpr size_t sm = SH::smem;
-  auto kern = k_pipe2d<T, M, WITH_A, PF, LD, EP>;
+  auto kern = k_pipe2d<T, M, WITH_A, PF, NT, LD, EP>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -807,15 +791,47 @@ void launch_pipe(const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const
   kern<<<dim3(g.nstrips, g.nsegs, c.J), NT, sm, s>>>(c, ca, g, ld, ep, act, partials, kid, bytes);
 }
 
+// Tile variants of the FP32 pipeline with one Chebyshev application (the default
+// degree): NT columns per block and PF rows of asynchronous look-ahead.  Other
+// degrees and FP64 (arithmetic-bound, fetched on use) use one configuration each.
+//   tile 0: NT 128, PF 2   1: NT 128, PF 1   2: NT 256, PF 1   3: NT 256, PF 2   4: NT 128, PF 3
+// Measured on the 4096^2 hexagonal workload, tile 3 with 128-row segments is fastest.
+constexpr int kTiles = 5;
+int tile_nt(int elem_bytes, int m, int tile) {
+  if (elem_bytes == 16) return 256;
+  if (m != 1) return 128;
+  return (tile == 2 || tile == 3) ? 256 : 128;
+}
+
+// fields: algorithmic whole-field transfers per amplitude (counted in units of one
+// complex field of precision T) reported to the measurement counters.
 template <typename T, bool WITH_A, class LD, class EP>
-bool dispatch(int m, const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const KScal* act, void* partials,
-              cudaStream_t s, int kid, int fields) {
-  switch (m) {
-    case 1: launch_pipe<T, 1, WITH_A>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
-    case 2: launch_pipe<T, 2, WITH_A>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
-    case 3: launch_pipe<T, 3, WITH_A>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
-    case 4: launch_pipe<T, 4, WITH_A>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
-    default: return false;
+bool dispatch(int m, int tile, const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const KScal* act,
+              void* partials, cudaStream_t s, int kid, int fields) {
+  if constexpr (sizeof(T) == 8) {
+    switch (m) {
+      case 1: launch_pipe<T, 1, WITH_A, 0, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+      case 2: launch_pipe<T, 2, WITH_A, 0, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+      case 3: launch_pipe<T, 3, WITH_A, 0, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+      case 4: launch_pipe<T, 4, WITH_A, 0, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+      default: return false;
+    }
+  } else {
+    if (m == 1) {
+      switch (tile) {
+        case 1: launch_pipe<T, 1, WITH_A, 1, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+        case 2: launch_pipe<T, 1, WITH_A, 1, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+        case 3: launch_pipe<T, 1, WITH_A, 2, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+        case 4: launch_pipe<T, 1, WITH_A, 3, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+        default: launch_pipe<T, 1, WITH_A, 2, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+      }
+    }
+    switch (m) {
+      case 2: launch_pipe<T, 2, WITH_A, 2, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+      case 3: launch_pipe<T, 3, WITH_A, 2, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+      case 4: launch_pipe<T, 4, WITH_A, 2, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+      default: return false;
+    }
   }
 }
 
@@ -854,64 +870,66 @@ __global__ void __launch_bounds__(kThreads) k_bicg_update(cplx<T>* __restrict__ 
 
 int fused2d_max_degree(int elem_bytes) { return elem_bytes == 8 ? 4 : 4; }
 
-int fused2d_npart(const OpCoef& c, int m, int Ly, int elem_bytes) {
-  return geom(c, 2 * m + 2, Ly, elem_bytes == 8 ? pipe_nt<float>() : pipe_nt<double>()).npart;
+int fused2d_npart(const OpCoef& c, int m, int Ly, int elem_bytes, int tile) {
+  return geom(c, 2 * m + 2, Ly, tile_nt(elem_bytes, m, tile)).npart;
 }
 
+int fused2d_tiles() { return kTiles; }
+
 template <typename T>
-bool launch_fused_v(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* p_old,
+bool launch_fused_v(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* p_old,
                     const cplx<T>* v_old, cplx<T>* p_new, cplx<T>* v_new, const cplx<T>* rhat, const KScal* act,
                     void* partials, cudaStream_t s) {
   LoadP<T> ld{r, p_old, v_old, p_new, c.pts};
   EpV<T> ep{v_new, rhat, c.pts};
   // reads r, p_old, v_old, rhat (2 fields each); writes p_new, v_new
-  return dispatch<T, true>(m, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV), 12);
+  return dispatch<T, true>(m, tile, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV), 12);
 }
 
 template <typename T>
-bool launch_fused_t(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
+bool launch_fused_t(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
                     cplx<T>* t_out, const KScal* act, void* partials, cudaStream_t s) {
   LoadS<T> ld{r, v, c.pts};
   EpT<T> ep{t_out, r, v, c.pts};
   // reads r, v; writes t
-  return dispatch<T, true>(m, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV), 6);
+  return dispatch<T, true>(m, tile, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV), 6);
 }
 
 template <typename T>
-bool launch_fused_pinv_add(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* u, double2* x64,
+bool launch_fused_pinv_add(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* u, double2* x64,
                            cudaStream_t s) {
   LoadPlain<T> ld{u, c.pts};
   EpAddX<T> ep{x64, c.pts};
   // reads u (2 fields); reads and writes the FP64 block x (2 FP64 fields each way)
   const int f = 2 + 4 * (int)(sizeof(double2) / sizeof(cplx<T>));
-  return dispatch<T, false>(m, c, w, Ly, ld, ep, nullptr, nullptr, s, kid_of<T>(KID_FUSED_PINV), f);
+  return dispatch<T, false>(m, tile, c, w, Ly, ld, ep, nullptr, nullptr, s, kid_of<T>(KID_FUSED_PINV), f);
 }
 
 template <typename T>
-bool launch_fused_pinv_store(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* b, cplx<T>* x,
+bool launch_fused_pinv_store(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* b, cplx<T>* x,
                              cudaStream_t s) {
   LoadPlain<T> ld{b, c.pts};
   EpStore<T> ep{x, c.pts};
-  return dispatch<T, false>(m, c, w, Ly, ld, ep, nullptr, nullptr, s, kid_of<T>(KID_FUSED_PINV), 4);
+  return dispatch<T, false>(m, tile, c, w, Ly, ld, ep, nullptr, nullptr, s, kid_of<T>(KID_FUSED_PINV), 4);
 }
 
 template <typename T>
-bool launch_fused_merged_v(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
+bool launch_fused_merged_v(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
                            const cplx<T>* t, const cplx<T>* p, cplx<T>* u, cplx<T>* r_new, cplx<T>* p_new,
                            cplx<T>* v_new, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s) {
   LoadPR<T> ld{r, v, t, p, u, r_new, p_new, c.pts};
   EpV<T> ep{v_new, rhat, c.pts};
   // reads r, v, t, p, u, rhat; writes r', p', u, v' (2 fields each)
-  return dispatch<T, true>(m, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV), 20);
+  return dispatch<T, true>(m, tile, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV), 20);
 }
 
 template <typename T>
-bool launch_fused_merged_t(int m, int Ly, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
+bool launch_fused_merged_t(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
                            cplx<T>* t_out, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s) {
   LoadS<T> ld{r, v, c.pts};
   EpT5<T> ep{t_out, r, v, rhat, c.pts};
   // reads r, v, rhat; writes t
-  return dispatch<T, true>(m, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV), 8);
+  return dispatch<T, true>(m, tile, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV_T), 8);
 }
 
 // u += alpha p + omega (r - alpha v) for amplitudes whose solve stopped in this iteration.
@@ -947,21 +965,21 @@ void launch_bicg_update(cplx<T>* r, const cplx<T>* v, const cplx<T>* p, cplx<T>*
 }
 
 #define APFC_FUSED_INST(T)                                                                                         \
-  template bool launch_fused_merged_v<T>(int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*, \
+  template bool launch_fused_merged_v<T>(int, int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*, \
                                          const cplx<T>*, const cplx<T>*, cplx<T>*, cplx<T>*, cplx<T>*, cplx<T>*,   \
                                          const cplx<T>*, const KScal*, void*, cudaStream_t);                      \
-  template bool launch_fused_merged_t<T>(int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*, \
+  template bool launch_fused_merged_t<T>(int, int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*, \
                                          cplx<T>*, const cplx<T>*, const KScal*, void*, cudaStream_t);            \
   template void launch_final_update<T>(const cplx<T>*, const cplx<T>*, const cplx<T>*, cplx<T>*, const KScal*,     \
                                        const OpCoef&, cudaStream_t);                                              \
-  template bool launch_fused_v<T>(int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*,        \
+  template bool launch_fused_v<T>(int, int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*,        \
                                   const cplx<T>*, cplx<T>*, cplx<T>*, const cplx<T>*, const KScal*, void*,         \
                                   cudaStream_t);                                                                   \
-  template bool launch_fused_t<T>(int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*,        \
+  template bool launch_fused_t<T>(int, int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*,        \
                                   cplx<T>*, const KScal*, void*, cudaStream_t);                                    \
-  template bool launch_fused_pinv_add<T>(int, int, const OpCoef&, const ChebStep*, const cplx<T>*, double2*,       \
+  template bool launch_fused_pinv_add<T>(int, int, int, const OpCoef&, const ChebStep*, const cplx<T>*, double2*,       \
                                          cudaStream_t);                                                            \
-  template bool launch_fused_pinv_store<T>(int, int, const OpCoef&, const ChebStep*, const cplx<T>*, cplx<T>*,     \
+  template bool launch_fused_pinv_store<T>(int, int, int, const OpCoef&, const ChebStep*, const cplx<T>*, cplx<T>*,     \
                                            cudaStream_t);                                                          \
   template void launch_bicg_update<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, cplx<T>*, const cplx<T>*,          \
                                       const cplx<T>*, const KScal*, void*, const OpCoef&, cudaStream_t);

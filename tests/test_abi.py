@@ -40,7 +40,7 @@ def test_exports_every_declared_symbol(lib):
 def test_default_opts(lib):
     o = A.apfc_default_opts()
     assert o.precision == A.APFC_FP64 and o.krylov == A.APFC_BICGSTAB
-    assert o.tol == 1e-10 and o.max_iter == 500 and o.cheb_degree == 3
+    assert o.tol == 1e-10 and o.max_iter == 500 and o.cheb_degree == 1 and o.tile == 3
     assert o.tau_mode == A.APFC_TAU_FOLD and 0 < o.tol_inner < 1 and o.check_every >= 1
 
 

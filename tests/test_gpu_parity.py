@@ -225,3 +225,15 @@ def test_full_size_voronoi_4096_one_step(prec):
     print(f"4096^2 precision {prec}: rel L2 per amplitude {errs}, stats {ctx.stats()}")
     assert max(errs) < 2e-9
     assert ctx.stats()["resid_last"] <= 1e-10
+
+
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("rows", [32, 128])
+def test_tile_variants_parity(tile, rows):
+    # Every FP32 variant of the fused pipeline (strip width, look-ahead depth, rows per
+    # segment) gives the same converged step: 530 columns span 3-5 strips, 300 rows 3-10 segments.
+    eta0 = inputs.random_amplitudes(3, (300, 530), seed=8, scale=0.1)
+    _trajectory_parity(
+        "hex", eta0, (300, 530), (1.2, 0.8), 2, dt=0.5, tol=1e-13, precision=A.APFC_FP32_REFINED, cheb_degree=1,
+        tile=tile, tile_rows=rows,
+    )
