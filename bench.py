@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=4096, help="grid points per side")
+    ap.add_argument("--size", type=int, default=4096, help="grid points per side")
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--timed-kernel", default="fused_apinv_f32")
@@ -226,7 +226,7 @@ def run_reference(args):
     world, rank, local = init_dist(args)
     if rank != 0:
         return
-    n_sample = min(args.n, 2048)
+    n_sample = min(args.size, 2048)
     rate, secs = oracle_rate(n_sample, args.steps, args.warmup)
     sample = (
         f"oracle FP64 step (numpy, exact FFT Schur solve) on a {n_sample}x{n_sample} sample of the workload, "
@@ -246,7 +246,7 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": workload_config(args.n, f"timed on a {n_sample}^2 sample"),
+        "config": workload_config(args.size, f"timed on a {n_sample}^2 sample"),
         "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -269,7 +269,7 @@ def run_ours(args):
     from paper_1902_09761_gb300 import inputs
 
     A.load()
-    n = args.n
+    n = args.size
     J = 3
     k = inputs.hex_vectors()
     lat = A.make_lattice(k, A.APFC_LATTICE_HEX2D)
