@@ -94,20 +94,52 @@ __device__ __forceinline__ cplx<T> cmul(double2 s, cplx<T> v) {
 
 __device__ __forceinline__ bool skip(const KScal* act, int j) { return act != nullptr && act[j].active == 0; }
 
-#define APFC_POINT_INDEX                                                  \
-  const int j = blockIdx.y;                                               \
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; \
-  if (p >= c.pts) return;
+// Per-pass kernels run on a 3D grid: 32 x 8 points per block in (x, y), blockIdx.z
+// = z + nz * j (plane z of amplitude j).  Periodic neighbours by comparison.
+__device__ __forceinline__ int amp_of(const OpCoef& c) { return (int)(blockIdx.z / (unsigned)c.nz); }
+
+__device__ __forceinline__ Nb neighbours3(int x, int y, int z, long long p, const OpCoef& c) {
+  Nb n;
+  n.c = p;
+  const long long nx = c.nx, plane = (long long)c.nx * c.ny;
+  n.xp = (x + 1 == c.nx) ? p - x : p + 1;
+  n.xm = (x == 0) ? p + nx - 1 : p - 1;
+  n.yp = (y + 1 == c.ny) ? p - (long long)y * nx : p + nx;
+  n.ym = (y == 0) ? p + (long long)(c.ny - 1) * nx : p - nx;
+  if (c.dim == 3) {
+    n.zp = (z + 1 == c.nz) ? p - (long long)z * plane : p + plane;
+    n.zm = (z == 0) ? p + (long long)(c.nz - 1) * plane : p - plane;
+  } else {
+    n.zp = n.zm = p;
+  }
+  return n;
+}
+
+// algorithmic bytes, counted once per amplitude (block (0, 0, plane 0) of amplitude j)
+__device__ __forceinline__ void prof_add3(const OpCoef& c, int kid, unsigned long long bytes) {
+  if (c.prof != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 &&
+      blockIdx.z % (unsigned)c.nz == 0)
+    atomicAdd(c.prof + kid, bytes);
+}
+
+#define APFC_POINT_INDEX                                                               \
+  const int j = amp_of(c);                                                             \
+  const int zz_ = (int)(blockIdx.z - (unsigned)j * (unsigned)c.nz);                    \
+  const int xx_ = blockIdx.x * 32 + (threadIdx.x & 31), yy_ = blockIdx.y * 8 + (threadIdx.x >> 5); \
+  if (xx_ >= c.nx || yy_ >= c.ny) return;                                              \
+  const long long p = ((long long)zz_ * c.ny + yy_) * c.nx + xx_;
+
+#define APFC_NEIGHBOURS neighbours3(xx_, yy_, zz_, p, c)
 
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void k_apply_A(const cplx<T>* __restrict__ x, cplx<T>* __restrict__ y, OpCoef c, const KScal* act) {
-  if (skip(act, blockIdx.y)) return;
-  prof_add(c, kid_of<T>(KID_APPLY_A), 4ull * (unsigned long long)c.pts * sizeof(cplx<T>));
+  if (skip(act, amp_of(c))) return;
+  prof_add3(c, kid_of<T>(KID_APPLY_A), 4ull * (unsigned long long)c.pts * sizeof(cplx<T>));
   APFC_POINT_INDEX
   const cplx<T>* z = x + 2LL * j * c.pts;
   const cplx<T>* e = z + c.pts;
-  const Nb n = neighbours(p, c);
+  const Nb n = APFC_NEIGHBOURS;
   const cplx<T> gz = opG<T>(z, n, c, j), ge = opG<T>(e, n, c, j);
   const cplx<T> zc = z[p], ec = e[p];
   cplx<T>* y1 = y + 2LL * j * c.pts;
@@ -119,12 +151,12 @@ __global__ void k_apply_A(const cplx<T>* __restrict__ x, cplx<T>* __restrict__ y
 template <typename T>
 __global__ void k_residual(const cplx<T>* __restrict__ b, const cplx<T>* __restrict__ x, cplx<T>* __restrict__ r,
                            cplx<T>* __restrict__ rhat, OpCoef c) {
-  prof_add(c, kid_of<T>(KID_RESIDUAL), 8ull * (unsigned long long)c.pts * sizeof(cplx<T>));
+  prof_add3(c, kid_of<T>(KID_RESIDUAL), 8ull * (unsigned long long)c.pts * sizeof(cplx<T>));
   APFC_POINT_INDEX
   const long long o = 2LL * j * c.pts;
   const cplx<T>* z = x + o;
   const cplx<T>* e = z + c.pts;
-  const Nb n = neighbours(p, c);
+  const Nb n = APFC_NEIGHBOURS;
   const cplx<T> gz = opG<T>(z, n, c, j), ge = opG<T>(e, n, c, j);
   const cplx<T> zc = z[p], ec = e[p];
   const cplx<T> b1 = b[o + p], b2 = b[o + c.pts + p];
@@ -140,12 +172,12 @@ __global__ void k_residual(const cplx<T>* __restrict__ b, const cplx<T>* __restr
 // Step 2 right-hand side of P^{-1}: f = beta2 - kt G_h beta1 (beta1' = beta1 since M = I).
 template <typename T>
 __global__ void k_pc_rhs(const cplx<T>* __restrict__ beta, FieldRef<T> f, OpCoef c, const KScal* act) {
-  if (skip(act, blockIdx.y)) return;
-  prof_add(c, kid_of<T>(KID_PC_RHS), 3ull * (unsigned long long)c.pts * sizeof(cplx<T>));
+  if (skip(act, amp_of(c))) return;
+  prof_add3(c, kid_of<T>(KID_PC_RHS), 3ull * (unsigned long long)c.pts * sizeof(cplx<T>));
   APFC_POINT_INDEX
   const cplx<T>* b1 = beta + 2LL * j * c.pts;
   const cplx<T> b2 = b1[c.pts + p];
-  const Nb n = neighbours(p, c);
+  const Nb n = APFC_NEIGHBOURS;
   const cplx<T> g = opG<T>(b1, n, c, j);
   const T kt = (T)c.kt[j];
   f.at(j)[p] = mkc<T>(b2.x - kt * g.x, b2.y - kt * g.y);
@@ -154,8 +186,8 @@ __global__ void k_pc_rhs(const cplx<T>* __restrict__ beta, FieldRef<T> f, OpCoef
 // Chebyshev with zero applications of D: X = f / theta.
 template <typename T>
 __global__ void k_cheb_zero(CFieldRef<T> f, FieldRef<T> X, OpCoef c, const KScal* act) {
-  if (skip(act, blockIdx.y)) return;
-  prof_add(c, kid_of<T>(KID_CHEB_ZERO), 2ull * (unsigned long long)c.pts * sizeof(cplx<T>));
+  if (skip(act, amp_of(c))) return;
+  prof_add3(c, kid_of<T>(KID_CHEB_ZERO), 2ull * (unsigned long long)c.pts * sizeof(cplx<T>));
   APFC_POINT_INDEX
   const T it = (T)c.inv_theta[j];
   const cplx<T> v = f.at(j)[p];
@@ -167,12 +199,12 @@ __global__ void k_cheb_zero(CFieldRef<T> f, FieldRef<T> X, OpCoef c, const KScal
 template <typename T>
 __global__ void k_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, ChebStep w, int last,
                              OpCoef c, const KScal* act) {
-  if (skip(act, blockIdx.y)) return;
-  prof_add(c, kid_of<T>(KID_CHEB_FIRST), (last ? 2ull : 4ull) * (unsigned long long)c.pts * sizeof(cplx<T>));
+  if (skip(act, amp_of(c))) return;
+  prof_add3(c, kid_of<T>(KID_CHEB_FIRST), (last ? 2ull : 4ull) * (unsigned long long)c.pts * sizeof(cplx<T>));
   APFC_POINT_INDEX
   const cplx<T>* fj = f.at(j);
 
-  const Nb n = neighbours(p, c);
+  const Nb n = APFC_NEIGHBOURS;
   const T it = (T)c.inv_theta[j];
   const cplx<T> Df = opD<T>(fj, n, c, j);
   const cplx<T> fc = fj[p];
@@ -193,11 +225,11 @@ __global__ void k_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, Field
 template <typename T>
 __global__ void k_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, ChebStep w, int last,
                              OpCoef c, const KScal* act) {
-  if (skip(act, blockIdx.y)) return;
-  prof_add(c, kid_of<T>(KID_CHEB_SWEEP), (last ? 4ull : 6ull) * (unsigned long long)c.pts * sizeof(cplx<T>));
+  if (skip(act, amp_of(c))) return;
+  prof_add3(c, kid_of<T>(KID_CHEB_SWEEP), (last ? 4ull : 6ull) * (unsigned long long)c.pts * sizeof(cplx<T>));
   APFC_POINT_INDEX
   const cplx<T>* dj = Dd.at(j);
-  const Nb n = neighbours(p, c);
+  const Nb n = APFC_NEIGHBOURS;
   const cplx<T> DD = opD<T>(dj, n, c, j);
   const cplx<T> d = dj[p];
   const cplx<T> x = X.at(j)[p];
@@ -219,8 +251,8 @@ __global__ void k_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, Fiel
 template <typename T>
 __global__ void k_pc_final(const cplx<T>* __restrict__ beta, CFieldRef<T> b2p, cplx<T>* __restrict__ chi, OpCoef c,
                            const KScal* act) {
-  if (skip(act, blockIdx.y)) return;
-  prof_add(c, kid_of<T>(KID_PC_FINAL), 4ull * (unsigned long long)c.pts * sizeof(cplx<T>));
+  if (skip(act, amp_of(c))) return;
+  prof_add3(c, kid_of<T>(KID_PC_FINAL), 4ull * (unsigned long long)c.pts * sizeof(cplx<T>));
   APFC_POINT_INDEX
   const long long o = 2LL * j * c.pts;
   const cplx<T> b1 = beta[o + p];
@@ -343,10 +375,10 @@ __global__ void k_rhs(const double2* __restrict__ x, double2* __restrict__ b, Op
 
 // zeta-part of the state = G_h (eta-part)
 __global__ void k_zeta(double2* __restrict__ x, OpCoef c) {
-  prof_add(c, KID_ZETA, 2ull * (unsigned long long)c.pts * sizeof(double2));
+  prof_add3(c, KID_ZETA, 2ull * (unsigned long long)c.pts * sizeof(double2));
   APFC_POINT_INDEX
   const double2* e = x + (2LL * j + 1) * c.pts;
-  const Nb n = neighbours(p, c);
+  const Nb n = APFC_NEIGHBOURS;
   x[2LL * j * c.pts + p] = opG<double>(e, n, c, j);
 }
 
@@ -581,6 +613,10 @@ __global__ void k_sum_partials(const double* __restrict__ partials, int n, doubl
   if (threadIdx.x == 0) out[0] = acc[0];
 }
 
+inline dim3 grid_pts3(const OpCoef& c) {
+  return dim3((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8), (unsigned)(c.nz * c.J));
+}
+
 inline dim3 grid_pts(const OpCoef& c, long long n) {
   return dim3((unsigned)((n + kThreads - 1) / kThreads), (unsigned)c.J);
 }
@@ -593,40 +629,40 @@ inline dim3 grid_pts(const OpCoef& c, long long n) {
 template <typename T>
 void launch_apply_A(const cplx<T>* x, cplx<T>* y, const OpCoef& c, const KScal* act, cudaStream_t s) {
   ProfScope ps_(kid_of<T>(KID_APPLY_A), s);
-  k_apply_A<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(x, y, c, act);
+  k_apply_A<T><<<grid_pts3(c), kThreads, 0, s>>>(x, y, c, act);
 }
 template <typename T>
 void launch_residual(const cplx<T>* b, const cplx<T>* x, cplx<T>* r, cplx<T>* rhat, const OpCoef& c, cudaStream_t s) {
   ProfScope ps_(kid_of<T>(KID_RESIDUAL), s);
-  k_residual<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(b, x, r, rhat, c);
+  k_residual<T><<<grid_pts3(c), kThreads, 0, s>>>(b, x, r, rhat, c);
 }
 template <typename T>
 void launch_pc_rhs(const cplx<T>* beta, FieldRef<T> f, const OpCoef& c, const KScal* act, cudaStream_t s) {
   ProfScope ps_(kid_of<T>(KID_PC_RHS), s);
-  k_pc_rhs<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(beta, f, c, act);
+  k_pc_rhs<T><<<grid_pts3(c), kThreads, 0, s>>>(beta, f, c, act);
 }
 template <typename T>
 void launch_cheb_zero(CFieldRef<T> f, FieldRef<T> X, const OpCoef& c, const KScal* act, cudaStream_t s) {
   ProfScope ps_(kid_of<T>(KID_CHEB_ZERO), s);
-  k_cheb_zero<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(f, X, c, act);
+  k_cheb_zero<T><<<grid_pts3(c), kThreads, 0, s>>>(f, X, c, act);
 }
 template <typename T>
 void launch_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
                        const OpCoef& c, const KScal* act, cudaStream_t s) {
   ProfScope ps_(kid_of<T>(KID_CHEB_FIRST), s);
-  k_cheb_first<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(f, X, R, Dn, w, last, c, act);
+  k_cheb_first<T><<<grid_pts3(c), kThreads, 0, s>>>(f, X, R, Dn, w, last, c, act);
 }
 template <typename T>
 void launch_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
                        const OpCoef& c, const KScal* act, cudaStream_t s) {
   ProfScope ps_(kid_of<T>(KID_CHEB_SWEEP), s);
-  k_cheb_sweep<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(Dd, X, R, Dn, w, last, c, act);
+  k_cheb_sweep<T><<<grid_pts3(c), kThreads, 0, s>>>(Dd, X, R, Dn, w, last, c, act);
 }
 template <typename T>
 void launch_pc_final(const cplx<T>* beta, CFieldRef<T> b2p, cplx<T>* chi, const OpCoef& c, const KScal* act,
                      cudaStream_t s) {
   ProfScope ps_(kid_of<T>(KID_PC_FINAL), s);
-  k_pc_final<T><<<grid_pts(c, c.pts), kThreads, 0, s>>>(beta, b2p, chi, c, act);
+  k_pc_final<T><<<grid_pts3(c), kThreads, 0, s>>>(beta, b2p, chi, c, act);
 }
 template <typename T>
 void launch_p_update(const cplx<T>* r, cplx<T>* p, const cplx<T>* v, const OpCoef& c, const KScal* k, cudaStream_t s) {
@@ -657,7 +693,7 @@ void launch_rhs(const double2* x, double2* b, const OpCoef& c, const NonlinTable
 }
 void launch_zeta(double2* x, const OpCoef& c, cudaStream_t s) {
   ProfScope ps_(KID_ZETA, s);
-  k_zeta<<<grid_pts(c, c.pts), kThreads, 0, s>>>(x, c);
+  k_zeta<<<grid_pts3(c), kThreads, 0, s>>>(x, c);
 }
 void launch_residual_refine(const double2* b, const double2* x, float2* r32, double* partials, const OpCoef& c,
                             cudaStream_t s) {
