@@ -563,7 +563,7 @@ apfc_status step_refined(apfc_ctx* ctx) {
   if (st != APFC_OK) return st;
   cudaStream_t s = ctx->stream;
   const size_t blk = sizeof(double2) * 2ull * ctx->J * ctx->pts;
-  const bool flat = ctx->dim == 2;  // the stencil-free initial residual and 2D residual kernel
+  const bool flat = true;  // stencil-free initial residual and tiled FP64 residual (2D and 3D)
   if (flat && ctx->r64_prev == nullptr) {
     CK(cudaMalloc(&ctx->b64_prev, blk));
     CK(cudaMalloc(&ctx->r64_prev, blk));
@@ -593,8 +593,15 @@ apfc_status step_refined(apfc_ctx* ctx) {
         launch_dots<double>(1, d, ctx->part64, ctx->coef, nullptr, s);
         launch_finalize64(1, ctx->part64, ctx->ks64, OP_BNORM, ctx->J, s);
       }
-      launch_residual_refine2d(ctx->b64, ctx->x64, r32, ctx->r64_prev, part, ctx->coef, s);
-      launch_finalize64(1, ctx->part64, ctx->ks64, OP_RNORM, ctx->J, s);
+      if (ctx->dim == 2) {
+        launch_residual_refine2d(ctx->b64, ctx->x64, r32, ctx->r64_prev, part, ctx->coef, s);
+        launch_finalize64(1, ctx->part64, ctx->ks64, OP_RNORM, ctx->J, s);
+      } else {
+        launch_residual_refine3d(ctx->b64, ctx->x64, r32, ctx->r64_prev, ctx->coef, s);
+        DotPairs<float> d{{r32, nullptr, nullptr}, {r32, nullptr, nullptr}};
+        launch_dots<float>(1, d, ctx->w32.partials, ctx->coef, nullptr, s);
+        launch_finalize<float>(1, ctx->w32.partials, ctx->ks64, OP_RNORM, ctx->J, s);
+      }
     } else {
       launch_residual_refine(ctx->b64, ctx->x64, r32, part, ctx->coef, s);
       launch_finalize64(2, ctx->part64, ctx->ks64, OP_NORMS, ctx->J, s);

@@ -613,6 +613,293 @@ __global__ void k_sum_partials(const double* __restrict__ partials, int n, doubl
   if (threadIdx.x == 0) out[0] = acc[0];
 }
 
+// ---------------------------------------------------------------------------
+// 3D grids: z-streaming stencil passes.  A block owns a 32 x 8 tile of (x, y)
+// and streams through a chunk of kZChunk planes; the current plane of every
+// stencil input sits in shared memory with a one-point halo (double-buffered
+// with the next plane), the own-column z-neighbours in registers.  Each input
+// value is read from HBM about once (the tile halo comes from L2).
+// ---------------------------------------------------------------------------
+constexpr int kZChunk = 64;
+constexpr int kZBuf = 6, kZAhead = 4;  // plane buffers and planes fetched ahead
+constexpr int kTX = 32, kTY = 8, kHX = kTX + 2, kHY = kTY + 2;
+
+template <typename T>
+struct N7 {
+  cplx<T> c, xm, xp, ym, yp, zm, zp;
+};
+
+template <typename T>
+__device__ __forceinline__ cplx<T> lap7(const N7<T>& n, const OpCoef& c) {
+  const T c0 = (T)c.c0, ix = (T)c.ih2[0], iy = (T)c.ih2[1], iz = (T)c.ih2[2];
+  return mkc<T>(c0 * n.c.x + ix * (n.xm.x + n.xp.x) + iy * (n.ym.x + n.yp.x) + iz * (n.zm.x + n.zp.x),
+                c0 * n.c.y + ix * (n.xm.y + n.xp.y) + iy * (n.ym.y + n.yp.y) + iz * (n.zm.y + n.zp.y));
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> G7(const N7<T>& n, const OpCoef& c, int j) {
+  const cplx<T> L = lap7(n, c);
+  const T kx = (T)c.kh[j][0], ky = (T)c.kh[j][1], kz = (T)c.kh[j][2];
+  const T ar = kx * (n.xp.x - n.xm.x) + ky * (n.yp.x - n.ym.x) + kz * (n.zp.x - n.zm.x);
+  const T ai = kx * (n.xp.y - n.xm.y) + ky * (n.yp.y - n.ym.y) + kz * (n.zp.y - n.zm.y);
+  return mkc<T>(L.x - ai, L.y + ar);
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> D7(const N7<T>& n, const OpCoef& c, int j) {
+  const cplx<T> L = lap7(n, c);
+  const T sD = (T)c.sD[j], mu = (T)c.mu[j];
+  return mkc<T>(sD * n.c.x - mu * L.x, sD * n.c.y - mu * L.y);
+}
+
+__device__ __forceinline__ int wrapi(int v, int n) {
+  v %= n;
+  return v < 0 ? v + n : v;
+}
+
+// OP: NS stencil inputs src(k, j) (plane-major [nz][ny][nx] per amplitude) and
+// apply(j, p, nbh[NS]) doing the pointwise work and the stores.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(cplx<T>* dst, const cplx<T>* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if constexpr (sizeof(cplx<T>) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src));
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
+
+template <typename T, class OP>
+__global__ void __launch_bounds__(256) k_stream3d(OpCoef c, OP op, const KScal* act) {
+  constexpr int NS = OP::NS;
+  // plane buffers: z (stencil), z+1 (its z+ neighbour), z+2 .. z+kZAhead (in flight)
+  __shared__ cplx<T> tile[NS][kZBuf][kHY][kHX];
+  const int nchunk = (c.nz + kZChunk - 1) / kZChunk;
+  const int j = (int)(blockIdx.z / (unsigned)nchunk);
+  if (act != nullptr && act[j].active == 0) return;
+  const int chunk = (int)(blockIdx.z - (unsigned)j * nchunk);
+  if (c.prof != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && chunk == 0 && threadIdx.x == 0)
+    atomicAdd(c.prof + op.kid, op.bytes);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+  const int x = x0 + tx, y = y0 + ty;
+  const bool inside = x < c.nx && y < c.ny;
+  const long long plane = (long long)c.nx * c.ny;
+  const int z0 = chunk * kZChunk, z1 = min(c.nz, z0 + kZChunk);
+  const cplx<T>* src[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) src[k] = op.src(k, j);
+  // each thread copies the same (at most two) halo-tile elements of every plane
+  long long qoff[2];
+  int hoff[2];
+  int ne = 0;
+  for (int e = threadIdx.x; e < kHX * kHY; e += 256, ++ne) {
+    const int hy = e / kHX, hx = e - hy * kHX;
+    qoff[ne] = (long long)wrapi(y0 - 1 + hy, c.ny) * c.nx + wrapi(x0 - 1 + hx, c.nx);
+    hoff[ne] = hy * kHX + hx;
+  }
+  auto issue_tile = [&](int buf, int z) {
+    const long long zo = (long long)wrapi(z, c.nz) * plane;
+    for (int i = 0; i < ne; ++i)
+#pragma unroll
+      for (int k = 0; k < NS; ++k) cp_async_elem<T>(&tile[k][buf][0][0] + hoff[i], src[k] + zo + qoff[i]);
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+  const long long pxy = (long long)(inside ? y : 0) * c.nx + (inside ? x : 0);
+  cplx<T> zm[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) zm[k] = src[k][(long long)wrapi(z0 - 1, c.nz) * plane + pxy];
+#pragma unroll
+  for (int a = 0; a < kZAhead; ++a) issue_tile(a, z0 + a);
+  int cb = 0;
+  for (int z = z0; z < z1; ++z) {
+    const int nb = cb + 1 == kZBuf ? 0 : cb + 1;
+    int fb = cb + kZAhead;
+    if (fb >= kZBuf) fb -= kZBuf;
+    issue_tile(fb, z + kZAhead);  // into a buffer no plane in use occupies
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kZAhead - 1));  // planes z and z+1 have landed
+    __syncthreads();
+    if (inside) {
+      N7<T> n[NS];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        n[k].c = tile[k][cb][ty + 1][tx + 1];
+        n[k].xm = tile[k][cb][ty + 1][tx];
+        n[k].xp = tile[k][cb][ty + 1][tx + 2];
+        n[k].ym = tile[k][cb][ty][tx + 1];
+        n[k].yp = tile[k][cb][ty + 2][tx + 1];
+        n[k].zm = zm[k];
+        n[k].zp = tile[k][nb][ty + 1][tx + 1];
+        zm[k] = n[k].c;
+      }
+      op.apply(j, (long long)z * plane + pxy, n, c);
+    }
+    __syncthreads();  // buffer cb is refilled two planes later
+    cb = nb;
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+// y = A x (both parts of x are stencil inputs)
+template <typename T>
+struct OpA3 {
+  static constexpr int NS = 2;
+  const cplx<T>* x;
+  cplx<T>* y;
+  long long pts;
+  int kid;
+  unsigned long long bytes;
+  __device__ const cplx<T>* src(int k, int j) const { return x + (2LL * j + k) * pts; }
+  __device__ void apply(int j, long long p, const N7<T> (&n)[2], const OpCoef& c) const {
+    const cplx<T> gz = G7(n[0], c, j), ge = G7(n[1], c, j);
+    const T kt = (T)c.kt[j], a = (T)c.a[j];
+    cplx<T>* y1 = y + 2LL * j * pts;
+    y1[p] = mkc<T>(n[0].c.x - ge.x, n[0].c.y - ge.y);
+    y1[pts + p] = mkc<T>(kt * gz.x + a * n[1].c.x, kt * gz.y + a * n[1].c.y);
+  }
+};
+
+// r = b - A x, rhat = r
+template <typename T>
+struct OpRes3 {
+  static constexpr int NS = 2;
+  const cplx<T>* x;
+  const cplx<T>* b;
+  cplx<T>* r;
+  cplx<T>* rhat;
+  long long pts;
+  int kid;
+  unsigned long long bytes;
+  __device__ const cplx<T>* src(int k, int j) const { return x + (2LL * j + k) * pts; }
+  __device__ void apply(int j, long long p, const N7<T> (&n)[2], const OpCoef& c) const {
+    const cplx<T> gz = G7(n[0], c, j), ge = G7(n[1], c, j);
+    const T kt = (T)c.kt[j], a = (T)c.a[j];
+    const long long o = 2LL * j * pts;
+    const cplx<T> b1 = b[o + p], b2 = b[o + pts + p];
+    const cplx<T> r1 = mkc<T>(b1.x - (n[0].c.x - ge.x), b1.y - (n[0].c.y - ge.y));
+    const cplx<T> r2 = mkc<T>(b2.x - (kt * gz.x + a * n[1].c.x), b2.y - (kt * gz.y + a * n[1].c.y));
+    r[o + p] = r1;
+    r[o + pts + p] = r2;
+    rhat[o + p] = r1;
+    rhat[o + pts + p] = r2;
+  }
+};
+
+// f = beta2 - kt G beta1
+template <typename T>
+struct OpPcRhs3 {
+  static constexpr int NS = 1;
+  const cplx<T>* beta;
+  FieldRef<T> f;
+  long long pts;
+  int kid;
+  unsigned long long bytes;
+  __device__ const cplx<T>* src(int, int j) const { return beta + 2LL * j * pts; }
+  __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c) const {
+    const cplx<T> g = G7(n[0], c, j);
+    const cplx<T> b2 = beta[2LL * j * pts + pts + p];
+    const T kt = (T)c.kt[j];
+    f.at(j)[p] = mkc<T>(b2.x - kt * g.x, b2.y - kt * g.y);
+  }
+};
+
+// first Chebyshev application (see k_cheb_first)
+template <typename T>
+struct OpChebFirst3 {
+  static constexpr int NS = 1;
+  CFieldRef<T> f;
+  FieldRef<T> X, R, Dn;
+  ChebStep w;
+  int last;
+  int kid;
+  unsigned long long bytes;
+  __device__ const cplx<T>* src(int, int j) const { return f.at(j); }
+  __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c) const {
+    const T it = (T)c.inv_theta[j];
+    const cplx<T> Df = D7(n[0], c, j);
+    const cplx<T> d0 = mkc<T>(it * n[0].c.x, it * n[0].c.y);
+    const cplx<T> r1 = mkc<T>(n[0].c.x - it * Df.x, n[0].c.y - it * Df.y);
+    const T c1 = (T)w.c1[j], c2 = (T)w.c2[j];
+    const cplx<T> d1 = mkc<T>(c1 * d0.x + c2 * r1.x, c1 * d0.y + c2 * r1.y);
+    if (last) {
+      X.at(j)[p] = mkc<T>(d0.x + d1.x, d0.y + d1.y);
+    } else {
+      X.at(j)[p] = d0;
+      R.at(j)[p] = r1;
+      Dn.at(j)[p] = d1;
+    }
+  }
+};
+
+// later Chebyshev application (see k_cheb_sweep)
+template <typename T>
+struct OpChebSweep3 {
+  static constexpr int NS = 1;
+  CFieldRef<T> Dd;
+  FieldRef<T> X, R, Dn;
+  ChebStep w;
+  int last;
+  int kid;
+  unsigned long long bytes;
+  __device__ const cplx<T>* src(int, int j) const { return Dd.at(j); }
+  __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c) const {
+    const cplx<T> DD = D7(n[0], c, j);
+    const cplx<T> d = n[0].c;
+    const cplx<T> x = X.at(j)[p], r = R.at(j)[p];
+    const cplx<T> xn = mkc<T>(x.x + d.x, x.y + d.y);
+    const cplx<T> rn = mkc<T>(r.x - DD.x, r.y - DD.y);
+    const T c1 = (T)w.c1[j], c2 = (T)w.c2[j];
+    const cplx<T> dn = mkc<T>(c1 * d.x + c2 * rn.x, c1 * d.y + c2 * rn.y);
+    if (last) {
+      X.at(j)[p] = mkc<T>(xn.x + dn.x, xn.y + dn.y);
+    } else {
+      X.at(j)[p] = xn;
+      R.at(j)[p] = rn;
+      Dn.at(j)[p] = dn;
+    }
+  }
+};
+
+// zeta-part of the state = G_h (eta-part), FP64
+struct OpZeta3 {
+  static constexpr int NS = 1;
+  double2* x;
+  long long pts;
+  int kid;
+  unsigned long long bytes;
+  __device__ const double2* src(int, int j) const { return x + (2LL * j + 1) * pts; }
+  __device__ void apply(int j, long long p, const N7<double> (&n)[1], const OpCoef& c) const {
+    x[2LL * j * pts + p] = G7(n[0], c, j);
+  }
+};
+
+// FP64 outer residual on 3D grids: r = b - A x (x, b FP64), written as FP32 and FP64.
+struct OpResRefine3 {
+  static constexpr int NS = 2;
+  const double2* x;
+  const double2* b;
+  float2* r32;
+  double2* r64;
+  long long pts;
+  int kid;
+  unsigned long long bytes;
+  __device__ const double2* src(int k, int j) const { return x + (2LL * j + k) * pts; }
+  __device__ void apply(int j, long long p, const N7<double> (&n)[2], const OpCoef& c) const {
+    const double2 gz = G7(n[0], c, j), ge = G7(n[1], c, j);
+    const double kt = c.kt[j], a = c.a[j];
+    const long long o = 2LL * j * pts;
+    const double2 b1 = b[o + p], b2 = b[o + pts + p];
+    const double r1x = (b1.x - n[0].c.x) + ge.x, r1y = (b1.y - n[0].c.y) + ge.y;
+    const double r2x = b2.x - fma(kt, gz.x, a * n[1].c.x), r2y = b2.y - fma(kt, gz.y, a * n[1].c.y);
+    r32[o + p] = make_float2((float)r1x, (float)r1y);
+    r32[o + pts + p] = make_float2((float)r2x, (float)r2y);
+    r64[o + p] = make_double2(r1x, r1y);
+    r64[o + pts + p] = make_double2(r2x, r2y);
+  }
+};
+
+inline dim3 grid_stream3d(const OpCoef& c) {
+  return dim3((unsigned)((c.nx + kTX - 1) / kTX), (unsigned)((c.ny + kTY - 1) / kTY),
+              (unsigned)(c.J * ((c.nz + kZChunk - 1) / kZChunk)));
+}
+
 inline dim3 grid_pts3(const OpCoef& c) {
   return dim3((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8), (unsigned)(c.nz * c.J));
 }
@@ -628,16 +915,34 @@ inline dim3 grid_pts(const OpCoef& c, long long n) {
 // ---------------------------------------------------------------------------
 template <typename T>
 void launch_apply_A(const cplx<T>* x, cplx<T>* y, const OpCoef& c, const KScal* act, cudaStream_t s) {
+  if (c.dim == 3) {
+    ProfScope ps3_(kid_of<T>(KID_APPLY_A), s);
+    OpA3<T> op{x, y, c.pts, kid_of<T>(KID_APPLY_A), 4ull * (unsigned long long)c.pts * sizeof(cplx<T>)};
+    k_stream3d<T, OpA3<T>><<<grid_stream3d(c), 256, 0, s>>>(c, op, act);
+    return;
+  }
   ProfScope ps_(kid_of<T>(KID_APPLY_A), s);
   k_apply_A<T><<<grid_pts3(c), kThreads, 0, s>>>(x, y, c, act);
 }
 template <typename T>
 void launch_residual(const cplx<T>* b, const cplx<T>* x, cplx<T>* r, cplx<T>* rhat, const OpCoef& c, cudaStream_t s) {
+  if (c.dim == 3) {
+    ProfScope ps3_(kid_of<T>(KID_RESIDUAL), s);
+    OpRes3<T> op{x, b, r, rhat, c.pts, kid_of<T>(KID_RESIDUAL), 8ull * (unsigned long long)c.pts * sizeof(cplx<T>)};
+    k_stream3d<T, OpRes3<T>><<<grid_stream3d(c), 256, 0, s>>>(c, op, nullptr);
+    return;
+  }
   ProfScope ps_(kid_of<T>(KID_RESIDUAL), s);
   k_residual<T><<<grid_pts3(c), kThreads, 0, s>>>(b, x, r, rhat, c);
 }
 template <typename T>
 void launch_pc_rhs(const cplx<T>* beta, FieldRef<T> f, const OpCoef& c, const KScal* act, cudaStream_t s) {
+  if (c.dim == 3) {
+    ProfScope ps3_(kid_of<T>(KID_PC_RHS), s);
+    OpPcRhs3<T> op{beta, f, c.pts, kid_of<T>(KID_PC_RHS), 3ull * (unsigned long long)c.pts * sizeof(cplx<T>)};
+    k_stream3d<T, OpPcRhs3<T>><<<grid_stream3d(c), 256, 0, s>>>(c, op, act);
+    return;
+  }
   ProfScope ps_(kid_of<T>(KID_PC_RHS), s);
   k_pc_rhs<T><<<grid_pts3(c), kThreads, 0, s>>>(beta, f, c, act);
 }
@@ -649,12 +954,24 @@ void launch_cheb_zero(CFieldRef<T> f, FieldRef<T> X, const OpCoef& c, const KSca
 template <typename T>
 void launch_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
                        const OpCoef& c, const KScal* act, cudaStream_t s) {
+  if (c.dim == 3) {
+    ProfScope ps3_(kid_of<T>(KID_CHEB_FIRST), s);
+    OpChebFirst3<T> op{f, X, R, Dn, w, last, kid_of<T>(KID_CHEB_FIRST), (last ? 2ull : 4ull) * (unsigned long long)c.pts * sizeof(cplx<T>)};
+    k_stream3d<T, OpChebFirst3<T>><<<grid_stream3d(c), 256, 0, s>>>(c, op, act);
+    return;
+  }
   ProfScope ps_(kid_of<T>(KID_CHEB_FIRST), s);
   k_cheb_first<T><<<grid_pts3(c), kThreads, 0, s>>>(f, X, R, Dn, w, last, c, act);
 }
 template <typename T>
 void launch_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
                        const OpCoef& c, const KScal* act, cudaStream_t s) {
+  if (c.dim == 3) {
+    ProfScope ps3_(kid_of<T>(KID_CHEB_SWEEP), s);
+    OpChebSweep3<T> op{Dd, X, R, Dn, w, last, kid_of<T>(KID_CHEB_SWEEP), (last ? 4ull : 6ull) * (unsigned long long)c.pts * sizeof(cplx<T>)};
+    k_stream3d<T, OpChebSweep3<T>><<<grid_stream3d(c), 256, 0, s>>>(c, op, act);
+    return;
+  }
   ProfScope ps_(kid_of<T>(KID_CHEB_SWEEP), s);
   k_cheb_sweep<T><<<grid_pts3(c), kThreads, 0, s>>>(Dd, X, R, Dn, w, last, c, act);
 }
@@ -692,6 +1009,12 @@ void launch_rhs(const double2* x, double2* b, const OpCoef& c, const NonlinTable
   k_rhs<<<(unsigned)((c.pts + kThreads - 1) / kThreads), kThreads, 0, s>>>(x, b, c, nt);
 }
 void launch_zeta(double2* x, const OpCoef& c, cudaStream_t s) {
+  if (c.dim == 3) {
+    ProfScope ps3_(KID_ZETA, s);
+    OpZeta3 op{x, c.pts, KID_ZETA, 2ull * (unsigned long long)c.pts * sizeof(double2)};
+    k_stream3d<double, OpZeta3><<<grid_stream3d(c), 256, 0, s>>>(c, op, nullptr);
+    return;
+  }
   ProfScope ps_(KID_ZETA, s);
   k_zeta<<<grid_pts3(c), kThreads, 0, s>>>(x, c);
 }
@@ -704,6 +1027,13 @@ void launch_residual_refine2d(const double2* b, const double2* x, float2* r32, d
                               const OpCoef& c, cudaStream_t s) {
   ProfScope ps_(KID_RESID_REFINE, s);
   k_residual_refine2d<<<dim3(kDotBlocks, c.J), 256, 0, s>>>(b, x, r32, r64, reinterpret_cast<double2*>(partials), c);
+}
+void launch_residual_refine3d(const double2* b, const double2* x, float2* r32, double2* r64, const OpCoef& c,
+                              cudaStream_t s) {
+  ProfScope ps_(KID_RESID_REFINE, s);
+  OpResRefine3 op{x, b, r32, r64, c.pts, KID_RESID_REFINE,
+                  (unsigned long long)c.pts * (6 * sizeof(double2) + 2 * sizeof(float2))};
+  k_stream3d<double, OpResRefine3><<<grid_stream3d(c), 256, 0, s>>>(c, op, nullptr);
 }
 void launch_rhs_resid(const double2* x, double2* b, const double2* b_prev, const double2* r_prev, float2* r32,
                       double* partials, const OpCoef& c, const NonlinTable& nt, cudaStream_t s) {

@@ -237,3 +237,18 @@ def test_tile_variants_parity(tile, rows):
         "hex", eta0, (300, 530), (1.2, 0.8), 2, dt=0.5, tol=1e-13, precision=A.APFC_FP32_REFINED, cheb_degree=1,
         tile=tile, tile_rows=rows,
     )
+
+
+@pytest.mark.parametrize("prec", [A.APFC_FP64, A.APFC_FP32_REFINED])
+def test_bcc_multi_tile_multi_chunk_parity(prec):
+    # 3D grids stream through z in 16-plane chunks over 32 x 8 (x, y) tiles: 40 x 12 x 20
+    # spans two tiles in x and y and two chunks in z, all ragged.
+    shape, h = (20, 12, 40), (1.0, 1.3, 0.9)
+    ctx, L = context("bcc", shape, h)
+    x = inputs.random_amplitudes(12, shape, seed=31, scale=1.0).reshape((6, 2) + shape)
+    y = ctx.apply_operator(0.9, x)
+    for j in range(6):
+        y1, y2 = O.apply_A(x[j, 0], x[j, 1], L.k[j], 0.9, P, h)
+        assert _max_rel(y[j, 0], y1) < 1e-13 and _max_rel(y[j, 1], y2) < 1e-13
+    eta0 = inputs.random_amplitudes(6, shape, seed=32, scale=0.1)
+    _trajectory_parity("bcc", eta0, shape, h, 2, dt=0.5, tol=1e-13, precision=prec, cheb_degree=2)
