@@ -232,6 +232,73 @@ apfc_status apfc_profile_read(apfc_ctx* ctx, int id, double* ms, long long* laun
                               long long* all_launches);
 apfc_status apfc_profile_stop(apfc_ctx* ctx);
 
+/* ---- batched independent runs ----------------------------------------------
+ * Many independent 2D simulations of one lattice, one parameter set and one
+ * spacing (hx, hy) on periodic grids of different sizes nx[r] x ny[r], advanced
+ * together by the step of apfc_step (Alg. 1 with one nonlinear iterate; the
+ * Sec. II.B preconditioner inside BiCGStab) in precision APFC_FP32_REFINED with
+ * the fused pipeline.  Every stage of the step is one launch over the work of
+ * all runs; each (run, amplitude) keeps its own Krylov scalars and stops on its
+ * own, and a run whose refinement has converged waits unchanged for the
+ * others.  Run r follows the same arithmetic as run r alone on an apfc_ctx
+ * with the same options (the same per-run reductions in the same order).
+ *
+ * Storage: the batch owns the concatenated block vectors of all runs (FP64
+ * state, right-hand sides and residuals; FP32 Krylov vectors), about
+ * 2 J sum_r(nx ny) x (4 x 16 + 10 x 8) bytes.  Amplitude buffers of run r are
+ * [J][ny[r]][nx[r]] complex128, owned by the caller, copied in or out.
+ *
+ * flags: APFC_BATCH_GRAPH replays the Krylov iteration blocks (check_every
+ * merged iterations) from captured CUDA graphs; the first block of each solve
+ * runs uncaptured.  With that flag a NULL stream makes the batch create and own
+ * a non-blocking stream (graphs cannot be captured on the legacy stream).
+ * Errors are sticky as on a context; ENAN / ENOCONV name the failing run in
+ * apfc_batch_last_error(). */
+typedef struct apfc_batch apfc_batch;
+#define APFC_BATCH_GRAPH 1
+
+/* Validate (lattice and parameters as apfc_init, dim 2, 1 <= nruns <= 65536,
+ * 3 <= nx[r], ny[r] <= 2^20, opts: precision APFC_FP32_REFINED, fused 1,
+ * cheb_degree 1..4; opts NULL = defaults with APFC_FP32_REFINED) and allocate.
+ * EINVAL on bad arguments, ETOOBIG if a launch over all runs would exceed the
+ * grid limit, ENOMEM if the device memory does not fit. */
+apfc_status apfc_batch_init(apfc_batch** b, const apfc_lattice* lat, const apfc_params* p, int nruns,
+                            const int* nx, const int* ny, double hx, double hy, const apfc_opts* opts,
+                            int flags, void* stream);
+apfc_status apfc_batch_set_opts(apfc_batch* b, const apfc_opts* opts);
+apfc_status apfc_batch_get_opts(const apfc_batch* b, apfc_opts* out);
+
+/* Per-run state: as apfc_set_amplitudes / apfc_get_amplitudes for run r. */
+apfc_status apfc_batch_set_amplitudes(apfc_batch* b, int run, const void* eta, int where);
+apfc_status apfc_batch_get_amplitudes(apfc_batch* b, int run, void* eta, int where);
+
+/* Advance every run n steps of size dt (all runs must have amplitudes). */
+apfc_status apfc_batch_step(apfc_batch* b, double dt, int n);
+
+/* Free energy of run r (as apfc_energy) and its solver statistics. */
+apfc_status apfc_batch_energy(apfc_batch* b, int run, double* F);
+apfc_status apfc_batch_stats(const apfc_batch* b, int run, apfc_stats_t* out);
+
+/* Tile autotuner: from the first refinement residual of a step of the current
+ * state (the state itself is not changed), time a fixed number of merged
+ * BiCGStab iterations over all runs for every tile variant (opts.tile 0..4)
+ * and segment height (64, 128, 256 rows), keep the fastest in the batch's
+ * options and return it (tile, rows, ms per iteration; null pointers skipped). */
+apfc_status apfc_batch_autotune(apfc_batch* b, double dt, int* tile, int* tile_rows, double* ms_per_iter);
+
+/* Number of captured-graph replays since creation (-1 for a null batch). */
+long long apfc_batch_graph_replays(const apfc_batch* b);
+
+const char* apfc_batch_last_error(const apfc_batch* b);
+void apfc_batch_destroy(apfc_batch* b);
+
+/* Measurement as apfc_profile_* on the batch's stream (graph replay is off
+ * while measuring, so that every launch is counted and can be timed). */
+apfc_status apfc_batch_profile_start(apfc_batch* b, int timed_id);
+apfc_status apfc_batch_profile_read(apfc_batch* b, int id, double* ms, long long* launches, double* bytes,
+                                    long long* all_launches);
+apfc_status apfc_batch_profile_stop(apfc_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

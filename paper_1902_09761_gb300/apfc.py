@@ -26,6 +26,7 @@ APFC_FP64, APFC_FP32_REFINED = 0, 1
 APFC_BICGSTAB = 0
 APFC_TAU_FOLD, APFC_TAU_PLAIN = 0, 1
 APFC_MAX_J = 8
+APFC_BATCH_GRAPH = 1
 
 
 class ApfcError(RuntimeError):
@@ -106,6 +107,32 @@ EXPORTS = {
         [C.POINTER(Lattice), C.POINTER(Params), C.POINTER(Grid), C.c_int, C.c_int, C.c_double, C.c_void_p,
          C.c_void_p, C.c_void_p],
     ),
+    "apfc_batch_init": (
+        C.c_int,
+        [C.POINTER(C.c_void_p), C.POINTER(Lattice), C.POINTER(Params), C.c_int, C.POINTER(C.c_int),
+         C.POINTER(C.c_int), C.c_double, C.c_double, C.POINTER(Opts), C.c_int, C.c_void_p],
+    ),
+    "apfc_batch_set_opts": (C.c_int, [C.c_void_p, C.POINTER(Opts)]),
+    "apfc_batch_get_opts": (C.c_int, [C.c_void_p, C.POINTER(Opts)]),
+    "apfc_batch_set_amplitudes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "apfc_batch_get_amplitudes": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "apfc_batch_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
+    "apfc_batch_energy": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
+    "apfc_batch_stats": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(Stats)]),
+    "apfc_batch_autotune": (
+        C.c_int,
+        [C.c_void_p, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)],
+    ),
+    "apfc_batch_graph_replays": (C.c_longlong, [C.c_void_p]),
+    "apfc_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "apfc_batch_destroy": (None, [C.c_void_p]),
+    "apfc_batch_profile_start": (C.c_int, [C.c_void_p, C.c_int]),
+    "apfc_batch_profile_read": (
+        C.c_int,
+        [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+         C.POINTER(C.c_longlong)],
+    ),
+    "apfc_batch_profile_stop": (C.c_int, [C.c_void_p]),
 }
 
 _lib = None
@@ -174,6 +201,12 @@ def apfc_uniform_amplitude(lattice: Lattice, params: Params) -> float:
 def _check(status, ctx=None):
     if status != APFC_OK:
         msg = load().apfc_last_error(ctx).decode() if ctx else ""
+        raise ApfcError(status, msg)
+
+
+def _check_batch(status, h=None):
+    if status != APFC_OK:
+        msg = load().apfc_batch_last_error(h).decode() if h else ""
         raise ApfcError(status, msg)
 
 
@@ -331,6 +364,115 @@ def apfc_apply_preconditioner_static(lattice: Lattice, params: Params, grid: Gri
         C.byref(lattice), C.byref(params), C.byref(grid), int(cheb_degree), int(tau_mode), float(dt),
         C.c_void_p(b_ptr), C.c_void_p(x_ptr), C.c_void_p(stream) if stream else None,
     )
+
+
+class Batch:
+    """Independent 2D runs of one lattice, parameter set and spacing on grids of
+    different sizes, stepped together (owns the library batch)."""
+
+    def __init__(self, k, kind, params, shapes, h, opts: Opts | None = None, graph: bool = True, stream=None):
+        lib = load()
+        self.k = np.asarray(k, dtype=float)
+        self.J, self.dim = self.k.shape
+        self.shapes = [tuple(int(v) for v in s) for s in shapes]  # (ny, nx) per run
+        self.R = len(self.shapes)
+        self.lattice = make_lattice(self.k, kind)
+        self.params = params if isinstance(params, Params) else make_params(*params)
+        if opts is None:
+            opts = apfc_default_opts(precision=APFC_FP32_REFINED)
+        ny = (C.c_int * self.R)(*[s[0] for s in self.shapes])
+        nx = (C.c_int * self.R)(*[s[1] for s in self.shapes])
+        handle = C.c_void_p()
+        st = lib.apfc_batch_init(
+            C.byref(handle), C.byref(self.lattice), C.byref(self.params), self.R, nx, ny, float(h[1]), float(h[0]),
+            C.byref(opts), APFC_BATCH_GRAPH if graph else 0, C.c_void_p(stream) if stream else None,
+        )
+        _check_batch(st)
+        self._h = handle
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().apfc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def amp_shape(self, run):
+        return (self.J,) + self.shapes[run]
+
+    @property
+    def opts(self) -> Opts:
+        o = Opts()
+        _check_batch(load().apfc_batch_get_opts(self._h, C.byref(o)), self._h)
+        return o
+
+    def set_opts(self, opts: Opts):
+        _check_batch(load().apfc_batch_set_opts(self._h, C.byref(opts)), self._h)
+
+    def set_amplitudes(self, run, eta):
+        p, where, keep = _ptr(eta)
+        _check_batch(load().apfc_batch_set_amplitudes(self._h, int(run), p, where), self._h)
+
+    def get_amplitudes(self, run, out=None):
+        out = np.empty(self.amp_shape(run), np.complex128) if out is None else out
+        p, where, keep = _ptr(out, True)
+        _check_batch(load().apfc_batch_get_amplitudes(self._h, int(run), p, where), self._h)
+        return out
+
+    def step(self, dt: float, n: int = 1):
+        _check_batch(load().apfc_batch_step(self._h, float(dt), int(n)), self._h)
+
+    def try_step(self, dt: float, n: int = 1) -> int:
+        return load().apfc_batch_step(self._h, float(dt), int(n))
+
+    def energy(self, run) -> float:
+        F = C.c_double()
+        _check_batch(load().apfc_batch_energy(self._h, int(run), C.byref(F)), self._h)
+        return F.value
+
+    def stats(self, run) -> dict:
+        s = Stats()
+        _check_batch(load().apfc_batch_stats(self._h, int(run), C.byref(s)), self._h)
+        return {name: getattr(s, name) for name, _ in Stats._fields_}
+
+    def autotune(self, dt: float) -> dict:
+        t, r, ms = C.c_int(), C.c_int(), C.c_double()
+        _check_batch(load().apfc_batch_autotune(self._h, float(dt), C.byref(t), C.byref(r), C.byref(ms)), self._h)
+        return {"tile": t.value, "tile_rows": r.value, "ms_per_iter": ms.value}
+
+    def graph_replays(self) -> int:
+        return load().apfc_batch_graph_replays(self._h)
+
+    def last_error(self) -> str:
+        return load().apfc_batch_last_error(self._h).decode()
+
+    def profile_start(self, timed: str | int | None = None):
+        if timed == "all":
+            tid = -2
+        else:
+            tid = -1 if timed is None else (timed if isinstance(timed, int) else kernel_ids()[timed])
+        _check_batch(load().apfc_batch_profile_start(self._h, tid), self._h)
+
+    def profile_read(self, kernel: str | int) -> dict:
+        kid = kernel if isinstance(kernel, int) else kernel_ids()[kernel]
+        ms, n, b, tot = C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong()
+        _check_batch(
+            load().apfc_batch_profile_read(self._h, kid, C.byref(ms), C.byref(n), C.byref(b), C.byref(tot)), self._h
+        )
+        return {"ms": ms.value, "launches": n.value, "bytes": b.value, "all_launches": tot.value}
+
+    def profile_stop(self):
+        _check_batch(load().apfc_batch_profile_stop(self._h), self._h)
 
 
 def kernel_ids() -> dict:

@@ -125,4 +125,177 @@ __device__ __forceinline__ void block_reduce(Acc<T>& a) {
   __syncthreads();
 }
 
+// ---- per-amplitude BiCGStab scalar recurrences -------------------------------
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double cabs2(double2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isfinite(a.y); }
+
+// Right-preconditioned BiCGStab scalar recurrences (van der Vorst 1992), one
+// amplitude per block.  d[q] are the finished inner products of this op.
+__device__ __forceinline__ void scalar_update(KScal& k, int op, const double2* d) {
+  switch (op) {
+    case OP_INIT: {  // d0 = (r, r), d1 = (b, b); rhat = r
+      k.rnorm2 = d[0].x;
+      k.bnorm2 = d[1].x;
+      k.tol2 = k.tolrel2 * (k.bnorm2 > 0.0 ? k.bnorm2 : k.rnorm2);
+      k.rho = d[0];
+      k.alpha = make_double2(0.0, 0.0);
+      k.omega = make_double2(0.0, 0.0);
+      k.beta = make_double2(0.0, 0.0);
+      k.iters = 0;
+      k.just_done = 0;
+      if (!isfinite(k.rnorm2) || !isfinite(k.bnorm2)) {
+        k.status = KS_NAN;
+        k.active = 0;
+      } else if (k.rnorm2 <= k.tol2) {
+        k.status = KS_CONVERGED;
+        k.active = 0;
+      } else {
+        k.status = KS_RUNNING;
+        k.active = 1;
+      }
+      break;
+    }
+    case OP_ALPHA: {  // d0 = (rhat, v)
+      if (!finite2(d[0]) || cabs2(d[0]) == 0.0) {
+        k.status = finite2(d[0]) ? KS_BREAKDOWN : KS_NAN;
+        k.active = 0;
+      } else {
+        k.alpha = cdiv(k.rho, d[0]);
+      }
+      break;
+    }
+    case OP_SNORM: {  // d0 = (s, s)
+      if (!isfinite(d[0].x)) {
+        k.status = KS_NAN;
+        k.active = 0;
+      } else if (d[0].x <= k.tol2) {
+        k.rnorm2 = d[0].x;
+        k.iters += 1;
+        k.status = KS_CONVERGED;
+        k.active = 0;
+      }
+      break;
+    }
+    case OP_OMEGA: {  // d0 = (t, s), d1 = (t, t)
+      if (!finite2(d[0]) || !isfinite(d[1].x)) {
+        k.status = KS_NAN;
+        k.active = 0;
+      } else if (d[1].x == 0.0 || cabs2(d[0]) == 0.0) {
+        k.status = KS_BREAKDOWN;
+        k.active = 0;
+      } else {
+        k.omega = make_double2(d[0].x / d[1].x, d[0].y / d[1].x);
+      }
+      break;
+    }
+    case OP_RHO: {  // d0 = (rhat, r), d1 = (r, r)
+      k.iters += 1;
+      k.rnorm2 = d[1].x;
+      if (!isfinite(k.rnorm2) || !finite2(d[0])) {
+        k.status = KS_NAN;
+        k.active = 0;
+      } else if (k.rnorm2 <= k.tol2) {
+        k.status = KS_CONVERGED;
+        k.active = 0;
+      } else if (k.iters >= k.max_iter) {
+        k.status = KS_NOCONV;
+        k.active = 0;
+      } else if (cabs2(d[0]) == 0.0) {
+        k.status = KS_BREAKDOWN;
+        k.active = 0;
+      } else {
+        k.beta = cmul2(cdiv(d[0], k.rho), cdiv(k.alpha, k.omega));
+        k.rho = d[0];
+      }
+      break;
+    }
+    case OP_OMEGA3: {  // d0 = (t, s), d1 = (t, t), d2 = (s, s)
+      if (!finite2(d[0]) || !isfinite(d[1].x) || !isfinite(d[2].x)) {
+        k.status = KS_NAN;
+        k.active = 0;
+      } else if (d[2].x <= k.tol2) {
+        k.omega = make_double2(0.0, 0.0);  // s already meets tol: the update sets r = s
+      } else if (d[1].x == 0.0 || cabs2(d[0]) == 0.0) {
+        k.status = KS_BREAKDOWN;
+        k.active = 0;
+      } else {
+        k.omega = make_double2(d[0].x / d[1].x, d[0].y / d[1].x);
+      }
+      break;
+    }
+    case OP_BNORM: {  // d0 = (b, b)
+      k.bnorm2 = d[0].x;
+      break;
+    }
+    case OP_RNORM: {  // d0 = (r, r); ||b||^2 from an earlier OP_NORMS / OP_BNORM
+      k.rnorm2 = d[0].x;
+      break;
+    }
+    case OP_OMEGA5: {
+      // merged iteration: d0 = (t, s), d1 = (t, t), d2 = (s, s), d3 = (rhat, s), d4 = (rhat, t).
+      // omega = (t, s)/(t, t); by linearity r' = s - omega t has
+      // (rhat, r') = (rhat, s) - omega (rhat, t) and
+      // ||r'||^2 = (s, s) - 2 Re(omega conj(t, s)) + |omega|^2 (t, t).
+      k.just_done = 0;
+      bool fin = true;
+      for (int q = 0; q < 5; ++q) fin = fin && finite2(d[q]);
+      if (!fin) {
+        k.status = KS_NAN;
+        k.active = 0;
+        break;
+      }
+      k.iters += 1;
+      if (d[2].x <= k.tol2) {
+        k.omega = make_double2(0.0, 0.0);  // s already meets tol: r' = s
+        k.rnorm2 = d[2].x;
+        k.status = KS_CONVERGED;
+        k.active = 0;
+        k.just_done = 1;
+        break;
+      }
+      if (d[1].x == 0.0 || cabs2(d[0]) == 0.0) {
+        k.status = KS_BREAKDOWN;
+        k.active = 0;
+        k.just_done = 1;
+        break;
+      }
+      k.omega = make_double2(d[0].x / d[1].x, d[0].y / d[1].x);
+      const double2 oc = cmul2(k.omega, make_double2(d[0].x, -d[0].y));
+      double rn2 = d[2].x - 2.0 * oc.x + cabs2(k.omega) * d[1].x;
+      k.rnorm2 = rn2 > 0.0 ? rn2 : 0.0;
+      const double2 rho_new = make_double2(d[3].x - (k.omega.x * d[4].x - k.omega.y * d[4].y),
+                                           d[3].y - (k.omega.x * d[4].y + k.omega.y * d[4].x));
+      if (k.rnorm2 <= k.tol2) {
+        k.status = KS_CONVERGED;
+        k.active = 0;
+        k.just_done = 1;
+      } else if (k.iters >= k.max_iter) {
+        k.status = KS_NOCONV;
+        k.active = 0;
+        k.just_done = 1;
+      } else if (cabs2(rho_new) == 0.0) {
+        k.status = KS_BREAKDOWN;
+        k.active = 0;
+        k.just_done = 1;
+      } else {
+        k.beta = cmul2(cdiv(rho_new, k.rho), cdiv(k.alpha, k.omega));
+        k.rho = rho_new;
+      }
+      break;
+    }
+    case OP_NORMS: {  // d0 = (r, r), d1 = (b, b): record only
+      k.rnorm2 = d[0].x;
+      k.bnorm2 = d[1].x;
+      break;
+    }
+  }
+}
+
 }  // namespace apfc

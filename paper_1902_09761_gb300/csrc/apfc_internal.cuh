@@ -121,6 +121,32 @@ __device__ __forceinline__ void prof_add(const OpCoef& c, int kid, unsigned long
   if (c.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(c.prof + kid, bytes);
 }
 
+// Batched runs: every run's block vectors sit one after another in shared
+// arrays; elem_off is the run's first element (of [J][2][pts]), part_off its
+// first 16-byte partial-sum slot.
+struct RunGeom {
+  int nx, ny;
+  long long pts, elem_off, part_off;
+  int blk[2];  // first block of the run in a fused launch: [0] with A, [1] P^{-1} alone
+  int npart;   // partial-sum slots per amplitude of the fused kernels with A
+  int pad;
+};
+struct BatchLaunch {
+  const RunGeom* dev;   // device copy of the run table
+  const RunGeom* host;  // host copy (launch sizes)
+  int R;
+};
+
+// Point a kernel's grid sizes at run `run`; returns the run's first element.
+__device__ __forceinline__ long long select_run(const RunGeom* rg, int run, OpCoef& c) {
+  const RunGeom& q = rg[run];
+  c.nx = q.nx;
+  c.ny = q.ny;
+  c.nz = 1;
+  c.pts = q.pts;
+  return q.elem_off;
+}
+
 // Chebyshev recurrence weights for one application (per amplitude):
 // d_{k+1} = c1 d_k + c2 r_{k+1}.
 struct ChebStep {
@@ -201,19 +227,23 @@ void launch_r_update(cplx<T>* r, const cplx<T>* t, cplx<T>* u, const OpCoef& c, 
 template <typename T>
 void launch_add_to(const cplx<T>* d, double2* x, const OpCoef& c, cudaStream_t s);
 
-void launch_rhs(const double2* x, double2* b, const OpCoef& c, const NonlinTable& nt, cudaStream_t s);
+// bl != nullptr (here and below): one launch over every run of a batch, c holding the
+// largest run's sizes; FP64 partials of run r start at slot r J kDotSlots kDotBlocks
+void launch_rhs(const double2* x, double2* b, const OpCoef& c, const NonlinTable& nt, cudaStream_t s,
+                const BatchLaunch* bl = nullptr);
 void launch_zeta(double2* x, const OpCoef& c, cudaStream_t s);
 void launch_residual_refine(const double2* b, const double2* x, float2* r32, double* partials, const OpCoef& c,
                             cudaStream_t s);
 // 2D only: FP64 residual with FP32 (and optional FP64) output
 void launch_residual_refine2d(const double2* b, const double2* x, float2* r32, double2* r64, double* partials,
-                              const OpCoef& c, cudaStream_t s);
+                              const OpCoef& c, cudaStream_t s, const BatchLaunch* bl = nullptr);
 // 3D: FP64 residual with FP32 and FP64 output (norm taken separately)
 void launch_residual_refine3d(const double2* b, const double2* x, float2* r32, double2* r64, const OpCoef& c,
                               cudaStream_t s);
 // new RHS and initial residual r0 = b - b_prev + r_prev (pointwise)
 void launch_rhs_resid(const double2* x, double2* b, const double2* b_prev, const double2* r_prev, float2* r32,
-                      double* partials, const OpCoef& c, const NonlinTable& nt, cudaStream_t s);
+                      double* partials, const OpCoef& c, const NonlinTable& nt, cudaStream_t s,
+                      const BatchLaunch* bl = nullptr);
 void launch_energy(const double2* x, double* partials, double* out, const OpCoef& c, const EnergyTable& et,
                    double Bx, cudaStream_t s);
 
@@ -237,7 +267,9 @@ bool launch_fused_t(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w,
 // x64 += P^{-1} u
 template <typename T>
 bool launch_fused_pinv_add(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* u, double2* x64,
-                           cudaStream_t s);
+                           cudaStream_t s, const BatchLaunch* bl = nullptr);
+// blocks of one fused launch over an nx x ny grid (J amplitudes); *npart = blocks per amplitude
+int fused2d_blocks(int nx, int ny, int J, int m, int Ly, int elem_bytes, int tile, bool with_a, int* npart);
 // x = P^{-1} b
 template <typename T>
 bool launch_fused_pinv_store(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* b, cplx<T>* x,
@@ -248,15 +280,17 @@ bool launch_fused_pinv_store(int m, int Ly, int tile, const OpCoef& c, const Che
 template <typename T>
 bool launch_fused_merged_v(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
                            const cplx<T>* t, const cplx<T>* p, cplx<T>* u, cplx<T>* r_new, cplx<T>* p_new,
-                           cplx<T>* v_new, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s);
+                           cplx<T>* v_new, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s,
+                           const BatchLaunch* bl = nullptr);
 // t = A P^{-1} s, s = r - alpha v; partials (t, s), (t, t), (s, s), (rhat, s), (rhat, t)
 template <typename T>
 bool launch_fused_merged_t(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
-                           cplx<T>* t_out, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s);
+                           cplx<T>* t_out, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s,
+                           const BatchLaunch* bl = nullptr);
 // the pending u += alpha p + omega (r - alpha v) of amplitudes that stopped in this iteration
 template <typename T>
 void launch_final_update(const cplx<T>* r, const cplx<T>* v, const cplx<T>* p, cplx<T>* u, const KScal* ks,
-                         const OpCoef& c, cudaStream_t s);
+                         const OpCoef& c, cudaStream_t s, const BatchLaunch* bl = nullptr);
 // s = r - alpha v; u += alpha p + omega s; r = s - omega t; partials (rhat, r), (r, r) in [J][kDotSlots][kDotBlocks]
 template <typename T>
 void launch_bicg_update(cplx<T>* r, const cplx<T>* v, const cplx<T>* p, cplx<T>* u, const cplx<T>* t,
@@ -265,14 +299,20 @@ void launch_bicg_update(cplx<T>* r, const cplx<T>* v, const cplx<T>* p, cplx<T>*
 // ---------------------------------------------------------------------------
 // reduce.cu
 // ---------------------------------------------------------------------------
+// bl != nullptr: one launch over every run of a batch (partials of run r from slot r J kDotSlots kDotBlocks)
 template <typename T>
 void launch_dots(int npair, const DotPairs<T>& pr, void* partials, const OpCoef& c, const KScal* act,
-                 cudaStream_t s);
+                 cudaStream_t s, const BatchLaunch* bl = nullptr);
 // npart: partial-sum slots per (amplitude, pair); layout [J][kDotSlots][npart].
 template <typename T>
 void launch_finalize(int npair, const void* partials, KScal* k, int op, int J, cudaStream_t s,
                      int npart = kDotBlocks);
 // partials in FP64 double2 layout regardless of T (for the fused FP64 residual)
 void launch_finalize64(int npair, const void* partials, KScal* k, int op, int J, cudaStream_t s);
+// batched runs: Krylov scalars k[run J + j]; npart_fixed > 0 for the k_dots layout
+// (kDotBlocks), 0 for the fused-pipeline layout (RunGeom part_off, npart)
+template <typename T>
+void launch_finalize_batch(int npair, const void* partials, int npart_fixed, const BatchLaunch& bl, int J, KScal* k,
+                           int op, cudaStream_t s);
 
 }  // namespace apfc

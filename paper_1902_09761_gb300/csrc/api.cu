@@ -10,7 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "apfc_internal.cuh"
+#include "host_common.h"
 
 using namespace apfc;
 
@@ -77,6 +77,83 @@ void prof_launch_end(int kid, cudaStream_t s) {
   cudaEventRecord(g_prof.ev[g_prof.used + 1], s);
   g_prof.used += 2;
 }
+
+bool profiler_on() { return g_prof.on; }
+
+bool profiler_start(cudaStream_t s, int timed_id, unsigned long long** dev, std::string& err) {
+  if (timed_id < -2 || timed_id >= 2 * KID_COUNT) {
+    err = "unknown kernel id";
+    return false;
+  }
+  if (g_prof.on && g_prof.stream != s) {
+    err = "measurement already running";
+    return false;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!g_prof.dev) e = cudaMalloc(&g_prof.dev, sizeof(unsigned long long) * 2 * KID_COUNT);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g_prof.dev, 0, sizeof(unsigned long long) * 2 * KID_COUNT, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    err = std::string("measurement setup: ") + cudaGetErrorString(e);
+    return false;
+  }
+  g_prof.on = true;
+  g_prof.timed = timed_id;
+  g_prof.stream = s;
+  g_prof.used = 0;
+  g_prof.failed = false;
+  std::memset(g_prof.launches, 0, sizeof(g_prof.launches));
+  g_prof.all = 0;
+  *dev = g_prof.dev;
+  return true;
+}
+
+bool profiler_read(cudaStream_t s, int id, double* ms, long long* launches, double* bytes, long long* all_launches,
+                   std::string& err) {
+  if (id < 0 || id >= 2 * KID_COUNT) {
+    err = "unknown kernel id";
+    return false;
+  }
+  if (!g_prof.dev) {
+    err = "measurement was never started";
+    return false;
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    err = cudaGetErrorString(e);
+    return false;
+  }
+  if (g_prof.failed) {
+    err = "event pool exhausted";
+    return false;
+  }
+  double total = 0.0;
+  if (id == g_prof.timed || g_prof.timed == -2) {
+    for (size_t i = 0; i + 1 < g_prof.used; i += 2) {
+      if (g_prof.ev_kid[i / 2] != id) continue;
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, g_prof.ev[i], g_prof.ev[i + 1]);
+      if (e != cudaSuccess) {
+        err = cudaGetErrorString(e);
+        return false;
+      }
+      total += t;
+    }
+  }
+  unsigned long long b[2 * KID_COUNT];
+  e = cudaMemcpy(b, g_prof.dev, sizeof(b), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    err = cudaGetErrorString(e);
+    return false;
+  }
+  if (ms) *ms = total;
+  if (launches) *launches = g_prof.launches[id];
+  if (bytes) *bytes = (double)b[id];
+  if (all_launches) *all_launches = g_prof.all;
+  return true;
+}
+
+void profiler_stop() { g_prof.on = false; }
 }  // namespace apfc
 
 struct apfc_ctx {
@@ -181,6 +258,88 @@ void free_work(Work<T>& w) {
   w.ready = false;
 }
 
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Operator coefficients for a time step dt
+// ---------------------------------------------------------------------------
+bool apfc::make_coef(const apfc_lattice& lat, const apfc_params& par, const apfc_grid& grid, int tau_mode, double dt,
+                     OpCoef& o, std::string& err) {
+  if (!(dt > 0.0) || !std::isfinite(dt)) {
+    err = "dt must be positive and finite";
+    return false;
+  }
+  unsigned long long* prof = o.prof;
+  std::memset(&o, 0, sizeof(o));
+  o.prof = prof;
+  const int dim = lat.dim;
+  o.J = lat.J;
+  o.dim = dim;
+  o.nx = grid.n[0];
+  o.ny = grid.n[1];
+  o.nz = dim == 3 ? grid.n[2] : 1;
+  o.pts = (long long)o.nx * o.ny * o.nz;
+  double lapmax = 0.0;
+  for (int d = 0; d < dim; ++d) {
+    const double h = grid.h[d];
+    o.ih2[d] = 1.0 / (h * h);
+    o.c0 -= 2.0 / (h * h);
+    lapmax += 4.0 / (h * h);
+  }
+  o.inv_dt = 1.0 / dt;
+  for (int j = 0; j < lat.J; ++j) {
+    double kap = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      o.kh[j][d] = lat.k[j][d] / grid.h[d];
+      kap += lat.k[j][d] * lat.k[j][d];
+    }
+    o.kap[j] = kap;
+    o.kt[j] = kap * par.Bx;
+    o.a[j] = 1.0 / dt + kap * par.dB;
+    const double inv_tau = 1.0 / dt + (tau_mode == APFC_TAU_FOLD ? kap * par.dB : 0.0);
+    if (!(o.a[j] > 0.0) || !(inv_tau > 0.0) || !(o.kt[j] > 0.0)) {
+      err = "need 1/dt + |k_j|^2 dB > 0 and |k_j|^2 Bx > 0";
+      return false;
+    }
+    o.sD[j] = std::sqrt(inv_tau);
+    o.mu[j] = std::sqrt(o.kt[j]);
+    o.inv_mu[j] = 1.0 / o.mu[j];
+    const double lmin = o.sD[j], lmax = o.sD[j] + o.mu[j] * lapmax;
+    o.inv_theta[j] = 2.0 / (lmax + lmin);
+  }
+  return true;
+}
+
+std::vector<ChebStep> apfc::cheb_weights_for(const OpCoef& c, const apfc_grid& grid, int m) {
+  std::vector<ChebStep> w(std::max(m, 1));
+  double lapmax = 0.0;
+  for (int d = 0; d < c.dim; ++d) lapmax += 4.0 / (grid.h[d] * grid.h[d]);
+  for (int j = 0; j < c.J; ++j) {
+    const double lmin = c.sD[j], lmax = c.sD[j] + c.mu[j] * lapmax;
+    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    for (int k = 0; k < m; ++k) {
+      const double rn = 1.0 / (2.0 * sigma - rho);
+      w[k].c1[j] = rn * rho;
+      w[k].c2[j] = 2.0 * rn / delta;
+      rho = rn;
+    }
+  }
+  return w;
+}
+
+namespace {
+
+bool build_coef(apfc_ctx* c, double dt, std::string& err) {
+  if (c->coef_dt == dt) return true;
+  if (!make_coef(c->lat, c->par, c->grid, c->opts.tau_mode, dt, c->coef, err)) return false;
+  c->coef_dt = dt;
+  return true;
+}
+
+// Chebyshev recurrence weights (Saad, Sec. 12.3) for application k of D.
+std::vector<ChebStep> cheb_weights(const apfc_ctx* c) { return cheb_weights_for(c->coef, c->grid, c->opts.cheb_degree); }
+
 // ---------------------------------------------------------------------------
 // Nonlinear-term tables from the resonance rule: <n^p> keeps the ordered
 // p-tuples of signed modes (j, s) whose wavevectors s k_j sum to zero.
@@ -216,7 +375,9 @@ void enumerate(const apfc_lattice& L, int p, std::map<std::vector<Mode>, int>& o
 
 inline int code_of(const Mode& m) { return 2 * m.j + (m.s < 0 ? 1 : 0); }
 
-bool build_tables(const apfc_lattice& L, const apfc_params& P, NonlinTable& nt, EnergyTable& et, std::string& err) {
+}  // namespace
+
+bool apfc::build_tables(const apfc_lattice& L, const apfc_params& P, NonlinTable& nt, EnergyTable& et, std::string& err) {
   std::memset(&nt, 0, sizeof(nt));
   std::memset(&et, 0, sizeof(et));
   nt.t = et.t = P.t;
@@ -271,76 +432,7 @@ bool build_tables(const apfc_lattice& L, const apfc_params& P, NonlinTable& nt, 
   return true;
 }
 
-// ---------------------------------------------------------------------------
-// Operator coefficients for a time step dt
-// ---------------------------------------------------------------------------
-bool build_coef(apfc_ctx* c, double dt, std::string& err) {
-  if (!(dt > 0.0) || !std::isfinite(dt)) {
-    err = "dt must be positive and finite";
-    return false;
-  }
-  if (c->coef_dt == dt) return true;
-  OpCoef& o = c->coef;
-  unsigned long long* prof = o.prof;
-  std::memset(&o, 0, sizeof(o));
-  o.prof = prof;
-  o.J = c->J;
-  o.dim = c->dim;
-  o.nx = c->grid.n[0];
-  o.ny = c->grid.n[1];
-  o.nz = c->dim == 3 ? c->grid.n[2] : 1;
-  o.pts = c->pts;
-  double lapmax = 0.0;
-  for (int d = 0; d < c->dim; ++d) {
-    const double h = c->grid.h[d];
-    o.ih2[d] = 1.0 / (h * h);
-    o.c0 -= 2.0 / (h * h);
-    lapmax += 4.0 / (h * h);
-  }
-  o.inv_dt = 1.0 / dt;
-  for (int j = 0; j < c->J; ++j) {
-    double kap = 0.0;
-    for (int d = 0; d < c->dim; ++d) {
-      o.kh[j][d] = c->lat.k[j][d] / c->grid.h[d];
-      kap += c->lat.k[j][d] * c->lat.k[j][d];
-    }
-    o.kap[j] = kap;
-    o.kt[j] = kap * c->par.Bx;
-    o.a[j] = 1.0 / dt + kap * c->par.dB;
-    const double inv_tau = 1.0 / dt + (c->opts.tau_mode == APFC_TAU_FOLD ? kap * c->par.dB : 0.0);
-    if (!(o.a[j] > 0.0) || !(inv_tau > 0.0) || !(o.kt[j] > 0.0)) {
-      err = "need 1/dt + |k_j|^2 dB > 0 and |k_j|^2 Bx > 0";
-      return false;
-    }
-    o.sD[j] = std::sqrt(inv_tau);
-    o.mu[j] = std::sqrt(o.kt[j]);
-    o.inv_mu[j] = 1.0 / o.mu[j];
-    const double lmin = o.sD[j], lmax = o.sD[j] + o.mu[j] * lapmax;
-    o.inv_theta[j] = 2.0 / (lmax + lmin);
-  }
-  c->coef_dt = dt;
-  return true;
-}
-
-// Chebyshev recurrence weights (Saad, Sec. 12.3) for application k of D.
-std::vector<ChebStep> cheb_weights(const apfc_ctx* c) {
-  const int m = c->opts.cheb_degree;
-  std::vector<ChebStep> w(std::max(m, 1));
-  double lapmax = 0.0;
-  for (int d = 0; d < c->dim; ++d) lapmax += 4.0 / (c->grid.h[d] * c->grid.h[d]);
-  for (int j = 0; j < c->J; ++j) {
-    const double lmin = c->coef.sD[j], lmax = c->coef.sD[j] + c->coef.mu[j] * lapmax;
-    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
-    double rho = 1.0 / sigma;
-    for (int k = 0; k < m; ++k) {
-      const double rn = 1.0 / (2.0 * sigma - rho);
-      w[k].c1[j] = rn * rho;
-      w[k].c2[j] = 2.0 * rn / delta;
-      rho = rn;
-    }
-  }
-  return w;
-}
+namespace {
 
 // chi = P^{-1} beta (four steps of Sec. II.B, M = I).
 template <typename T>
@@ -648,23 +740,6 @@ apfc_status step_refined(apfc_ctx* ctx) {
   return status_of(ctx, worst);
 }
 
-bool valid_opts(const apfc_opts& o, std::string& e) {
-  if (o.precision != APFC_FP64 && o.precision != APFC_FP32_REFINED) e = "precision";
-  else if (o.krylov != APFC_BICGSTAB) e = "krylov";
-  else if (o.max_iter < 1) e = "max_iter";
-  else if (o.cheb_degree < 0 || o.cheb_degree > kMaxCheb) e = "cheb_degree";
-  else if (o.tau_mode != APFC_TAU_FOLD && o.tau_mode != APFC_TAU_PLAIN) e = "tau_mode";
-  else if (o.max_refine < 0) e = "max_refine";
-  else if (o.check_every < 1) e = "check_every";
-  else if (o.fused != 0 && o.fused != 1) e = "fused";
-  else if (o.tile < 0 || o.tile >= fused2d_tiles()) e = "tile";
-  else if (o.tile_rows < 0 || o.tile_rows > 65536) e = "tile_rows";
-  else if (!(o.tol > 0.0) || !(o.tol_inner > 0.0) || !(o.tol_inner < 1.0)) e = "tol";
-  else return true;
-  e = "invalid option: " + e;
-  return false;
-}
-
 apfc_status copy_in_block(apfc_ctx* ctx, double2* dst_dev, const void* src, int where) {
   const cudaMemcpyKind k = where == APFC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   CK(cudaMemcpyAsync(dst_dev, src, sizeof(double2) * 2ull * ctx->J * ctx->pts, k, ctx->stream));
@@ -695,6 +770,41 @@ apfc_status copy_part(apfc_ctx* ctx, void* plain, int where, int part, bool to_s
 }
 
 }  // namespace
+
+bool apfc::valid_opts(const apfc_opts& o, std::string& e) {
+  if (o.precision != APFC_FP64 && o.precision != APFC_FP32_REFINED) e = "precision";
+  else if (o.krylov != APFC_BICGSTAB) e = "krylov";
+  else if (o.max_iter < 1) e = "max_iter";
+  else if (o.cheb_degree < 0 || o.cheb_degree > kMaxCheb) e = "cheb_degree";
+  else if (o.tau_mode != APFC_TAU_FOLD && o.tau_mode != APFC_TAU_PLAIN) e = "tau_mode";
+  else if (o.max_refine < 0) e = "max_refine";
+  else if (o.check_every < 1) e = "check_every";
+  else if (o.fused != 0 && o.fused != 1) e = "fused";
+  else if (o.tile < 0 || o.tile >= fused2d_tiles()) e = "tile";
+  else if (o.tile_rows < 0 || o.tile_rows > 65536) e = "tile_rows";
+  else if (!(o.tol > 0.0) || !(o.tol_inner > 0.0) || !(o.tol_inner < 1.0)) e = "tol";
+  else return true;
+  e = "invalid option: " + e;
+  return false;
+}
+
+bool apfc::valid_problem(const apfc_lattice& lat, const apfc_params& p) {
+  if (lat.dim != 2 && lat.dim != 3) return false;
+  if (lat.J < 1 || lat.J > kMaxJ) return false;
+  if (lat.lattice != APFC_LATTICE_CUSTOM && lat.lattice != APFC_LATTICE_HEX2D && lat.lattice != APFC_LATTICE_BCC3D)
+    return false;
+  for (int j = 0; j < lat.J; ++j)
+    for (int d = 0; d < lat.dim; ++d)
+      if (!std::isfinite(lat.k[j][d])) return false;
+  if (lat.lattice == APFC_LATTICE_HEX2D) {
+    if (lat.J != 3 || lat.dim != 2) return false;
+    for (int d = 0; d < 2; ++d)
+      if (std::fabs(lat.k[0][d] + lat.k[1][d] + lat.k[2][d]) > 1e-12) return false;
+  }
+  if (lat.lattice == APFC_LATTICE_BCC3D && (lat.J != 6 || lat.dim != 3)) return false;
+  if (!std::isfinite(p.dB) || !std::isfinite(p.t) || !std::isfinite(p.v) || !(p.Bx > 0.0)) return false;
+  return true;
+}
 
 // ===========================================================================
 extern "C" {
@@ -739,20 +849,7 @@ apfc_status apfc_init(apfc_ctx** out, const apfc_lattice* lat, const apfc_params
                       const apfc_opts* opts, void* stream) {
   if (!out || !lat || !p || !g) return APFC_EINVAL;
   *out = nullptr;
-  if (lat->dim != 2 && lat->dim != 3) return APFC_EINVAL;
-  if (lat->J < 1 || lat->J > kMaxJ) return APFC_EINVAL;
-  if (lat->lattice != APFC_LATTICE_CUSTOM && lat->lattice != APFC_LATTICE_HEX2D && lat->lattice != APFC_LATTICE_BCC3D)
-    return APFC_EINVAL;
-  for (int j = 0; j < lat->J; ++j)
-    for (int d = 0; d < lat->dim; ++d)
-      if (!std::isfinite(lat->k[j][d])) return APFC_EINVAL;
-  if (lat->lattice == APFC_LATTICE_HEX2D) {
-    if (lat->J != 3 || lat->dim != 2) return APFC_EINVAL;
-    for (int d = 0; d < 2; ++d)
-      if (std::fabs(lat->k[0][d] + lat->k[1][d] + lat->k[2][d]) > 1e-12) return APFC_EINVAL;
-  }
-  if (lat->lattice == APFC_LATTICE_BCC3D && (lat->J != 6 || lat->dim != 3)) return APFC_EINVAL;
-  if (!std::isfinite(p->dB) || !std::isfinite(p->t) || !std::isfinite(p->v) || !(p->Bx > 0.0)) return APFC_EINVAL;
+  if (!valid_problem(*lat, *p)) return APFC_EINVAL;
   for (int d = 0; d < lat->dim; ++d)
     if (g->n[d] < 3 || !(g->h[d] > 0.0) || !std::isfinite(g->h[d])) return APFC_EINVAL;
   if (lat->dim == 2 && g->n[2] != 1) return APFC_EINVAL;
@@ -904,49 +1001,23 @@ const char* apfc_kernel_name(int id) {
 }
 
 apfc_status apfc_profile_start(apfc_ctx* ctx, int timed_id) {
-  if (!ctx || timed_id < -2 || timed_id >= 2 * KID_COUNT) return APFC_EINVAL;
-  if (g_prof.on && g_prof.stream != ctx->stream) return fail(ctx, APFC_EINVAL, "measurement already running");
-  if (!g_prof.dev) CK(cudaMalloc(&g_prof.dev, sizeof(unsigned long long) * 2 * KID_COUNT));
-  CK(cudaMemsetAsync(g_prof.dev, 0, sizeof(unsigned long long) * 2 * KID_COUNT, ctx->stream));
-  CK(cudaStreamSynchronize(ctx->stream));
-  g_prof.on = true;
-  g_prof.timed = timed_id;
-  g_prof.stream = ctx->stream;
-  g_prof.used = 0;
-  g_prof.failed = false;
-  std::memset(g_prof.launches, 0, sizeof(g_prof.launches));
-  g_prof.all = 0;
-  ctx->coef.prof = g_prof.dev;
+  if (!ctx) return APFC_EINVAL;
+  std::string e;
+  if (!profiler_start(ctx->stream, timed_id, &ctx->coef.prof, e)) return fail(ctx, APFC_EINVAL, e);
   return APFC_OK;
 }
 
 apfc_status apfc_profile_read(apfc_ctx* ctx, int id, double* ms, long long* launches, double* bytes,
                               long long* all_launches) {
-  if (!ctx || id < 0 || id >= 2 * KID_COUNT) return APFC_EINVAL;
-  if (!g_prof.dev) return fail(ctx, APFC_ESTATE, "measurement was never started");
-  CK(cudaStreamSynchronize(ctx->stream));
-  if (g_prof.failed) return fail(ctx, APFC_ENOMEM, "event pool exhausted");
-  double total = 0.0;
-  if (id == g_prof.timed || g_prof.timed == -2) {
-    for (size_t i = 0; i + 1 < g_prof.used; i += 2) {
-      if (g_prof.ev_kid[i / 2] != id) continue;
-      float t = 0.f;
-      CK(cudaEventElapsedTime(&t, g_prof.ev[i], g_prof.ev[i + 1]));
-      total += t;
-    }
-  }
-  unsigned long long b[2 * KID_COUNT];
-  CK(cudaMemcpy(b, g_prof.dev, sizeof(b), cudaMemcpyDeviceToHost));
-  if (ms) *ms = total;
-  if (launches) *launches = g_prof.launches[id];
-  if (bytes) *bytes = (double)b[id];
-  if (all_launches) *all_launches = g_prof.all;
+  if (!ctx) return APFC_EINVAL;
+  std::string e;
+  if (!profiler_read(ctx->stream, id, ms, launches, bytes, all_launches, e)) return fail(ctx, APFC_EINVAL, e);
   return APFC_OK;
 }
 
 apfc_status apfc_profile_stop(apfc_ctx* ctx) {
   if (!ctx) return APFC_EINVAL;
-  g_prof.on = false;
+  profiler_stop();
   ctx->coef.prof = nullptr;
   return APFC_OK;
 }

@@ -161,6 +161,11 @@ struct LoadPlain {
   const cplx<T>* b;
   long long pts;
   long long off;
+  // batched runs: move every array to this run's block vectors
+  __device__ void rebase(long long e, long long n) {
+    b += e;
+    pts = n;
+  }
   __device__ void setup(int j, const KScal*) { off = 2LL * j * pts; }
   __device__ const cplx<T>* in(int i) const { return b + off + i * pts; }
   __device__ const cplx<T>* re(int) const { return b + off; }
@@ -182,6 +187,14 @@ struct LoadP {
   long long pts;
   cplx<T> beta, omega;
   long long off;
+  // batched runs: move every array to this run's block vectors
+  __device__ void rebase(long long e, long long n) {
+    r += e;
+    po += e;
+    vo += e;
+    pn += e;
+    pts = n;
+  }
   __device__ void setup(int j, const KScal* k) {
     beta = to_c<T>(k[j].beta);
     omega = to_c<T>(k[j].omega);
@@ -216,6 +229,12 @@ struct LoadS {
   long long pts;
   cplx<T> alpha;
   long long off;
+  // batched runs: move every array to this run's block vectors
+  __device__ void rebase(long long e, long long n) {
+    r += e;
+    v += e;
+    pts = n;
+  }
   __device__ void setup(int j, const KScal* k) {
     alpha = to_c<T>(k[j].alpha);
     off = 2LL * j * pts;
@@ -246,6 +265,17 @@ struct LoadPR {
   long long pts;
   cplx<T> al, om, be;
   long long off;
+  // batched runs: move every array to this run's block vectors
+  __device__ void rebase(long long e, long long n) {
+    r += e;
+    v += e;
+    t += e;
+    p += e;
+    u += e;
+    rn += e;
+    pn += e;
+    pts = n;
+  }
   __device__ void setup(int j, const KScal* k) {
     al = to_c<T>(k[j].alpha);
     om = to_c<T>(k[j].omega);
@@ -298,6 +328,14 @@ struct EpT5 {
   long long off;
   cplx<T> alpha;
   Acc<T> acc[5];
+  // batched runs: move every array to this run's block vectors
+  __device__ void rebase(long long e, long long n) {
+    t += e;
+    r += e;
+    v += e;
+    rhat += e;
+    pts = n;
+  }
   __device__ void setup(int j, const KScal* k) {
     off = 2LL * j * pts;
     alpha = to_c<T>(k[j].alpha);
@@ -326,6 +364,11 @@ struct EpStore {  // out = y
   long long pts;
   long long off;
   Acc<T> acc[1];
+  // batched runs: move every array to this run's block vectors
+  __device__ void rebase(long long e, long long n) {
+    out += e;
+    pts = n;
+  }
   __device__ void setup(int j, const KScal*) { off = 2LL * j * pts; }
   __device__ const cplx<T>* ep(int) const { return nullptr; }
   __device__ void put(const cplx<T>*, int, long long p, cplx<T> y1, cplx<T> y2) {
@@ -341,6 +384,11 @@ struct EpAddX {  // x64 += y (the Krylov correction P^{-1} u)
   long long pts;
   long long off;
   Acc<T> acc[1];
+  // batched runs: move every array to this run's block vectors
+  __device__ void rebase(long long e, long long n) {
+    x += e;
+    pts = n;
+  }
   __device__ void setup(int j, const KScal*) { off = 2LL * j * pts; }
   __device__ const cplx<T>* ep(int) const { return nullptr; }
   __device__ void put(const cplx<T>*, int, long long p, cplx<T> y1, cplx<T> y2) {
@@ -362,6 +410,12 @@ struct EpV {  // v = y; (rhat, v)
   long long pts;
   long long off;
   Acc<T> acc[1];
+  // batched runs: move every array to this run's block vectors
+  __device__ void rebase(long long e, long long n) {
+    v += e;
+    rhat += e;
+    pts = n;
+  }
   __device__ void setup(int j, const KScal*) { off = 2LL * j * pts; }
   __device__ const cplx<T>* ep(int i) const { return rhat + off + i * pts; }
   __device__ void put(const cplx<T>* raw, int st, long long p, cplx<T> y1, cplx<T> y2) {
@@ -382,6 +436,13 @@ struct EpT {  // t = y; (t, s), (t, t), (s, s) with s = r - alpha v
   long long off;
   cplx<T> alpha;
   Acc<T> acc[3];
+  // batched runs: move every array to this run's block vectors
+  __device__ void rebase(long long e, long long n) {
+    t += e;
+    r += e;
+    v += e;
+    pts = n;
+  }
   __device__ void setup(int j, const KScal* k) {
     off = 2LL * j * pts;
     alpha = to_c<T>(k[j].alpha);
@@ -468,7 +529,7 @@ __device__ __forceinline__ int wrap_inc(int y, int n) { return y + 1 == n ? 0 : 
 
 template <typename T, int M, bool WITH_A, int PF, int NT_, class LD, class EP>
 __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g, LD ld, EP ep, const KScal* act,
-                                                void* partials, int kid, unsigned long long bytes_per_amp) {
+                                                void* partials, int kid, int fields, const RunGeom* rg, int R) {
   using SH = PipeShape<T, M, WITH_A, PF, NT_, LD, EP>;
   constexpr int NT = SH::NT;
   constexpr int S = SH::S;
@@ -478,7 +539,42 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* stage_buf = sm + SH::ring_elems;
 
-  const int j = blockIdx.z;
+  // work item: strip sx, row segment sy, amplitude j (of run `run` when batched)
+  int sx, sy, j;
+  if (rg == nullptr) {
+    sx = blockIdx.x;
+    sy = blockIdx.y;
+    j = blockIdx.z;
+  } else {
+    // runs are laid out one after another in the linear block index; rg[].blk
+    // holds each run's first block (index 0: kernels with A, 1: P^{-1} alone)
+    const int b0 = blockIdx.x;
+    int lo = 0, hi = R - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (rg[mid].blk[WITH_A ? 0 : 1] <= b0) lo = mid;
+      else hi = mid - 1;
+    }
+    const int run = lo;
+    int b = b0 - rg[run].blk[WITH_A ? 0 : 1];
+    const RunGeom& rq = rg[run];
+    g.nx = rq.nx;
+    g.ny = rq.ny;
+    g.Ly = g.Ly < rq.ny ? g.Ly : rq.ny;
+    g.wv = NT_ - 2 * S;
+    g.nstrips = (rq.nx + g.wv - 1) / g.wv;
+    g.nsegs = (rq.ny + g.Ly - 1) / g.Ly;
+    g.npart = g.nstrips * g.nsegs;
+    g.pts = rq.pts;
+    sx = b % g.nstrips;
+    b /= g.nstrips;
+    sy = b % g.nsegs;
+    j = b / g.nsegs;
+    ld.rebase(rq.elem_off, rq.pts);
+    ep.rebase(rq.elem_off, rq.pts);
+    if (act != nullptr) act += (long long)run * c.J;
+    if (partials != nullptr) partials = reinterpret_cast<char*>(partials) + 16ll * rq.part_off;
+  }
   if (act != nullptr && act[j].active == 0) return;
   const int t = threadIdx.x;
   const JCoef<T> q = jcoef<T>(c, j);
@@ -492,17 +588,18 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
   ep.setup(j, act);
 #pragma unroll
   for (int k = 0; k < EP::NDOT; ++k) ep.acc[k].zero();
-  if (c.prof != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && t == 0) atomicAdd(c.prof + kid, bytes_per_amp);
+  if (c.prof != nullptr && sx == 0 && sy == 0 && t == 0)
+    atomicAdd(c.prof + kid, (unsigned long long)fields * (unsigned long long)g.pts * sizeof(cplx<T>));
 
   // zero the rings (garbage in invalid halo columns must stay finite)
   for (int i = t; i < (int)SH::ring_elems; i += NT) sm[i] = mkc<T>((T)0, (T)0);
 
-  const int x_first = blockIdx.x * g.wv - S;  // global column of thread 0 (unwrapped)
+  const int x_first = sx * g.wv - S;  // global column of thread 0 (unwrapped)
   int gx = (x_first + t) % g.nx;
   if (gx < 0) gx += g.nx;
-  const int xo = blockIdx.x * g.wv + (t - S);  // output column of this thread
+  const int xo = sx * g.wv + (t - S);  // output column of this thread
   const bool col_own = (t >= S) && (t < NT - S) && (xo < g.nx);
-  const int y0 = blockIdx.y * g.Ly;
+  const int y0 = sy * g.Ly;
   const int rows_in = g.Ly + 2 * S;  // local rows 0 .. rows_in-1 = global y0-S ..
   const int steps = g.Ly + 3 * S;
 
@@ -745,7 +842,7 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
   if constexpr (PF > 0) cp_wait<0>();
 
   if constexpr (EP::NDOT > 0) {
-    const int blk = blockIdx.y * g.nstrips + blockIdx.x;
+    const int blk = sy * g.nstrips + sx;
 #pragma unroll
     for (int k = 0; k < EP::NDOT; ++k) {
       ep.acc[k].flush();
@@ -769,8 +866,8 @@ PipeGeom geom(const OpCoef& c, int S, int Ly, int NT) {
 }
 
 template <typename T, int M, bool WITH_A, int PF, int NT, class LD, class EP>
-void launch_pipe(const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const KScal* act, void* partials,
-                 cudaStream_t s, int kid, int fields) {
+bool launch_pipe(const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const KScal* act, void* partials,
+                 cudaStream_t s, int kid, int fields, const BatchLaunch* bl) {
   using SH = PipeShape<T, M, WITH_A, PF, NT, LD, EP>;
   const PipeGeom g = geom(c, SH::S, Ly, NT);
   constexpr size_t sm = SH::smem;
@@ -787,8 +884,23 @@ void launch_pipe(const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const
       ca.c1[k][i] = k < M ? w[k].c1[i] : 0.0;
       ca.c2[k][i] = k < M ? w[k].c2[i] : 0.0;
     }
-  const unsigned long long bytes = (unsigned long long)fields * (unsigned long long)g.pts * sizeof(cplx<T>);
-  kern<<<dim3(g.nstrips, g.nsegs, c.J), NT, sm, s>>>(c, ca, g, ld, ep, act, partials, kid, bytes);
+  if (bl == nullptr) {
+    kern<<<dim3(g.nstrips, g.nsegs, c.J), NT, sm, s>>>(c, ca, g, ld, ep, act, partials, kid, fields, nullptr, 0);
+    return true;
+  } else {
+    // every run's first block must match the table the kernel searches
+    int total = 0;
+    for (int r = 0; r < bl->R; ++r) {
+      if (bl->host[r].blk[WITH_A ? 0 : 1] != total) return false;
+      OpCoef cr = c;
+      cr.nx = bl->host[r].nx;
+      cr.ny = bl->host[r].ny;
+      const PipeGeom gr = geom(cr, SH::S, Ly, NT);
+      total += gr.nstrips * gr.nsegs * c.J;
+    }
+    if (total > 0) kern<<<dim3(total), NT, sm, s>>>(c, ca, g, ld, ep, act, partials, kid, fields, bl->dev, bl->R);
+    return true;
+  }
 }
 
 // Tile variants of the FP32 pipeline with one Chebyshev application (the default
@@ -807,29 +919,29 @@ int tile_nt(int elem_bytes, int m, int tile) {
 // complex field of precision T) reported to the measurement counters.
 template <typename T, bool WITH_A, class LD, class EP>
 bool dispatch(int m, int tile, const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const KScal* act,
-              void* partials, cudaStream_t s, int kid, int fields) {
+              void* partials, cudaStream_t s, int kid, int fields, const BatchLaunch* bl = nullptr) {
   if constexpr (sizeof(T) == 8) {
     switch (m) {
-      case 1: launch_pipe<T, 1, WITH_A, 0, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
-      case 2: launch_pipe<T, 2, WITH_A, 0, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
-      case 3: launch_pipe<T, 3, WITH_A, 0, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
-      case 4: launch_pipe<T, 4, WITH_A, 0, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+      case 1: return launch_pipe<T, 1, WITH_A, 0, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+      case 2: return launch_pipe<T, 2, WITH_A, 0, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+      case 3: return launch_pipe<T, 3, WITH_A, 0, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+      case 4: return launch_pipe<T, 4, WITH_A, 0, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
       default: return false;
     }
   } else {
     if (m == 1) {
       switch (tile) {
-        case 1: launch_pipe<T, 1, WITH_A, 1, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
-        case 2: launch_pipe<T, 1, WITH_A, 1, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
-        case 3: launch_pipe<T, 1, WITH_A, 2, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
-        case 4: launch_pipe<T, 1, WITH_A, 3, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
-        default: launch_pipe<T, 1, WITH_A, 2, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+        case 1: return launch_pipe<T, 1, WITH_A, 1, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+        case 2: return launch_pipe<T, 1, WITH_A, 1, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+        case 3: return launch_pipe<T, 1, WITH_A, 2, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+        case 4: return launch_pipe<T, 1, WITH_A, 3, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+        default: return launch_pipe<T, 1, WITH_A, 2, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
       }
     }
     switch (m) {
-      case 2: launch_pipe<T, 2, WITH_A, 2, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
-      case 3: launch_pipe<T, 3, WITH_A, 2, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
-      case 4: launch_pipe<T, 4, WITH_A, 2, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields); return true;
+      case 2: return launch_pipe<T, 2, WITH_A, 2, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+      case 3: return launch_pipe<T, 3, WITH_A, 2, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+      case 4: return launch_pipe<T, 4, WITH_A, 2, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
       default: return false;
     }
   }
@@ -876,6 +988,15 @@ int fused2d_npart(const OpCoef& c, int m, int Ly, int elem_bytes, int tile) {
 
 int fused2d_tiles() { return kTiles; }
 
+int fused2d_blocks(int nx, int ny, int J, int m, int Ly, int elem_bytes, int tile, bool with_a, int* npart) {
+  OpCoef c{};
+  c.nx = nx;
+  c.ny = ny;
+  const PipeGeom g = geom(c, 2 * m + 1 + (with_a ? 1 : 0), Ly, tile_nt(elem_bytes, m, tile));
+  if (npart) *npart = g.npart;
+  return g.npart * J;
+}
+
 template <typename T>
 bool launch_fused_v(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* p_old,
                     const cplx<T>* v_old, cplx<T>* p_new, cplx<T>* v_new, const cplx<T>* rhat, const KScal* act,
@@ -897,12 +1018,12 @@ bool launch_fused_t(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w,
 
 template <typename T>
 bool launch_fused_pinv_add(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* u, double2* x64,
-                           cudaStream_t s) {
+                           cudaStream_t s, const BatchLaunch* bl) {
   LoadPlain<T> ld{u, c.pts};
   EpAddX<T> ep{x64, c.pts};
   // reads u (2 fields); reads and writes the FP64 block x (2 FP64 fields each way)
   const int f = 2 + 4 * (int)(sizeof(double2) / sizeof(cplx<T>));
-  return dispatch<T, false>(m, tile, c, w, Ly, ld, ep, nullptr, nullptr, s, kid_of<T>(KID_FUSED_PINV), f);
+  return dispatch<T, false>(m, tile, c, w, Ly, ld, ep, nullptr, nullptr, s, kid_of<T>(KID_FUSED_PINV), f, bl);
 }
 
 template <typename T>
@@ -916,33 +1037,42 @@ bool launch_fused_pinv_store(int m, int Ly, int tile, const OpCoef& c, const Che
 template <typename T>
 bool launch_fused_merged_v(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
                            const cplx<T>* t, const cplx<T>* p, cplx<T>* u, cplx<T>* r_new, cplx<T>* p_new,
-                           cplx<T>* v_new, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s) {
+                           cplx<T>* v_new, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s,
+                           const BatchLaunch* bl) {
   LoadPR<T> ld{r, v, t, p, u, r_new, p_new, c.pts};
   EpV<T> ep{v_new, rhat, c.pts};
   // reads r, v, t, p, u, rhat; writes r', p', u, v' (2 fields each)
-  return dispatch<T, true>(m, tile, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV), 20);
+  return dispatch<T, true>(m, tile, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV), 20, bl);
 }
 
 template <typename T>
 bool launch_fused_merged_t(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
-                           cplx<T>* t_out, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s) {
+                           cplx<T>* t_out, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s,
+                           const BatchLaunch* bl) {
   LoadS<T> ld{r, v, c.pts};
   EpT5<T> ep{t_out, r, v, rhat, c.pts};
   // reads r, v, rhat; writes t
-  return dispatch<T, true>(m, tile, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV_T), 8);
+  return dispatch<T, true>(m, tile, c, w, Ly, ld, ep, act, partials, s, kid_of<T>(KID_FUSED_APINV_T), 8, bl);
 }
 
 // u += alpha p + omega (r - alpha v) for amplitudes whose solve stopped in this iteration.
+// Batched runs: blockIdx.z selects the run.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_final_update(const cplx<T>* __restrict__ r,
                                                            const cplx<T>* __restrict__ v,
                                                            const cplx<T>* __restrict__ p, cplx<T>* __restrict__ u,
-                                                           const KScal* ks, OpCoef c) {
+                                                           const KScal* ks, OpCoef c, const RunGeom* rg) {
   const int j = blockIdx.y;
+  long long o = 0;
+  if (rg != nullptr) {
+    o = select_run(rg, blockIdx.z, c);
+    ks += (long long)blockIdx.z * c.J;
+  }
   if (ks[j].just_done == 0) return;
   prof_add(c, kid_of<T>(KID_BICG_UPDATE), 10ull * (unsigned long long)c.pts * sizeof(cplx<T>));
   const cplx<T> al = to_c<T>(ks[j].alpha), om = to_c<T>(ks[j].omega);
-  const long long n = 2 * c.pts, o = 2LL * j * c.pts;
+  const long long n = 2 * c.pts;
+  o += 2LL * j * c.pts;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const long long q = o + i;
     const cplx<T> s = csub(r[q], cmulz(al, v[q]));
@@ -952,9 +1082,13 @@ __global__ void __launch_bounds__(kThreads) k_final_update(const cplx<T>* __rest
 
 template <typename T>
 void launch_final_update(const cplx<T>* r, const cplx<T>* v, const cplx<T>* p, cplx<T>* u, const KScal* ks,
-                         const OpCoef& c, cudaStream_t s) {
+                         const OpCoef& c, cudaStream_t s, const BatchLaunch* bl) {
   ProfScope ps_(kid_of<T>(KID_BICG_UPDATE), s);
-  k_final_update<T><<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(r, v, p, u, ks, c);
+  if (bl != nullptr) {
+    k_final_update<T><<<dim3(kDotBlocks, c.J, bl->R), kThreads, 0, s>>>(r, v, p, u, ks, c, bl->dev);
+    return;
+  }
+  k_final_update<T><<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(r, v, p, u, ks, c, nullptr);
 }
 
 template <typename T>
@@ -967,18 +1101,19 @@ void launch_bicg_update(cplx<T>* r, const cplx<T>* v, const cplx<T>* p, cplx<T>*
 #define APFC_FUSED_INST(T)                                                                                         \
   template bool launch_fused_merged_v<T>(int, int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*, \
                                          const cplx<T>*, const cplx<T>*, cplx<T>*, cplx<T>*, cplx<T>*, cplx<T>*,   \
-                                         const cplx<T>*, const KScal*, void*, cudaStream_t);                      \
+                                         const cplx<T>*, const KScal*, void*, cudaStream_t, const BatchLaunch*);  \
   template bool launch_fused_merged_t<T>(int, int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*, \
-                                         cplx<T>*, const cplx<T>*, const KScal*, void*, cudaStream_t);            \
+                                         cplx<T>*, const cplx<T>*, const KScal*, void*, cudaStream_t,             \
+                                         const BatchLaunch*);                                                     \
   template void launch_final_update<T>(const cplx<T>*, const cplx<T>*, const cplx<T>*, cplx<T>*, const KScal*,     \
-                                       const OpCoef&, cudaStream_t);                                              \
+                                       const OpCoef&, cudaStream_t, const BatchLaunch*);                          \
   template bool launch_fused_v<T>(int, int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*,        \
                                   const cplx<T>*, cplx<T>*, cplx<T>*, const cplx<T>*, const KScal*, void*,         \
                                   cudaStream_t);                                                                   \
   template bool launch_fused_t<T>(int, int, int, const OpCoef&, const ChebStep*, const cplx<T>*, const cplx<T>*,        \
                                   cplx<T>*, const KScal*, void*, cudaStream_t);                                    \
   template bool launch_fused_pinv_add<T>(int, int, int, const OpCoef&, const ChebStep*, const cplx<T>*, double2*,       \
-                                         cudaStream_t);                                                            \
+                                         cudaStream_t, const BatchLaunch*);                                        \
   template bool launch_fused_pinv_store<T>(int, int, int, const OpCoef&, const ChebStep*, const cplx<T>*, cplx<T>*,     \
                                            cudaStream_t);                                                          \
   template void launch_bicg_update<T>(cplx<T>*, const cplx<T>*, const cplx<T>*, cplx<T>*, const cplx<T>*,          \

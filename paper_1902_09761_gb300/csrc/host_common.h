@@ -1,0 +1,36 @@
+// Host-side helpers shared by the single-grid context (api.cu) and the batch
+// driver (batch.cu): validation, nonlinear-term tables, operator coefficients,
+// Chebyshev weights and the process-wide measurement state.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "apfc_internal.cuh"
+
+namespace apfc {
+
+// lattice and parameters of Sec. II (k_j finite, hex: J = 3 in 2D with sum k_j = 0,
+// bcc: J = 6 in 3D, Bx > 0)
+bool valid_problem(const apfc_lattice& lat, const apfc_params& p);
+bool valid_opts(const apfc_opts& o, std::string& err);
+
+// <n^p> resonance tables of the nonlinear term and the energy (Sec. II.A)
+bool build_tables(const apfc_lattice& L, const apfc_params& P, NonlinTable& nt, EnergyTable& et, std::string& err);
+
+// Operator coefficients of the block system for a time step dt on grid (n, h).
+bool make_coef(const apfc_lattice& lat, const apfc_params& par, const apfc_grid& grid, int tau_mode, double dt,
+               OpCoef& o, std::string& err);
+
+// Chebyshev recurrence weights for m applications of D (Saad, Sec. 12.3); they
+// depend on the spacing only, not on the grid size.
+std::vector<ChebStep> cheb_weights_for(const OpCoef& c, const apfc_grid& grid, int m);
+
+// Measurement (see apfc_profile_start): dev receives the device byte counters.
+bool profiler_start(cudaStream_t s, int timed_id, unsigned long long** dev, std::string& err);
+bool profiler_read(cudaStream_t s, int id, double* ms, long long* launches, double* bytes, long long* all_launches,
+                   std::string& err);
+void profiler_stop();
+bool profiler_on();
+
+}  // namespace apfc

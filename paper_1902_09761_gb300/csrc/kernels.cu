@@ -335,7 +335,14 @@ __device__ __forceinline__ double2 cm(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 
-__global__ void k_rhs(const double2* __restrict__ x, double2* __restrict__ b, OpCoef c, NonlinTable nt) {
+// Batched runs (rg != nullptr): blockIdx.y selects the run.
+__global__ void k_rhs(const double2* __restrict__ x, double2* __restrict__ b, OpCoef c, NonlinTable nt,
+                      const RunGeom* rg) {
+  if (rg != nullptr) {
+    const long long o = select_run(rg, blockIdx.y, c);
+    x += o;
+    b += o;
+  }
   prof_add(c, KID_RHS, 2ull * c.J * (unsigned long long)c.pts * sizeof(double2));
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= c.pts) return;
@@ -446,8 +453,16 @@ __global__ void k_residual_refine(const double2* __restrict__ b, const double2* 
 __global__ void __launch_bounds__(256) k_residual_refine2d(const double2* __restrict__ b,
                                                            const double2* __restrict__ x, float2* __restrict__ r32,
                                                            double2* __restrict__ r64, double2* __restrict__ partials,
-                                                           OpCoef c) {
+                                                           OpCoef c, const RunGeom* rg) {
   const int j = blockIdx.y;
+  if (rg != nullptr) {  // batched runs: blockIdx.z selects the run
+    const long long ro = select_run(rg, blockIdx.z, c);
+    b += ro;
+    x += ro;
+    r32 += ro;
+    if (r64 != nullptr) r64 += ro;
+    partials += (long long)blockIdx.z * c.J * kDotSlots * kDotBlocks;
+  }
   prof_add(c, KID_RESID_REFINE,
            (unsigned long long)c.pts * (4 * sizeof(double2) + 2 * sizeof(float2) + (r64 ? 2 * sizeof(double2) : 0)));
   const long long o = 2LL * j * c.pts;
@@ -501,7 +516,17 @@ __global__ void __launch_bounds__(256) k_residual_refine2d(const double2* __rest
 __global__ void __launch_bounds__(256) k_rhs_resid(const double2* __restrict__ x, double2* __restrict__ b,
                                                    const double2* __restrict__ b_prev,
                                                    const double2* __restrict__ r_prev, float2* __restrict__ r32,
-                                                   double2* __restrict__ partials, OpCoef c, NonlinTable nt) {
+                                                   double2* __restrict__ partials, OpCoef c, NonlinTable nt,
+                                                   const RunGeom* rg) {
+  if (rg != nullptr) {  // batched runs: blockIdx.y selects the run
+    const long long ro = select_run(rg, blockIdx.y, c);
+    x += ro;
+    b += ro;
+    b_prev += ro;
+    r_prev += ro;
+    r32 += ro;
+    partials += (long long)blockIdx.y * c.J * kDotSlots * kDotBlocks;
+  }
   prof_add(c, KID_RHS, (unsigned long long)c.J * c.pts * (5 * sizeof(double2) + 2 * sizeof(float2)));
   float accf[2 * kMaxJ];
 #pragma unroll
@@ -1004,9 +1029,12 @@ void launch_add_to(const cplx<T>* d, double2* x, const OpCoef& c, cudaStream_t s
   k_add_to<T><<<(unsigned)((n + kThreads - 1) / kThreads), kThreads, 0, s>>>(d, x, n, c);
 }
 
-void launch_rhs(const double2* x, double2* b, const OpCoef& c, const NonlinTable& nt, cudaStream_t s) {
+void launch_rhs(const double2* x, double2* b, const OpCoef& c, const NonlinTable& nt, cudaStream_t s,
+                const BatchLaunch* bl) {
   ProfScope ps_(KID_RHS, s);
-  k_rhs<<<(unsigned)((c.pts + kThreads - 1) / kThreads), kThreads, 0, s>>>(x, b, c, nt);
+  // batched: c.pts is the largest run's point count
+  const dim3 g((unsigned)((c.pts + kThreads - 1) / kThreads), bl ? bl->R : 1);
+  k_rhs<<<g, kThreads, 0, s>>>(x, b, c, nt, bl ? bl->dev : nullptr);
 }
 void launch_zeta(double2* x, const OpCoef& c, cudaStream_t s) {
   if (c.dim == 3) {
@@ -1024,9 +1052,10 @@ void launch_residual_refine(const double2* b, const double2* x, float2* r32, dou
   k_residual_refine<<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(b, x, r32, reinterpret_cast<double2*>(partials), c);
 }
 void launch_residual_refine2d(const double2* b, const double2* x, float2* r32, double2* r64, double* partials,
-                              const OpCoef& c, cudaStream_t s) {
+                              const OpCoef& c, cudaStream_t s, const BatchLaunch* bl) {
   ProfScope ps_(KID_RESID_REFINE, s);
-  k_residual_refine2d<<<dim3(kDotBlocks, c.J), 256, 0, s>>>(b, x, r32, r64, reinterpret_cast<double2*>(partials), c);
+  k_residual_refine2d<<<dim3(kDotBlocks, c.J, bl ? bl->R : 1), 256, 0, s>>>(
+      b, x, r32, r64, reinterpret_cast<double2*>(partials), c, bl ? bl->dev : nullptr);
 }
 void launch_residual_refine3d(const double2* b, const double2* x, float2* r32, double2* r64, const OpCoef& c,
                               cudaStream_t s) {
@@ -1036,9 +1065,11 @@ void launch_residual_refine3d(const double2* b, const double2* x, float2* r32, d
   k_stream3d<double, OpResRefine3><<<grid_stream3d(c), 256, 0, s>>>(c, op, nullptr);
 }
 void launch_rhs_resid(const double2* x, double2* b, const double2* b_prev, const double2* r_prev, float2* r32,
-                      double* partials, const OpCoef& c, const NonlinTable& nt, cudaStream_t s) {
+                      double* partials, const OpCoef& c, const NonlinTable& nt, cudaStream_t s,
+                      const BatchLaunch* bl) {
   ProfScope ps_(KID_RHS, s);
-  k_rhs_resid<<<kDotBlocks, kThreads, 0, s>>>(x, b, b_prev, r_prev, r32, reinterpret_cast<double2*>(partials), c, nt);
+  k_rhs_resid<<<dim3(kDotBlocks, bl ? bl->R : 1), kThreads, 0, s>>>(
+      x, b, b_prev, r_prev, r32, reinterpret_cast<double2*>(partials), c, nt, bl ? bl->dev : nullptr);
 }
 void launch_energy(const double2* x, double* partials, double* out, const OpCoef& c, const EnergyTable& et, double Bx,
                    cudaStream_t s) {

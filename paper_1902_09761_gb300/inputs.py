@@ -156,3 +156,22 @@ def bcc_sphere(phi, n=256, radius=60.0, seed=2):
     """3D bcc, n^3, h = pi/2, sphere R = 60 rotated 8 deg about [001] in an unrotated matrix."""
     h = (HEX_H,) * 3
     return single_grain(bcc_vectors(), phi, (n, n, n), h, radius, 8.0, seed=seed, noise=1e-3, matrix=phi)
+
+
+def batch_spec(nruns=64, sizes=(128, 256, 512, 1024), theta_max_deg=10.0, seed=7):
+    """Independent 2D hexagonal runs: grid size N drawn uniformly from ``sizes``
+    (N x N), grain rotation U[-max, max] deg, and a noise seed per run.
+    Returns a list of (N, theta_deg, noise_seed)."""
+    rng = np.random.default_rng(seed)
+    ns = rng.choice(np.asarray(sizes), size=nruns)
+    th = rng.uniform(-theta_max_deg, theta_max_deg, size=nruns)
+    return [(int(ns[r]), float(th[r]), int(seed * 100003 + r)) for r in range(nruns)]
+
+
+def batch_run_state(phi, n, theta_deg, noise_seed, shape=None):
+    """One run of a batch: a circular grain of radius n h / 4 (a fifth of the box
+    area) rotated ``theta_deg`` in liquid at the centre of an n x n hexagonal box
+    (or of ``shape``), h = pi/2, noise 1e-3."""
+    shape = (n, n) if shape is None else tuple(shape)
+    radius = 0.25 * min(shape) * HEX_H
+    return single_grain(hex_vectors(), phi, shape, (HEX_H, HEX_H), radius, theta_deg, seed=noise_seed, noise=1e-3)

@@ -118,3 +118,47 @@ def test_binding_fails_loudly_without_library(tmp_path):
             A.load(str(tmp_path / "missing.so"))
     finally:
         A._lib = saved
+
+
+@pytest.mark.parametrize("case", ["nruns0", "nx2", "bcc", "fp64", "unfused", "flags", "hx0", "cheb5"])
+def test_batch_init_rejects_invalid_arguments_before_touching_cuda(lib, case):
+    import ctypes as C
+
+    k, kind = O.hex_k(), A.APFC_LATTICE_HEX2D
+    prm = A.make_params(P.dB, P.Bx, P.t, P.v)
+    opts = A.apfc_default_opts(precision=A.APFC_FP32_REFINED)
+    nx, ny, R, hx, flags = [64, 128], [64, 96], 2, 1.0, 0
+    if case == "nruns0":
+        R = 0
+    elif case == "nx2":
+        nx[1] = 2
+    elif case == "bcc":
+        k, kind = O.bcc_k(), A.APFC_LATTICE_BCC3D
+    elif case == "fp64":
+        opts.precision = A.APFC_FP64
+    elif case == "unfused":
+        opts.fused = 0
+    elif case == "flags":
+        flags = 6
+    elif case == "hx0":
+        hx = 0.0
+    elif case == "cheb5":
+        opts.cheb_degree = 5
+    L = A.make_lattice(k, kind)
+    h_ = C.c_void_p()
+    st = lib.apfc_batch_init(
+        C.byref(h_), C.byref(L), C.byref(prm), R, (C.c_int * 2)(*nx), (C.c_int * 2)(*ny), hx, 1.0, C.byref(opts),
+        flags, None,
+    )
+    assert st == A.APFC_EINVAL
+    assert not h_.value
+
+
+def test_batch_spec_draws_sizes_and_rotations():
+    from paper_1902_09761_gb300 import inputs
+
+    spec = inputs.batch_spec(64, seed=7)
+    assert len(spec) == 64
+    assert {n for n, _, _ in spec} <= {128, 256, 512, 1024} and len({n for n, _, _ in spec}) == 4
+    assert all(-10 <= th <= 10 for _, th, _ in spec)
+    assert spec == inputs.batch_spec(64, seed=7)
