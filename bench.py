@@ -58,6 +58,14 @@ def parse():
     ap.add_argument("--tol-inner", type=float, default=1e-4, help="relative tolerance of each FP32 inner solve")
     ap.add_argument("--breakdown-steps", type=int, default=3, help="steps of the per-kernel timing pass (0: off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument(
+        "--workload", choices=["voronoi", "batch"], default="voronoi",
+        help="voronoi: one n x n polycrystal (default); batch: independent runs of uneven sizes in one batch",
+    )
+    ap.add_argument("--runs", type=int, default=64, help="batch: number of independent runs")
+    ap.add_argument("--no-graph", action="store_true", help="batch: launch the Krylov blocks without graphs")
+    ap.add_argument("--no-autotune", action="store_true", help="batch: keep --tile / --rows")
+    ap.add_argument("--alone-steps", type=int, default=4, help="batch: steps of each run alone (0: skip)")
     return ap.parse_args()
 
 
@@ -441,6 +449,267 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Batched workload: independent hexagonal runs of uneven sizes
+# ---------------------------------------------------------------------------
+
+BATCH_SIZES = (128, 256, 512, 1024)
+
+
+def batch_config(args, spec, tuned=None):
+    ns = [n for n, _, _ in spec]
+    cfg = {
+        "workload": f"hex2d-batch{len(spec)}-N{min(BATCH_SIZES)}-{max(BATCH_SIZES)}",
+        "lattice": "triangular, J=3",
+        "runs": len(spec),
+        "sizes": {str(n): ns.count(n) for n in BATCH_SIZES},
+        "grain": "one circular grain (radius N h / 4) per run, rotation U[-10, 10] deg, in liquid",
+        "h": "pi/2",
+        "dt": 1.0,
+        "params": {"dB": PARAMS[0], "Bx": PARAMS[1], "t": PARAMS[2], "v": PARAMS[3]},
+        "tol": TOL,
+        "tol_inner": TOL_INNER,
+        "cheb_degree": CHEB,
+        "graph": not args.no_graph,
+        "l2": "inputs larger than L2 (FP64 state of all runs about 2 GB); no flush",
+    }
+    if tuned:
+        cfg["autotuned"] = tuned
+    return cfg
+
+
+def batch_states(spec, phi):
+    from paper_1902_09761_gb300 import inputs
+
+    return [inputs.batch_run_state(phi, n, th, seed) for n, th, seed in spec]
+
+
+def oracle_batch_rate(spec, states):
+    """Oracle step time of one run of each size, summed over the batch's runs."""
+    import oracle as O
+
+    P = O.params_from_paper(0.98, 0.01, 0.25, 0.5)
+    L = O.hex_lattice()
+    per_n, total_s, dof = {}, 0.0, 0
+    for (n, _, _), eta in zip(spec, states):
+        if n not in per_n:
+            t0 = time.perf_counter()
+            O.step(eta, 1.0, P, L, (H, H))
+            per_n[n] = time.perf_counter() - t0
+        total_s += per_n[n]
+        dof += 3 * n * n
+    sample = (
+        "one oracle FP64 step (numpy, exact FFT Schur solve) of one run of each size "
+        + ", ".join(f"{n}^2 {per_n[n]:.2f} s" for n in sorted(per_n))
+        + f"; batch step estimated as the sum over its {len(spec)} runs"
+    )
+    return dof / total_s, total_s, sample
+
+
+def run_batch_reference(args):
+    world, rank, local = init_dist(args)
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1902_09761_gb300 import inputs
+
+    P = O.params_from_paper(0.98, 0.01, 0.25, 0.5)
+    spec = inputs.batch_spec(args.runs, BATCH_SIZES, seed=7)
+    states = batch_states(spec, O.uniform_solid_hex(P))
+    rate, secs, sample = oracle_batch_rate(spec, states)
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": rate,
+        "unit": UNIT,
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": batch_config(args, spec),
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    import torch
+
+    world, rank, local = init_dist(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1902_09761_gb300 import apfc as A
+    from paper_1902_09761_gb300 import inputs
+
+    A.load()
+    k = inputs.hex_vectors()
+    lat = A.make_lattice(k, A.APFC_LATTICE_HEX2D)
+    prm = A.make_params(*PARAMS)
+    phi = A.apfc_uniform_amplitude(lat, prm)
+    spec = inputs.batch_spec(args.runs, BATCH_SIZES, seed=7 + rank)
+    states = batch_states(spec, phi)
+    shapes = [(n, n) for n, _, _ in spec]
+    dof = 3 * sum(n * n for n, _, _ in spec)
+    stream = torch.cuda.Stream(dev)  # graph capture needs a non-default stream
+
+    opts = A.apfc_default_opts(
+        precision=A.APFC_FP32_REFINED, tol=TOL, cheb_degree=args.cheb, tol_inner=args.tol_inner, tile=args.tile,
+        tile_rows=args.rows,
+    )
+    b = A.Batch(k, A.APFC_LATTICE_HEX2D, prm, shapes, (H, H), opts, graph=not args.no_graph,
+                stream=stream.cuda_stream)
+    dev_states = [torch.from_numpy(e).to(dev) for e in states]
+
+    def reset():
+        for r, e in enumerate(dev_states):
+            b.set_amplitudes(r, e)
+
+    tuned = None
+    reset()
+    if not args.no_autotune:
+        tuned = b.autotune(1.0)
+
+    def timed(nsteps, sampler=None):
+        reset()
+        b.step(1.0, args.warmup)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        if sampler:
+            sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(1.0, nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        clocks = sampler.stop() if sampler else None
+        barrier(world)
+        return allmax(world, e0.elapsed_time(e1), dev), clocks
+
+    # --- headline: all runs in one batch (graphs on, no measurement hooks) ----------
+    sampler = ClockSampler(local)
+    ms, clocks = timed(args.steps, sampler)
+    stats = [b.stats(r) for r in range(len(spec))]
+    value = world * dof * args.steps / (ms * 1e-3)
+    replays = b.graph_replays()
+
+    # --- measurement pass: dominant kernel and launch count -------------------------
+    reset()
+    b.step(1.0, args.warmup)
+    b.profile_start(args.timed_kernel)
+    torch.cuda.synchronize(dev)
+    b.step(1.0, max(args.breakdown_steps, 1))
+    prof = b.profile_read(args.timed_kernel)
+    b.profile_stop()
+    peak, peak_src = measured_peaks()
+    avg_ms = prof["ms"] / max(prof["launches"], 1)
+    bytes_per_launch = prof["bytes"] / max(prof["launches"], 1)
+    achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else None
+    launches_per_step = prof["all_launches"] / max(args.breakdown_steps, 1)
+
+    # --- end to end through the C ABI with pinned host buffers ------------------------
+    h_in = [torch.from_numpy(e).pin_memory() for e in states]
+    h_out = [torch.empty(e.shape, dtype=torch.complex128).pin_memory().numpy() for e in states]
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        for r in range(len(spec)):
+            b.set_amplitudes(r, h_in[r])
+        b.step(1.0, 1)
+        for r in range(len(spec)):
+            b.get_amplitudes(r, h_out[r])
+    torch.cuda.synchronize(dev)
+    e2e_s = allmax(world, time.perf_counter() - t0, dev)
+    e2e = world * dof * args.e2e_steps / e2e_s
+    bytes_step = sum(e.nbytes for e in states)
+    tuned_opts = b.opts
+    b.close()
+
+    # --- the same runs one at a time: FP32-refined and plain FP64 ---------------------
+    def alone(o, nsteps):
+        if nsteps <= 0:
+            return None
+        total = 0.0
+        for r, (n, _, _) in enumerate(spec):
+            with A.Context(k, A.APFC_LATTICE_HEX2D, prm, (n, n), (H, H), o, stream=stream.cuda_stream) as c:
+                c.set_amplitudes(dev_states[r])
+                c.step(1.0, args.warmup)
+                torch.cuda.synchronize(dev)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                c.step(1.0, nsteps)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                total += e0.elapsed_time(e1) / nsteps
+        return total
+
+    alone32 = alone(tuned_opts, args.alone_steps)
+    alone64 = alone(
+        A.apfc_default_opts(precision=A.APFC_FP64, tol=TOL, cheb_degree=args.cheb), min(args.alone_steps, args.fp64_steps)
+    )
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, secs, sample = oracle_batch_rate(spec, states)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    if rank != 0:
+        return
+    ms_step = ms / args.steps
+    per_n = {}
+    for (n, _, _), st in zip(spec, stats):
+        per_n.setdefault(str(n), []).append(st["iters_last"])
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 Krylov + f64 refinement",
+        "data": "synthetic",
+        "config": dict(batch_config(args, spec, tuned), parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
+        "per_run_ms_per_step": ms_step / len(spec),
+        "iters_last_by_size": {n: max(v) for n, v in per_n.items()},
+        "resid_last_max": max(st["resid_last"] for st in stats),
+        "graph_replays": replays,
+        "alone_fp32_refined_ms_per_step": alone32,
+        "alone_fp64_ms_per_step": alone64,
+        "speedup_batch_vs_alone_fp32_refined": (alone32 / ms_step) if alone32 else None,
+        "speedup_batch_vs_alone_fp64": (alone64 / ms_step) if alone64 else None,
+        "roofline": {
+            "bound": "hbm",
+            "kernel": args.timed_kernel,
+            "achieved": achieved,
+            "peak": peak,
+            "peak_source": peak_src,
+            "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": None,
+            "algorithmic_bytes_per_launch": bytes_per_launch,
+            "avg_launch_ms": avg_ms,
+            "launches": prof["launches"],
+        },
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step},
+        "gpu_launches_per_step": launches_per_step,
+        "gpu_launches": int(launches_per_step * args.steps),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 CHEB = 1
 TOL_INNER = 1e-4
 
@@ -449,7 +718,9 @@ def main():
     global CHEB, TOL_INNER
     args = parse()
     CHEB, TOL_INNER = args.cheb, args.tol_inner
-    if args.impl == "reference":
+    if args.workload == "batch":
+        run_batch_reference(args) if args.impl == "reference" else run_batch(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -127,13 +127,12 @@ __device__ __forceinline__ void prof_add(const OpCoef& c, int kid, unsigned long
 struct RunGeom {
   int nx, ny;
   long long pts, elem_off, part_off;
-  int blk[2];  // first block of the run in a fused launch: [0] with A, [1] P^{-1} alone
-  int npart;   // partial-sum slots per amplitude of the fused kernels with A
+  int npart;  // partial-sum slots per amplitude of the fused kernels with A
   int pad;
 };
 struct BatchLaunch {
-  const RunGeom* dev;   // device copy of the run table
-  const RunGeom* host;  // host copy (launch sizes)
+  const RunGeom* dev;   // device copy of the run table (per-point kernels, reductions)
+  const RunGeom* host;  // host copy (the fused kernels carry it in their parameters)
   int R;
 };
 

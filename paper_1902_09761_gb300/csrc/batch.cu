@@ -92,12 +92,12 @@ apfc_status bfail(apfc_batch* b, apfc_status s, const std::string& msg) {
 
 int rows_of(const apfc_opts& o) { return o.tile_rows > 0 ? o.tile_rows : kDefaultRows; }
 
-// Run table for (tile, rows): element offsets, fused-launch block offsets and
-// partial-sum offsets of every run.  Returns the partial slots it needs, or -1
-// when a launch would exceed the grid limit.
+// Run table for (tile, rows): element offsets and partial-sum offsets of every
+// run.  Returns the partial slots it needs, or -1 when a fused launch would
+// exceed the grid limit.
 long long make_table(const apfc_batch* b, int tile, int rows, std::vector<RunGeom>& t) {
   t.resize(b->R);
-  long long eoff = 0, poff = 0, blk_a = 0, blk_p = 0;
+  long long eoff = 0, poff = 0;
   const int m = b->opts.cheb_degree, eb = (int)sizeof(float2);
   for (int r = 0; r < b->R; ++r) {
     RunGeom& g = t[r];
@@ -107,15 +107,13 @@ long long make_table(const apfc_batch* b, int tile, int rows, std::vector<RunGeo
     g.pts = (long long)g.nx * g.ny;
     g.elem_off = eoff;
     g.part_off = poff;
-    g.blk[0] = (int)blk_a;
-    g.blk[1] = (int)blk_p;
     int np = 0;
-    blk_a += fused2d_blocks(g.nx, g.ny, b->J, m, rows, eb, tile, true, &np);
-    blk_p += fused2d_blocks(g.nx, g.ny, b->J, m, rows, eb, tile, false, nullptr);
+    const long long nb = fused2d_blocks(g.nx, g.ny, b->J, m, rows, eb, tile, false, nullptr);
+    fused2d_blocks(g.nx, g.ny, b->J, m, rows, eb, tile, true, &np);
     g.npart = np;
     eoff += 2LL * b->J * g.pts;
     poff += (long long)b->J * kDotSlots * np;
-    if (blk_a > 0x7fffffffLL || blk_p > 0x7fffffffLL) return -1;
+    if (nb > 0x7fffffffLL) return -1;
   }
   return poff;
 }

@@ -26,6 +26,8 @@
 #include "acc.cuh"
 #include "apfc_internal.cuh"
 
+#include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 namespace apfc {
@@ -525,11 +527,30 @@ __device__ __forceinline__ Nbh<T> fetch_d(const cplx<T>* ring, int mask, int row
   return n;
 }
 
+
+// Batched runs: the geometry of up to kTabRuns runs of one launch travels in
+// the kernel parameters (a constant-bank table indexed by blockIdx.y), so that
+// the work-item indices and grid sizes stay block-uniform values.
+constexpr int kTabRuns = 64;
+struct RunRec {
+  long long pts, elem_off, part_off;
+  int nx, ny, Ly, nstrips, nsegs, nblk, run, pad;
+};
+struct RunTab {
+  RunRec run[kTabRuns];
+};
+struct NoTab {};
+
+// ---------------------------------------------------------------------------
 __device__ __forceinline__ int wrap_inc(int y, int n) { return y + 1 == n ? 0 : y + 1; }
 
-template <typename T, int M, bool WITH_A, int PF, int NT_, class LD, class EP>
+// Grid: (nstrips, nsegs, J) for one grid (TAB = NoTab); for batched runs
+// (TAB = RunTab) (blocks of the largest run, runs of the table), each block
+// taking item blockIdx.x = sx + nstrips (sy + nsegs j) of run blockIdx.y.
+template <typename T, int M, bool WITH_A, int PF, int NT_, class LD, class EP, class TAB>
 __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g, LD ld, EP ep, const KScal* act,
-                                                void* partials, int kid, int fields, const RunGeom* rg, int R) {
+                                                void* partials, int kid, int fields,
+                                                const __grid_constant__ TAB tab) {
   using SH = PipeShape<T, M, WITH_A, PF, NT_, LD, EP>;
   constexpr int NT = SH::NT;
   constexpr int S = SH::S;
@@ -539,41 +560,30 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
   cplx<T>* stage_buf = sm + SH::ring_elems;
 
-  // work item: strip sx, row segment sy, amplitude j (of run `run` when batched)
+  // work item: strip sx, row segment sy, amplitude j (of run blockIdx.y when batched)
   int sx, sy, j;
-  if (rg == nullptr) {
+  if constexpr (std::is_same<TAB, RunTab>::value) {
+    const RunRec& rq = tab.run[blockIdx.y];
+    const int b = blockIdx.x;
+    if (b >= rq.nblk) return;
+    g.nx = rq.nx;
+    g.ny = rq.ny;
+    g.Ly = rq.Ly;
+    g.nstrips = rq.nstrips;
+    g.nsegs = rq.nsegs;
+    g.npart = rq.nstrips * rq.nsegs;
+    g.pts = rq.pts;
+    sx = b % rq.nstrips;
+    sy = (b / rq.nstrips) % rq.nsegs;
+    j = b / g.npart;
+    ld.rebase(rq.elem_off, rq.pts);
+    ep.rebase(rq.elem_off, rq.pts);
+    if (act != nullptr) act += (long long)rq.run * c.J;
+    if (partials != nullptr) partials = reinterpret_cast<char*>(partials) + 16ll * rq.part_off;
+  } else {
     sx = blockIdx.x;
     sy = blockIdx.y;
     j = blockIdx.z;
-  } else {
-    // runs are laid out one after another in the linear block index; rg[].blk
-    // holds each run's first block (index 0: kernels with A, 1: P^{-1} alone)
-    const int b0 = blockIdx.x;
-    int lo = 0, hi = R - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (rg[mid].blk[WITH_A ? 0 : 1] <= b0) lo = mid;
-      else hi = mid - 1;
-    }
-    const int run = lo;
-    int b = b0 - rg[run].blk[WITH_A ? 0 : 1];
-    const RunGeom& rq = rg[run];
-    g.nx = rq.nx;
-    g.ny = rq.ny;
-    g.Ly = g.Ly < rq.ny ? g.Ly : rq.ny;
-    g.wv = NT_ - 2 * S;
-    g.nstrips = (rq.nx + g.wv - 1) / g.wv;
-    g.nsegs = (rq.ny + g.Ly - 1) / g.Ly;
-    g.npart = g.nstrips * g.nsegs;
-    g.pts = rq.pts;
-    sx = b % g.nstrips;
-    b /= g.nstrips;
-    sy = b % g.nsegs;
-    j = b / g.nsegs;
-    ld.rebase(rq.elem_off, rq.pts);
-    ep.rebase(rq.elem_off, rq.pts);
-    if (act != nullptr) act += (long long)run * c.J;
-    if (partials != nullptr) partials = reinterpret_cast<char*>(partials) + 16ll * rq.part_off;
   }
   if (act != nullptr && act[j].active == 0) return;
   const int t = threadIdx.x;
@@ -865,18 +875,23 @@ PipeGeom geom(const OpCoef& c, int S, int Ly, int NT) {
   return g;
 }
 
+template <typename T, int M, bool WITH_A, int PF, int NT, class LD, class EP, class TAB>
+void set_smem_attr() {
+  using SH = PipeShape<T, M, WITH_A, PF, NT, LD, EP>;
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_pipe2d<T, M, WITH_A, PF, NT, LD, EP, TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)SH::smem);
+    done = true;
+  }
+}
+
 template <typename T, int M, bool WITH_A, int PF, int NT, class LD, class EP>
 bool launch_pipe(const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const KScal* act, void* partials,
                  cudaStream_t s, int kid, int fields, const BatchLaunch* bl) {
   using SH = PipeShape<T, M, WITH_A, PF, NT, LD, EP>;
   const PipeGeom g = geom(c, SH::S, Ly, NT);
   constexpr size_t sm = SH::smem;
-  auto kern = k_pipe2d<T, M, WITH_A, PF, NT, LD, EP>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    attr_set = true;
-  }
   ProfScope ps_(kid, s);
   ChebAll ca;
   for (int k = 0; k < kMaxCheb; ++k)
@@ -885,20 +900,44 @@ bool launch_pipe(const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const
       ca.c2[k][i] = k < M ? w[k].c2[i] : 0.0;
     }
   if (bl == nullptr) {
-    kern<<<dim3(g.nstrips, g.nsegs, c.J), NT, sm, s>>>(c, ca, g, ld, ep, act, partials, kid, fields, nullptr, 0);
+    set_smem_attr<T, M, WITH_A, PF, NT, LD, EP, NoTab>();
+    k_pipe2d<T, M, WITH_A, PF, NT, LD, EP, NoTab>
+        <<<dim3(g.nstrips, g.nsegs, c.J), NT, sm, s>>>(c, ca, g, ld, ep, act, partials, kid, fields, NoTab{});
     return true;
+  }
+  if constexpr (sizeof(T) == 8) {
+    return false;  // batched runs are FP32
   } else {
-    // every run's first block must match the table the kernel searches
-    int total = 0;
-    for (int r = 0; r < bl->R; ++r) {
-      if (bl->host[r].blk[WITH_A ? 0 : 1] != total) return false;
-      OpCoef cr = c;
-      cr.nx = bl->host[r].nx;
-      cr.ny = bl->host[r].ny;
-      const PipeGeom gr = geom(cr, SH::S, Ly, NT);
-      total += gr.nstrips * gr.nsegs * c.J;
+    set_smem_attr<T, M, WITH_A, PF, NT, LD, EP, RunTab>();
+    // one launch per kTabRuns runs; the table holds this launch's geometry of each run
+    for (int r0 = 0; r0 < bl->R; r0 += kTabRuns) {
+      const int nr = std::min(kTabRuns, bl->R - r0);
+      RunTab tab;
+      std::memset(&tab, 0, sizeof(tab));
+      int maxblk = 0;
+      for (int i = 0; i < nr; ++i) {
+        const RunGeom& q = bl->host[r0 + i];
+        OpCoef cr = c;
+        cr.nx = q.nx;
+        cr.ny = q.ny;
+        const PipeGeom gr = geom(cr, SH::S, Ly, NT);
+        RunRec& e = tab.run[i];
+        e.pts = q.pts;
+        e.elem_off = q.elem_off;
+        e.part_off = q.part_off;
+        e.nx = q.nx;
+        e.ny = q.ny;
+        e.Ly = gr.Ly;
+        e.nstrips = gr.nstrips;
+        e.nsegs = gr.nsegs;
+        e.nblk = gr.npart * c.J;
+        e.run = r0 + i;
+        if (WITH_A && gr.npart != q.npart) return false;  // partial layout must match the run table
+        maxblk = std::max(maxblk, e.nblk);
+      }
+      k_pipe2d<T, M, WITH_A, PF, NT, LD, EP, RunTab>
+          <<<dim3(maxblk, nr), NT, sm, s>>>(c, ca, g, ld, ep, act, partials, kid, fields, tab);
     }
-    if (total > 0) kern<<<dim3(total), NT, sm, s>>>(c, ca, g, ld, ep, act, partials, kid, fields, bl->dev, bl->R);
     return true;
   }
 }
