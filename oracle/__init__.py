@@ -14,3 +14,4 @@ Parity status per function is listed in the module docstring of
 ``oracle.apfc``.
 """
 from .apfc import *  # noqa: F401,F403
+from .adjoint import *  # noqa: F401,F403
