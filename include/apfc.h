@@ -232,6 +232,49 @@ apfc_status apfc_profile_read(apfc_ctx* ctx, int id, double* ms, long long* laun
                               long long* all_launches);
 apfc_status apfc_profile_stop(apfc_ctx* ctx);
 
+/* ---- parameters and the adjoint of the step ---------------------------------
+ * Gradient convention: for a real loss L of complex fields, the gradient with
+ * respect to a field eta is the complex field dL/dRe(eta) + i dL/dIm(eta) (twice
+ * the Wirtinger derivative dL/d conj(eta); PyTorch's convention), so that
+ * dL = Re sum conj(grad) d(eta).  Fields are [J][nz][ny][nx] complex128. */
+
+/* Replace (dB, Bx, t, v) (validated as in apfc_init); the state is kept.  The
+ * next step rebuilds the coefficients; a recorded rollout is dropped. */
+apfc_status apfc_set_params(apfc_ctx* ctx, const apfc_params* p);
+
+/* Adjoint of one step of size dt (the map eta^n -> eta^{n+1} of apfc_step: per
+ * amplitude eta_j^{n+1} = S_j^{-1} (eta_j^n/dt - kap_j N_j(eta^n)) with
+ * S_j = (1/dt + kap_j dB) I + kap_j Bx G_h^2, kap_j = |k_j|^2).  Given
+ * lam_np1 = grad of L wrt eta^{n+1}, returns lam_n = grad of L wrt eta^n
+ * through this step and *dB_grad = dL/d dB through S:
+ *   g_j = S_j^{-1} lam_np1_j   (S_j is Hermitian since G_h is: the adjoint solve
+ *                               is the block solve of the step with right-hand
+ *                               side (0, lam_np1_j), to opts.tol in opts.precision),
+ *   lam_n_k = g_k/dt - sum_j kap_j [g_j conj(dN_j/d eta_k) + conj(g_j) dN_j/d conj(eta_k)],
+ *   *dB_grad = -sum_j kap_j Re sum_points conj(g_j) eta_np1_j.
+ * eta_n, eta_np1: the step's input and output.  The solve starts from zero. */
+apfc_status apfc_adjoint_step(apfc_ctx* ctx, double dt, const void* eta_n, const void* eta_np1,
+                              const void* lam_np1, void* lam_n, double* dB_grad, int where);
+
+/* Gradient of the free energy F of apfc_energy at eta:
+ *   grad_j = 2 h^d [ (dB + Bx G_h^2) eta_j + N_j(eta) ],
+ * and *dF_ddB = h^d sum_points sum_j |eta_j|^2 (F is affine in dB); dF_ddB may be NULL. */
+apfc_status apfc_energy_gradient(apfc_ctx* ctx, const void* eta, void* grad, double* dF_ddB, int where);
+
+/* Checkpointed rollout.  apfc_rollout_forward advances the state n steps of size
+ * dt like apfc_step, keeping eta every `every` steps and at the end on the device
+ * (owned by the context: (ceil(n/every) + 1) fields).  At each checkpoint the
+ * step restarts from (G_h eta, eta) without the previous step's residual, so that
+ * the backward pass can recompute every segment bit for bit.
+ * apfc_rollout_backward takes lam_n = grad of L wrt eta^n and returns
+ * lam_0 = grad of L wrt eta^0 through all n steps and *dB_grad = the sum over the
+ * steps of their dL/d dB (as apfc_adjoint_step; each adjoint solve starts from
+ * the previous one's solution).  It recomputes each segment's states from its
+ * checkpoint (one more forward pass in total; every + 1 fields of scratch) and
+ * leaves the state at eta^n.  ESTATE without a recorded rollout. */
+apfc_status apfc_rollout_forward(apfc_ctx* ctx, double dt, int n, int every);
+apfc_status apfc_rollout_backward(apfc_ctx* ctx, const void* lam_n, void* lam_0, double* dB_grad, int where);
+
 /* ---- batched independent runs ----------------------------------------------
  * Many independent 2D simulations of one lattice, one parameter set and one
  * spacing (hx, hy) on periodic grids of different sizes nx[r] x ny[r], advanced

@@ -107,6 +107,16 @@ EXPORTS = {
         [C.POINTER(Lattice), C.POINTER(Params), C.POINTER(Grid), C.c_int, C.c_int, C.c_double, C.c_void_p,
          C.c_void_p, C.c_void_p],
     ),
+    "apfc_set_params": (C.c_int, [C.c_void_p, C.POINTER(Params)]),
+    "apfc_adjoint_step": (
+        C.c_int,
+        [C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int],
+    ),
+    "apfc_energy_gradient": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int]),
+    "apfc_rollout_forward": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int]),
+    "apfc_rollout_backward": (
+        C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int]
+    ),
     "apfc_batch_init": (
         C.c_int,
         [C.POINTER(C.c_void_p), C.POINTER(Lattice), C.POINTER(Params), C.c_int, C.POINTER(C.c_int),
@@ -355,6 +365,44 @@ class Context:
 
     def nonlinear_rhs(self, dt, eta, out=None):
         return self._binary(load().apfc_nonlinear_rhs, dt, eta, self.amp_shape, out)
+
+    # -- parameters and adjoint --------------------------------------------
+    def set_params(self, params):
+        self.params = params if isinstance(params, Params) else make_params(*params)
+        _check(load().apfc_set_params(self._h, C.byref(self.params)), self._h)
+
+    def _same_side(self, *bufs):
+        ptrs = [_ptr(b, i == len(bufs) - 1) for i, b in enumerate(bufs)]
+        if len({w for _, w, _ in ptrs}) != 1:
+            raise TypeError("buffers must all be host or all be device buffers")
+        return ptrs
+
+    def adjoint_step(self, dt, eta_n, eta_np1, lam_np1, out=None):
+        """(grad wrt eta^n, dL/d dB) of one step, given grad wrt eta^{n+1}."""
+        out = np.empty(self.amp_shape, np.complex128) if out is None else out
+        (a, w, ka), (b, _, kb), (c, _, kc), (d, _, kd) = self._same_side(eta_n, eta_np1, lam_np1, out)
+        g = C.c_double()
+        _check(load().apfc_adjoint_step(self._h, float(dt), a, b, c, d, C.byref(g), w), self._h)
+        return out, g.value
+
+    def energy_gradient(self, eta, out=None):
+        """(grad of F wrt eta, dF/d dB)."""
+        out = np.empty(self.amp_shape, np.complex128) if out is None else out
+        (a, w, ka), (d, _, kd) = self._same_side(eta, out)
+        g = C.c_double()
+        _check(load().apfc_energy_gradient(self._h, a, d, C.byref(g), w), self._h)
+        return out, g.value
+
+    def rollout_forward(self, dt: float, n: int, every: int):
+        _check(load().apfc_rollout_forward(self._h, float(dt), int(n), int(every)), self._h)
+
+    def rollout_backward(self, lam_n, out=None):
+        """(grad wrt eta^0, dL/d dB) of the recorded rollout, given grad wrt eta^n."""
+        out = np.empty(self.amp_shape, np.complex128) if out is None else out
+        (a, w, ka), (d, _, kd) = self._same_side(lam_n, out)
+        g = C.c_double()
+        _check(load().apfc_rollout_backward(self._h, a, d, C.byref(g), w), self._h)
+        return out, g.value
 
 
 def apfc_apply_preconditioner_static(lattice: Lattice, params: Params, grid: Grid, cheb_degree: int, tau_mode: int,

@@ -100,6 +100,8 @@ enum KernelId {
   KID_FUSED_PINV,
   KID_BICG_UPDATE,
   KID_FUSED_APINV_T,
+  KID_ADJ_NONLIN,
+  KID_ENERGY_GRAD,
   KID_COUNT
 };
 template <typename T>
@@ -245,6 +247,15 @@ void launch_rhs_resid(const double2* x, double2* b, const double2* b_prev, const
                       const BatchLaunch* bl = nullptr);
 void launch_energy(const double2* x, double* partials, double* out, const OpCoef& c, const EnergyTable& et,
                    double Bx, cudaStream_t s);
+// Adjoint of the explicit right-hand side of a step (eta0, eta1: [J][pts]; xg: block whose
+// eta-part is g = S^{-1} lam_{n+1}): lam = g/dt - sum_j kap_j [g_j conj(dN_j/deta) +
+// conj(g_j) dN_j/dconj(eta)]; *out = sum_j kap_j Re sum conj(g_j) eta1_j (device scalar)
+void launch_adj_nonlin(const double2* eta0, const double2* xg, const double2* eta1, double2* lam, double* partials,
+                       double* out, const OpCoef& c, const NonlinTable& nt, cudaStream_t s);
+// Real gradient of the free energy: grad_j = scale [dB eta_j + Bx G_h zeta_j + N_j(eta)] from a
+// block x with zeta = G_h eta; *out = sum_j sum |eta_j|^2 (device scalar)
+void launch_energy_grad(const double2* x, double2* grad, double scale, double dB, double Bx, double* partials,
+                        double* out, const OpCoef& c, const NonlinTable& nt, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // fused2d.cu: row-streaming fused P^{-1} / A P^{-1} for 2D grids, Chebyshev

@@ -188,6 +188,21 @@ struct apfc_ctx {
   apfc_stats_t stats{};
   OpCoef coef{};
   double coef_dt = -1.0;
+  // adjoint (allocated on first use): solve block x = (zeta', g), right-hand side
+  // (0, lam), a scratch block for the energy gradient, four [J][pts] staging fields
+  double2* xadj = nullptr;
+  double2* badj = nullptr;
+  double2* eblk = nullptr;
+  double2* afld[4] = {};
+  // checkpointed rollout: states every r_every steps plus the final one, and the
+  // states of one segment recomputed during the backward pass
+  double2* ckpt = nullptr;
+  size_t ckpt_cap = 0;  // states
+  double2* seg = nullptr;
+  size_t seg_cap = 0;
+  double r_dt = 0.0;
+  int r_n = 0, r_every = 0;
+  bool r_ready = false;
 };
 
 namespace {
@@ -649,54 +664,41 @@ apfc_status step_fp64(apfc_ctx* ctx) {
   return status_of(ctx, worst);
 }
 
-// One step with FP32 Krylov inside FP64 iterative refinement.
-apfc_status step_refined(apfc_ctx* ctx) {
+// FP32 Krylov inside FP64 iterative refinement: A x = b to opts.tol, starting
+// from x.  resid_ready: the FP32 initial residual and the partials of ||r0||^2 and
+// ||b||^2 are already in place (the pointwise initial residual of a step).
+// r64_keep != nullptr receives the FP64 residual b - A x of every stencil
+// residual sweep.  *stencil_last: the final check was such a sweep.
+apfc_status refine_solve(apfc_ctx* ctx, const double2* b, double2* x, double2* r64_keep, bool resid_ready,
+                         int* total_it, int* sweeps, int* worst_out, bool* stencil_last) {
   apfc_status st = alloc_work<float>(ctx, ctx->w32);
   if (st != APFC_OK) return st;
   cudaStream_t s = ctx->stream;
-  const size_t blk = sizeof(double2) * 2ull * ctx->J * ctx->pts;
-  const bool flat = true;  // stencil-free initial residual and tiled FP64 residual (2D and 3D)
-  if (flat && ctx->r64_prev == nullptr) {
-    CK(cudaMalloc(&ctx->b64_prev, blk));
-    CK(cudaMalloc(&ctx->r64_prev, blk));
-    CK(cudaMemsetAsync(ctx->b64_prev, 0, blk, s));
-    ctx->have_prev = false;
-  }
   float2* r32 = ctx->w32.blk[7];
   double* part = reinterpret_cast<double*>(ctx->part64);
-  bool resid_ready = false;
-  if (flat && ctx->have_prev && ctx->prev_dt == ctx->coef_dt) {
-    // b_prev is the RHS the last residual was taken against; the new RHS goes to the other buffer
-    launch_rhs_resid(ctx->x64, ctx->b64_prev, ctx->b64, ctx->r64_prev, r32, part, ctx->coef, ctx->nt, s);
-    std::swap(ctx->b64, ctx->b64_prev);
-    resid_ready = true;
-  } else {
-    launch_rhs(ctx->x64, ctx->b64, ctx->coef, ctx->nt, s);
-  }
-  ctx->have_prev = false;
-  int total_it = 0, worst = KS_CONVERGED, sweep = 0;
+  int total = 0, worst = KS_CONVERGED, sweep = 0;
+  bool stencil = false;
   const double tol2 = ctx->opts.tol * ctx->opts.tol;
   for (;; ++sweep) {
     if (resid_ready) {
       launch_finalize64(2, ctx->part64, ctx->ks64, OP_NORMS, ctx->J, s);  // ||r0||^2 and ||b||^2
-    } else if (flat) {
-      if (sweep == 0) {  // ||b||^2 once per step
-        DotPairs<double> d{{ctx->b64, nullptr, nullptr}, {ctx->b64, nullptr, nullptr}};
+      stencil = false;
+    } else {
+      if (sweep == 0) {  // ||b||^2 once per solve
+        DotPairs<double> d{{b, nullptr, nullptr}, {b, nullptr, nullptr}};
         launch_dots<double>(1, d, ctx->part64, ctx->coef, nullptr, s);
         launch_finalize64(1, ctx->part64, ctx->ks64, OP_BNORM, ctx->J, s);
       }
       if (ctx->dim == 2) {
-        launch_residual_refine2d(ctx->b64, ctx->x64, r32, ctx->r64_prev, part, ctx->coef, s);
+        launch_residual_refine2d(b, x, r32, r64_keep, part, ctx->coef, s);
         launch_finalize64(1, ctx->part64, ctx->ks64, OP_RNORM, ctx->J, s);
       } else {
-        launch_residual_refine3d(ctx->b64, ctx->x64, r32, ctx->r64_prev, ctx->coef, s);
+        launch_residual_refine3d(b, x, r32, r64_keep, ctx->coef, s);
         DotPairs<float> d{{r32, nullptr, nullptr}, {r32, nullptr, nullptr}};
         launch_dots<float>(1, d, ctx->w32.partials, ctx->coef, nullptr, s);
         launch_finalize<float>(1, ctx->w32.partials, ctx->ks64, OP_RNORM, ctx->J, s);
       }
-    } else {
-      launch_residual_refine(ctx->b64, ctx->x64, r32, part, ctx->coef, s);
-      launch_finalize64(2, ctx->part64, ctx->ks64, OP_NORMS, ctx->J, s);
+      stencil = true;
     }
     resid_ready = false;
     CK(cudaGetLastError());
@@ -714,10 +716,6 @@ apfc_status step_refined(apfc_ctx* ctx) {
     }
     if (done) {
       worst = KS_CONVERGED;
-      // after at least one sweep the last check was a stencil residual that stored
-      // b - A x in r64_prev, which seeds the next step's initial residual
-      ctx->have_prev = flat && sweep > 0;
-      ctx->prev_dt = ctx->coef_dt;
       break;
     }
     if (sweep >= ctx->opts.max_refine) {
@@ -725,17 +723,59 @@ apfc_status step_refined(apfc_ctx* ctx) {
       break;
     }
     int it = 0, w = 0;
-    st = krylov<float>(ctx, ctx->w32, r32, ctx->x64, ctx->opts.tol_inner, ctx->opts.max_iter, &it, &w);
+    st = krylov<float>(ctx, ctx->w32, r32, x, ctx->opts.tol_inner, ctx->opts.max_iter, &it, &w);
     if (st != APFC_OK) return st;
-    total_it += it;
+    total += it;
     if (w == KS_NAN) {
       worst = KS_NAN;
       break;
     }
   }
+  *total_it = total;
+  *sweeps = sweep;
+  *worst_out = worst;
+  *stencil_last = stencil;
+  return APFC_OK;
+}
+
+// One step with FP32 Krylov inside FP64 iterative refinement.
+apfc_status step_refined(apfc_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  const size_t blk = sizeof(double2) * 2ull * ctx->J * ctx->pts;
+  if (ctx->r64_prev == nullptr) {
+    CK(cudaMalloc(&ctx->b64_prev, blk));
+    CK(cudaMalloc(&ctx->r64_prev, blk));
+    CK(cudaMemsetAsync(ctx->b64_prev, 0, blk, s));
+    ctx->have_prev = false;
+  }
+  apfc_status st = alloc_work<float>(ctx, ctx->w32);
+  if (st != APFC_OK) return st;
+  float2* r32 = ctx->w32.blk[7];
+  double* part = reinterpret_cast<double*>(ctx->part64);
+  bool resid_ready = false;
+  if (ctx->have_prev && ctx->prev_dt == ctx->coef_dt) {
+    // r0 = b - b_prev + r_prev with the previous step's final residual r_prev = b_prev - A x;
+    // b_prev is the RHS that residual was taken against; the new RHS goes to the other buffer
+    launch_rhs_resid(ctx->x64, ctx->b64_prev, ctx->b64, ctx->r64_prev, r32, part, ctx->coef, ctx->nt, s);
+    std::swap(ctx->b64, ctx->b64_prev);
+    resid_ready = true;
+  } else {
+    launch_rhs(ctx->x64, ctx->b64, ctx->coef, ctx->nt, s);
+  }
+  ctx->have_prev = false;
+  int total_it = 0, sweeps = 0, worst = KS_CONVERGED;
+  bool stencil_last = false;
+  st = refine_solve(ctx, ctx->b64, ctx->x64, ctx->r64_prev, resid_ready, &total_it, &sweeps, &worst, &stencil_last);
+  if (st != APFC_OK) return st;
+  if (worst == KS_CONVERGED) {
+    // after at least one sweep the last check was a stencil residual of the final
+    // state, kept in r64_prev: it seeds the next step's initial residual
+    ctx->have_prev = sweeps > 0 && stencil_last;
+    ctx->prev_dt = ctx->coef_dt;
+  }
   ctx->stats.iters_last = total_it;
   ctx->stats.iters_total += total_it;
-  ctx->stats.refine_last = sweep;
+  ctx->stats.refine_last = sweeps;
   ctx->stats.resid_last = max_rel_resid(ctx->ks64_host, ctx->J);
   return status_of(ctx, worst);
 }
@@ -767,6 +807,119 @@ apfc_status copy_part(apfc_ctx* ctx, void* plain, int where, int part, bool to_s
     CK(cudaMemcpy2DAsync(plain, row, base, 2 * row, row, ctx->J, k, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return APFC_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// Adjoint of the step and checkpointed rollouts
+// ---------------------------------------------------------------------------
+size_t field_elems(const apfc_ctx* ctx) { return (size_t)ctx->J * (size_t)ctx->pts; }
+
+apfc_status alloc_adjoint(apfc_ctx* ctx) {
+  if (ctx->xadj) return APFC_OK;
+  const size_t blk = sizeof(double2) * 2 * field_elems(ctx), fld = sizeof(double2) * field_elems(ctx);
+  CK(cudaMalloc(&ctx->xadj, blk));
+  CK(cudaMalloc(&ctx->badj, blk));
+  CK(cudaMalloc(&ctx->eblk, blk));
+  for (auto& f : ctx->afld) CK(cudaMalloc(&f, fld));
+  CK(cudaMemsetAsync(ctx->xadj, 0, blk, ctx->stream));
+  CK(cudaMemsetAsync(ctx->badj, 0, blk, ctx->stream));  // its zeta-parts stay zero
+  return APFC_OK;
+}
+
+// [J][pts] field <-> one part (0 zeta, 1 eta) of a block vector, device to device
+apfc_status field_to_block(apfc_ctx* ctx, double2* block, int part, const double2* field) {
+  const size_t row = sizeof(double2) * (size_t)ctx->pts;
+  CK(cudaMemcpy2DAsync(block + (size_t)part * ctx->pts, 2 * row, field, row, row, ctx->J, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+  return APFC_OK;
+}
+apfc_status block_to_field(apfc_ctx* ctx, double2* field, const double2* block, int part) {
+  const size_t row = sizeof(double2) * (size_t)ctx->pts;
+  CK(cudaMemcpy2DAsync(field, row, block + (size_t)part * ctx->pts, 2 * row, row, ctx->J, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+  return APFC_OK;
+}
+
+// state = (G_h eta, eta) from a device [J][pts] field
+apfc_status load_state(apfc_ctx* ctx, const double2* eta) {
+  apfc_status st = field_to_block(ctx, ctx->x64, 1, eta);
+  if (st != APFC_OK) return st;
+  launch_zeta(ctx->x64, ctx->coef, ctx->stream);
+  CK(cudaGetLastError());
+  ctx->have_prev = false;
+  return APFC_OK;
+}
+
+// A x = b to opts.tol in the context's precision, from the given x.
+apfc_status solve_block(apfc_ctx* ctx, const double2* b, double2* x, int* iters) {
+  int worst = KS_CONVERGED;
+  apfc_status st;
+  if (ctx->opts.precision == APFC_FP64) {
+    if ((st = alloc_work<double>(ctx, ctx->w64)) != APFC_OK) return st;
+    st = krylov<double>(ctx, ctx->w64, b, x, ctx->opts.tol, ctx->opts.max_iter, iters, &worst);
+  } else {
+    int sweeps = 0;
+    bool stencil = false;
+    st = refine_solve(ctx, b, x, nullptr, false, iters, &sweeps, &worst, &stencil);
+  }
+  if (st != APFC_OK) return st;
+  return status_of(ctx, worst);
+}
+
+// lam_n = adjoint of one step applied to lam_np1 (all device [J][pts] fields);
+// *dB_acc += the step's derivative through S with respect to dB.  warm: start the
+// adjoint solve from the previous one's solution, else from zero.
+apfc_status adjoint_step_dev(apfc_ctx* ctx, const double2* eta_n, const double2* eta_np1, const double2* lam_np1,
+                             double2* lam_n, double* dB_acc, bool warm) {
+  apfc_status st = alloc_adjoint(ctx);
+  if (st != APFC_OK) return st;
+  // g = S^{-1} lam_np1: S is Hermitian, so the adjoint solve is the block solve with
+  // right-hand side (0, lam_np1); g is the eta-part of its solution
+  if ((st = field_to_block(ctx, ctx->badj, 1, lam_np1)) != APFC_OK) return st;
+  if (!warm) CK(cudaMemsetAsync(ctx->xadj, 0, sizeof(double2) * 2 * field_elems(ctx), ctx->stream));
+  int iters = 0;
+  if ((st = solve_block(ctx, ctx->badj, ctx->xadj, &iters)) != APFC_OK) return st;
+  ctx->stats.iters_total += iters;
+  launch_adj_nonlin(eta_n, ctx->xadj, eta_np1, lam_n, ctx->epart, ctx->eout, ctx->coef, ctx->nt, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->eout_host, ctx->eout, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *dB_acc -= ctx->eout_host[0];
+  return APFC_OK;
+}
+
+// Real gradient of F at eta (device fields) and dF/d dB.
+apfc_status energy_grad_dev(apfc_ctx* ctx, const double2* eta, double2* grad, double* dF_ddB) {
+  apfc_status st = alloc_adjoint(ctx);
+  if (st != APFC_OK) return st;
+  if ((st = field_to_block(ctx, ctx->eblk, 1, eta)) != APFC_OK) return st;
+  launch_zeta(ctx->eblk, ctx->coef, ctx->stream);
+  double vol = 1.0;
+  for (int d = 0; d < ctx->dim; ++d) vol *= ctx->grid.h[d];
+  launch_energy_grad(ctx->eblk, grad, 2.0 * vol, ctx->par.dB, ctx->par.Bx, ctx->epart, ctx->eout, ctx->coef, ctx->nt,
+                     ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(ctx->eout_host, ctx->eout, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (dF_ddB) *dF_ddB = vol * ctx->eout_host[0];
+  return APFC_OK;
+}
+
+apfc_status ensure_states(apfc_ctx* ctx, double2** buf, size_t* cap, size_t n) {
+  if (*cap >= n) return APFC_OK;
+  cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  CK(cudaMalloc(buf, sizeof(double2) * field_elems(ctx) * n));
+  *cap = n;
+  return APFC_OK;
+}
+
+apfc_status one_step(apfc_ctx* ctx) {
+  apfc_status st = ctx->opts.precision == APFC_FP64 ? step_fp64(ctx) : step_refined(ctx);
+  if (st == APFC_OK) ctx->stats.steps += 1;
+  return st;
 }
 
 }  // namespace
@@ -983,13 +1136,19 @@ void apfc_destroy(apfc_ctx* ctx) {
   cudaFree(ctx->part64);
   free_work(ctx->w64);
   free_work(ctx->w32);
+  cudaFree(ctx->xadj);
+  cudaFree(ctx->badj);
+  cudaFree(ctx->eblk);
+  for (auto& f : ctx->afld) cudaFree(f);
+  cudaFree(ctx->ckpt);
+  cudaFree(ctx->seg);
   delete ctx;
 }
 
 static const char* kKernelNames[KID_COUNT] = {
     "apply_A", "residual", "pc_rhs", "cheb_zero", "cheb_first", "cheb_sweep", "pc_final", "p_update", "s_update",
     "r_update", "add_to", "dots", "finalize", "rhs", "zeta", "residual_refine", "energy", "fused_apinv",
-    "fused_pinv", "bicg_update", "fused_apinv_t"};
+    "fused_pinv", "bicg_update", "fused_apinv_t", "adj_nonlin", "energy_grad"};
 
 int apfc_kernel_count(void) { return 2 * KID_COUNT; }
 
@@ -1086,6 +1245,151 @@ apfc_status apfc_nonlinear_rhs(apfc_ctx* ctx, double dt, const void* eta, void* 
   CK(cudaGetLastError());
   CK(cudaMemcpy2DAsync(rhs, row, outb + ctx->pts, 2 * row, row, ctx->J, kout, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  return APFC_OK;
+}
+
+
+apfc_status apfc_set_params(apfc_ctx* ctx, const apfc_params* p) {
+  if (!ctx || !p) return APFC_EINVAL;
+  if (!valid_problem(ctx->lat, *p)) return fail(ctx, APFC_EINVAL, "invalid parameters");
+  NonlinTable nt;
+  EnergyTable et;
+  std::string e;
+  if (!build_tables(ctx->lat, *p, nt, et, e)) return fail(ctx, APFC_EINVAL, e);
+  ctx->par = *p;
+  ctx->nt = nt;
+  ctx->et = et;
+  ctx->coef_dt = -1.0;  // a and the preconditioner's shift depend on dB
+  ctx->have_prev = false;
+  ctx->r_ready = false;
+  return APFC_OK;
+}
+
+apfc_status apfc_adjoint_step(apfc_ctx* ctx, double dt, const void* eta_n, const void* eta_np1, const void* lam_np1,
+                              void* lam_n, double* dB_grad, int where) {
+  if (!ctx || !eta_n || !eta_np1 || !lam_np1 || !lam_n || (where != APFC_HOST && where != APFC_DEVICE))
+    return APFC_EINVAL;
+  if (ctx->failed) return APFC_ESTATE;
+  std::string e;
+  if (!build_coef(ctx, dt, e)) return fail(ctx, APFC_EINVAL, e);
+  apfc_status st = alloc_adjoint(ctx);
+  if (st != APFC_OK) return st;
+  const size_t bytes = sizeof(double2) * field_elems(ctx);
+  const double2 *en = static_cast<const double2*>(eta_n), *e1 = static_cast<const double2*>(eta_np1),
+                *l1 = static_cast<const double2*>(lam_np1);
+  double2* l0 = static_cast<double2*>(lam_n);
+  if (where == APFC_HOST) {
+    CK(cudaMemcpyAsync(ctx->afld[0], eta_n, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->afld[1], eta_np1, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->afld[2], lam_np1, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    en = ctx->afld[0];
+    e1 = ctx->afld[1];
+    l1 = ctx->afld[2];
+    l0 = ctx->afld[3];
+  }
+  double dB = 0.0;
+  if ((st = adjoint_step_dev(ctx, en, e1, l1, l0, &dB, false)) != APFC_OK) return st;
+  if (where == APFC_HOST) CK(cudaMemcpyAsync(lam_n, l0, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (dB_grad) *dB_grad = dB;
+  return APFC_OK;
+}
+
+apfc_status apfc_energy_gradient(apfc_ctx* ctx, const void* eta, void* grad, double* dF_ddB, int where) {
+  if (!ctx || !eta || !grad || (where != APFC_HOST && where != APFC_DEVICE)) return APFC_EINVAL;
+  std::string e;
+  if (!build_coef(ctx, ctx->coef_dt > 0 ? ctx->coef_dt : 1.0, e)) return fail(ctx, APFC_EINVAL, e);
+  apfc_status st = alloc_adjoint(ctx);
+  if (st != APFC_OK) return st;
+  const size_t bytes = sizeof(double2) * field_elems(ctx);
+  const double2* in = static_cast<const double2*>(eta);
+  double2* out = static_cast<double2*>(grad);
+  if (where == APFC_HOST) {
+    CK(cudaMemcpyAsync(ctx->afld[0], eta, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    in = ctx->afld[0];
+    out = ctx->afld[3];
+  }
+  if ((st = energy_grad_dev(ctx, in, out, dF_ddB)) != APFC_OK) return st;
+  if (where == APFC_HOST) CK(cudaMemcpyAsync(grad, out, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return APFC_OK;
+}
+
+apfc_status apfc_rollout_forward(apfc_ctx* ctx, double dt, int n, int every) {
+  if (!ctx || n < 0 || every < 1) return APFC_EINVAL;
+  if (ctx->failed) return APFC_ESTATE;
+  if (!ctx->has_state) return fail(ctx, APFC_ESTATE, "no amplitudes set");
+  std::string e;
+  if (!build_coef(ctx, dt, e)) return fail(ctx, APFC_EINVAL, e);
+  ctx->r_ready = false;
+  const int nseg = (n + every - 1) / every;
+  apfc_status st = ensure_states(ctx, &ctx->ckpt, &ctx->ckpt_cap, (size_t)nseg + 1);
+  if (st != APFC_OK) return st;
+  const size_t fe = field_elems(ctx);
+  for (int i = 0; i < n; ++i) {
+    if (i % every == 0) {
+      // checkpoint eta^i and restart from (G_h eta^i, eta^i) without the previous
+      // residual, exactly as the backward pass will when it recomputes this segment
+      double2* ck = ctx->ckpt + (size_t)(i / every) * fe;
+      if ((st = block_to_field(ctx, ck, ctx->x64, 1)) != APFC_OK) return st;
+      if ((st = load_state(ctx, ck)) != APFC_OK) return st;
+    }
+    if ((st = one_step(ctx)) != APFC_OK) return st;
+  }
+  if ((st = block_to_field(ctx, ctx->ckpt + (size_t)nseg * fe, ctx->x64, 1)) != APFC_OK) return st;
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->r_dt = dt;
+  ctx->r_n = n;
+  ctx->r_every = every;
+  ctx->r_ready = true;
+  return APFC_OK;
+}
+
+apfc_status apfc_rollout_backward(apfc_ctx* ctx, const void* lam_n, void* lam_0, double* dB_grad, int where) {
+  if (!ctx || !lam_n || !lam_0 || (where != APFC_HOST && where != APFC_DEVICE)) return APFC_EINVAL;
+  if (ctx->failed) return APFC_ESTATE;
+  if (!ctx->r_ready) return fail(ctx, APFC_ESTATE, "no rollout to differentiate");
+  std::string e;
+  if (!build_coef(ctx, ctx->r_dt, e)) return fail(ctx, APFC_EINVAL, e);
+  apfc_status st = alloc_adjoint(ctx);
+  if (st != APFC_OK) return st;
+  const int n = ctx->r_n, every = ctx->r_every, nseg = (n + every - 1) / every;
+  if ((st = ensure_states(ctx, &ctx->seg, &ctx->seg_cap, (size_t)std::min(every, std::max(n, 1)) + 1)) != APFC_OK)
+    return st;
+  const size_t fe = field_elems(ctx), bytes = sizeof(double2) * fe;
+  double2* lam[2] = {ctx->afld[2], ctx->afld[3]};
+  CK(cudaMemcpyAsync(lam[0], lam_n, bytes, where == APFC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  CK(cudaMemsetAsync(ctx->xadj, 0, 2 * bytes, ctx->stream));
+  const apfc_stats_t keep = ctx->stats;  // the recomputation is not user stepping
+  double dB = 0.0;
+  int cur = 0;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int s0 = sg * every, s1 = std::min(s0 + every, n);
+    // recompute eta^{s0} .. eta^{s1} from the checkpoint, as the forward pass did
+    const double2* ck = ctx->ckpt + (size_t)sg * fe;
+    CK(cudaMemcpyAsync(ctx->seg, ck, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    if ((st = load_state(ctx, ck)) != APFC_OK) return st;
+    for (int i = s0; i < s1; ++i) {
+      if ((st = one_step(ctx)) != APFC_OK) return st;
+      if ((st = block_to_field(ctx, ctx->seg + (size_t)(i - s0 + 1) * fe, ctx->x64, 1)) != APFC_OK) return st;
+    }
+    for (int i = s1 - 1; i >= s0; --i) {
+      const double2* en = ctx->seg + (size_t)(i - s0) * fe;
+      const double2* e1 = ctx->seg + (size_t)(i - s0 + 1) * fe;
+      if ((st = adjoint_step_dev(ctx, en, e1, lam[cur], lam[1 - cur], &dB, true)) != APFC_OK) return st;
+      cur = 1 - cur;
+    }
+  }
+  CK(cudaMemcpyAsync(lam_0, lam[cur], bytes, where == APFC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  // leave the state at eta^n, as after the forward pass
+  if ((st = load_state(ctx, ctx->ckpt + (size_t)nseg * fe)) != APFC_OK) return st;
+  CK(cudaStreamSynchronize(ctx->stream));
+  const long long adj_iters = ctx->stats.iters_total - keep.iters_total;
+  ctx->stats = keep;
+  ctx->stats.iters_total += adj_iters;
+  if (dB_grad) *dB_grad = dB;
   return APFC_OK;
 }
 

@@ -933,6 +933,126 @@ inline dim3 grid_pts(const OpCoef& c, long long n) {
   return dim3((unsigned)((n + kThreads - 1) / kThreads), (unsigned)c.J);
 }
 
+
+// ---------------------------------------------------------------------------
+// Adjoint of the step (real-gradient convention: grad = dL/dRe + i dL/dIm)
+// ---------------------------------------------------------------------------
+
+// N_j(eta) at one point (closed form on the triangular lattice, else the table).
+__device__ __forceinline__ double2 nonlin_at(const double2* eta, int j, const OpCoef& c, const NonlinTable& nt) {
+  if (nt.hex) {
+    double A2 = 0.0;
+    for (int m = 0; m < 3; ++m) A2 += eta[m].x * eta[m].x + eta[m].y * eta[m].y;
+    A2 *= 2.0;
+    const int k1 = (j + 1) % 3, k2 = (j + 2) % 3;
+    const double m2 = eta[j].x * eta[j].x + eta[j].y * eta[j].y;
+    const double s = 3.0 * nt.v * (A2 - m2);
+    const double2 pr = cconj(cm(eta[k1], eta[k2]));
+    return make_double2(s * eta[j].x - 2.0 * nt.t * pr.x, s * eta[j].y - 2.0 * nt.t * pr.y);
+  }
+  double2 N = make_double2(0.0, 0.0);
+  for (int q = nt.start[j]; q < nt.start[j + 1]; ++q) {
+    double2 prod = make_double2(nt.coef[q], 0.0);
+    for (int f = 0; f < nt.nf[q]; ++f) {
+      const int code = nt.f[q][f];
+      prod = cm(prod, (code & 1) ? cconj(eta[code >> 1]) : eta[code >> 1]);
+    }
+    N.x += prod.x;
+    N.y += prod.y;
+  }
+  return N;
+}
+
+__device__ __forceinline__ double2 cadd2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub2(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// out_k -= sum_j [w_j conj(dN_j/deta_k) + conj(w_j) dN_j/dconj(eta_k)] at one point.
+__device__ __forceinline__ void nonlin_vjp_sub(const double2* eta, const double2* w, double2* out, const OpCoef& c,
+                                               const NonlinTable& nt) {
+  if (nt.hex) {
+    double A2 = 0.0;
+    for (int m = 0; m < 3; ++m) A2 += eta[m].x * eta[m].x + eta[m].y * eta[m].y;
+    A2 *= 2.0;
+    for (int j = 0; j < 3; ++j) {
+      // dN_j/deta_j = 3v A^2 (real), dN_j/dconj(eta_j) = 3v eta_j^2
+      const double a = 3.0 * nt.v * A2;
+      const double2 e2 = cm(eta[j], eta[j]);
+      const double2 b = make_double2(3.0 * nt.v * e2.x, 3.0 * nt.v * e2.y);
+      out[j] = csub2(out[j], cadd2(make_double2(a * w[j].x, a * w[j].y), cm(cconj(w[j]), b)));
+      for (int m = 0; m < 3; ++m) {
+        if (m == j) continue;
+        const int o = 3 - j - m;
+        // dN_j/deta_m = 6v eta_j conj(eta_m); dN_j/dconj(eta_m) = 6v eta_j eta_m - 2t conj(eta_o)
+        const double2 am = cm(eta[j], cconj(eta[m]));
+        const double2 em = cm(eta[j], eta[m]);
+        const double2 a6 = make_double2(6.0 * nt.v * am.x, 6.0 * nt.v * am.y);
+        const double2 b6 = make_double2(6.0 * nt.v * em.x - 2.0 * nt.t * eta[o].x, 6.0 * nt.v * em.y + 2.0 * nt.t * eta[o].y);
+        out[m] = csub2(out[m], cadd2(cm(w[j], cconj(a6)), cm(cconj(w[j]), b6)));
+      }
+    }
+    return;
+  }
+  for (int j = 0; j < c.J; ++j) {
+    for (int q = nt.start[j]; q < nt.start[j + 1]; ++q) {
+      for (int f = 0; f < nt.nf[q]; ++f) {
+        double2 d = make_double2(nt.coef[q], 0.0);  // derivative of the term by its factor f
+        for (int g = 0; g < nt.nf[q]; ++g) {
+          if (g == f) continue;
+          const int code = nt.f[q][g];
+          d = cm(d, (code & 1) ? cconj(eta[code >> 1]) : eta[code >> 1]);
+        }
+        const int code = nt.f[q][f], cf = code >> 1;
+        out[cf] = csub2(out[cf], (code & 1) ? cm(cconj(w[j]), d) : cm(w[j], cconj(d)));
+      }
+    }
+  }
+}
+
+__global__ void k_adj_nonlin(const double2* __restrict__ eta0, const double2* __restrict__ xg,
+                             const double2* __restrict__ eta1, double2* __restrict__ lam,
+                             double* __restrict__ partials, OpCoef c, NonlinTable nt) {
+  prof_add(c, KID_ADJ_NONLIN, 4ull * c.J * (unsigned long long)c.pts * sizeof(double2));
+  double acc[1] = {0.0};
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < c.pts;
+       p += (long long)gridDim.x * blockDim.x) {
+    double2 e[kMaxJ], w[kMaxJ], out[kMaxJ];
+    for (int j = 0; j < c.J; ++j) {
+      e[j] = eta0[j * c.pts + p];
+      const double2 g = xg[(2LL * j + 1) * c.pts + p];
+      const double2 e1 = eta1[j * c.pts + p];
+      acc[0] += c.kap[j] * (g.x * e1.x + g.y * e1.y);
+      w[j] = make_double2(c.kap[j] * g.x, c.kap[j] * g.y);
+      out[j] = make_double2(g.x * c.inv_dt, g.y * c.inv_dt);
+    }
+    nonlin_vjp_sub(e, w, out, c, nt);
+    for (int j = 0; j < c.J; ++j) lam[j * c.pts + p] = out[j];
+  }
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
+}
+
+__global__ void k_energy_grad(const double2* __restrict__ x, double2* __restrict__ grad, double scale, double dB,
+                              double Bx, double* __restrict__ partials, OpCoef c, NonlinTable nt) {
+  prof_add(c, KID_ENERGY_GRAD, 3ull * c.J * (unsigned long long)c.pts * sizeof(double2));
+  double acc[1] = {0.0};
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < c.pts;
+       p += (long long)gridDim.x * blockDim.x) {
+    const Nb n = neighbours(p, c);
+    double2 e[kMaxJ];
+    for (int j = 0; j < c.J; ++j) {
+      e[j] = x[(2LL * j + 1) * c.pts + p];
+      acc[0] += e[j].x * e[j].x + e[j].y * e[j].y;
+    }
+    for (int j = 0; j < c.J; ++j) {
+      const double2 gz = opG<double>(x + 2LL * j * c.pts, n, c, j);
+      const double2 N = nonlin_at(e, j, c, nt);
+      grad[j * c.pts + p] = make_double2(scale * (dB * e[j].x + Bx * gz.x + N.x), scale * (dB * e[j].y + Bx * gz.y + N.y));
+    }
+  }
+  block_sum<1>(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1075,6 +1195,19 @@ void launch_energy(const double2* x, double* partials, double* out, const OpCoef
                    cudaStream_t s) {
   ProfScope ps_(KID_ENERGY, s);
   k_energy<<<kDotBlocks, kThreads, 0, s>>>(x, partials, c, et, Bx);
+  k_sum_partials<<<1, kThreads, 0, s>>>(partials, kDotBlocks, out);
+}
+
+void launch_adj_nonlin(const double2* eta0, const double2* xg, const double2* eta1, double2* lam, double* partials,
+                       double* out, const OpCoef& c, const NonlinTable& nt, cudaStream_t s) {
+  ProfScope ps_(KID_ADJ_NONLIN, s);
+  k_adj_nonlin<<<kDotBlocks, kThreads, 0, s>>>(eta0, xg, eta1, lam, partials, c, nt);
+  k_sum_partials<<<1, kThreads, 0, s>>>(partials, kDotBlocks, out);
+}
+void launch_energy_grad(const double2* x, double2* grad, double scale, double dB, double Bx, double* partials,
+                        double* out, const OpCoef& c, const NonlinTable& nt, cudaStream_t s) {
+  ProfScope ps_(KID_ENERGY_GRAD, s);
+  k_energy_grad<<<kDotBlocks, kThreads, 0, s>>>(x, grad, scale, dB, Bx, partials, c, nt);
   k_sum_partials<<<1, kThreads, 0, s>>>(partials, kDotBlocks, out);
 }
 
