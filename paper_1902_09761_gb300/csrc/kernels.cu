@@ -895,7 +895,8 @@ struct OpZeta3 {
   }
 };
 
-// FP64 outer residual on 3D grids: r = b - A x (x, b FP64), written as FP32 and FP64.
+// FP64 outer residual on 3D grids: r = b - A x (x, b FP64), written as FP32 and, if
+// r64 != nullptr, as FP64.
 struct OpResRefine3 {
   static constexpr int NS = 2;
   const double2* x;
@@ -915,8 +916,10 @@ struct OpResRefine3 {
     const double r2x = b2.x - fma(kt, gz.x, a * n[1].c.x), r2y = b2.y - fma(kt, gz.y, a * n[1].c.y);
     r32[o + p] = make_float2((float)r1x, (float)r1y);
     r32[o + pts + p] = make_float2((float)r2x, (float)r2y);
-    r64[o + p] = make_double2(r1x, r1y);
-    r64[o + pts + p] = make_double2(r2x, r2y);
+    if (r64 != nullptr) {
+      r64[o + p] = make_double2(r1x, r1y);
+      r64[o + pts + p] = make_double2(r2x, r2y);
+    }
   }
 };
 
@@ -1181,7 +1184,7 @@ void launch_residual_refine3d(const double2* b, const double2* x, float2* r32, d
                               cudaStream_t s) {
   ProfScope ps_(KID_RESID_REFINE, s);
   OpResRefine3 op{x, b, r32, r64, c.pts, KID_RESID_REFINE,
-                  (unsigned long long)c.pts * (6 * sizeof(double2) + 2 * sizeof(float2))};
+                  (unsigned long long)c.pts * ((r64 ? 6 : 4) * sizeof(double2) + 2 * sizeof(float2))};
   k_stream3d<double, OpResRefine3><<<grid_stream3d(c), 256, 0, s>>>(c, op, nullptr);
 }
 void launch_rhs_resid(const double2* x, double2* b, const double2* b_prev, const double2* r_prev, float2* r32,
