@@ -59,9 +59,13 @@ def parse():
     ap.add_argument("--breakdown-steps", type=int, default=3, help="steps of the per-kernel timing pass (0: off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument(
-        "--workload", choices=["voronoi", "batch"], default="voronoi",
-        help="voronoi: one n x n polycrystal (default); batch: independent runs of uneven sizes in one batch",
+        "--workload", choices=["voronoi", "batch", "adjoint"], default="voronoi",
+        help="voronoi: one n x n polycrystal (default); batch: independent runs of uneven sizes in one batch; "
+        "adjoint: gradient of a rollout loss by the checkpointed adjoint",
     )
+    ap.add_argument("--rollout", type=int, default=200, help="adjoint: steps per rollout")
+    ap.add_argument("--every", type=int, default=20, help="adjoint: steps between checkpoints")
+    ap.add_argument("--adj-size", type=int, default=1024, help="adjoint: grid points per side")
     ap.add_argument("--runs", type=int, default=64, help="batch: number of independent runs")
     ap.add_argument("--no-graph", action="store_true", help="batch: launch the Krylov blocks without graphs")
     ap.add_argument("--no-autotune", action="store_true", help="batch: keep --tile / --rows")
@@ -711,6 +715,194 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Adjoint workload: gradient of L = misfit + F after a rollout, wrt eta0 and dB
+# ---------------------------------------------------------------------------
+
+
+def adjoint_config(args, tuned=None):
+    return {
+        "workload": f"hex2d-{args.adj_size}x{args.adj_size}-adjoint-{args.rollout}steps",
+        "lattice": "triangular, J=3",
+        "grid": [args.adj_size, args.adj_size],
+        "initial": "8 Voronoi grains, rotations U[-10, 10] deg, noise 1e-3, seed 3",
+        "loss": "1/2 h^2 sum |eta^K - target|^2 + F(eta^K), target seeded N(0, 0.1^2) complex",
+        "grad": "wrt eta0 (complex128) and dB",
+        "rollout_steps": args.rollout,
+        "checkpoint_every": args.every,
+        "h": "pi/2",
+        "dt": 1.0,
+        "params": {"dB": PARAMS[0], "Bx": PARAMS[1], "t": PARAMS[2], "v": PARAMS[3]},
+        "tol": TOL,
+        "unit_note": "one DOF-step = one amplitude DOF through one step forward and its adjoint",
+        "l2": "inputs larger than L2 (states 50 MB each, checkpoints 0.55 GB); no flush",
+    }
+
+
+def adjoint_states(n, phi):
+    from paper_1902_09761_gb300 import inputs
+
+    eta0 = inputs.voronoi_grains(inputs.hex_vectors(), phi, (n, n), (H, H), 8, 10.0, seed=3, noise=1e-3)
+    rng = np.random.default_rng(4)
+    target = 0.1 * (rng.standard_normal(eta0.shape) + 1j * rng.standard_normal(eta0.shape))
+    return eta0, target
+
+
+def oracle_adjoint_rate(n, steps):
+    import oracle as O
+    from paper_1902_09761_gb300 import inputs
+
+    P = O.params_from_paper(0.98, 0.01, 0.25, 0.5)
+    L = O.hex_lattice()
+    eta0 = inputs.voronoi_grains(inputs.hex_vectors(), O.uniform_solid_hex(P), (n, n), (H, H), 8, 10.0, seed=3,
+                                 noise=1e-3)
+    target = np.zeros_like(eta0)
+    t0 = time.perf_counter()
+    O.rollout_gradient(eta0, P.dB, target, 1.0, steps, P, L, (H, H))
+    secs = time.perf_counter() - t0
+    return 3.0 * n * n * steps / secs, secs
+
+
+def run_adjoint_reference(args):
+    world, rank, local = init_dist(args)
+    if rank != 0:
+        return
+    n = min(args.adj_size, 512)
+    steps = min(args.rollout, 20)
+    rate, secs = oracle_adjoint_rate(n, steps)
+    sample = f"oracle rollout gradient (FFT-exact forward and adjoint solves) on {n}x{n}, {steps} steps, {secs:.1f} s"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": adjoint_config(args),
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_adjoint(args):
+    import torch
+
+    world, rank, local = init_dist(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1902_09761_gb300 import apfc as A
+    from paper_1902_09761_gb300 import inputs
+    from paper_1902_09761_gb300.autograd import Rollout
+
+    A.load()
+    n, K = args.adj_size, args.rollout
+    phi = A.apfc_uniform_amplitude(A.make_lattice(inputs.hex_vectors(), A.APFC_LATTICE_HEX2D), A.make_params(*PARAMS))
+    eta0, target = adjoint_states(n, phi)
+    dof = 3 * n * n
+    vol = H * H
+    stream = torch.cuda.current_stream(dev)
+    opts = A.apfc_default_opts(precision=A.APFC_FP32_REFINED, tol=TOL, cheb_degree=args.cheb,
+                               tol_inner=args.tol_inner, tile=args.tile, tile_rows=args.rows)
+    ro = Rollout(inputs.hex_vectors(), A.APFC_LATTICE_HEX2D, PARAMS, (n, n), (H, H), 1.0, K, args.every, opts,
+                 device=dev)
+    e0_dev = torch.from_numpy(eta0).to(dev)
+    tg = torch.from_numpy(target).to(dev)
+
+    def grad_once():
+        e0 = e0_dev.clone().requires_grad_(True)
+        dB = torch.tensor(PARAMS[0], dtype=torch.float64, requires_grad=True)
+        etaN, F = ro(e0, dB)
+        loss = 0.5 * vol * (etaN - tg).abs().pow(2).sum() + F
+        loss.backward()
+        return e0.grad, dB.grad
+
+    for _ in range(args.warmup):
+        grad_once()
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0t = torch.cuda.Event(enable_timing=True)
+    e1t = torch.cuda.Event(enable_timing=True)
+    e0t.record(stream)
+    for _ in range(args.steps):
+        grad_once()
+    e1t.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = allmax(world, e0t.elapsed_time(e1t), dev) / args.steps  # per gradient evaluation
+    value = world * dof * K / (ms * 1e-3)
+
+    # forward and backward separately, and the dominant kernel's roofline
+    ctx = ro.ctx
+    ctx.set_amplitudes(e0_dev)
+    torch.cuda.synchronize(dev)
+    f0 = torch.cuda.Event(enable_timing=True)
+    f1 = torch.cuda.Event(enable_timing=True)
+    b1 = torch.cuda.Event(enable_timing=True)
+    ctx.profile_start(args.timed_kernel)
+    f0.record(stream)
+    ctx.rollout_forward(1.0, K, args.every)
+    f1.record(stream)
+    lamN = torch.zeros_like(e0_dev)
+    lam0 = torch.empty_like(e0_dev)
+    ctx.rollout_backward(lamN + 1e-3, lam0)
+    b1.record(stream)
+    torch.cuda.synchronize(dev)
+    prof = ctx.profile_read(args.timed_kernel)
+    ctx.profile_stop()
+    fwd_ms, bwd_ms = f0.elapsed_time(f1), f1.elapsed_time(b1)
+    peak, peak_src = measured_peaks()
+    avg_ms = prof["ms"] / max(prof["launches"], 1)
+    bpl = prof["bytes"] / max(prof["launches"], 1)
+    achieved = bpl / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else None
+
+    # end to end with host buffers: the same gradient through host-resident inputs and outputs
+    h_e0 = torch.from_numpy(eta0).pin_memory()
+    h_tg = torch.from_numpy(target).pin_memory()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e0 = h_e0.to(dev, non_blocking=True).requires_grad_(True)
+    dB = torch.tensor(PARAMS[0], dtype=torch.float64, requires_grad=True)
+    etaN, F = ro(e0, dB)
+    loss = 0.5 * vol * (etaN - h_tg.to(dev, non_blocking=True)).abs().pow(2).sum() + F
+    loss.backward()
+    g_host = e0.grad.cpu()
+    _ = float(dB.grad)
+    e2e_s = allmax(world, time.perf_counter() - t0, dev)
+    e2e = world * dof * K / e2e_s
+    ro.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ns, ks = min(n, 512), min(K, 20)
+        rate, secs = oracle_adjoint_rate(ns, ks)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle rollout gradient (FFT-exact solves) on {ns}x{ns}, {ks} steps, {secs:.1f} s"}
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 Krylov + f64 refinement", "data": "synthetic",
+        "config": dict(adjoint_config(args), parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
+        "ms_per_gradient": ms,
+        "forward_ms_per_step": fwd_ms / K,
+        "backward_ms_per_step": bwd_ms / K,
+        "backward_over_forward": bwd_ms / fwd_ms,
+        "roofline": {
+            "bound": "hbm", "kernel": args.timed_kernel, "achieved": achieved, "peak": peak,
+            "peak_source": peak_src, "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+            "traffic": None, "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg_ms,
+            "launches": prof["launches"],
+        },
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * eta0.nbytes,
+                "d2h_bytes_per_step": g_host.numel() * 16 + 8},
+        "gpu_launches": prof["all_launches"],
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 CHEB = 1
 TOL_INNER = 1e-4
 
@@ -721,6 +913,8 @@ def main():
     CHEB, TOL_INNER = args.cheb, args.tol_inner
     if args.workload == "batch":
         run_batch_reference(args) if args.impl == "reference" else run_batch(args)
+    elif args.workload == "adjoint":
+        run_adjoint_reference(args) if args.impl == "reference" else run_adjoint(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

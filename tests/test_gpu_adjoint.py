@@ -93,7 +93,7 @@ def test_rollout_gradient_matches_oracle(prec):
     assert rel_l2(e0.grad.cpu().numpy(), ref) <= 1e-9
     assert float(dB.grad) == pytest.approx(ref_dB, rel=1e-9)
     # the loss itself is the oracle's
-    assert float(loss) == pytest.approx(O.rollout_loss(eta0, P.dB, target, dt, n, P, L, H2), rel=1e-11)
+    assert float(loss.detach()) == pytest.approx(O.rollout_loss(eta0, P.dB, target, dt, n, P, L, H2), rel=1e-11)
     ro.close()
 
 
