@@ -275,6 +275,33 @@ apfc_status apfc_energy_gradient(apfc_ctx* ctx, const void* eta, void* grad, dou
 apfc_status apfc_rollout_forward(apfc_ctx* ctx, double dt, int n, int every);
 apfc_status apfc_rollout_backward(apfc_ctx* ctx, const void* lam_n, void* lam_0, double* dB_grad, int where);
 
+/* ---- rotation diagnostic and adaptivity map (Sec. II.D) ----------------------
+ * Analysis output of the current state (nothing of the step depends on it).
+ * omega: the rotation tensor omega_il = 1/2 (du_i/dx_l - du_l/dx_i) (Eq. rot) of
+ * the displacement u solving k_j . u = arg(eta_j) in the least-squares sense,
+ * u = M^{-1} sum_j k_j arg(eta_j), M = sum_j k_j k_j^T; the phase gradients are
+ * central differences of the unwrapped phase, arg(eta_j(r+h e_d) conj(eta_j(r-h e_d)))/(2h_d),
+ * so a grain rotated by theta about z gives omega_12 = sin(theta) exactly.
+ * Layout: [ncomp][nz][ny][nx] doubles, ncomp = 1 in 2D (omega_12) and 3 in 3D
+ * (omega_23, omega_31, omega_12); 0 where some |eta_j|^2 < 1e-12 (the liquid).
+ * amp (may be NULL): A = sqrt(2 sum_j |eta_j|^2), [nz][ny][nx] doubles.
+ * hmap (may be NULL; needs adapt): the local grid size of Eq. hhh,
+ *   h_int                              where |grad A| >= eps (central differences),
+ *   min(max(h_amp, h_int), h_max)      where A > A_min,
+ *   h_max                              elsewhere,
+ * with h_amp = pi / (n max_j |k_j| sin(theta/2)), theta = asin(min(max_d |omega_d|, 1))
+ * (lambda_j(theta) = 2 pi / |dk_j(theta)| at |dk_j| = 2 |k_j| sin(theta/2); theta = 0
+ * gives h_amp = infinity).  EINVAL for n <= 0, h_int <= 0, h_max < h_int or eps < 0. */
+typedef struct {
+  double n;      /* grid points per smallest amplitude wavelength (the paper uses >= 10) */
+  double h_int;  /* grid size at interfaces and defects                                 */
+  double h_max;  /* largest grid size                                                   */
+  double eps;    /* threshold on |grad A|                                               */
+  double A_min;  /* "A > 0" threshold of the solid                                      */
+} apfc_adapt;
+apfc_status apfc_rotation_field(apfc_ctx* ctx, void* omega, void* amp, void* hmap, const apfc_adapt* adapt,
+                                int where);
+
 /* ---- batched independent runs ----------------------------------------------
  * Many independent 2D simulations of one lattice, one parameter set and one
  * spacing (hx, hy) on periodic grids of different sizes nx[r] x ny[r], advanced

@@ -64,6 +64,11 @@ class Opts(C.Structure):
     ]
 
 
+class Adapt(C.Structure):
+    _fields_ = [("n", C.c_double), ("h_int", C.c_double), ("h_max", C.c_double), ("eps", C.c_double),
+                ("A_min", C.c_double)]
+
+
 class Stats(C.Structure):
     _fields_ = [
         ("steps", C.c_longlong),
@@ -117,6 +122,7 @@ EXPORTS = {
     "apfc_rollout_backward": (
         C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_int]
     ),
+    "apfc_rotation_field": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "apfc_batch_init": (
         C.c_int,
         [C.POINTER(C.c_void_p), C.POINTER(Lattice), C.POINTER(Params), C.c_int, C.POINTER(C.c_int),
@@ -392,6 +398,30 @@ class Context:
         g = C.c_double()
         _check(load().apfc_energy_gradient(self._h, a, d, C.byref(g), w), self._h)
         return out, g.value
+
+    def rotation_field(self, adapt: dict | None = None, device=None):
+        """(omega, A, h) of the current state as numpy arrays (host) or torch tensors (device=...).
+
+        omega has shape (ncomp,) + grid; h is None without ``adapt`` (keys n, h_int, h_max, eps, A_min)."""
+        nc = 1 if self.dim == 2 else 3
+        a = Adapt(**adapt) if adapt is not None else None
+        if device is None:
+            om = np.empty((nc,) + self.shape)
+            am = np.empty(self.shape)
+            hm = np.empty(self.shape) if a is not None else None
+            ptr = lambda v: v.ctypes.data_as(C.c_void_p) if v is not None else None  # noqa: E731
+            where = APFC_HOST
+        else:
+            import torch
+
+            om = torch.empty((nc,) + self.shape, dtype=torch.float64, device=device)
+            am = torch.empty(self.shape, dtype=torch.float64, device=device)
+            hm = torch.empty(self.shape, dtype=torch.float64, device=device) if a is not None else None
+            ptr = lambda v: C.c_void_p(v.data_ptr()) if v is not None else None  # noqa: E731
+            where = APFC_DEVICE
+        _check(load().apfc_rotation_field(self._h, ptr(om), ptr(am), ptr(hm), C.byref(a) if a else None, where),
+               self._h)
+        return om, am, hm
 
     def rollout_forward(self, dt: float, n: int, every: int):
         _check(load().apfc_rollout_forward(self._h, float(dt), int(n), int(every)), self._h)

@@ -102,6 +102,7 @@ enum KernelId {
   KID_FUSED_APINV_T,
   KID_ADJ_NONLIN,
   KID_ENERGY_GRAD,
+  KID_ROTATION,
   KID_COUNT
 };
 template <typename T>
@@ -252,6 +253,16 @@ void launch_energy(const double2* x, double* partials, double* out, const OpCoef
 // conj(g_j) dN_j/dconj(eta)]; *out = sum_j kap_j Re sum conj(g_j) eta1_j (device scalar)
 void launch_adj_nonlin(const double2* eta0, const double2* xg, const double2* eta1, double2* lam, double* partials,
                        double* out, const OpCoef& c, const NonlinTable& nt, cudaStream_t s);
+// Rotation diagnostic and adaptivity map (Sec. II.D): per point the rotation
+// tensor components omega (1 in 2D: omega_12; 3 in 3D: omega_23, omega_31,
+// omega_12), A = sqrt(2 sum |eta_j|^2) and the local grid size h of Eq. hhh.
+struct RotParams {
+  double W[kMaxJ][3];  // M^{-1} k_j, M = sum_j k_j k_j^T
+  double hd[3];        // grid spacings
+  double n, h_int, h_max, eps, A_min, amp_floor, kmax;
+};
+void launch_rotation(const double2* x, double* omega, double* amp, double* hmap, const RotParams& rp,
+                     const OpCoef& c, cudaStream_t s);
 // Real gradient of the free energy: grad_j = scale [dB eta_j + Bx G_h zeta_j + N_j(eta)] from a
 // block x with zeta = G_h eta; *out = sum_j sum |eta_j|^2 (device scalar)
 void launch_energy_grad(const double2* x, double2* grad, double scale, double dB, double Bx, double* partials,

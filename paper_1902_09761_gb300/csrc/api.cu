@@ -1148,7 +1148,7 @@ void apfc_destroy(apfc_ctx* ctx) {
 static const char* kKernelNames[KID_COUNT] = {
     "apply_A", "residual", "pc_rhs", "cheb_zero", "cheb_first", "cheb_sweep", "pc_final", "p_update", "s_update",
     "r_update", "add_to", "dots", "finalize", "rhs", "zeta", "residual_refine", "energy", "fused_apinv",
-    "fused_pinv", "bicg_update", "fused_apinv_t", "adj_nonlin", "energy_grad"};
+    "fused_pinv", "bicg_update", "fused_apinv_t", "adj_nonlin", "energy_grad", "rotation"};
 
 int apfc_kernel_count(void) { return 2 * KID_COUNT; }
 
@@ -1390,6 +1390,82 @@ apfc_status apfc_rollout_backward(apfc_ctx* ctx, const void* lam_n, void* lam_0,
   ctx->stats = keep;
   ctx->stats.iters_total += adj_iters;
   if (dB_grad) *dB_grad = dB;
+  return APFC_OK;
+}
+
+
+apfc_status apfc_rotation_field(apfc_ctx* ctx, void* omega, void* amp, void* hmap, const apfc_adapt* adapt,
+                                int where) {
+  if (!ctx || !omega || (where != APFC_HOST && where != APFC_DEVICE)) return APFC_EINVAL;
+  if (hmap && !adapt) return APFC_EINVAL;
+  if (adapt && (!(adapt->n > 0.0) || !(adapt->h_int > 0.0) || !(adapt->h_max >= adapt->h_int) ||
+                !(adapt->eps >= 0.0) || !std::isfinite(adapt->A_min)))
+    return fail(ctx, APFC_EINVAL, "invalid adaptivity parameters");
+  if (!ctx->has_state) return fail(ctx, APFC_ESTATE, "no amplitudes set");
+  std::string e;
+  if (!build_coef(ctx, ctx->coef_dt > 0 ? ctx->coef_dt : 1.0, e)) return fail(ctx, APFC_EINVAL, e);
+  const int dim = ctx->dim, J = ctx->J;
+  // W_j = M^{-1} k_j with M = sum_j k_j k_j^T (Gauss-Jordan on [M | k_1 .. k_J])
+  double Mk[3][3 + kMaxJ] = {};
+  for (int a = 0; a < dim; ++a) {
+    for (int b = 0; b < dim; ++b)
+      for (int j = 0; j < J; ++j) Mk[a][b] += ctx->lat.k[j][a] * ctx->lat.k[j][b];
+    for (int j = 0; j < J; ++j) Mk[a][dim + j] = ctx->lat.k[j][a];
+  }
+  for (int col = 0; col < dim; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < dim; ++r)
+      if (std::fabs(Mk[r][col]) > std::fabs(Mk[piv][col])) piv = r;
+    if (std::fabs(Mk[piv][col]) < 1e-12) return fail(ctx, APFC_EINVAL, "lattice vectors do not span the space");
+    for (int q = 0; q < dim + J; ++q) std::swap(Mk[col][q], Mk[piv][q]);
+    const double inv = 1.0 / Mk[col][col];
+    for (int q = 0; q < dim + J; ++q) Mk[col][q] *= inv;
+    for (int r = 0; r < dim; ++r) {
+      if (r == col) continue;
+      const double f = Mk[r][col];
+      for (int q = 0; q < dim + J; ++q) Mk[r][q] -= f * Mk[col][q];
+    }
+  }
+  RotParams rp{};
+  double kmax = 0.0;
+  for (int j = 0; j < J; ++j) {
+    double k2 = 0.0;
+    for (int a = 0; a < dim; ++a) {
+      rp.W[j][a] = Mk[a][dim + j];
+      k2 += ctx->lat.k[j][a] * ctx->lat.k[j][a];
+    }
+    kmax = std::max(kmax, std::sqrt(k2));
+  }
+  for (int a = 0; a < 3; ++a) rp.hd[a] = ctx->grid.h[a];
+  rp.kmax = kmax;
+  rp.amp_floor = 1e-12;
+  if (adapt) {
+    rp.n = adapt->n;
+    rp.h_int = adapt->h_int;
+    rp.h_max = adapt->h_max;
+    rp.eps = adapt->eps;
+    rp.A_min = adapt->A_min;
+  }
+  const int nc = dim == 2 ? 1 : 3;
+  const size_t pts = (size_t)ctx->pts;
+  double *om = static_cast<double*>(omega), *am = static_cast<double*>(amp), *hm = static_cast<double*>(hmap);
+  double* scratch = nullptr;
+  if (where == APFC_HOST) {
+    CK(cudaMalloc(&scratch, sizeof(double) * pts * (nc + 2)));
+    om = scratch;
+    am = amp ? scratch + nc * pts : nullptr;
+    hm = hmap ? scratch + (nc + 1) * pts : nullptr;
+  }
+  launch_rotation(ctx->x64, om, am, hm, rp, ctx->coef, ctx->stream);
+  cudaError_t err = cudaGetLastError();
+  if (err == cudaSuccess && where == APFC_HOST) {
+    err = cudaMemcpyAsync(omega, om, sizeof(double) * pts * nc, cudaMemcpyDeviceToHost, ctx->stream);
+    if (err == cudaSuccess && amp) err = cudaMemcpyAsync(amp, am, sizeof(double) * pts, cudaMemcpyDeviceToHost, ctx->stream);
+    if (err == cudaSuccess && hmap) err = cudaMemcpyAsync(hmap, hm, sizeof(double) * pts, cudaMemcpyDeviceToHost, ctx->stream);
+  }
+  if (err == cudaSuccess) err = cudaStreamSynchronize(ctx->stream);
+  cudaFree(scratch);
+  if (err != cudaSuccess) return fail(ctx, APFC_ECUDA, std::string("rotation field: ") + cudaGetErrorString(err));
   return APFC_OK;
 }
 

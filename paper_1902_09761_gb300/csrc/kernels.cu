@@ -5,6 +5,8 @@
 //   G_h u  = L_h u + 2i sum_d k_d (u(+e_d) - u(-e_d)) / (2 h_d)
 //   A_j (zeta, eta) = (zeta - G_h eta, kt G_h zeta + a eta)       (Eq. linear_system2, M = I)
 //   D u    = sD u - mu L_h u                                      (diffusion part of Eq. preconditioner)
+#include <algorithm>
+
 #include "apfc_internal.cuh"
 
 namespace apfc {
@@ -1056,6 +1058,76 @@ __global__ void k_energy_grad(const double2* __restrict__ x, double2* __restrict
   if (threadIdx.x == 0) partials[blockIdx.x] = acc[0];
 }
 
+
+// ---------------------------------------------------------------------------
+// Rotation diagnostic and adaptivity map (Sec. II.D, Eqs. rot and hhh)
+// ---------------------------------------------------------------------------
+__global__ void k_rotation(const double2* __restrict__ x, double* __restrict__ omega, double* __restrict__ amp,
+                           double* __restrict__ hmap, RotParams rp, OpCoef c) {
+  prof_add(c, KID_ROTATION, (unsigned long long)c.pts * (c.J * sizeof(double2) + (c.dim == 2 ? 3 : 5) * sizeof(double)));
+  const int dim = c.dim;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < c.pts;
+       p += (long long)gridDim.x * blockDim.x) {
+    const Nb n = neighbours(p, c);
+    const long long nbp[3] = {n.xp, n.yp, n.zp}, nbm[3] = {n.xm, n.ym, n.zm};
+    double du[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double s2c = 0.0, s2p[3] = {0, 0, 0}, s2m[3] = {0, 0, 0};
+    bool ok = true;
+    for (int j = 0; j < c.J; ++j) {
+      const double2* e = x + (2LL * j + 1) * c.pts;
+      const double2 ec = e[p];
+      const double m2 = ec.x * ec.x + ec.y * ec.y;
+      s2c += m2;
+      ok = ok && (m2 >= rp.amp_floor);
+      for (int d = 0; d < dim; ++d) {
+        const double2 a = e[nbp[d]], b = e[nbm[d]];
+        s2p[d] += a.x * a.x + a.y * a.y;
+        s2m[d] += b.x * b.x + b.y * b.y;
+        // arg(a conj(b)): central difference of the unwrapped phase
+        const double g = atan2(a.y * b.x - a.x * b.y, a.x * b.x + a.y * b.y) / (2.0 * rp.hd[d]);
+        for (int i = 0; i < dim; ++i) du[i][d] += rp.W[j][i] * g;
+      }
+    }
+    double om[3];
+    int nc;
+    if (dim == 2) {
+      om[0] = 0.5 * (du[0][1] - du[1][0]);
+      nc = 1;
+    } else {
+      om[0] = 0.5 * (du[1][2] - du[2][1]);
+      om[1] = 0.5 * (du[2][0] - du[0][2]);
+      om[2] = 0.5 * (du[0][1] - du[1][0]);
+      nc = 3;
+    }
+    double wmax = 0.0;
+    for (int q = 0; q < nc; ++q) {
+      if (!ok) om[q] = 0.0;
+      omega[q * c.pts + p] = om[q];
+      wmax = fmax(wmax, fabs(om[q]));
+    }
+    const double A = sqrt(2.0 * s2c);
+    if (amp != nullptr) amp[p] = A;
+    if (hmap != nullptr) {
+      double g2 = 0.0;
+      for (int d = 0; d < dim; ++d) {
+        const double gd = (sqrt(2.0 * s2p[d]) - sqrt(2.0 * s2m[d])) / (2.0 * rp.hd[d]);
+        g2 += gd * gd;
+      }
+      double hv;
+      if (sqrt(g2) >= rp.eps) {
+        hv = rp.h_int;
+      } else if (A > rp.A_min) {
+        const double s = sin(0.5 * asin(fmin(wmax, 1.0)));
+        const double h_amp = s > 0.0 ? M_PI / (rp.n * rp.kmax * s) : INFINITY;
+        hv = fmin(fmax(h_amp, rp.h_int), rp.h_max);
+      } else {
+        hv = rp.h_max;
+      }
+      hmap[p] = hv;
+    }
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1214,6 +1286,12 @@ void launch_energy_grad(const double2* x, double2* grad, double scale, double dB
   k_sum_partials<<<1, kThreads, 0, s>>>(partials, kDotBlocks, out);
 }
 
+void launch_rotation(const double2* x, double* omega, double* amp, double* hmap, const RotParams& rp,
+                     const OpCoef& c, cudaStream_t s) {
+  ProfScope ps_(KID_ROTATION, s);
+  k_rotation<<<(unsigned)std::min<long long>((c.pts + kThreads - 1) / kThreads, 8 * kDotBlocks), kThreads, 0, s>>>(
+      x, omega, amp, hmap, rp, c);
+}
 #define APFC_INST(T)                                                                                                 \
   template void launch_apply_A<T>(const cplx<T>*, cplx<T>*, const OpCoef&, const KScal*, cudaStream_t);             \
   template void launch_residual<T>(const cplx<T>*, const cplx<T>*, cplx<T>*, cplx<T>*, const OpCoef&,               \
