@@ -104,6 +104,10 @@ typedef struct {
   int tile;                  /* fused 2D kernel variant 0..4 (columns per block and
                                 rows of look-ahead), default 3                     */
   int tile_rows;             /* rows per block of the fused 2D kernels (0 = 128)   */
+  int picard_iters;          /* K of Alg. 1: Picard iterations per step, 1..100;
+                                1 (default) with jacobian 0 is the explicit step   */
+  int jacobian;              /* 1: linearise N_j with D_j = dN_j/d eta_j (the
+                                paper's J^j, h^j) in every Picard iteration        */
 } apfc_opts;
 
 typedef struct {
@@ -116,7 +120,7 @@ typedef struct {
 
 /* Fill *o with defaults: FP64, BiCGStab, tol 1e-10, max_iter 500,
  * cheb_degree 1, tau fold, max_refine 10, tol_inner 1e-4, check_every 4, fused 1,
- * tile 3, tile_rows 0 (128). */
+ * tile 3, tile_rows 0 (128), picard_iters 1, jacobian 0. */
 apfc_status apfc_default_opts(apfc_opts* o);
 
 /* Relaxed-solid amplitude phi of a uniform crystal (eta_j = phi for all j):
@@ -144,11 +148,17 @@ apfc_status apfc_set_amplitudes(apfc_ctx* ctx, const void* eta, int where);
 apfc_status apfc_get_amplitudes(apfc_ctx* ctx, void* eta, int where);
 apfc_status apfc_get_zeta(apfc_ctx* ctx, void* zeta, int where);
 
-/* Advance n steps of size dt (Alg. 1 with one nonlinear iterate): explicit
- * nonlinear right-hand side from eta^n for all amplitudes, then one
- * preconditioned Krylov solve per amplitude from the initial guess
- * (zeta^n, eta^n).  Returns after the last step; ENOCONV / ENAN if a solve
- * failed (the state then holds the last iterate). */
+/* Advance n steps of size dt (Alg. 1).  Default (picard_iters 1, jacobian 0):
+ * one nonlinear iterate, explicit nonlinear right-hand side from eta^n for all
+ * amplitudes, then one preconditioned Krylov solve per amplitude from the
+ * initial guess (zeta^n, eta^n).  With picard_iters K > 1 or jacobian 1: K
+ * iterations k, each solving per amplitude (all amplitudes reading eta^(k-1))
+ *   [ I, -G_h ; kap Bx G_h, (1/dt + kap dB) I + kap D_j ] (zeta, eta)
+ *     = (0, eta^n/dt - kap (N_j - D_j eta_j)(eta^(k-1))),
+ * D_j = dN_j/d eta_j at eta^(k-1) with the Jacobian (a real diagonal), else 0,
+ * from the previous iterate; the preconditioner keeps its constant coefficients
+ * and the Jacobian runs the per-pass kernels.  Returns after the last step;
+ * ENOCONV / ENAN if a solve failed (the state then holds the last iterate). */
 apfc_status apfc_step(apfc_ctx* ctx, double dt, int n);
 
 /* Discrete free energy (Eq. energyamplitude with the gradient term scaled so
@@ -242,7 +252,8 @@ apfc_status apfc_profile_stop(apfc_ctx* ctx);
  * next step rebuilds the coefficients; a recorded rollout is dropped. */
 apfc_status apfc_set_params(apfc_ctx* ctx, const apfc_params* p);
 
-/* Adjoint of one step of size dt (the map eta^n -> eta^{n+1} of apfc_step: per
+/* Adjoint of one step of size dt (the map eta^n -> eta^{n+1} of apfc_step with
+ * picard_iters 1 and jacobian 0, else EINVAL; per
  * amplitude eta_j^{n+1} = S_j^{-1} (eta_j^n/dt - kap_j N_j(eta^n)) with
  * S_j = (1/dt + kap_j dB) I + kap_j Bx G_h^2, kap_j = |k_j|^2).  Given
  * lam_np1 = grad of L wrt eta^{n+1}, returns lam_n = grad of L wrt eta^n

@@ -61,6 +61,8 @@ class Opts(C.Structure):
         ("tol_inner", C.c_double),
         ("tile", C.c_int),
         ("tile_rows", C.c_int),
+        ("picard_iters", C.c_int),
+        ("jacobian", C.c_int),
     ]
 
 

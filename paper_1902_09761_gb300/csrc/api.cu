@@ -203,6 +203,9 @@ struct apfc_ctx {
   double r_dt = 0.0;
   int r_n = 0, r_every = 0;
   bool r_ready = false;
+  // Picard iterations: eta^n, and kap_j D_j with the Jacobian
+  double2* eta_step = nullptr;
+  double* jd = nullptr;
 };
 
 namespace {
@@ -480,7 +483,7 @@ void apply_pinv(apfc_ctx* ctx, Work<T>& w, const cplx<T>* beta, cplx<T>* chi, co
 int fused_rows(const apfc_ctx* ctx) { return ctx->opts.tile_rows > 0 ? ctx->opts.tile_rows : kFusedRows; }
 
 bool use_fused(const apfc_ctx* ctx, int elem_bytes) {
-  return ctx->dim == 2 && ctx->opts.fused != 0 && ctx->opts.cheb_degree >= 1 &&
+  return ctx->dim == 2 && ctx->opts.fused != 0 && ctx->coef.jd == nullptr && ctx->opts.cheb_degree >= 1 &&
          ctx->opts.cheb_degree <= fused2d_max_degree(elem_bytes);
 }
 
@@ -916,8 +919,39 @@ apfc_status ensure_states(apfc_ctx* ctx, double2** buf, size_t* cap, size_t n) {
   return APFC_OK;
 }
 
+// One step of Alg. 1 with K = picard_iters iterations, the Jacobian optional.
+apfc_status step_picard(apfc_ctx* ctx) {
+  const size_t fe = field_elems(ctx);
+  if (!ctx->eta_step) CK(cudaMalloc(&ctx->eta_step, sizeof(double2) * fe));
+  const bool jac = ctx->opts.jacobian != 0;
+  if (jac && !ctx->jd) CK(cudaMalloc(&ctx->jd, sizeof(double) * fe));
+  apfc_status st = block_to_field(ctx, ctx->eta_step, ctx->x64, 1);
+  if (st != APFC_OK) return st;
+  ctx->have_prev = false;
+  int total = 0;
+  for (int k = 0; k < ctx->opts.picard_iters; ++k) {
+    // b and kap D from eta^(k-1), the eta-parts of the state; solve from x^(k-1)
+    launch_rhs_picard(ctx->x64, ctx->eta_step, ctx->b64, jac ? ctx->jd : nullptr, ctx->coef, ctx->nt, ctx->stream);
+    ctx->coef.jd = jac ? ctx->jd : nullptr;
+    int it = 0;
+    st = solve_block(ctx, ctx->b64, ctx->x64, &it);
+    ctx->coef.jd = nullptr;
+    total += it;
+    if (st != APFC_OK) return st;
+  }
+  ctx->stats.iters_last = total;
+  ctx->stats.iters_total += total;
+  ctx->stats.refine_last = ctx->opts.picard_iters;
+  ctx->stats.resid_last = max_rel_resid(ctx->opts.precision == APFC_FP64 ? ctx->w64.ks_host : ctx->ks64_host, ctx->J);
+  return APFC_OK;
+}
+
+bool explicit_step(const apfc_ctx* ctx) { return ctx->opts.picard_iters == 1 && ctx->opts.jacobian == 0; }
+
 apfc_status one_step(apfc_ctx* ctx) {
-  apfc_status st = ctx->opts.precision == APFC_FP64 ? step_fp64(ctx) : step_refined(ctx);
+  apfc_status st = !explicit_step(ctx)               ? step_picard(ctx)
+                   : ctx->opts.precision == APFC_FP64 ? step_fp64(ctx)
+                                                      : step_refined(ctx);
   if (st == APFC_OK) ctx->stats.steps += 1;
   return st;
 }
@@ -935,6 +969,8 @@ bool apfc::valid_opts(const apfc_opts& o, std::string& e) {
   else if (o.fused != 0 && o.fused != 1) e = "fused";
   else if (o.tile < 0 || o.tile >= fused2d_tiles()) e = "tile";
   else if (o.tile_rows < 0 || o.tile_rows > 65536) e = "tile_rows";
+  else if (o.picard_iters < 1 || o.picard_iters > 100) e = "picard_iters";
+  else if (o.jacobian != 0 && o.jacobian != 1) e = "jacobian";
   else if (!(o.tol > 0.0) || !(o.tol_inner > 0.0) || !(o.tol_inner < 1.0)) e = "tol";
   else return true;
   e = "invalid option: " + e;
@@ -977,6 +1013,8 @@ apfc_status apfc_default_opts(apfc_opts* o) {
   o->fused = 1;
   o->tile = 3;
   o->tile_rows = 0;
+  o->picard_iters = 1;
+  o->jacobian = 0;
   return APFC_OK;
 }
 
@@ -1093,9 +1131,8 @@ apfc_status apfc_step(apfc_ctx* ctx, double dt, int n) {
   std::string e;
   if (!build_coef(ctx, dt, e)) return fail(ctx, APFC_EINVAL, e);
   for (int i = 0; i < n; ++i) {
-    apfc_status st = ctx->opts.precision == APFC_FP64 ? step_fp64(ctx) : step_refined(ctx);
+    apfc_status st = one_step(ctx);
     if (st != APFC_OK) return st;
-    ctx->stats.steps += 1;
   }
   return APFC_OK;
 }
@@ -1142,6 +1179,8 @@ void apfc_destroy(apfc_ctx* ctx) {
   for (auto& f : ctx->afld) cudaFree(f);
   cudaFree(ctx->ckpt);
   cudaFree(ctx->seg);
+  cudaFree(ctx->eta_step);
+  cudaFree(ctx->jd);
   delete ctx;
 }
 
@@ -1270,6 +1309,7 @@ apfc_status apfc_adjoint_step(apfc_ctx* ctx, double dt, const void* eta_n, const
   if (!ctx || !eta_n || !eta_np1 || !lam_np1 || !lam_n || (where != APFC_HOST && where != APFC_DEVICE))
     return APFC_EINVAL;
   if (ctx->failed) return APFC_ESTATE;
+  if (!explicit_step(ctx)) return fail(ctx, APFC_EINVAL, "the adjoint is that of the explicit step");
   std::string e;
   if (!build_coef(ctx, dt, e)) return fail(ctx, APFC_EINVAL, e);
   apfc_status st = alloc_adjoint(ctx);
@@ -1349,6 +1389,7 @@ apfc_status apfc_rollout_backward(apfc_ctx* ctx, const void* lam_n, void* lam_0,
   if (!ctx || !lam_n || !lam_0 || (where != APFC_HOST && where != APFC_DEVICE)) return APFC_EINVAL;
   if (ctx->failed) return APFC_ESTATE;
   if (!ctx->r_ready) return fail(ctx, APFC_ESTATE, "no rollout to differentiate");
+  if (!explicit_step(ctx)) return fail(ctx, APFC_EINVAL, "the adjoint is that of the explicit step");
   std::string e;
   if (!build_coef(ctx, ctx->r_dt, e)) return fail(ctx, APFC_EINVAL, e);
   apfc_status st = alloc_adjoint(ctx);

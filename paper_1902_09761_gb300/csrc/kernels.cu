@@ -145,7 +145,7 @@ __global__ void k_apply_A(const cplx<T>* __restrict__ x, cplx<T>* __restrict__ y
   const cplx<T> gz = opG<T>(z, n, c, j), ge = opG<T>(e, n, c, j);
   const cplx<T> zc = z[p], ec = e[p];
   cplx<T>* y1 = y + 2LL * j * c.pts;
-  const T kt = (T)c.kt[j], a = (T)c.a[j];
+  const T kt = (T)c.kt[j], a = (T)a_at(c, j, p);
   y1[p] = mkc<T>(zc.x - ge.x, zc.y - ge.y);
   y1[c.pts + p] = mkc<T>(kt * gz.x + a * ec.x, kt * gz.y + a * ec.y);
 }
@@ -162,7 +162,7 @@ __global__ void k_residual(const cplx<T>* __restrict__ b, const cplx<T>* __restr
   const cplx<T> gz = opG<T>(z, n, c, j), ge = opG<T>(e, n, c, j);
   const cplx<T> zc = z[p], ec = e[p];
   const cplx<T> b1 = b[o + p], b2 = b[o + c.pts + p];
-  const T kt = (T)c.kt[j], a = (T)c.a[j];
+  const T kt = (T)c.kt[j], a = (T)a_at(c, j, p);
   const cplx<T> r1 = mkc<T>(b1.x - (zc.x - ge.x), b1.y - (zc.y - ge.y));
   const cplx<T> r2 = mkc<T>(b2.x - (kt * gz.x + a * ec.x), b2.y - (kt * gz.y + a * ec.y));
   r[o + p] = r1;
@@ -432,7 +432,8 @@ __global__ void k_residual_refine(const double2* __restrict__ b, const double2* 
     const double2 zc = z[p], ec = e[p];
     const double2 b1 = b[o + p], b2 = b[o + c.pts + p];
     const double r1x = b1.x - (zc.x - ge.x), r1y = b1.y - (zc.y - ge.y);
-    const double r2x = b2.x - (kt * gz.x + a * ec.x), r2y = b2.y - (kt * gz.y + a * ec.y);
+    const double ap = c.jd == nullptr ? a : a_at(c, j, p);
+    const double r2x = b2.x - (kt * gz.x + ap * ec.x), r2y = b2.y - (kt * gz.y + ap * ec.y);
     r32[o + p] = make_float2((float)r1x, (float)r1y);
     r32[o + c.pts + p] = make_float2((float)r2x, (float)r2y);
     acc[0] += r1x * r1x + r1y * r1y + r2x * r2x + r2y * r2y;
@@ -496,7 +497,8 @@ __global__ void __launch_bounds__(256) k_residual_refine2d(const double2* __rest
     const double2 zc = z[pc], ec = e[pc];
     const double2 b1 = b[o + pc], b2 = b[o + c.pts + pc];
     const double r1x = (b1.x - zc.x) + ge.x, r1y = (b1.y - zc.y) + ge.y;
-    const double r2x = b2.x - fma(kt, gz.x, a * ec.x), r2y = b2.y - fma(kt, gz.y, a * ec.y);
+    const double ap = c.jd == nullptr ? a : a_at(c, j, pc);
+    const double r2x = b2.x - fma(kt, gz.x, ap * ec.x), r2y = b2.y - fma(kt, gz.y, ap * ec.y);
     const float2 f1 = make_float2((float)r1x, (float)r1y), f2 = make_float2((float)r2x, (float)r2y);
     r32[o + pc] = f1;
     r32[o + c.pts + pc] = f2;
@@ -776,7 +778,7 @@ struct OpA3 {
   __device__ const cplx<T>* src(int k, int j) const { return x + (2LL * j + k) * pts; }
   __device__ void apply(int j, long long p, const N7<T> (&n)[2], const OpCoef& c) const {
     const cplx<T> gz = G7(n[0], c, j), ge = G7(n[1], c, j);
-    const T kt = (T)c.kt[j], a = (T)c.a[j];
+    const T kt = (T)c.kt[j], a = (T)a_at(c, j, p);
     cplx<T>* y1 = y + 2LL * j * pts;
     y1[p] = mkc<T>(n[0].c.x - ge.x, n[0].c.y - ge.y);
     y1[pts + p] = mkc<T>(kt * gz.x + a * n[1].c.x, kt * gz.y + a * n[1].c.y);
@@ -797,7 +799,7 @@ struct OpRes3 {
   __device__ const cplx<T>* src(int k, int j) const { return x + (2LL * j + k) * pts; }
   __device__ void apply(int j, long long p, const N7<T> (&n)[2], const OpCoef& c) const {
     const cplx<T> gz = G7(n[0], c, j), ge = G7(n[1], c, j);
-    const T kt = (T)c.kt[j], a = (T)c.a[j];
+    const T kt = (T)c.kt[j], a = (T)a_at(c, j, p);
     const long long o = 2LL * j * pts;
     const cplx<T> b1 = b[o + p], b2 = b[o + pts + p];
     const cplx<T> r1 = mkc<T>(b1.x - (n[0].c.x - ge.x), b1.y - (n[0].c.y - ge.y));
@@ -911,7 +913,7 @@ struct OpResRefine3 {
   __device__ const double2* src(int k, int j) const { return x + (2LL * j + k) * pts; }
   __device__ void apply(int j, long long p, const N7<double> (&n)[2], const OpCoef& c) const {
     const double2 gz = G7(n[0], c, j), ge = G7(n[1], c, j);
-    const double kt = c.kt[j], a = c.a[j];
+    const double kt = c.kt[j], a = a_at(c, j, p);
     const long long o = 2LL * j * pts;
     const double2 b1 = b[o + p], b2 = b[o + pts + p];
     const double r1x = (b1.x - n[0].c.x) + ge.x, r1y = (b1.y - n[0].c.y) + ge.y;
@@ -1009,6 +1011,55 @@ __device__ __forceinline__ void nonlin_vjp_sub(const double2* eta, const double2
         const int code = nt.f[q][f], cf = code >> 1;
         out[cf] = csub2(out[cf], (code & 1) ? cm(cconj(w[j]), d) : cm(w[j], cconj(d)));
       }
+    }
+  }
+}
+
+
+// D_j = dN_j/d eta_j at one point (the Jacobian of Alg. 1 in direction eta_j): 3v A^2 on the
+// triangular lattice, else the derivative of every table monomial by its unconjugated
+// eta_j factors.  The exact value is real (a mixed second derivative of the real bulk
+// density); the real part is returned.
+__device__ __forceinline__ double jac_diag_at(const double2* eta, int j, const OpCoef& c, const NonlinTable& nt) {
+  if (nt.hex) {
+    double A2 = 0.0;
+    for (int m = 0; m < 3; ++m) A2 += eta[m].x * eta[m].x + eta[m].y * eta[m].y;
+    return 3.0 * nt.v * 2.0 * A2;
+  }
+  double2 D = make_double2(0.0, 0.0);
+  for (int q = nt.start[j]; q < nt.start[j + 1]; ++q) {
+    for (int f = 0; f < nt.nf[q]; ++f) {
+      if (nt.f[q][f] != 2 * j) continue;  // an unconjugated eta_j factor
+      double2 d = make_double2(nt.coef[q], 0.0);
+      for (int g = 0; g < nt.nf[q]; ++g) {
+        if (g == f) continue;
+        const int code = nt.f[q][g];
+        d = cm(d, (code & 1) ? cconj(eta[code >> 1]) : eta[code >> 1]);
+      }
+      D = cadd2(D, d);
+    }
+  }
+  return D.x;
+}
+
+// Right-hand side of Picard iteration k (Alg. 1): from the previous iterate eta (the
+// eta-parts of x), b_j = eta_prev_j/dt - kap_j (N_j - D_j eta_j) and jd_j = kap_j D_j
+// (jd == nullptr: plain Picard, D = 0).
+__global__ void k_rhs_picard(const double2* __restrict__ x, const double2* __restrict__ eta_prev,
+                             double2* __restrict__ b, double* __restrict__ jd, OpCoef c, NonlinTable nt) {
+  prof_add(c, KID_RHS, (unsigned long long)c.J * c.pts * (3 * sizeof(double2) + (jd ? sizeof(double) : 0)));
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < c.pts;
+       p += (long long)gridDim.x * blockDim.x) {
+    double2 eta[kMaxJ];
+    for (int j = 0; j < c.J; ++j) eta[j] = x[(2LL * j + 1) * c.pts + p];
+    for (int j = 0; j < c.J; ++j) {
+      const double2 N = nonlin_at(eta, j, c, nt);
+      const double D = jd != nullptr ? jac_diag_at(eta, j, c, nt) : 0.0;
+      const double kap = c.kap[j];
+      const double2 ep = eta_prev[j * c.pts + p];
+      b[(2LL * j + 1) * c.pts + p] = make_double2(ep.x * c.inv_dt - kap * (N.x - D * eta[j].x),
+                                                 ep.y * c.inv_dt - kap * (N.y - D * eta[j].y));
+      if (jd != nullptr) jd[j * c.pts + p] = kap * D;
     }
   }
 }
@@ -1291,6 +1342,12 @@ void launch_rotation(const double2* x, double* omega, double* amp, double* hmap,
   ProfScope ps_(KID_ROTATION, s);
   k_rotation<<<(unsigned)std::min<long long>((c.pts + kThreads - 1) / kThreads, 8 * kDotBlocks), kThreads, 0, s>>>(
       x, omega, amp, hmap, rp, c);
+}
+void launch_rhs_picard(const double2* x, const double2* eta_prev, double2* b, double* jd, const OpCoef& c,
+                       const NonlinTable& nt, cudaStream_t s) {
+  ProfScope ps_(KID_RHS, s);
+  k_rhs_picard<<<(unsigned)std::min<long long>((c.pts + kThreads - 1) / kThreads, 8 * kDotBlocks), kThreads, 0, s>>>(
+      x, eta_prev, b, jd, c, nt);
 }
 #define APFC_INST(T)                                                                                                 \
   template void launch_apply_A<T>(const cplx<T>*, cplx<T>*, const OpCoef&, const KScal*, cudaStream_t);             \

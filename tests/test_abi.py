@@ -41,6 +41,7 @@ def test_default_opts(lib):
     o = A.apfc_default_opts()
     assert o.precision == A.APFC_FP64 and o.krylov == A.APFC_BICGSTAB
     assert o.tol == 1e-10 and o.max_iter == 500 and o.cheb_degree == 1 and o.tile == 3
+    assert o.picard_iters == 1 and o.jacobian == 0
     assert o.tau_mode == A.APFC_TAU_FOLD and 0 < o.tol_inner < 1 and o.check_every >= 1
 
 
@@ -70,6 +71,9 @@ def test_uniform_amplitude_matches_closed_forms(lib):
         "cheb_big",
         "tol_zero",
         "prec",
+        "picard0",
+        "picard101",
+        "jac2",
     ],
 )
 def test_init_rejects_invalid_arguments_before_touching_cuda(lib, case):
@@ -102,6 +106,12 @@ def test_init_rejects_invalid_arguments_before_touching_cuda(lib, case):
         opts.tol = 0.0
     elif case == "prec":
         opts.precision = 7
+    elif case == "picard0":
+        opts.picard_iters = 0
+    elif case == "picard101":
+        opts.picard_iters = 101
+    elif case == "jac2":
+        opts.jacobian = 2
     import ctypes as C
 
     h_ = C.c_void_p()
@@ -120,7 +130,7 @@ def test_binding_fails_loudly_without_library(tmp_path):
         A._lib = saved
 
 
-@pytest.mark.parametrize("case", ["nruns0", "nx2", "bcc", "fp64", "unfused", "flags", "hx0", "cheb5"])
+@pytest.mark.parametrize("case", ["nruns0", "nx2", "bcc", "fp64", "unfused", "flags", "hx0", "cheb5", "picard", "jac"])
 def test_batch_init_rejects_invalid_arguments_before_touching_cuda(lib, case):
     import ctypes as C
 
@@ -144,6 +154,10 @@ def test_batch_init_rejects_invalid_arguments_before_touching_cuda(lib, case):
         hx = 0.0
     elif case == "cheb5":
         opts.cheb_degree = 5
+    elif case == "picard":
+        opts.picard_iters = 2
+    elif case == "jac":
+        opts.jacobian = 1
     L = A.make_lattice(k, kind)
     h_ = C.c_void_p()
     st = lib.apfc_batch_init(
