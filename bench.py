@@ -63,6 +63,8 @@ def parse():
         help="voronoi: one n x n polycrystal (default); batch: independent runs of uneven sizes in one batch; "
         "adjoint: gradient of a rollout loss by the checkpointed adjoint",
     )
+    ap.add_argument("--picard", type=int, default=1, help="Picard iterations per step (Alg. 1's K)")
+    ap.add_argument("--jacobian", action="store_true", help="Picard iterations with the Jacobian in direction eta_j")
     ap.add_argument("--rollout", type=int, default=200, help="adjoint: steps per rollout")
     ap.add_argument("--every", type=int, default=20, help="adjoint: steps between checkpoints")
     ap.add_argument("--adj-size", type=int, default=1024, help="adjoint: grid points per side")
@@ -85,6 +87,8 @@ def workload_config(n, steps_note=None):
         "krylov": "right-preconditioned BiCGStab, Schur-complement preconditioner",
         "cheb_degree": CHEB,
         "tol_inner": TOL_INNER,
+        "picard_iters": PICARD[0],
+        "jacobian": PICARD[1],
         "l2": "inputs larger than L2 (FP64 state 805 MB per 4096^2 replica); no flush",
     }
     if steps_note:
@@ -294,7 +298,7 @@ def run_ours(args):
 
     opts = A.apfc_default_opts(
         precision=A.APFC_FP32_REFINED, tol=TOL, cheb_degree=args.cheb, tol_inner=args.tol_inner, tile=args.tile,
-        tile_rows=args.rows,
+        tile_rows=args.rows, picard_iters=args.picard, jacobian=int(args.jacobian),
     )
     ctx = A.Context(k, A.APFC_LATTICE_HEX2D, prm, (n, n), (H, H), opts, stream=stream.cuda_stream)
     eta_dev = torch.from_numpy(eta0).to(dev)
@@ -364,7 +368,8 @@ def run_ours(args):
         }
 
     # --- plain FP64 path at the same final residual ------------------------------
-    ctx.set_opts(A.apfc_default_opts(precision=A.APFC_FP64, tol=TOL, cheb_degree=args.cheb, tile_rows=args.rows))
+    ctx.set_opts(A.apfc_default_opts(precision=A.APFC_FP64, tol=TOL, cheb_degree=args.cheb, tile_rows=args.rows,
+                                     picard_iters=args.picard, jacobian=int(args.jacobian)))
     ms64, _ = timed_steps(args.fp64_steps)
     st64 = ctx.stats()
     value64 = world * dof * args.fp64_steps / (ms64 * 1e-3)
@@ -389,6 +394,30 @@ def run_ours(args):
     barrier(world)
     e2e = world * dof * args.e2e_steps / e2e_s
     bytes_step = eta0.nbytes
+
+    # --- rotation diagnostic and adaptivity map of the final state (Sec. II.D) ------
+    ctx.set_amplitudes(eta_dev)
+    ctx.step(1.0, 1)
+    adapt = dict(n=10.0, h_int=2.0, h_max=40.0, eps=0.02, A_min=0.05)
+    ctx.rotation_field(adapt, device=dev)
+    ctx.profile_start("rotation_f64")
+    torch.cuda.synchronize(dev)
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    reps = 5
+    for _ in range(reps):
+        ctx.rotation_field(adapt, device=dev)
+    r1.record(stream)
+    torch.cuda.synchronize(dev)
+    rot = ctx.profile_read("rotation_f64")
+    ctx.profile_stop()
+    rot_ms = rot["ms"] / max(rot["launches"], 1)
+    rotation = {
+        "ms": rot_ms,
+        "gbs": (rot["bytes"] / max(rot["launches"], 1)) / (rot_ms * 1e-3) / 1e9 if rot_ms > 0 else None,
+        "wall_ms_per_call": r0.elapsed_time(r1) / reps,
+    }
 
     # --- CPU baseline: the oracle on this host's cores (rank 0, N = 1 only) -----
     cpu = None
@@ -449,6 +478,7 @@ def run_ours(args):
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step},
         "gpu_launches": prof["all_launches"],
         "breakdown": breakdown,
+        "rotation_diagnostic": rotation,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -905,12 +935,14 @@ def run_adjoint(args):
 
 CHEB = 1
 TOL_INNER = 1e-4
+PICARD = (1, False)
 
 
 def main():
-    global CHEB, TOL_INNER
+    global CHEB, TOL_INNER, PICARD
     args = parse()
     CHEB, TOL_INNER = args.cheb, args.tol_inner
+    PICARD = (args.picard, bool(args.jacobian))
     if args.workload == "batch":
         run_batch_reference(args) if args.impl == "reference" else run_batch(args)
     elif args.workload == "adjoint":
