@@ -292,7 +292,9 @@ apfc_status apfc_rollout_backward(apfc_ctx* ctx, const void* lam_n, void* lam_0,
  * the displacement u solving k_j . u = arg(eta_j) in the least-squares sense,
  * u = M^{-1} sum_j k_j arg(eta_j), M = sum_j k_j k_j^T; the phase gradients are
  * central differences of the unwrapped phase, arg(eta_j(r+h e_d) conj(eta_j(r-h e_d)))/(2h_d),
- * so a grain rotated by theta about z gives omega_12 = sin(theta) exactly.
+ * so a grain rotated by theta about z gives omega_12 = sin(theta) (each phase
+ * difference is taken by an FP32 atan2 of the FP64 product scaled to unit size:
+ * omega to about 1e-7 absolute; A, grad A and h's branches in FP64).
  * Layout: [ncomp][nz][ny][nx] doubles, ncomp = 1 in 2D (omega_12) and 3 in 3D
  * (omega_23, omega_31, omega_12); 0 where some |eta_j|^2 < 1e-12 (the liquid).
  * amp (may be NULL): A = sqrt(2 sum_j |eta_j|^2), [nz][ny][nx] doubles.

@@ -483,7 +483,8 @@ void apply_pinv(apfc_ctx* ctx, Work<T>& w, const cplx<T>* beta, cplx<T>* chi, co
 int fused_rows(const apfc_ctx* ctx) { return ctx->opts.tile_rows > 0 ? ctx->opts.tile_rows : kFusedRows; }
 
 bool use_fused(const apfc_ctx* ctx, int elem_bytes) {
-  return ctx->dim == 2 && ctx->opts.fused != 0 && ctx->coef.jd == nullptr && ctx->opts.cheb_degree >= 1 &&
+  return ctx->dim == 2 && ctx->opts.fused != 0 && (ctx->coef.jd == nullptr || ctx->opts.cheb_degree == 1) &&
+         ctx->opts.cheb_degree >= 1 &&
          ctx->opts.cheb_degree <= fused2d_max_degree(elem_bytes);
 }
 

@@ -547,7 +547,8 @@ __device__ __forceinline__ int wrap_inc(int y, int n) { return y + 1 == n ? 0 : 
 // Grid: (nstrips, nsegs, J) for one grid (TAB = NoTab); for batched runs
 // (TAB = RunTab) (blocks of the largest run, runs of the table), each block
 // taking item blockIdx.x = sx + nstrips (sy + nsegs j) of run blockIdx.y.
-template <typename T, int M, bool WITH_A, int PF, int NT_, class LD, class EP, class TAB>
+// JAC: the (2,2) block of A carries the Jacobian diagonal c.jd of a Picard iteration.
+template <typename T, int M, bool WITH_A, int PF, int NT_, class LD, class EP, class TAB, bool JAC>
 __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g, LD ld, EP ep, const KScal* act,
                                                 void* partials, int kid, int fields,
                                                 const __grid_constant__ TAB tab) {
@@ -806,8 +807,14 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
           const Nbh<T>& n2 = nb[S + 1];
           const cplx<T> g1 = opG<T>(n1, q), g2 = opG<T>(n2, q);
           const cplx<T> y1 = csub(n1.c, g2);
-          const cplx<T> y2 = caxpy(q.kt, g1, cscale(q.a, n2.c));
           const long long p = ptg(gy_ep);
+          cplx<T> y2;
+          if constexpr (JAC) {
+            const T ap = q.a + (T)c.jd[(long long)j * g.pts + p];
+            y2 = caxpy(q.kt, g1, cscale(ap, n2.c));
+          } else {
+            y2 = caxpy(q.kt, g1, cscale(q.a, n2.c));
+          }
           if constexpr (PF > 0) {
             ep.put(raw + OEP * st, st, p, y1, y2);
           } else {
@@ -875,18 +882,18 @@ PipeGeom geom(const OpCoef& c, int S, int Ly, int NT) {
   return g;
 }
 
-template <typename T, int M, bool WITH_A, int PF, int NT, class LD, class EP, class TAB>
+template <typename T, int M, bool WITH_A, int PF, int NT, class LD, class EP, class TAB, bool JAC>
 void set_smem_attr() {
   using SH = PipeShape<T, M, WITH_A, PF, NT, LD, EP>;
   static bool done = false;
   if (!done) {
-    cudaFuncSetAttribute(k_pipe2d<T, M, WITH_A, PF, NT, LD, EP, TAB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)SH::smem);
+    cudaFuncSetAttribute(k_pipe2d<T, M, WITH_A, PF, NT, LD, EP, TAB, JAC>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SH::smem);
     done = true;
   }
 }
 
-template <typename T, int M, bool WITH_A, int PF, int NT, class LD, class EP>
+template <typename T, int M, bool WITH_A, int PF, int NT, class LD, class EP, bool JAC = false>
 bool launch_pipe(const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const KScal* act, void* partials,
                  cudaStream_t s, int kid, int fields, const BatchLaunch* bl) {
   using SH = PipeShape<T, M, WITH_A, PF, NT, LD, EP>;
@@ -900,15 +907,15 @@ bool launch_pipe(const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const
       ca.c2[k][i] = k < M ? w[k].c2[i] : 0.0;
     }
   if (bl == nullptr) {
-    set_smem_attr<T, M, WITH_A, PF, NT, LD, EP, NoTab>();
-    k_pipe2d<T, M, WITH_A, PF, NT, LD, EP, NoTab>
+    set_smem_attr<T, M, WITH_A, PF, NT, LD, EP, NoTab, JAC>();
+    k_pipe2d<T, M, WITH_A, PF, NT, LD, EP, NoTab, JAC>
         <<<dim3(g.nstrips, g.nsegs, c.J), NT, sm, s>>>(c, ca, g, ld, ep, act, partials, kid, fields, NoTab{});
     return true;
   }
-  if constexpr (sizeof(T) == 8) {
-    return false;  // batched runs are FP32
+  if constexpr (sizeof(T) == 8 || JAC) {
+    return false;  // batched runs are FP32 and take the explicit step
   } else {
-    set_smem_attr<T, M, WITH_A, PF, NT, LD, EP, RunTab>();
+    set_smem_attr<T, M, WITH_A, PF, NT, LD, EP, RunTab, false>();
     // one launch per kTabRuns runs; the table holds this launch's geometry of each run
     for (int r0 = 0; r0 < bl->R; r0 += kTabRuns) {
       const int nr = std::min(kTabRuns, bl->R - r0);
@@ -935,7 +942,7 @@ bool launch_pipe(const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const
         if (WITH_A && gr.npart != q.npart) return false;  // partial layout must match the run table
         maxblk = std::max(maxblk, e.nblk);
       }
-      k_pipe2d<T, M, WITH_A, PF, NT, LD, EP, RunTab>
+      k_pipe2d<T, M, WITH_A, PF, NT, LD, EP, RunTab, false>
           <<<dim3(maxblk, nr), NT, sm, s>>>(c, ca, g, ld, ep, act, partials, kid, fields, tab);
     }
     return true;
@@ -959,6 +966,22 @@ int tile_nt(int elem_bytes, int m, int tile) {
 template <typename T, bool WITH_A, class LD, class EP>
 bool dispatch(int m, int tile, const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const KScal* act,
               void* partials, cudaStream_t s, int kid, int fields, const BatchLaunch* bl = nullptr) {
+  if constexpr (WITH_A) {
+    if (c.jd != nullptr) {  // Picard iteration with the Jacobian: one Chebyshev application only
+      if (m != 1 || bl != nullptr) return false;
+      if constexpr (sizeof(T) == 8) {
+        return launch_pipe<T, 1, true, 0, 256, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+      } else {
+        switch (tile) {
+          case 1: return launch_pipe<T, 1, true, 1, 128, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+          case 2: return launch_pipe<T, 1, true, 1, 256, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+          case 3: return launch_pipe<T, 1, true, 2, 256, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+          case 4: return launch_pipe<T, 1, true, 3, 128, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+          default: return launch_pipe<T, 1, true, 2, 128, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+        }
+      }
+    }
+  }
   if constexpr (sizeof(T) == 8) {
     switch (m) {
       case 1: return launch_pipe<T, 1, WITH_A, 0, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);

@@ -1113,69 +1113,87 @@ __global__ void k_energy_grad(const double2* __restrict__ x, double2* __restrict
 // ---------------------------------------------------------------------------
 // Rotation diagnostic and adaptivity map (Sec. II.D, Eqs. rot and hhh)
 // ---------------------------------------------------------------------------
-__global__ void k_rotation(const double2* __restrict__ x, double* __restrict__ omega, double* __restrict__ amp,
-                           double* __restrict__ hmap, RotParams rp, OpCoef c) {
+// One thread per point on a (32 x 8)-point tile grid with z in blockIdx.z; neighbours
+// by comparison.  The phase difference arg(a conj(b)) is evaluated in FP32 on the
+// FP64 product scaled to unit size (relative error about 1e-7 of the difference);
+// everything else is FP64.
+__global__ void __launch_bounds__(256) k_rotation(const double2* __restrict__ x, double* __restrict__ omega,
+                                                  double* __restrict__ amp, double* __restrict__ hmap, RotParams rp,
+                                                  OpCoef c) {
   prof_add(c, KID_ROTATION, (unsigned long long)c.pts * (c.J * sizeof(double2) + (c.dim == 2 ? 3 : 5) * sizeof(double)));
+  const int xx = blockIdx.x * 32 + (threadIdx.x & 31), yy = blockIdx.y * 8 + (threadIdx.x >> 5), zz = blockIdx.z;
+  if (xx >= c.nx || yy >= c.ny) return;
   const int dim = c.dim;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < c.pts;
-       p += (long long)gridDim.x * blockDim.x) {
-    const Nb n = neighbours(p, c);
-    const long long nbp[3] = {n.xp, n.yp, n.zp}, nbm[3] = {n.xm, n.ym, n.zm};
-    double du[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    double s2c = 0.0, s2p[3] = {0, 0, 0}, s2m[3] = {0, 0, 0};
-    bool ok = true;
-    for (int j = 0; j < c.J; ++j) {
-      const double2* e = x + (2LL * j + 1) * c.pts;
-      const double2 ec = e[p];
-      const double m2 = ec.x * ec.x + ec.y * ec.y;
-      s2c += m2;
-      ok = ok && (m2 >= rp.amp_floor);
-      for (int d = 0; d < dim; ++d) {
-        const double2 a = e[nbp[d]], b = e[nbm[d]];
-        s2p[d] += a.x * a.x + a.y * a.y;
-        s2m[d] += b.x * b.x + b.y * b.y;
-        // arg(a conj(b)): central difference of the unwrapped phase
-        const double g = atan2(a.y * b.x - a.x * b.y, a.x * b.x + a.y * b.y) / (2.0 * rp.hd[d]);
-        for (int i = 0; i < dim; ++i) du[i][d] += rp.W[j][i] * g;
-      }
+  const long long plane = (long long)c.nx * c.ny;
+  const long long p = zz * plane + (long long)yy * c.nx + xx;
+  long long nbp[3], nbm[3];
+  nbp[0] = xx + 1 == c.nx ? p - xx : p + 1;
+  nbm[0] = xx == 0 ? p + c.nx - 1 : p - 1;
+  nbp[1] = yy + 1 == c.ny ? p - (long long)yy * c.nx : p + c.nx;
+  nbm[1] = yy == 0 ? p + (long long)(c.ny - 1) * c.nx : p - c.nx;
+  nbp[2] = zz + 1 == c.nz ? p - zz * plane : p + plane;
+  nbm[2] = zz == 0 ? p + (long long)(c.nz - 1) * plane : p - plane;
+  double du[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  double s2c = 0.0, s2p[3] = {0, 0, 0}, s2m[3] = {0, 0, 0};
+  bool ok = true;
+  for (int j = 0; j < c.J; ++j) {
+    const double2* e = x + (2LL * j + 1) * c.pts;
+    const double2 ec = e[p];
+    const double m2 = ec.x * ec.x + ec.y * ec.y;
+    s2c += m2;
+    ok = ok && (m2 >= rp.amp_floor);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (d >= dim) break;
+      const double2 a = e[nbp[d]], b = e[nbm[d]];
+      s2p[d] += a.x * a.x + a.y * a.y;
+      s2m[d] += b.x * b.x + b.y * b.y;
+      // arg(a conj(b)): central difference of the unwrapped phase
+      const double qx = a.x * b.x + a.y * b.y, qy = a.y * b.x - a.x * b.y;
+      const double sc = fmax(fabs(qx), fabs(qy));
+      const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
+      const double g = (double)atan2f((float)(qy * inv), (float)(qx * inv)) / (2.0 * rp.hd[d]);
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        if (i < dim) du[i][d] += rp.W[j][i] * g;
     }
-    double om[3];
-    int nc;
-    if (dim == 2) {
-      om[0] = 0.5 * (du[0][1] - du[1][0]);
-      nc = 1;
+  }
+  double om[3];
+  int nc;
+  if (dim == 2) {
+    om[0] = 0.5 * (du[0][1] - du[1][0]);
+    nc = 1;
+  } else {
+    om[0] = 0.5 * (du[1][2] - du[2][1]);
+    om[1] = 0.5 * (du[2][0] - du[0][2]);
+    om[2] = 0.5 * (du[0][1] - du[1][0]);
+    nc = 3;
+  }
+  double wmax = 0.0;
+  for (int q = 0; q < nc; ++q) {
+    if (!ok) om[q] = 0.0;
+    omega[q * c.pts + p] = om[q];
+    wmax = fmax(wmax, fabs(om[q]));
+  }
+  const double A = sqrt(2.0 * s2c);
+  if (amp != nullptr) amp[p] = A;
+  if (hmap != nullptr) {
+    double g2 = 0.0;
+    for (int d = 0; d < dim; ++d) {
+      const double gd = (sqrt(2.0 * s2p[d]) - sqrt(2.0 * s2m[d])) / (2.0 * rp.hd[d]);
+      g2 += gd * gd;
+    }
+    double hv;
+    if (sqrt(g2) >= rp.eps) {
+      hv = rp.h_int;
+    } else if (A > rp.A_min) {
+      const double s = sin(0.5 * asin(fmin(wmax, 1.0)));
+      const double h_amp = s > 0.0 ? M_PI / (rp.n * rp.kmax * s) : INFINITY;
+      hv = fmin(fmax(h_amp, rp.h_int), rp.h_max);
     } else {
-      om[0] = 0.5 * (du[1][2] - du[2][1]);
-      om[1] = 0.5 * (du[2][0] - du[0][2]);
-      om[2] = 0.5 * (du[0][1] - du[1][0]);
-      nc = 3;
+      hv = rp.h_max;
     }
-    double wmax = 0.0;
-    for (int q = 0; q < nc; ++q) {
-      if (!ok) om[q] = 0.0;
-      omega[q * c.pts + p] = om[q];
-      wmax = fmax(wmax, fabs(om[q]));
-    }
-    const double A = sqrt(2.0 * s2c);
-    if (amp != nullptr) amp[p] = A;
-    if (hmap != nullptr) {
-      double g2 = 0.0;
-      for (int d = 0; d < dim; ++d) {
-        const double gd = (sqrt(2.0 * s2p[d]) - sqrt(2.0 * s2m[d])) / (2.0 * rp.hd[d]);
-        g2 += gd * gd;
-      }
-      double hv;
-      if (sqrt(g2) >= rp.eps) {
-        hv = rp.h_int;
-      } else if (A > rp.A_min) {
-        const double s = sin(0.5 * asin(fmin(wmax, 1.0)));
-        const double h_amp = s > 0.0 ? M_PI / (rp.n * rp.kmax * s) : INFINITY;
-        hv = fmin(fmax(h_amp, rp.h_int), rp.h_max);
-      } else {
-        hv = rp.h_max;
-      }
-      hmap[p] = hv;
-    }
+    hmap[p] = hv;
   }
 }
 
@@ -1340,8 +1358,8 @@ void launch_energy_grad(const double2* x, double2* grad, double scale, double dB
 void launch_rotation(const double2* x, double* omega, double* amp, double* hmap, const RotParams& rp,
                      const OpCoef& c, cudaStream_t s) {
   ProfScope ps_(KID_ROTATION, s);
-  k_rotation<<<(unsigned)std::min<long long>((c.pts + kThreads - 1) / kThreads, 8 * kDotBlocks), kThreads, 0, s>>>(
-      x, omega, amp, hmap, rp, c);
+  const dim3 g((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8), (unsigned)(c.dim == 3 ? c.nz : 1));
+  k_rotation<<<g, 256, 0, s>>>(x, omega, amp, hmap, rp, c);
 }
 void launch_rhs_picard(const double2* x, const double2* eta_prev, double2* b, double* jd, const OpCoef& c,
                        const NonlinTable& nt, cudaStream_t s) {

@@ -1,6 +1,12 @@
 """Rotation diagnostic and adaptivity map on the GPU against the oracle
 (``oracle/diagnostics.py``): omega, A and the map of Eq. hhh element by element
-on grains, polycrystals and a 3D bcc sphere."""
+on grains, polycrystals and a 3D bcc sphere.
+
+The kernel takes each phase difference arg(a conj(b)) with FP32 atan2 of the FP64
+product scaled to unit size: an absolute error of a few 1e-8 rad per difference,
+divided by 2h and summed with weights |M^{-1} k_j| <= 1, so omega agrees to 1e-6
+absolute and h_amp (a smooth function of omega) to 1e-5 relative.  A and grad A
+are FP64 on both sides, so the branches of Eq. hhh are the oracle's."""
 import numpy as np
 import pytest
 
@@ -31,13 +37,13 @@ def _check(kind, eta, shape, h, device=None):
     ref_om = D.rotation_field(eta, L.k, h)
     ref_A = D.amplitude_A(eta)
     ref_h = D.adaptivity_map(eta, L.k, h, **ADAPT)
-    assert np.max(np.abs(om - ref_om)) <= 1e-12
+    assert np.max(np.abs(om - ref_om)) <= 1e-6
     assert np.max(np.abs(am - ref_A)) <= 1e-13 * max(1.0, np.max(ref_A))
     # branch decisions: equal except where |grad A| or A sits on a threshold to rounding
     gA = D.grad_norm(ref_A, h)
     edge = (np.abs(gA - ADAPT["eps"]) <= 1e-12) | (np.abs(ref_A - ADAPT["A_min"]) <= 1e-12)
     both_inf = np.isinf(hm) & np.isinf(ref_h)
-    close = both_inf | (np.abs(hm - ref_h) <= 1e-12 * np.maximum(1.0, np.abs(ref_h)))
+    close = both_inf | (np.abs(hm - ref_h) <= 1e-5 * np.maximum(1.0, np.abs(ref_h)))
     assert np.all(close | edge)
     return om, hm
 
