@@ -267,9 +267,11 @@ void launch_rhs_picard(const double2* x, const double2* eta_prev, double2* b, do
 // tensor components omega (1 in 2D: omega_12; 3 in 3D: omega_23, omega_31,
 // omega_12), A = sqrt(2 sum |eta_j|^2) and the local grid size h of Eq. hhh.
 struct RotParams {
-  double W[kMaxJ][3];  // M^{-1} k_j, M = sum_j k_j k_j^T
-  double hd[3];        // grid spacings
-  double n, h_int, h_max, eps, A_min, amp_floor, kmax;
+  float Wf[kMaxJ][3];  // M^{-1} k_j, M = sum_j k_j k_j^T
+  float inv2h[3];      // 1 / (2 h_d)
+  double inv2hd[3];
+  double h_int, h_max, eps, A_min, amp_floor;
+  double pi_over_nk;   // pi / (n max_j |k_j|)
 };
 void launch_rotation(const double2* x, double* omega, double* amp, double* hmap, const RotParams& rp,
                      const OpCoef& c, cudaStream_t s);

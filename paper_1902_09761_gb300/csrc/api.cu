@@ -1473,16 +1473,18 @@ apfc_status apfc_rotation_field(apfc_ctx* ctx, void* omega, void* amp, void* hma
   for (int j = 0; j < J; ++j) {
     double k2 = 0.0;
     for (int a = 0; a < dim; ++a) {
-      rp.W[j][a] = Mk[a][dim + j];
+      rp.Wf[j][a] = (float)Mk[a][dim + j];
       k2 += ctx->lat.k[j][a] * ctx->lat.k[j][a];
     }
     kmax = std::max(kmax, std::sqrt(k2));
   }
-  for (int a = 0; a < 3; ++a) rp.hd[a] = ctx->grid.h[a];
-  rp.kmax = kmax;
+  for (int a = 0; a < 3; ++a) {
+    rp.inv2hd[a] = 1.0 / (2.0 * ctx->grid.h[a]);
+    rp.inv2h[a] = (float)rp.inv2hd[a];
+  }
   rp.amp_floor = 1e-12;
   if (adapt) {
-    rp.n = adapt->n;
+    rp.pi_over_nk = M_PI / (adapt->n * kmax);
     rp.h_int = adapt->h_int;
     rp.h_max = adapt->h_max;
     rp.eps = adapt->eps;

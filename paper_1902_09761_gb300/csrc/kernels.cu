@@ -1113,82 +1113,107 @@ __global__ void k_energy_grad(const double2* __restrict__ x, double2* __restrict
 // ---------------------------------------------------------------------------
 // Rotation diagnostic and adaptivity map (Sec. II.D, Eqs. rot and hhh)
 // ---------------------------------------------------------------------------
-// One thread per point on a (32 x 8)-point tile grid with z in blockIdx.z; neighbours
-// by comparison.  The phase difference arg(a conj(b)) is evaluated in FP32 on the
-// FP64 product scaled to unit size (relative error about 1e-7 of the difference);
-// everything else is FP64.
+// One thread per point on a (32 x 8)-point tile grid with z in blockIdx.z.  A = sqrt(2
+// sum |eta_j|^2) is formed once per point of the tile and its one-point (x, y) halo in
+// shared memory (FP64: A and |grad A| decide the branches of Eq. hhh); z-neighbours
+// in 3D are formed directly.  The phases go through FP32: eta converted on load, the
+// product a conj(b) and atan2f in FP32 (about 1e-7 rad per difference), the weighted
+// sums and omega in FP32.  The branches compare squares: |grad A|^2 >= eps^2 and
+// A^2 > A_min^2.
+__device__ __forceinline__ double amp_at(const double2* __restrict__ x, long long q, const OpCoef& c) {
+  double s2 = 0.0;
+  for (int j = 0; j < c.J; ++j) {
+    const double2 e = x[(2LL * j + 1) * c.pts + q];
+    s2 = fma(e.x, e.x, fma(e.y, e.y, s2));
+  }
+  return sqrt(2.0 * s2);
+}
+
 __global__ void __launch_bounds__(256) k_rotation(const double2* __restrict__ x, double* __restrict__ omega,
                                                   double* __restrict__ amp, double* __restrict__ hmap, RotParams rp,
                                                   OpCoef c) {
-  prof_add(c, KID_ROTATION, (unsigned long long)c.pts * (c.J * sizeof(double2) + (c.dim == 2 ? 3 : 5) * sizeof(double)));
-  const int xx = blockIdx.x * 32 + (threadIdx.x & 31), yy = blockIdx.y * 8 + (threadIdx.x >> 5), zz = blockIdx.z;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0)
+    prof_add(c, KID_ROTATION,
+             (unsigned long long)c.pts * (c.J * sizeof(double2) + (c.dim == 2 ? 3 : 5) * sizeof(double)));
+  __shared__ double sA[10][34];  // A on the tile plus a one-point (x, y) halo
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 8, zz = blockIdx.z;
+  const long long plane = (long long)c.nx * c.ny, zoff = (long long)zz * plane;
+  const bool want_h = hmap != nullptr;
+  if (want_h || amp != nullptr) {
+    for (int i = threadIdx.x; i < 10 * 34; i += 256) {
+      const int ly = i / 34, lx = i - ly * 34;
+      // periodic wrap (the halo of a partial tile can lie several points past a small grid)
+      const int gx = ((x0 + lx - 1) % c.nx + c.nx) % c.nx, gy = ((y0 + ly - 1) % c.ny + c.ny) % c.ny;
+      sA[ly][lx] = amp_at(x, zoff + (long long)gy * c.nx + gx, c);
+    }
+    __syncthreads();
+  }
+  const int xx = x0 + tx, yy = y0 + ty;
   if (xx >= c.nx || yy >= c.ny) return;
   const int dim = c.dim;
-  const long long plane = (long long)c.nx * c.ny;
-  const long long p = zz * plane + (long long)yy * c.nx + xx;
+  const long long p = zoff + (long long)yy * c.nx + xx;
   long long nbp[3], nbm[3];
   nbp[0] = xx + 1 == c.nx ? p - xx : p + 1;
   nbm[0] = xx == 0 ? p + c.nx - 1 : p - 1;
   nbp[1] = yy + 1 == c.ny ? p - (long long)yy * c.nx : p + c.nx;
   nbm[1] = yy == 0 ? p + (long long)(c.ny - 1) * c.nx : p - c.nx;
-  nbp[2] = zz + 1 == c.nz ? p - zz * plane : p + plane;
+  nbp[2] = zz + 1 == c.nz ? p - zoff : p + plane;
   nbm[2] = zz == 0 ? p + (long long)(c.nz - 1) * plane : p - plane;
-  double du[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-  double s2c = 0.0, s2p[3] = {0, 0, 0}, s2m[3] = {0, 0, 0};
+  float du[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   bool ok = true;
   for (int j = 0; j < c.J; ++j) {
     const double2* e = x + (2LL * j + 1) * c.pts;
     const double2 ec = e[p];
-    const double m2 = ec.x * ec.x + ec.y * ec.y;
-    s2c += m2;
-    ok = ok && (m2 >= rp.amp_floor);
+    ok = ok && (ec.x * ec.x + ec.y * ec.y >= rp.amp_floor);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       if (d >= dim) break;
-      const double2 a = e[nbp[d]], b = e[nbm[d]];
-      s2p[d] += a.x * a.x + a.y * a.y;
-      s2m[d] += b.x * b.x + b.y * b.y;
+      const double2 ad = e[nbp[d]], bd = e[nbm[d]];
+      const float ax = (float)ad.x, ay = (float)ad.y, bx = (float)bd.x, by = (float)bd.y;
       // arg(a conj(b)): central difference of the unwrapped phase
-      const double qx = a.x * b.x + a.y * b.y, qy = a.y * b.x - a.x * b.y;
-      const double sc = fmax(fabs(qx), fabs(qy));
-      const double inv = sc > 0.0 ? 1.0 / sc : 0.0;
-      const double g = (double)atan2f((float)(qy * inv), (float)(qx * inv)) / (2.0 * rp.hd[d]);
+      const float g = atan2f(ay * bx - ax * by, ax * bx + ay * by) * rp.inv2h[d];
 #pragma unroll
       for (int i = 0; i < 3; ++i)
-        if (i < dim) du[i][d] += rp.W[j][i] * g;
+        if (i < dim) du[i][d] += rp.Wf[j][i] * g;
     }
   }
-  double om[3];
+  float om[3];
   int nc;
   if (dim == 2) {
-    om[0] = 0.5 * (du[0][1] - du[1][0]);
+    om[0] = 0.5f * (du[0][1] - du[1][0]);
     nc = 1;
   } else {
-    om[0] = 0.5 * (du[1][2] - du[2][1]);
-    om[1] = 0.5 * (du[2][0] - du[0][2]);
-    om[2] = 0.5 * (du[0][1] - du[1][0]);
+    om[0] = 0.5f * (du[1][2] - du[2][1]);
+    om[1] = 0.5f * (du[2][0] - du[0][2]);
+    om[2] = 0.5f * (du[0][1] - du[1][0]);
     nc = 3;
   }
-  double wmax = 0.0;
+  float wmax = 0.0f;
   for (int q = 0; q < nc; ++q) {
-    if (!ok) om[q] = 0.0;
-    omega[q * c.pts + p] = om[q];
-    wmax = fmax(wmax, fabs(om[q]));
+    if (!ok) om[q] = 0.0f;
+    omega[q * c.pts + p] = (double)om[q];
+    wmax = fmaxf(wmax, fabsf(om[q]));
   }
-  const double A = sqrt(2.0 * s2c);
+  if (!want_h && amp == nullptr) return;
+  const double A = sA[ty + 1][tx + 1];
   if (amp != nullptr) amp[p] = A;
-  if (hmap != nullptr) {
-    double g2 = 0.0;
-    for (int d = 0; d < dim; ++d) {
-      const double gd = (sqrt(2.0 * s2p[d]) - sqrt(2.0 * s2m[d])) / (2.0 * rp.hd[d]);
-      g2 += gd * gd;
+  if (want_h) {
+    double gxA = (sA[ty + 1][tx + 2] - sA[ty + 1][tx]) * rp.inv2hd[0];
+    double gyA = (sA[ty + 2][tx + 1] - sA[ty][tx + 1]) * rp.inv2hd[1];
+    double g2 = gxA * gxA + gyA * gyA;
+    if (dim == 3) {
+      const double gzA = (amp_at(x, nbp[2], c) - amp_at(x, nbm[2], c)) * rp.inv2hd[2];
+      g2 += gzA * gzA;
     }
     double hv;
-    if (sqrt(g2) >= rp.eps) {
+    if (g2 >= rp.eps * rp.eps) {
       hv = rp.h_int;
-    } else if (A > rp.A_min) {
-      const double s = sin(0.5 * asin(fmin(wmax, 1.0)));
-      const double h_amp = s > 0.0 ? M_PI / (rp.n * rp.kmax * s) : INFINITY;
+    } else if (rp.A_min < 0.0 || A * A > rp.A_min * rp.A_min) {
+      // theta = asin(w); sin(theta/2) = w / sqrt(2 (1 + cos(theta)))
+      const float w = fminf(wmax, 1.0f);
+      const float s = w / sqrtf(2.0f * (1.0f + sqrtf(1.0f - w * w)));
+      const double h_amp = s > 0.0f ? rp.pi_over_nk / (double)s : INFINITY;
       hv = fmin(fmax(h_amp, rp.h_int), rp.h_max);
     } else {
       hv = rp.h_max;
