@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--timed-kernel", default="fused_apinv_f32")
     ap.add_argument("--tile", type=int, default=3)
+    ap.add_argument("--tile-t", type=int, default=1, help="tile variant of the t-kernel (-1: same as --tile)")
     ap.add_argument("--rows", type=int, default=0)
     ap.add_argument("--cheb", type=int, default=1, help="Chebyshev applications per diffusion solve")
     ap.add_argument("--tol-inner", type=float, default=1e-4, help="relative tolerance of each FP32 inner solve")
@@ -298,7 +299,7 @@ def run_ours(args):
 
     opts = A.apfc_default_opts(
         precision=A.APFC_FP32_REFINED, tol=TOL, cheb_degree=args.cheb, tol_inner=args.tol_inner, tile=args.tile,
-        tile_rows=args.rows, picard_iters=args.picard, jacobian=int(args.jacobian),
+        tile_rows=args.rows, picard_iters=args.picard, jacobian=int(args.jacobian), tile_t=args.tile_t,
     )
     ctx = A.Context(k, A.APFC_LATTICE_HEX2D, prm, (n, n), (H, H), opts, stream=stream.cuda_stream)
     eta_dev = torch.from_numpy(eta0).to(dev)
@@ -830,7 +831,7 @@ def run_adjoint(args):
     vol = H * H
     stream = torch.cuda.current_stream(dev)
     opts = A.apfc_default_opts(precision=A.APFC_FP32_REFINED, tol=TOL, cheb_degree=args.cheb,
-                               tol_inner=args.tol_inner, tile=args.tile, tile_rows=args.rows)
+                               tol_inner=args.tol_inner, tile=args.tile, tile_rows=args.rows, tile_t=args.tile_t)
     ro = Rollout(inputs.hex_vectors(), A.APFC_LATTICE_HEX2D, PARAMS, (n, n), (H, H), 1.0, K, args.every, opts,
                  device=dev)
     e0_dev = torch.from_numpy(eta0).to(dev)

@@ -108,6 +108,9 @@ typedef struct {
                                 1 (default) with jacobian 0 is the explicit step   */
   int jacobian;              /* 1: linearise N_j with D_j = dN_j/d eta_j (the
                                 paper's J^j, h^j) in every Picard iteration        */
+  int tile_t;                /* variant 0..4 of the fused kernel t = A P^{-1} s of
+                                the merged iteration (-1: same as tile), default 1;
+                                batched runs use tile for both kernels             */
 } apfc_opts;
 
 typedef struct {
@@ -120,7 +123,7 @@ typedef struct {
 
 /* Fill *o with defaults: FP64, BiCGStab, tol 1e-10, max_iter 500,
  * cheb_degree 1, tau fold, max_refine 10, tol_inner 1e-4, check_every 4, fused 1,
- * tile 3, tile_rows 0 (128), picard_iters 1, jacobian 0. */
+ * tile 3, tile_rows 0 (128), picard_iters 1, jacobian 0, tile_t 1. */
 apfc_status apfc_default_opts(apfc_opts* o);
 
 /* Relaxed-solid amplitude phi of a uniform crystal (eta_j = phi for all j):

@@ -63,6 +63,7 @@ class Opts(C.Structure):
         ("tile_rows", C.c_int),
         ("picard_iters", C.c_int),
         ("jacobian", C.c_int),
+        ("tile_t", C.c_int),
     ]
 
 

@@ -556,6 +556,9 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
     const int m = ctx->opts.cheb_degree;
     const int tile = ctx->opts.tile, rows = fused_rows(ctx);
     const int npart = fused ? fused2d_npart(c, m, rows, (int)sizeof(cplx<T>), tile) : kDotBlocks;
+    // the t-kernel is latency-bound: its own tile (less look-ahead, more blocks per SM)
+    const int tile_t = ctx->opts.tile_t >= 0 ? ctx->opts.tile_t : tile;
+    const int npart_t = fused ? fused2d_npart(c, m, rows, (int)sizeof(cplx<T>), tile_t) : kDotBlocks;
     cplx<T>* pp[2] = {p, w.blk[8]};
     cplx<T>* vv[2] = {v, w.blk[9]};
     cplx<T>* rr[2] = {r, w.blk[10]};
@@ -575,9 +578,9 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
                                    pp[1 - cur], vv[1 - cur], rhat, w.ks, w.partials, s);
           launch_finalize<T>(1, w.partials, w.ks, OP_ALPHA, ctx->J, s, npart);  // alpha = rho / (rhat, v')
           // t = A P^{-1} s, s = r' - alpha v'; omega, rho', beta and ||r''||^2 from five inner products
-          launch_fused_merged_t<T>(m, rows, tile, c, cw.data(), rr[1 - cur], vv[1 - cur], t, rhat, w.ks, w.partials,
-                                   s);
-          launch_finalize<T>(5, w.partials, w.ks, OP_OMEGA5, ctx->J, s, npart);
+          launch_fused_merged_t<T>(m, rows, tile_t, c, cw.data(), rr[1 - cur], vv[1 - cur], t, rhat, w.ks,
+                                   w.partials, s);
+          launch_finalize<T>(5, w.partials, w.ks, OP_OMEGA5, ctx->J, s, npart_t);
           // amplitudes that stopped now still owe u += alpha p' + omega s
           launch_final_update<T>(rr[1 - cur], vv[1 - cur], pp[1 - cur], u, w.ks, c, s);
           cur = 1 - cur;
@@ -969,6 +972,7 @@ bool apfc::valid_opts(const apfc_opts& o, std::string& e) {
   else if (o.check_every < 1) e = "check_every";
   else if (o.fused != 0 && o.fused != 1) e = "fused";
   else if (o.tile < 0 || o.tile >= fused2d_tiles()) e = "tile";
+  else if (o.tile_t < -1 || o.tile_t >= fused2d_tiles()) e = "tile_t";
   else if (o.tile_rows < 0 || o.tile_rows > 65536) e = "tile_rows";
   else if (o.picard_iters < 1 || o.picard_iters > 100) e = "picard_iters";
   else if (o.jacobian != 0 && o.jacobian != 1) e = "jacobian";
@@ -1016,6 +1020,7 @@ apfc_status apfc_default_opts(apfc_opts* o) {
   o->tile_rows = 0;
   o->picard_iters = 1;
   o->jacobian = 0;
+  o->tile_t = 1;
   return APFC_OK;
 }
 

@@ -41,7 +41,7 @@ def test_default_opts(lib):
     o = A.apfc_default_opts()
     assert o.precision == A.APFC_FP64 and o.krylov == A.APFC_BICGSTAB
     assert o.tol == 1e-10 and o.max_iter == 500 and o.cheb_degree == 1 and o.tile == 3
-    assert o.picard_iters == 1 and o.jacobian == 0
+    assert o.picard_iters == 1 and o.jacobian == 0 and o.tile_t == 1
     assert o.tau_mode == A.APFC_TAU_FOLD and 0 < o.tol_inner < 1 and o.check_every >= 1
 
 
@@ -74,6 +74,8 @@ def test_uniform_amplitude_matches_closed_forms(lib):
         "picard0",
         "picard101",
         "jac2",
+        "tile_t5",
+        "tile_t_neg2",
     ],
 )
 def test_init_rejects_invalid_arguments_before_touching_cuda(lib, case):
@@ -112,6 +114,10 @@ def test_init_rejects_invalid_arguments_before_touching_cuda(lib, case):
         opts.picard_iters = 101
     elif case == "jac2":
         opts.jacobian = 2
+    elif case == "tile_t5":
+        opts.tile_t = 5
+    elif case == "tile_t_neg2":
+        opts.tile_t = -2
     import ctypes as C
 
     h_ = C.c_void_p()

@@ -235,7 +235,18 @@ def test_tile_variants_parity(tile, rows):
     eta0 = inputs.random_amplitudes(3, (300, 530), seed=8, scale=0.1)
     _trajectory_parity(
         "hex", eta0, (300, 530), (1.2, 0.8), 2, dt=0.5, tol=1e-13, precision=A.APFC_FP32_REFINED, cheb_degree=1,
-        tile=tile, tile_rows=rows,
+        tile=tile, tile_rows=rows, tile_t=-1,
+    )
+
+
+@pytest.mark.parametrize("tile_t", [0, 1, 2, 4])
+def test_separate_t_kernel_tile_parity(tile_t):
+    # the t-kernel of the merged iteration on its own tile variant (its partial sums
+    # follow that variant's block grid)
+    eta0 = inputs.random_amplitudes(3, (300, 530), seed=9, scale=0.1)
+    _trajectory_parity(
+        "hex", eta0, (300, 530), (1.2, 0.8), 2, dt=0.5, tol=1e-13, precision=A.APFC_FP32_REFINED, cheb_degree=1,
+        tile=3, tile_t=tile_t,
     )
 
 
