@@ -39,7 +39,8 @@ def _states(shapes, seed=3):
 
 
 def _opts(**kw):
-    base = dict(precision=A.APFC_FP32_REFINED, tol=1e-12)
+    # tile_t = -1: the run alone uses the batch's tile for both fused kernels
+    base = dict(precision=A.APFC_FP32_REFINED, tol=1e-12, tile_t=-1)
     base.update(kw)
     return A.apfc_default_opts(**base)
 
