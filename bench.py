@@ -118,8 +118,9 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, workload):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current sources."""
+def ncu_traffic(kernel, algorithmic_bytes_per_launch):
+    """DRAM bytes per launch: the committed ncu ratio of DRAM to algorithmic bytes (taken on
+    the current kernel sources) times this run's algorithmic bytes per launch; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -127,7 +128,7 @@ def ncu_traffic(kernel, workload):
         e = d[kernel]
         if e.get("source_hash") != kernel_source_hash():
             return None
-        return float(e["dram_bytes_per_launch_full_size"])
+        return float(e["dram_over_algorithmic"]) * float(algorithmic_bytes_per_launch)
     except Exception:
         return None
 
@@ -336,7 +337,7 @@ def run_ours(args):
     avg_ms = prof["ms"] / max(prof["launches"], 1)
     bytes_per_launch = prof["bytes"] / max(prof["launches"], 1)
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else None
-    traffic = ncu_traffic(args.timed_kernel, f"hex2d-{n}")
+    traffic = ncu_traffic(args.timed_kernel, bytes_per_launch)
 
     # --- per-kernel breakdown: every launch bracketed by events (separate pass) ----
     breakdown = None
