@@ -206,6 +206,8 @@ struct apfc_ctx {
   // Picard iterations: eta^n, and kap_j D_j with the Jacobian
   double2* eta_step = nullptr;
   double* jd = nullptr;
+  // contiguous device copy of host amplitudes (one full-bandwidth host-to-device copy)
+  double2* stage = nullptr;
 };
 
 namespace {
@@ -808,7 +810,13 @@ apfc_status copy_part(apfc_ctx* ctx, void* plain, int where, int part, bool to_s
     k = where == APFC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   else
     k = where == APFC_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  if (to_state)
+  if (to_state && where == APFC_HOST) {
+    // a strided copy from host memory runs at a fraction of the link's bandwidth:
+    // one contiguous copy to the device, then the strided copy on the device
+    if (!ctx->stage) CK(cudaMalloc(&ctx->stage, row * ctx->J));
+    CK(cudaMemcpyAsync(ctx->stage, plain, row * ctx->J, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpy2DAsync(base, 2 * row, ctx->stage, row, row, ctx->J, cudaMemcpyDeviceToDevice, ctx->stream));
+  } else if (to_state)
     CK(cudaMemcpy2DAsync(base, 2 * row, plain, row, row, ctx->J, k, ctx->stream));
   else
     CK(cudaMemcpy2DAsync(plain, row, base, 2 * row, row, ctx->J, k, ctx->stream));
@@ -1187,6 +1195,7 @@ void apfc_destroy(apfc_ctx* ctx) {
   cudaFree(ctx->seg);
   cudaFree(ctx->eta_step);
   cudaFree(ctx->jd);
+  cudaFree(ctx->stage);
   delete ctx;
 }
 
