@@ -101,14 +101,14 @@ typedef struct {
                                 0: one kernel per stencil pass                         */
   double tol;                /* stop at ||b - A x||_2 <= tol ||b||_2 (block norm, per amplitude) */
   double tol_inner;          /* relative tolerance of each FP32 inner solve         */
-  int tile;                  /* fused 2D kernel variant 0..4 (columns per block and
+  int tile;                  /* fused 2D kernel variant 0..5 (columns per block and
                                 rows of look-ahead), default 3                     */
   int tile_rows;             /* rows per block of the fused 2D kernels (0 = 128)   */
   int picard_iters;          /* K of Alg. 1: Picard iterations per step, 1..100;
                                 1 (default) with jacobian 0 is the explicit step   */
   int jacobian;              /* 1: linearise N_j with D_j = dN_j/d eta_j (the
                                 paper's J^j, h^j) in every Picard iteration        */
-  int tile_t;                /* variant 0..4 of the fused kernel t = A P^{-1} s of
+  int tile_t;                /* variant 0..5 of the fused kernel t = A P^{-1} s of
                                 the merged iteration (-1: same as tile), default 1;
                                 batched runs use tile for both kernels             */
 } apfc_opts;
@@ -367,7 +367,7 @@ apfc_status apfc_batch_stats(const apfc_batch* b, int run, apfc_stats_t* out);
 
 /* Tile autotuner: from the first refinement residual of a step of the current
  * state (the state itself is not changed), time a fixed number of merged
- * BiCGStab iterations over all runs for every tile variant (opts.tile 0..4)
+ * BiCGStab iterations over all runs for every tile variant (opts.tile 0..5)
  * and segment height (64, 128, 256 rows), keep the fastest in the batch's
  * options and return it (tile, rows, ms per iteration; null pointers skipped). */
 apfc_status apfc_batch_autotune(apfc_batch* b, double dt, int* tile, int* tile_rows, double* ms_per_iter);

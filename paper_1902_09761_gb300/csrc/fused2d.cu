@@ -953,12 +953,14 @@ bool launch_pipe(const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const
 // degree): NT columns per block and PF rows of asynchronous look-ahead.  Other
 // degrees and FP64 (arithmetic-bound, fetched on use) use one configuration each.
 //   tile 0: NT 128, PF 2   1: NT 128, PF 1   2: NT 256, PF 1   3: NT 256, PF 2   4: NT 128, PF 3
-// Measured on the 4096^2 hexagonal workload, tile 3 with 128-row segments is fastest.
-constexpr int kTiles = 5;
+//   tile 5: NT 256, PF 3
+// Measured on the 4096^2 hexagonal workload with 128-row segments: the v-kernel is fastest
+// with tile 3, the t-kernel (latency-bound) with tile 1.
+constexpr int kTiles = 6;
 int tile_nt(int elem_bytes, int m, int tile) {
   if (elem_bytes == 16) return 256;
   if (m != 1) return 128;
-  return (tile == 2 || tile == 3) ? 256 : 128;
+  return (tile == 2 || tile == 3 || tile == 5) ? 256 : 128;
 }
 
 // fields: algorithmic whole-field transfers per amplitude (counted in units of one
@@ -977,6 +979,7 @@ bool dispatch(int m, int tile, const OpCoef& c, const ChebStep* w, int Ly, LD ld
           case 2: return launch_pipe<T, 1, true, 1, 256, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
           case 3: return launch_pipe<T, 1, true, 2, 256, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
           case 4: return launch_pipe<T, 1, true, 3, 128, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+          case 5: return launch_pipe<T, 1, true, 3, 256, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
           default: return launch_pipe<T, 1, true, 2, 128, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
         }
       }
@@ -997,6 +1000,7 @@ bool dispatch(int m, int tile, const OpCoef& c, const ChebStep* w, int Ly, LD ld
         case 2: return launch_pipe<T, 1, WITH_A, 1, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
         case 3: return launch_pipe<T, 1, WITH_A, 2, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
         case 4: return launch_pipe<T, 1, WITH_A, 3, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+        case 5: return launch_pipe<T, 1, WITH_A, 3, 256>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
         default: return launch_pipe<T, 1, WITH_A, 2, 128>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
       }
     }

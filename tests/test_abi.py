@@ -115,7 +115,7 @@ def test_init_rejects_invalid_arguments_before_touching_cuda(lib, case):
     elif case == "jac2":
         opts.jacobian = 2
     elif case == "tile_t5":
-        opts.tile_t = 5
+        opts.tile_t = 6
     elif case == "tile_t_neg2":
         opts.tile_t = -2
     import ctypes as C

@@ -128,7 +128,7 @@ def test_autotune_keeps_state_and_parity():
     with _batch(states, shapes, opts) as b:
         before = [b.get_amplitudes(r) for r in range(len(shapes))]
         best = b.autotune(1.0)
-        assert 0 <= best["tile"] < 5 and best["tile_rows"] in (64, 128, 256) and best["ms_per_iter"] > 0
+        assert 0 <= best["tile"] < 6 and best["tile_rows"] in (64, 128, 256) and best["ms_per_iter"] > 0
         o = b.opts
         assert o.tile == best["tile"] and o.tile_rows == best["tile_rows"]
         for r in range(len(shapes)):

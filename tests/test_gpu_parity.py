@@ -227,7 +227,7 @@ def test_full_size_voronoi_4096_one_step(prec):
     assert ctx.stats()["resid_last"] <= 1e-10
 
 
-@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("rows", [32, 128])
 def test_tile_variants_parity(tile, rows):
     # Every FP32 variant of the fused pipeline (strip width, look-ahead depth, rows per
@@ -239,7 +239,7 @@ def test_tile_variants_parity(tile, rows):
     )
 
 
-@pytest.mark.parametrize("tile_t", [0, 1, 2, 4])
+@pytest.mark.parametrize("tile_t", [0, 1, 2, 4, 5])
 def test_separate_t_kernel_tile_parity(tile_t):
     # the t-kernel of the merged iteration on its own tile variant (its partial sums
     # follow that variant's block grid)
