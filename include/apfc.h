@@ -109,8 +109,7 @@ typedef struct {
   int jacobian;              /* 1: linearise N_j with D_j = dN_j/d eta_j (the
                                 paper's J^j, h^j) in every Picard iteration        */
   int tile_t;                /* variant 0..5 of the fused kernel t = A P^{-1} s of
-                                the merged iteration (-1: same as tile), default 1;
-                                batched runs use tile for both kernels             */
+                                the merged iteration (-1: same as tile), default 1 */
 } apfc_opts;
 
 typedef struct {
@@ -367,9 +366,11 @@ apfc_status apfc_batch_stats(const apfc_batch* b, int run, apfc_stats_t* out);
 
 /* Tile autotuner: from the first refinement residual of a step of the current
  * state (the state itself is not changed), time a fixed number of merged
- * BiCGStab iterations over all runs for every tile variant (opts.tile 0..5)
- * and segment height (64, 128, 256 rows), keep the fastest in the batch's
- * options and return it (tile, rows, ms per iteration; null pointers skipped). */
+ * BiCGStab iterations over all runs, first for every tile variant (0..5) and
+ * segment height (64, 128, 256 rows) shared by both fused kernels, then for every
+ * variant of the t-kernel alone with the rest fixed; keep the fastest in the
+ * batch's options (tile, tile_rows, tile_t; see apfc_batch_get_opts) and return
+ * tile, rows and ms per iteration (null pointers skipped). */
 apfc_status apfc_batch_autotune(apfc_batch* b, double dt, int* tile, int* tile_rows, double* ms_per_iter);
 
 /* Number of captured-graph replays since creation (-1 for a null batch). */

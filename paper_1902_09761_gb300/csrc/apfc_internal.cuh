@@ -135,14 +135,15 @@ __device__ __forceinline__ void prof_add(const OpCoef& c, int kid, unsigned long
 // first 16-byte partial-sum slot.
 struct RunGeom {
   int nx, ny;
-  long long pts, elem_off, part_off;
-  int npart;  // partial-sum slots per amplitude of the fused kernels with A
-  int pad;
+  long long pts, elem_off;
+  long long part_off, part_off_t;  // first partial-sum slot: v-kernel layout, t-kernel layout
+  int npart, npart_t;              // partial-sum slots per amplitude in each layout
 };
 struct BatchLaunch {
   const RunGeom* dev;   // device copy of the run table (per-point kernels, reductions)
   const RunGeom* host;  // host copy (the fused kernels carry it in their parameters)
   int R;
+  int tlay;  // 1: partial sums in the t-kernel layout (its own tile variant)
 };
 
 // Point a kernel's grid sizes at run `run`; returns the run's first element.

@@ -40,7 +40,8 @@ struct apfc_batch {
   std::vector<int> nx, ny;
   std::vector<RunGeom> rg;  // run table of the current tile / rows
   RunGeom* rg_dev = nullptr;
-  BatchLaunch bl{};
+  BatchLaunch bl{};    // v-kernel partial layout
+  BatchLaunch bl_t{};  // t-kernel partial layout (its own tile variant)
   long long elems = 0;  // complex entries of one concatenated block vector
   NonlinTable nt{};
   EnergyTable et{};
@@ -91,13 +92,15 @@ apfc_status bfail(apfc_batch* b, apfc_status s, const std::string& msg) {
   } while (0)
 
 int rows_of(const apfc_opts& o) { return o.tile_rows > 0 ? o.tile_rows : kDefaultRows; }
+int tile_t_of(const apfc_opts& o) { return o.tile_t >= 0 ? o.tile_t : o.tile; }
 
-// Run table for (tile, rows): element offsets and partial-sum offsets of every
-// run.  Returns the partial slots it needs, or -1 when a fused launch would
-// exceed the grid limit.
-long long make_table(const apfc_batch* b, int tile, int rows, std::vector<RunGeom>& t) {
+// Run table for (tile, rows) of the v-kernel and tile_t of the t-kernel: element
+// offsets and the partial-sum offsets of both layouts for every run.  Returns the
+// partial slots the larger layout needs (the two kernels use the buffer in turn),
+// or -1 when a fused launch would exceed the grid limit.
+long long make_table(const apfc_batch* b, int tile, int rows, int tile_t, std::vector<RunGeom>& t) {
   t.resize(b->R);
-  long long eoff = 0, poff = 0;
+  long long eoff = 0, poff = 0, poff_t = 0;
   const int m = b->opts.cheb_degree, eb = (int)sizeof(float2);
   for (int r = 0; r < b->R; ++r) {
     RunGeom& g = t[r];
@@ -107,15 +110,19 @@ long long make_table(const apfc_batch* b, int tile, int rows, std::vector<RunGeo
     g.pts = (long long)g.nx * g.ny;
     g.elem_off = eoff;
     g.part_off = poff;
-    int np = 0;
+    g.part_off_t = poff_t;
+    int np = 0, np_t = 0;
     const long long nb = fused2d_blocks(g.nx, g.ny, b->J, m, rows, eb, tile, false, nullptr);
     fused2d_blocks(g.nx, g.ny, b->J, m, rows, eb, tile, true, &np);
+    fused2d_blocks(g.nx, g.ny, b->J, m, rows, eb, tile_t, true, &np_t);
     g.npart = np;
+    g.npart_t = np_t;
     eoff += 2LL * b->J * g.pts;
     poff += (long long)b->J * kDotSlots * np;
+    poff_t += (long long)b->J * kDotSlots * np_t;
     if (nb > 0x7fffffffLL) return -1;
   }
-  return poff;
+  return std::max(poff, poff_t);
 }
 
 void drop_graphs(apfc_batch* b) {
@@ -123,10 +130,10 @@ void drop_graphs(apfc_batch* b) {
     if (g) cudaGraphExecDestroy(g), g = nullptr;
 }
 
-// Install the run table of (tile, rows) on the device.
-apfc_status use_table(apfc_batch* b, int tile, int rows) {
+// Install the run table of (tile, rows, tile_t) on the device.
+apfc_status use_table(apfc_batch* b, int tile, int rows, int tile_t) {
   std::vector<RunGeom> t;
-  const long long need = make_table(b, tile, rows, t);
+  const long long need = make_table(b, tile, rows, tile_t, t);
   if (need < 0) return bfail(b, APFC_ETOOBIG, "batch too large for one launch");
   if (need > b->part_pipe_cap) return bfail(b, APFC_EINVAL, "partial-sum buffer too small for this tile");
   BK(cudaMemcpyAsync(b->rg_dev, t.data(), sizeof(RunGeom) * b->R, cudaMemcpyHostToDevice, b->stream));
@@ -135,6 +142,9 @@ apfc_status use_table(apfc_batch* b, int tile, int rows) {
   b->bl.dev = b->rg_dev;
   b->bl.host = b->rg.data();
   b->bl.R = b->R;
+  b->bl.tlay = 0;
+  b->bl_t = b->bl;
+  b->bl_t.tlay = 1;
   drop_graphs(b);
   return APFC_OK;
 }
@@ -177,7 +187,7 @@ Vecs vecs(apfc_batch* b) {
 }
 
 // `every` merged BiCGStab iterations over all runs, starting on side `cur`.
-bool issue_block(apfc_batch* b, int cur, int every, int tile, int rows) {
+bool issue_block(apfc_batch* b, int cur, int every, int tile, int rows, int tile_t) {
   const Vecs x = vecs(b);
   const int m = b->opts.cheb_degree;
   cudaStream_t s = b->stream;
@@ -186,10 +196,10 @@ bool issue_block(apfc_batch* b, int cur, int every, int tile, int rows) {
                                       x.r[1 - cur], x.p[1 - cur], x.v[1 - cur], x.rhat, b->ks, b->part_pipe, s, &b->bl))
       return false;
     launch_finalize_batch<float>(1, b->part_pipe, 0, b->bl, b->J, b->ks, OP_ALPHA, s);
-    if (!launch_fused_merged_t<float>(m, rows, tile, b->coef, b->cw.data(), x.r[1 - cur], x.v[1 - cur], x.t, x.rhat,
-                                      b->ks, b->part_pipe, s, &b->bl))
+    if (!launch_fused_merged_t<float>(m, rows, tile_t, b->coef, b->cw.data(), x.r[1 - cur], x.v[1 - cur], x.t,
+                                      x.rhat, b->ks, b->part_pipe, s, &b->bl_t))
       return false;
-    launch_finalize_batch<float>(5, b->part_pipe, 0, b->bl, b->J, b->ks, OP_OMEGA5, s);
+    launch_finalize_batch<float>(5, b->part_pipe, 0, b->bl_t, b->J, b->ks, OP_OMEGA5, s);
     launch_final_update<float>(x.r[1 - cur], x.v[1 - cur], x.p[1 - cur], x.u, b->ks, b->coef, s, &b->bl);
     cur = 1 - cur;
   }
@@ -237,7 +247,7 @@ apfc_status krylov_init(apfc_batch* b, const std::vector<char>& skip, double tol
 }
 
 // Iterate until every (run, amplitude) has stopped.
-apfc_status krylov_iterate(apfc_batch* b, int max_iter, int tile, int rows) {
+apfc_status krylov_iterate(apfc_batch* b, int max_iter, int tile, int rows, int tile_t) {
   const int every = std::max(1, b->opts.check_every);
   const bool graph = (b->flags & APFC_BATCH_GRAPH) && !profiler_on();
   int cur = 0;
@@ -250,7 +260,7 @@ apfc_status krylov_iterate(apfc_batch* b, int max_iter, int tile, int rows) {
       if (!b->gexec[cur]) {
         cudaGraph_t g = nullptr;
         BK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-        const bool ok = issue_block(b, cur, every, tile, rows);
+        const bool ok = issue_block(b, cur, every, tile, rows, tile_t);
         const cudaError_t ec = cudaStreamEndCapture(b->stream, &g);
         if (!ok) {
           if (g) cudaGraphDestroy(g);
@@ -263,7 +273,7 @@ apfc_status krylov_iterate(apfc_batch* b, int max_iter, int tile, int rows) {
       }
       BK(cudaGraphLaunch(b->gexec[cur], b->stream));
       b->graph_replays += 1;
-    } else if (!issue_block(b, cur, every, tile, rows)) {
+    } else if (!issue_block(b, cur, every, tile, rows, tile_t)) {
       return bfail(b, APFC_EINVAL, "fused pipeline cannot run these options");
     }
     ++blocks;
@@ -279,7 +289,7 @@ apfc_status krylov_iterate(apfc_batch* b, int max_iter, int tile, int rows) {
 // One step of every run: FP32 Krylov solves inside FP64 iterative refinement.
 apfc_status batch_step(apfc_batch* b) {
   cudaStream_t s = b->stream;
-  const int tile = b->opts.tile, rows = rows_of(b->opts);
+  const int tile = b->opts.tile, rows = rows_of(b->opts), tile_t = tile_t_of(b->opts);
   const Vecs x = vecs(b);
   double* part = reinterpret_cast<double*>(b->part_fix);
   bool resid_ready = false;
@@ -337,7 +347,7 @@ apfc_status batch_step(apfc_batch* b) {
     st = krylov_init(b, done, b->opts.tol_inner, b->opts.max_iter, &any);
     if (st != APFC_OK) return st;
     if (any) {
-      st = krylov_iterate(b, b->opts.max_iter, tile, rows);
+      st = krylov_iterate(b, b->opts.max_iter, tile, rows, tile_t);
       if (st != APFC_OK) return st;
       // x += P^{-1} u (u = 0 for runs that did not iterate)
       if (!launch_fused_pinv_add<float>(b->opts.cheb_degree, rows, tile, b->coef, b->cw.data(), x.u, b->x64, s,
@@ -473,7 +483,7 @@ apfc_status apfc_batch_init(apfc_batch** out, const apfc_lattice* lat, const apf
     for (int rows : {32, 64, 128, 256, 512, 1024, o.tile_rows}) {
       if (rows <= 0) continue;
       std::vector<RunGeom> t;
-      const long long need = make_table(b, tile, rows, t);
+      const long long need = make_table(b, tile, rows, tile, t);
       if (need < 0) return cleanup(APFC_ETOOBIG);
       cap = std::max(cap, need);
     }
@@ -501,7 +511,7 @@ apfc_status apfc_batch_init(apfc_batch** out, const apfc_lattice* lat, const apf
   if (cudaMemsetAsync(b->b64, 0, blk64, b->stream) != cudaSuccess) return cleanup(APFC_ECUDA);
   if (cudaMemsetAsync(b->b64_prev, 0, blk64, b->stream) != cudaSuccess) return cleanup(APFC_ECUDA);
   if (cudaMemsetAsync(b->ks64, 0, nks, b->stream) != cudaSuccess) return cleanup(APFC_ECUDA);
-  if (use_table(b, o.tile, rows_of(o)) != APFC_OK) return cleanup(APFC_ECUDA);
+  if (use_table(b, o.tile, rows_of(o), tile_t_of(o)) != APFC_OK) return cleanup(APFC_ECUDA);
   if (!set_coef(b, 1.0, e)) return cleanup(APFC_EINVAL);
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return cleanup(APFC_ECUDA);
   *out = b;
@@ -513,16 +523,16 @@ apfc_status apfc_batch_set_opts(apfc_batch* b, const apfc_opts* opts) {
   std::string e;
   if (!valid_batch_opts(*opts, e)) return bfail(b, APFC_EINVAL, e);
   const bool retable = opts->tile != b->opts.tile || rows_of(*opts) != rows_of(b->opts) ||
-                       opts->cheb_degree != b->opts.cheb_degree;
+                       tile_t_of(*opts) != tile_t_of(b->opts) || opts->cheb_degree != b->opts.cheb_degree;
   const apfc_opts old = b->opts;
   b->opts = *opts;
   if (retable) {
     std::vector<RunGeom> t;
-    if (make_table(b, opts->tile, rows_of(*opts), t) > b->part_pipe_cap) {
+    if (make_table(b, opts->tile, rows_of(*opts), tile_t_of(*opts), t) > b->part_pipe_cap) {
       b->opts = old;
       return bfail(b, APFC_EINVAL, "tile_rows outside the sizes the batch was created for");
     }
-    apfc_status st = use_table(b, opts->tile, rows_of(*opts));
+    apfc_status st = use_table(b, opts->tile, rows_of(*opts), tile_t_of(*opts));
     if (st != APFC_OK) return st;
   }
   const double dt = b->coef_dt;
@@ -616,39 +626,54 @@ apfc_status apfc_batch_autotune(apfc_batch* b, double dt, int* tile_out, int* ro
   cudaEvent_t e0, e1;
   BK(cudaEventCreate(&e0));
   BK(cudaEventCreate(&e1));
-  int best_tile = b->opts.tile, best_rows = rows_of(b->opts);
+  int best_tile = b->opts.tile, best_rows = rows_of(b->opts), best_t = tile_t_of(b->opts);
   double best = 1e300;
   std::vector<char> none(b->R, 0);
   apfc_status st = APFC_OK;
+  // time kTuneIters merged iterations for one (tile, rows, tile_t)
+  auto time_candidate = [&](int tile, int rows, int tile_t, double* ms) -> apfc_status {
+    *ms = 1e300;
+    apfc_status s2 = use_table(b, tile, rows, tile_t);
+    if (s2 != APFC_OK) return s2;
+    for (int rep = 0; rep < 2; ++rep) {  // the first pass warms up
+      bool any = false;
+      // a tolerance no solve reaches within kTuneIters iterations
+      if ((s2 = krylov_init(b, none, 1e-30, 1 << 20, &any)) != APFC_OK) return s2;
+      BK(cudaEventRecord(e0, s));
+      if (!issue_block(b, 0, kTuneIters, tile, rows, tile_t))
+        return bfail(b, APFC_EINVAL, "fused pipeline cannot run these options");
+      BK(cudaEventRecord(e1, s));
+      BK(cudaEventSynchronize(e1));
+      float f = 0.f;
+      BK(cudaEventElapsedTime(&f, e0, e1));
+      *ms = f;
+    }
+    return APFC_OK;
+  };
+  // pass 1: both kernels on one variant; pass 2: the t-kernel's variant with the rest fixed
   for (int tile = 0; tile < fused2d_tiles() && st == APFC_OK; ++tile)
     for (int rows : kTuneRows) {
       std::vector<RunGeom> t;
-      if (make_table(b, tile, rows, t) > b->part_pipe_cap) continue;
-      if ((st = use_table(b, tile, rows)) != APFC_OK) break;
+      if (make_table(b, tile, rows, tile, t) > b->part_pipe_cap) continue;
       double ms = 1e300;
-      for (int rep = 0; rep < 2 && st == APFC_OK; ++rep) {  // the first pass warms up
-        bool any = false;
-        // a tolerance no solve reaches within kTuneIters iterations
-        if ((st = krylov_init(b, none, 1e-30, 1 << 20, &any)) != APFC_OK) break;
-        BK(cudaEventRecord(e0, s));
-        if (!issue_block(b, 0, kTuneIters, tile, rows)) {
-          st = bfail(b, APFC_EINVAL, "fused pipeline cannot run these options");
-          break;
-        }
-        BK(cudaEventRecord(e1, s));
-        BK(cudaEventSynchronize(e1));
-        float f = 0.f;
-        BK(cudaEventElapsedTime(&f, e0, e1));
-        ms = f;
-      }
-      if (st == APFC_OK && ms < best) best = ms, best_tile = tile, best_rows = rows;
+      if ((st = time_candidate(tile, rows, tile, &ms)) != APFC_OK) break;
+      if (ms < best) best = ms, best_tile = tile, best_rows = rows, best_t = tile;
     }
+  for (int tile_t = 0; tile_t < fused2d_tiles() && st == APFC_OK; ++tile_t) {
+    if (tile_t == best_t) continue;
+    std::vector<RunGeom> t;
+    if (make_table(b, best_tile, best_rows, tile_t, t) > b->part_pipe_cap) continue;
+    double ms = 1e300;
+    if ((st = time_candidate(best_tile, best_rows, tile_t, &ms)) != APFC_OK) break;
+    if (ms < best) best = ms, best_t = tile_t;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != APFC_OK) return st;
   b->opts.tile = best_tile;
   b->opts.tile_rows = best_rows;
-  st = use_table(b, best_tile, best_rows);
+  b->opts.tile_t = best_t;
+  st = use_table(b, best_tile, best_rows, best_t);
   if (st != APFC_OK) return st;
   if (tile_out) *tile_out = best_tile;
   if (rows_out) *rows_out = best_rows;

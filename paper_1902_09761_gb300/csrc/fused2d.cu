@@ -931,7 +931,7 @@ bool launch_pipe(const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const
         RunRec& e = tab.run[i];
         e.pts = q.pts;
         e.elem_off = q.elem_off;
-        e.part_off = q.part_off;
+        e.part_off = bl->tlay ? q.part_off_t : q.part_off;
         e.nx = q.nx;
         e.ny = q.ny;
         e.Ly = gr.Ly;
@@ -939,7 +939,7 @@ bool launch_pipe(const OpCoef& c, const ChebStep* w, int Ly, LD ld, EP ep, const
         e.nsegs = gr.nsegs;
         e.nblk = gr.npart * c.J;
         e.run = r0 + i;
-        if (WITH_A && gr.npart != q.npart) return false;  // partial layout must match the run table
+        if (WITH_A && gr.npart != (bl->tlay ? q.npart_t : q.npart)) return false;  // layout must match the table
         maxblk = std::max(maxblk, e.nblk);
       }
       k_pipe2d<T, M, WITH_A, PF, NT, LD, EP, RunTab, false>

@@ -82,12 +82,21 @@ __global__ void k_finalize(const void* partials, int npart, KScal* ks, int op) {
 }
 
 // Batched runs: block run * J + j.  npart_fixed > 0: the run's partials follow the
-// fixed layout of k_dots; 0: the fused-pipeline layout of the run table.
+// fixed layout of k_dots; 0: the fused-pipeline layout of the run table (the
+// t-kernel's when tlay).
 template <typename T, int NP>
-__global__ void k_finalize_batch(const void* partials, int npart_fixed, const RunGeom* rg, int J, KScal* ks, int op) {
+__global__ void k_finalize_batch(const void* partials, int npart_fixed, const RunGeom* rg, int J, KScal* ks, int op,
+                                 int tlay) {
   const int run = blockIdx.x / J, j = blockIdx.x - run * J;
-  const long long base = npart_fixed > 0 ? (long long)run * J * kDotSlots * npart_fixed : rg[run].part_off;
-  const int npart = npart_fixed > 0 ? npart_fixed : rg[run].npart;
+  long long base;
+  int npart;
+  if (npart_fixed > 0) {
+    base = (long long)run * J * kDotSlots * npart_fixed;
+    npart = npart_fixed;
+  } else {
+    base = tlay ? rg[run].part_off_t : rg[run].part_off;
+    npart = tlay ? rg[run].npart_t : rg[run].npart;
+  }
   finalize_one<T, NP>(partials, base, npart, j, ks[blockIdx.x], op);
 }
 
@@ -126,11 +135,11 @@ void launch_finalize_batch(int npair, const void* partials, int npart_fixed, con
   ProfScope ps_(kid_of<T>(KID_FINALIZE), s);
   const int nb = bl.R * J;
   if (npair == 1)
-    k_finalize_batch<T, 1><<<nb, kThreads, 0, s>>>(partials, npart_fixed, bl.dev, J, k, op);
+    k_finalize_batch<T, 1><<<nb, kThreads, 0, s>>>(partials, npart_fixed, bl.dev, J, k, op, bl.tlay);
   else if (npair == 2)
-    k_finalize_batch<T, 2><<<nb, kThreads, 0, s>>>(partials, npart_fixed, bl.dev, J, k, op);
+    k_finalize_batch<T, 2><<<nb, kThreads, 0, s>>>(partials, npart_fixed, bl.dev, J, k, op, bl.tlay);
   else
-    k_finalize_batch<T, 5><<<nb, kThreads, 0, s>>>(partials, npart_fixed, bl.dev, J, k, op);
+    k_finalize_batch<T, 5><<<nb, kThreads, 0, s>>>(partials, npart_fixed, bl.dev, J, k, op, bl.tlay);
 }
 
 void launch_finalize64(int npair, const void* partials, KScal* k, int op, int J, cudaStream_t s) {

@@ -39,8 +39,7 @@ def _states(shapes, seed=3):
 
 
 def _opts(**kw):
-    # tile_t = -1: the run alone uses the batch's tile for both fused kernels
-    base = dict(precision=A.APFC_FP32_REFINED, tol=1e-12, tile_t=-1)
+    base = dict(precision=A.APFC_FP32_REFINED, tol=1e-12)
     base.update(kw)
     return A.apfc_default_opts(**base)
 
@@ -91,11 +90,11 @@ def test_each_batched_run_equals_the_run_alone(graph):
         assert replays == 0
 
 
-@pytest.mark.parametrize("m,tile,rows", [(1, 0, 64), (1, 2, 256), (3, 0, 128)])
-def test_batched_runs_equal_alone_across_tiles_and_degrees(m, tile, rows):
+@pytest.mark.parametrize("m,tile,rows,tile_t", [(1, 0, 64, -1), (1, 2, 256, 4), (1, 5, 128, 0), (3, 0, 128, -1)])
+def test_batched_runs_equal_alone_across_tiles_and_degrees(m, tile, rows, tile_t):
     shapes = SHAPES[:4] + [(300, 530)]
     states = _states(shapes, seed=9)
-    opts = _opts(cheb_degree=m, tile=tile, tile_rows=rows, check_every=3)
+    opts = _opts(cheb_degree=m, tile=tile, tile_rows=rows, check_every=3, tile_t=tile_t)
     with _batch(states, shapes, opts) as b:
         b.step(1.0, 2)
         got = [b.get_amplitudes(r) for r in range(len(shapes))]
@@ -130,7 +129,7 @@ def test_autotune_keeps_state_and_parity():
         best = b.autotune(1.0)
         assert 0 <= best["tile"] < 6 and best["tile_rows"] in (64, 128, 256) and best["ms_per_iter"] > 0
         o = b.opts
-        assert o.tile == best["tile"] and o.tile_rows == best["tile_rows"]
+        assert o.tile == best["tile"] and o.tile_rows == best["tile_rows"] and 0 <= o.tile_t < 6
         for r in range(len(shapes)):
             assert np.array_equal(b.get_amplitudes(r), before[r])
         b.step(1.0, 2)
