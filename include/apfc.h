@@ -103,7 +103,9 @@ typedef struct {
   double tol_inner;          /* relative tolerance of each FP32 inner solve         */
   int tile;                  /* fused 2D kernel variant 0..5 (columns per block and
                                 rows of look-ahead), default 3                     */
-  int tile_rows;             /* rows per block of the fused 2D kernels (0 = 128)   */
+  int tile_rows;             /* rows per block of the fused 2D kernels; 0 (default):
+                                the tallest of 128, 64, 32 rows that gives the first
+                                fused kernel's launch >= 1.5 blocks per SM         */
   int picard_iters;          /* K of Alg. 1: Picard iterations per step, 1..100;
                                 1 (default) with jacobian 0 is the explicit step   */
   int jacobian;              /* 1: linearise N_j with D_j = dN_j/d eta_j (the
@@ -122,7 +124,7 @@ typedef struct {
 
 /* Fill *o with defaults: FP64, BiCGStab, tol 1e-10, max_iter 500,
  * cheb_degree 1, tau fold, max_refine 10, tol_inner 1e-4, check_every 4, fused 1,
- * tile 3, tile_rows 0 (128), picard_iters 1, jacobian 0, tile_t 1. */
+ * tile 3, tile_rows 0 (automatic), picard_iters 1, jacobian 0, tile_t 1. */
 apfc_status apfc_default_opts(apfc_opts* o);
 
 /* Relaxed-solid amplitude phi of a uniform crystal (eta_j = phi for all j):

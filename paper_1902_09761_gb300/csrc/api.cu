@@ -157,6 +157,7 @@ void profiler_stop() { g_prof.on = false; }
 }  // namespace apfc
 
 struct apfc_ctx {
+  int sms = 152;  // multiprocessors of the context's device
   apfc_lattice lat;
   apfc_params par;
   apfc_grid grid;
@@ -482,7 +483,21 @@ void apply_pinv(apfc_ctx* ctx, Work<T>& w, const cplx<T>* beta, cplx<T>* chi, co
   launch_pc_final<T>(beta, CFieldRef<T>{b2p.p, P}, chi, c, act, ctx->stream);
 }
 
-int fused_rows(const apfc_ctx* ctx) { return ctx->opts.tile_rows > 0 ? ctx->opts.tile_rows : kFusedRows; }
+// Rows per block segment of the fused kernels.  tile_rows 0: the tallest of 128, 64 and
+// 32 rows that still gives the v-kernel's launch about 1.5 blocks per SM (taller segments
+// waste less on the 3S-row pipeline fill, but on small grids they leave SMs idle:
+// 512^2 runs twice as fast with 32-row segments as with 128).
+int fused_rows(const apfc_ctx* ctx) {
+  if (ctx->opts.tile_rows > 0) return ctx->opts.tile_rows;
+  const int elem = ctx->opts.precision == APFC_FP64 ? (int)sizeof(double2) : (int)sizeof(float2);
+  const int m = std::max(1, ctx->opts.cheb_degree);
+  for (int rows : {kFusedRows, kFusedRows / 2}) {
+    int np = 0;
+    fused2d_blocks(ctx->grid.n[0], ctx->grid.n[1], ctx->J, m, rows, elem, ctx->opts.tile, true, &np);
+    if (2LL * np * ctx->J >= 3LL * ctx->sms) return rows;
+  }
+  return kFusedRows / 4;
+}
 
 bool use_fused(const apfc_ctx* ctx, int elem_bytes) {
   return ctx->dim == 2 && ctx->opts.fused != 0 && (ctx->coef.jd == nullptr || ctx->opts.cheb_degree == 1) &&
@@ -1072,6 +1087,12 @@ apfc_status apfc_init(apfc_ctx** out, const apfc_lattice* lat, const apfc_params
   if (lat->dim == 2) ctx->grid.n[2] = 1, ctx->grid.h[2] = 1.0;
   ctx->opts = o;
   ctx->stream = static_cast<cudaStream_t>(stream);
+  {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        sms > 0)
+      ctx->sms = sms;
+  }
   ctx->J = lat->J;
   ctx->dim = lat->dim;
   ctx->pts = (long long)g->n[0] * g->n[1] * (lat->dim == 3 ? g->n[2] : 1);
