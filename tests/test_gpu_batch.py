@@ -39,7 +39,9 @@ def _states(shapes, seed=3):
 
 
 def _opts(**kw):
-    base = dict(precision=A.APFC_FP32_REFINED, tol=1e-12)
+    # explicit segment height: a batch uses one height for all runs (tile_rows 0 is 128
+    # rows there), a run alone would pick its own
+    base = dict(precision=A.APFC_FP32_REFINED, tol=1e-12, tile_rows=128)
     base.update(kw)
     return A.apfc_default_opts(**base)
 
