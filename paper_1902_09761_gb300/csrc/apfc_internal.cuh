@@ -71,6 +71,7 @@ struct OpCoef {
   double inv_theta[kMaxJ];  // Chebyshev: 1/theta, theta = centre of D's interval
   unsigned long long* prof; // device byte counters per kernel id (nullptr: not measuring)
   const double* jd;         // Picard with Jacobian: kap_j D_j per point, [J][pts] (nullptr: none)
+  const float2* jd32;       // the same as {value, 0} for the FP32 fused kernels' staged fetch
 };
 
 // (2,2) block of A_j at point p: a_j, plus kap_j D_j(p) when the Jacobian is on.
@@ -262,8 +263,8 @@ void launch_adj_nonlin(const double2* eta0, const double2* xg, const double2* et
                        double* out, const OpCoef& c, const NonlinTable& nt, cudaStream_t s);
 // Picard iteration of Alg. 1: b_j = eta_prev_j/dt - kap_j (N_j - D_j eta_j) from the
 // previous iterate (eta-parts of x); jd (nullable) receives kap_j D_j, D_j = dN_j/d eta_j
-void launch_rhs_picard(const double2* x, const double2* eta_prev, double2* b, double* jd, const OpCoef& c,
-                       const NonlinTable& nt, cudaStream_t s);
+void launch_rhs_picard(const double2* x, const double2* eta_prev, double2* b, double* jd, float2* jd32,
+                       const OpCoef& c, const NonlinTable& nt, cudaStream_t s);
 // Rotation diagnostic and adaptivity map (Sec. II.D): per point the rotation
 // tensor components omega (1 in 2D: omega_12; 3 in 3D: omega_23, omega_31,
 // omega_12), A = sqrt(2 sum |eta_j|^2) and the local grid size h of Eq. hhh.

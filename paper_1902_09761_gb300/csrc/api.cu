@@ -207,6 +207,7 @@ struct apfc_ctx {
   // Picard iterations: eta^n, and kap_j D_j with the Jacobian
   double2* eta_step = nullptr;
   double* jd = nullptr;
+  float2* jd32 = nullptr;
   // contiguous device copy of host amplitudes (one full-bandwidth host-to-device copy)
   double2* stage = nullptr;
 };
@@ -952,17 +953,21 @@ apfc_status step_picard(apfc_ctx* ctx) {
   if (!ctx->eta_step) CK(cudaMalloc(&ctx->eta_step, sizeof(double2) * fe));
   const bool jac = ctx->opts.jacobian != 0;
   if (jac && !ctx->jd) CK(cudaMalloc(&ctx->jd, sizeof(double) * fe));
+  if (jac && !ctx->jd32) CK(cudaMalloc(&ctx->jd32, sizeof(float2) * fe));
   apfc_status st = block_to_field(ctx, ctx->eta_step, ctx->x64, 1);
   if (st != APFC_OK) return st;
   ctx->have_prev = false;
   int total = 0;
   for (int k = 0; k < ctx->opts.picard_iters; ++k) {
     // b and kap D from eta^(k-1), the eta-parts of the state; solve from x^(k-1)
-    launch_rhs_picard(ctx->x64, ctx->eta_step, ctx->b64, jac ? ctx->jd : nullptr, ctx->coef, ctx->nt, ctx->stream);
+    launch_rhs_picard(ctx->x64, ctx->eta_step, ctx->b64, jac ? ctx->jd : nullptr, jac ? ctx->jd32 : nullptr,
+                      ctx->coef, ctx->nt, ctx->stream);
     ctx->coef.jd = jac ? ctx->jd : nullptr;
+    ctx->coef.jd32 = jac ? ctx->jd32 : nullptr;
     int it = 0;
     st = solve_block(ctx, ctx->b64, ctx->x64, &it);
     ctx->coef.jd = nullptr;
+    ctx->coef.jd32 = nullptr;
     total += it;
     if (st != APFC_OK) return st;
   }
@@ -1216,6 +1221,7 @@ void apfc_destroy(apfc_ctx* ctx) {
   cudaFree(ctx->seg);
   cudaFree(ctx->eta_step);
   cudaFree(ctx->jd);
+  cudaFree(ctx->jd32);
   cudaFree(ctx->stage);
   delete ctx;
 }

@@ -428,6 +428,22 @@ struct EpV {  // v = y; (rhat, v)
   }
 };
 
+// Epilogue of a Picard iteration with the Jacobian on FP32 grids: the wrapped epilogue's
+// operands plus kap_j D_j of the point (stored as {value, 0}), staged with them.
+template <class EP, typename T>
+struct EpJ : EP {
+  static constexpr int NEP = EP::NEP + 1;
+  const float2* jd32;
+  long long jo;
+  __device__ void setup(int j, const KScal* k) {
+    EP::setup(j, k);
+    jo = (long long)j * EP::pts;
+  }
+  __device__ const cplx<T>* ep(int i) const {
+    return i < EP::NEP ? EP::ep(i) : reinterpret_cast<const cplx<T>*>(jd32 + jo);
+  }
+};
+
 template <typename T>
 struct EpT {  // t = y; (t, s), (t, t), (s, s) with s = r - alpha v
   static constexpr int NDOT = 3, NEP = 4;
@@ -810,7 +826,13 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
           const long long p = ptg(gy_ep);
           cplx<T> y2;
           if constexpr (JAC) {
-            const T ap = q.a + (T)c.jd[(long long)j * g.pts + p];
+            T jdv;
+            if constexpr (PF > 0 && sizeof(T) == 4) {
+              jdv = raw[(OEP + EP::NEP - 1) * st].x;  // staged with the epilogue operands (EpJ)
+            } else {
+              jdv = (T)c.jd[(long long)j * g.pts + p];
+            }
+            const T ap = q.a + jdv;
             y2 = caxpy(q.kt, g1, cscale(ap, n2.c));
           } else {
             y2 = caxpy(q.kt, g1, cscale(q.a, n2.c));
@@ -974,13 +996,18 @@ bool dispatch(int m, int tile, const OpCoef& c, const ChebStep* w, int Ly, LD ld
       if constexpr (sizeof(T) == 8) {
         return launch_pipe<T, 1, true, 0, 256, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
       } else {
+        if (c.jd32 == nullptr) return false;
+        EpJ<EP, T> ej{};
+        static_cast<EP&>(ej) = ep;
+        ej.jd32 = c.jd32;
+        using EJ = EpJ<EP, T>;
         switch (tile) {
-          case 1: return launch_pipe<T, 1, true, 1, 128, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
-          case 2: return launch_pipe<T, 1, true, 1, 256, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
-          case 3: return launch_pipe<T, 1, true, 2, 256, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
-          case 4: return launch_pipe<T, 1, true, 3, 128, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
-          case 5: return launch_pipe<T, 1, true, 3, 256, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
-          default: return launch_pipe<T, 1, true, 2, 128, LD, EP, true>(c, w, Ly, ld, ep, act, partials, s, kid, fields, bl);
+          case 1: return launch_pipe<T, 1, true, 1, 128, LD, EJ, true>(c, w, Ly, ld, ej, act, partials, s, kid, fields, bl);
+          case 2: return launch_pipe<T, 1, true, 1, 256, LD, EJ, true>(c, w, Ly, ld, ej, act, partials, s, kid, fields, bl);
+          case 3: return launch_pipe<T, 1, true, 2, 256, LD, EJ, true>(c, w, Ly, ld, ej, act, partials, s, kid, fields, bl);
+          case 4: return launch_pipe<T, 1, true, 3, 128, LD, EJ, true>(c, w, Ly, ld, ej, act, partials, s, kid, fields, bl);
+          case 5: return launch_pipe<T, 1, true, 3, 256, LD, EJ, true>(c, w, Ly, ld, ej, act, partials, s, kid, fields, bl);
+          default: return launch_pipe<T, 1, true, 2, 128, LD, EJ, true>(c, w, Ly, ld, ej, act, partials, s, kid, fields, bl);
         }
       }
     }

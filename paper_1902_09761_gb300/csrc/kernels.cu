@@ -1046,7 +1046,8 @@ __device__ __forceinline__ double jac_diag_at(const double2* eta, int j, const O
 // eta-parts of x), b_j = eta_prev_j/dt - kap_j (N_j - D_j eta_j) and jd_j = kap_j D_j
 // (jd == nullptr: plain Picard, D = 0).
 __global__ void k_rhs_picard(const double2* __restrict__ x, const double2* __restrict__ eta_prev,
-                             double2* __restrict__ b, double* __restrict__ jd, OpCoef c, NonlinTable nt) {
+                             double2* __restrict__ b, double* __restrict__ jd, float2* __restrict__ jd32, OpCoef c,
+                             NonlinTable nt) {
   prof_add(c, KID_RHS, (unsigned long long)c.J * c.pts * (3 * sizeof(double2) + (jd ? sizeof(double) : 0)));
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < c.pts;
        p += (long long)gridDim.x * blockDim.x) {
@@ -1060,6 +1061,7 @@ __global__ void k_rhs_picard(const double2* __restrict__ x, const double2* __res
       b[(2LL * j + 1) * c.pts + p] = make_double2(ep.x * c.inv_dt - kap * (N.x - D * eta[j].x),
                                                  ep.y * c.inv_dt - kap * (N.y - D * eta[j].y));
       if (jd != nullptr) jd[j * c.pts + p] = kap * D;
+      if (jd32 != nullptr) jd32[j * c.pts + p] = make_float2((float)(kap * D), 0.f);
     }
   }
 }
@@ -1386,11 +1388,11 @@ void launch_rotation(const double2* x, double* omega, double* amp, double* hmap,
   const dim3 g((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8), (unsigned)(c.dim == 3 ? c.nz : 1));
   k_rotation<<<g, 256, 0, s>>>(x, omega, amp, hmap, rp, c);
 }
-void launch_rhs_picard(const double2* x, const double2* eta_prev, double2* b, double* jd, const OpCoef& c,
-                       const NonlinTable& nt, cudaStream_t s) {
+void launch_rhs_picard(const double2* x, const double2* eta_prev, double2* b, double* jd, float2* jd32,
+                       const OpCoef& c, const NonlinTable& nt, cudaStream_t s) {
   ProfScope ps_(KID_RHS, s);
   k_rhs_picard<<<(unsigned)std::min<long long>((c.pts + kThreads - 1) / kThreads, 8 * kDotBlocks), kThreads, 0, s>>>(
-      x, eta_prev, b, jd, c, nt);
+      x, eta_prev, b, jd, jd32, c, nt);
 }
 #define APFC_INST(T)                                                                                                 \
   template void launch_apply_A<T>(const cplx<T>*, cplx<T>*, const OpCoef&, const KScal*, cudaStream_t);             \
