@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--breakdown-steps", type=int, default=3, help="steps of the per-kernel timing pass (0: off)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument(
-        "--workload", choices=["voronoi", "batch", "adjoint"], default="voronoi",
+        "--workload", choices=["voronoi", "batch", "adjoint", "bcc3d"], default="voronoi",
         help="voronoi: one n x n polycrystal (default); batch: independent runs of uneven sizes in one batch; "
         "adjoint: gradient of a rollout loss by the checkpointed adjoint",
     )
@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--rollout", type=int, default=200, help="adjoint: steps per rollout")
     ap.add_argument("--every", type=int, default=20, help="adjoint: steps between checkpoints")
     ap.add_argument("--adj-size", type=int, default=1024, help="adjoint: grid points per side")
+    ap.add_argument("--bcc-size", type=int, default=256, help="bcc3d: grid points per side")
     ap.add_argument("--runs", type=int, default=64, help="batch: number of independent runs")
     ap.add_argument("--no-graph", action="store_true", help="batch: launch the Krylov blocks without graphs")
     ap.add_argument("--no-autotune", action="store_true", help="batch: keep --tile / --rows")
@@ -937,6 +938,181 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# 3D bcc workload: a rotated spherical grain in an unrotated matrix
+# ---------------------------------------------------------------------------
+
+
+def bcc_config(args):
+    n = args.bcc_size
+    return {
+        "workload": f"bcc3d-{n}^3-sphere",
+        "lattice": "bcc, J=6, k = <110>/sqrt2",
+        "grid": [n, n, n],
+        "initial": "sphere R = 60 rotated 8 deg about [001] in an unrotated matrix, noise 1e-3, seed 2",
+        "h": "pi/2",
+        "dt": 1.0,
+        "params": {"dB": PARAMS[0], "Bx": PARAMS[1], "t": PARAMS[2], "v": PARAMS[3]},
+        "tol": TOL,
+        "tol_inner": TOL_INNER,
+        "cheb_degree": CHEB,
+        "kernels": "one kernel per stencil pass, z-streaming 32x8 tiles",
+        "l2": f"inputs larger than L2 (FP64 state {16 * 12 * n ** 3 / 1e9:.1f} GB); no flush",
+    }
+
+
+def run_bcc_reference(args):
+    world, rank, local = init_dist(args)
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_1902_09761_gb300 import inputs
+
+    P = O.params_from_paper(0.98, 0.01, 0.25, 0.5)
+    L = O.bcc_lattice()
+    ns = min(args.bcc_size, 64)
+    eta = inputs.single_grain(inputs.bcc_vectors(), O.uniform_solid_bcc(P), (ns,) * 3, (H,) * 3, 0.25 * ns * H, 8.0,
+                              seed=2, noise=1e-3, matrix=O.uniform_solid_bcc(P))
+    t0 = time.perf_counter()
+    O.step(eta, 1.0, P, L, (H,) * 3)
+    secs = time.perf_counter() - t0
+    rate = 6.0 * ns ** 3 / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": bcc_config(args),
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one oracle FP64 step (FFT exact solve) of a {ns}^3 bcc sphere, {secs:.2f} s"},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_bcc(args):
+    import torch
+
+    world, rank, local = init_dist(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1902_09761_gb300 import apfc as A
+    from paper_1902_09761_gb300 import inputs
+
+    A.load()
+    n = args.bcc_size
+    k = inputs.bcc_vectors()
+    lat = A.make_lattice(k, A.APFC_LATTICE_BCC3D)
+    prm = A.make_params(*PARAMS)
+    phi = A.apfc_uniform_amplitude(lat, prm)
+    eta0 = inputs.bcc_sphere(phi, n=n)
+    dof = 6 * n ** 3
+    stream = torch.cuda.current_stream(dev)
+    opts = A.apfc_default_opts(precision=A.APFC_FP32_REFINED, tol=TOL, cheb_degree=args.cheb,
+                               tol_inner=args.tol_inner)
+    ctx = A.Context(k, A.APFC_LATTICE_BCC3D, prm, (n, n, n), (H, H, H), opts, stream=stream.cuda_stream)
+    eta_dev = torch.from_numpy(eta0).to(dev)
+
+    def timed(nsteps, sampler=None):
+        ctx.set_amplitudes(eta_dev)
+        ctx.step(1.0, args.warmup)
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        if sampler:
+            sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(1.0, nsteps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        clocks = sampler.stop() if sampler else None
+        barrier(world)
+        return allmax(world, e0.elapsed_time(e1), dev), clocks
+
+    sampler = ClockSampler(local)
+    ms, clocks = timed(args.steps, sampler)
+    st = ctx.stats()
+    value = world * dof * args.steps / (ms * 1e-3)
+
+    # per-kernel breakdown (every launch bracketed by events) and the dominant kernel's roofline
+    ctx.set_amplitudes(eta_dev)
+    ctx.step(1.0, args.warmup)
+    ctx.profile_start("all")
+    torch.cuda.synchronize(dev)
+    ctx.step(1.0, max(args.breakdown_steps, 1))
+    per = {}
+    for name in A.kernel_ids():
+        r = ctx.profile_read(name)
+        if r["launches"]:
+            per[name] = {"ms_per_step": r["ms"] / max(args.breakdown_steps, 1),
+                         "launches_per_step": r["launches"] / max(args.breakdown_steps, 1),
+                         "gbs": (r["bytes"] / (r["ms"] * 1e-3) / 1e9) if r["ms"] > 0 else None,
+                         "bytes": r["bytes"], "launches": r["launches"], "ms": r["ms"]}
+    all_launches = ctx.profile_read("dots_f32")["all_launches"]
+    ctx.profile_stop()
+    top = max(per, key=lambda nm: per[nm]["ms_per_step"])
+    peak, peak_src = measured_peaks()
+    avg_ms = per[top]["ms"] / per[top]["launches"]
+    bpl = per[top]["bytes"] / per[top]["launches"]
+    achieved = bpl / (avg_ms * 1e-3) / 1e9
+
+    # plain FP64 at the same final residual
+    ctx.set_opts(A.apfc_default_opts(precision=A.APFC_FP64, tol=TOL, cheb_degree=args.cheb))
+    ms64, _ = timed(args.fp64_steps)
+    ctx.set_opts(opts)
+
+    # end to end: host-resident state copied in and out every step
+    h_state = torch.empty(eta0.shape, dtype=torch.complex128).pin_memory()
+    h_np = h_state.numpy()
+    ctx.set_amplitudes(eta_dev)
+    ctx.step(1.0, args.warmup)
+    ctx.get_amplitudes(h_np)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        ctx.set_amplitudes(h_np)
+        ctx.step(1.0, 1)
+        ctx.get_amplitudes(h_np)
+    torch.cuda.synchronize(dev)
+    e2e = world * dof * args.e2e_steps / allmax(world, time.perf_counter() - t0, dev)
+    ctx.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+
+        P = O.params_from_paper(0.98, 0.01, 0.25, 0.5)
+        ns = min(n, 64)
+        eta_s = inputs.single_grain(k, phi, (ns,) * 3, (H,) * 3, 0.25 * ns * H, 8.0, seed=2, noise=1e-3, matrix=phi)
+        t1 = time.perf_counter()
+        O.step(eta_s, 1.0, P, O.bcc_lattice(), (H,) * 3)
+        secs = time.perf_counter() - t1
+        cpu = {"value": 6.0 * ns ** 3 / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one oracle FP64 step (FFT exact solve) of a {ns}^3 bcc sphere, {secs:.2f} s"}
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 Krylov + f64 refinement", "data": "synthetic",
+        "config": dict(bcc_config(args), parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
+        "iters_per_step_last": st["iters_last"], "refine_sweeps_last": st["refine_last"],
+        "resid_last": st["resid_last"],
+        "fp64": {"value": world * dof * args.fp64_steps / (ms64 * 1e-3), "unit": UNIT,
+                 "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps},
+        "speedup_fp32_refined_vs_fp64": (ms64 / args.fp64_steps) / (ms / args.steps),
+        "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "peak_source": peak_src,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg_ms, "launches": per[top]["launches"]},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": eta0.nbytes, "d2h_bytes_per_step": eta0.nbytes},
+        "gpu_launches": int(all_launches / max(args.breakdown_steps, 1) * args.steps),
+        "breakdown": {nm: {kk: v[kk] for kk in ("ms_per_step", "launches_per_step", "gbs")}
+                      for nm, v in sorted(per.items(), key=lambda kv: -kv[1]["ms_per_step"])},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 CHEB = 1
 TOL_INNER = 1e-4
 PICARD = (1, False)
@@ -951,6 +1127,8 @@ def main():
         run_batch_reference(args) if args.impl == "reference" else run_batch(args)
     elif args.workload == "adjoint":
         run_adjoint_reference(args) if args.impl == "reference" else run_adjoint(args)
+    elif args.workload == "bcc3d":
+        run_bcc_reference(args) if args.impl == "reference" else run_bcc(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
