@@ -174,6 +174,11 @@ struct NonlinTable {
   double coef[kMaxTerms];
   int nf[kMaxTerms];
   int f[kMaxTerms][3];
+  // the same N_j with its |eta_m|^2 eta_j monomials gathered: N_j = eta_j sum_m
+  // wdiag[j][m] |eta_m|^2 + the monomials ridx[rstart[j] .. rstart[j+1]) of the list above
+  double wdiag[kMaxJ][kMaxJ];
+  int rstart[kMaxJ + 1];
+  int ridx[kMaxTerms];
 };
 
 // Bulk energy density beyond dB/2 A^2 for table lattices: sum_e ecoef Re(prod).

@@ -435,6 +435,29 @@ bool apfc::build_tables(const apfc_lattice& L, const apfc_params& P, NonlinTable
     }
   }
   nt.start[L.J] = n;
+  // gather the monomials |eta_m|^2 eta_j (modes (j,+1), (m,+1), (m,-1)) into weights
+  int nr = 0;
+  for (int j = 0; j < L.J; ++j) {
+    nt.rstart[j] = nr;
+    for (int q = nt.start[j]; q < nt.start[j + 1]; ++q) {
+      int diag_m = -1;
+      if (nt.nf[q] == 3) {
+        int cj = -1;  // position of an unconjugated eta_j factor
+        for (int a = 0; a < 3; ++a)
+          if (nt.f[q][a] == 2 * j) cj = a;
+        if (cj >= 0) {
+          const int o1 = nt.f[q][(cj + 1) % 3], o2 = nt.f[q][(cj + 2) % 3];
+          if ((o1 >> 1) == (o2 >> 1) && (o1 & 1) != (o2 & 1)) diag_m = o1 >> 1;
+        }
+      }
+      if (diag_m >= 0) {
+        nt.wdiag[j][diag_m] += nt.coef[q];
+      } else {
+        nt.ridx[nr++] = q;
+      }
+    }
+  }
+  nt.rstart[L.J] = nr;
   int ne = 0;
   for (int pass = 0; pass < 2; ++pass) {
     const auto& tab = pass == 0 ? m3 : m4;

@@ -337,48 +337,68 @@ __device__ __forceinline__ double2 cm(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 
-// Batched runs (rg != nullptr): blockIdx.y selects the run.
-__global__ void k_rhs(const double2* __restrict__ x, double2* __restrict__ b, OpCoef c, NonlinTable nt,
-                      const RunGeom* rg) {
-  if (rg != nullptr) {
-    const long long o = select_run(rg, blockIdx.y, c);
-    x += o;
-    b += o;
+// N_j at one point from amplitudes held in shared memory (column threadIdx.x of se): the
+// triangular closed form, or eta_j sum_m wdiag[j][m] |eta_m|^2 plus the remaining table
+// monomials.  Shared memory keeps the table's run-time amplitude indices off local memory.
+__device__ __forceinline__ double2 nonlin_shared(const double2 (*se)[kThreads], int j, int J, double A2,
+                                                 const NonlinTable& nt) {
+  const int t = threadIdx.x;
+  const double2 ej = se[j][t];
+  if (nt.hex) {
+    // N_j = 3v (A^2 - |eta_j|^2) eta_j - 2t conj(eta_k eta_l)
+    const int k1 = j == 2 ? 0 : j + 1, k2 = j == 0 ? 2 : j - 1;
+    const double m2 = ej.x * ej.x + ej.y * ej.y;
+    const double s = 3.0 * nt.v * (A2 - m2);
+    const double2 pr = cconj(cm(se[k1][t], se[k2][t]));
+    return make_double2(s * ej.x - 2.0 * nt.t * pr.x, s * ej.y - 2.0 * nt.t * pr.y);
   }
-  prof_add(c, KID_RHS, 2ull * c.J * (unsigned long long)c.pts * sizeof(double2));
+  double w = 0.0;
+  for (int m = 0; m < J; ++m) {
+    const double2 em = se[m][t];
+    w += nt.wdiag[j][m] * (em.x * em.x + em.y * em.y);
+  }
+  double2 N = make_double2(w * ej.x, w * ej.y);
+  for (int i = nt.rstart[j]; i < nt.rstart[j + 1]; ++i) {
+    const int q = nt.ridx[i];
+    double2 prod = make_double2(nt.coef[q], 0.0);
+    for (int f = 0; f < nt.nf[q]; ++f) {
+      const int code = nt.f[q][f];
+      const double2 e = se[code >> 1][t];
+      prod = cm(prod, (code & 1) ? cconj(e) : e);
+    }
+    N.x += prod.x;
+    N.y += prod.y;
+  }
+  return N;
+}
+
+// Batched runs (rg != nullptr): blockIdx.y selects the run.
+__global__ void k_rhs(const double2* __restrict__ x, double2* __restrict__ b, const __grid_constant__ OpCoef c,
+                      const __grid_constant__ NonlinTable nt, const RunGeom* rg) {
+  long long pts = c.pts;  // the run's own size when batched (c stays untouched: no local copy)
+  if (rg != nullptr) {
+    const RunGeom& q = rg[blockIdx.y];
+    pts = q.pts;
+    x += q.elem_off;
+    b += q.elem_off;
+  }
+  if (c.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
+    atomicAdd(c.prof + KID_RHS, 2ull * c.J * (unsigned long long)pts * sizeof(double2));
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= c.pts) return;
-  double2 eta[kMaxJ];
+  __shared__ double2 se[kMaxJ][kThreads];
+  if (p >= pts) return;
   double A2 = 0.0;
   for (int j = 0; j < c.J; ++j) {
-    eta[j] = x[(2LL * j + 1) * c.pts + p];
-    A2 += eta[j].x * eta[j].x + eta[j].y * eta[j].y;
+    const double2 e = x[(2LL * j + 1) * pts + p];
+    se[j][threadIdx.x] = e;
+    A2 += e.x * e.x + e.y * e.y;
   }
   A2 *= 2.0;
   for (int j = 0; j < c.J; ++j) {
-    double2 N;
-    if (nt.hex) {
-      // N_j = 3v (A^2 - |eta_j|^2) eta_j - 2t conj(eta_k eta_l)
-      const int k1 = (j + 1) % 3, k2 = (j + 2) % 3;
-      const double m2 = eta[j].x * eta[j].x + eta[j].y * eta[j].y;
-      const double s = 3.0 * nt.v * (A2 - m2);
-      const double2 pr = cconj(cm(eta[k1], eta[k2]));
-      N = make_double2(s * eta[j].x - 2.0 * nt.t * pr.x, s * eta[j].y - 2.0 * nt.t * pr.y);
-    } else {
-      N = make_double2(0.0, 0.0);
-      for (int q = nt.start[j]; q < nt.start[j + 1]; ++q) {
-        double2 prod = make_double2(nt.coef[q], 0.0);
-        for (int f = 0; f < nt.nf[q]; ++f) {
-          const int code = nt.f[q][f];
-          const double2 m = (code & 1) ? cconj(eta[code >> 1]) : eta[code >> 1];
-          prod = cm(prod, m);
-        }
-        N.x += prod.x;
-        N.y += prod.y;
-      }
-    }
+    const double2 N = nonlin_shared(se, j, c.J, A2, nt);
+    const double2 ej = se[j][threadIdx.x];
     const double kap = c.kap[j];
-    b[(2LL * j + 1) * c.pts + p] = make_double2(eta[j].x * c.inv_dt - kap * N.x, eta[j].y * c.inv_dt - kap * N.y);
+    b[(2LL * j + 1) * pts + p] = make_double2(ej.x * c.inv_dt - kap * N.x, ej.y * c.inv_dt - kap * N.y);
   }
 }
 
@@ -520,53 +540,40 @@ __global__ void __launch_bounds__(256) k_residual_refine2d(const double2* __rest
 __global__ void __launch_bounds__(256) k_rhs_resid(const double2* __restrict__ x, double2* __restrict__ b,
                                                    const double2* __restrict__ b_prev,
                                                    const double2* __restrict__ r_prev, float2* __restrict__ r32,
-                                                   double2* __restrict__ partials, OpCoef c, NonlinTable nt,
-                                                   const RunGeom* rg) {
+                                                   double2* __restrict__ partials, const __grid_constant__ OpCoef c,
+                                                   const __grid_constant__ NonlinTable nt, const RunGeom* rg) {
+  long long pts = c.pts;  // the run's own size when batched (c stays untouched: no local copy)
   if (rg != nullptr) {  // batched runs: blockIdx.y selects the run
-    const long long ro = select_run(rg, blockIdx.y, c);
-    x += ro;
-    b += ro;
-    b_prev += ro;
-    r_prev += ro;
-    r32 += ro;
+    const RunGeom& q = rg[blockIdx.y];
+    pts = q.pts;
+    x += q.elem_off;
+    b += q.elem_off;
+    b_prev += q.elem_off;
+    r_prev += q.elem_off;
+    r32 += q.elem_off;
     partials += (long long)blockIdx.y * c.J * kDotSlots * kDotBlocks;
   }
-  prof_add(c, KID_RHS, (unsigned long long)c.J * c.pts * (5 * sizeof(double2) + 2 * sizeof(float2)));
+  if (c.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
+    atomicAdd(c.prof + KID_RHS, (unsigned long long)c.J * pts * (5 * sizeof(double2) + 2 * sizeof(float2)));
+  __shared__ double2 se[kMaxJ][kThreads];
   float accf[2 * kMaxJ];
 #pragma unroll
   for (int i = 0; i < 2 * kMaxJ; ++i) accf[i] = 0.f;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < c.pts;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < pts;
        p += (long long)gridDim.x * blockDim.x) {
-    double2 eta[kMaxJ];
     double A2 = 0.0;
     for (int j = 0; j < c.J; ++j) {
-      eta[j] = x[(2LL * j + 1) * c.pts + p];
-      A2 += eta[j].x * eta[j].x + eta[j].y * eta[j].y;
+      const double2 e = x[(2LL * j + 1) * pts + p];
+      se[j][threadIdx.x] = e;
+      A2 += e.x * e.x + e.y * e.y;
     }
     A2 *= 2.0;
     for (int j = 0; j < c.J; ++j) {
-      double2 N;
-      if (nt.hex) {
-        const int k1 = (j + 1) % 3, k2 = (j + 2) % 3;
-        const double m2 = eta[j].x * eta[j].x + eta[j].y * eta[j].y;
-        const double s = 3.0 * nt.v * (A2 - m2);
-        const double2 pr = cconj(cm(eta[k1], eta[k2]));
-        N = make_double2(s * eta[j].x - 2.0 * nt.t * pr.x, s * eta[j].y - 2.0 * nt.t * pr.y);
-      } else {
-        N = make_double2(0.0, 0.0);
-        for (int q = nt.start[j]; q < nt.start[j + 1]; ++q) {
-          double2 prod = make_double2(nt.coef[q], 0.0);
-          for (int f = 0; f < nt.nf[q]; ++f) {
-            const int code = nt.f[q][f];
-            prod = cm(prod, (code & 1) ? cconj(eta[code >> 1]) : eta[code >> 1]);
-          }
-          N.x += prod.x;
-          N.y += prod.y;
-        }
-      }
+      const double2 N = nonlin_shared(se, j, c.J, A2, nt);
+      const double2 ej = se[j][threadIdx.x];
       const double kap = c.kap[j];
-      const long long q1 = 2LL * j * c.pts + p, q2 = q1 + c.pts;
-      const double2 bn = make_double2(eta[j].x * c.inv_dt - kap * N.x, eta[j].y * c.inv_dt - kap * N.y);
+      const long long q1 = 2LL * j * pts + p, q2 = q1 + pts;
+      const double2 bn = make_double2(ej.x * c.inv_dt - kap * N.x, ej.y * c.inv_dt - kap * N.y);
       b[q2] = bn;
       const double2 bp = b_prev[q2], rp2 = r_prev[q2], rp1 = r_prev[q1];
       const double r2x = (bn.x - bp.x) + rp2.x, r2y = (bn.y - bp.y) + rp2.y;
@@ -651,7 +658,11 @@ __global__ void k_sum_partials(const double* __restrict__ partials, int n, doubl
 // ---------------------------------------------------------------------------
 constexpr int kZChunk = 64;
 constexpr int kZBuf = 6, kZAhead = 4;  // plane buffers and planes fetched ahead
-constexpr int kTX = 32, kTY = 8, kHX = kTX + 2, kHY = kTY + 2;
+constexpr int kTX = 32, kHX = kTX + 2;
+// tile rows: FP32 passes take two rows per thread (32 x 16 tiles: more work per barrier,
+// less halo); FP64 passes (arithmetic-bound, twice the shared memory) keep 32 x 8
+template <typename T>
+__host__ __device__ constexpr int tile_rows3() { return sizeof(T) == 4 ? 16 : 8; }
 
 template <typename T>
 struct N7 {
@@ -698,6 +709,7 @@ __device__ __forceinline__ void cp_async_elem(cplx<T>* dst, const cplx<T>* src) 
 template <typename T, class OP>
 __global__ void __launch_bounds__(256) k_stream3d(OpCoef c, OP op, const KScal* act) {
   constexpr int NS = OP::NS;
+  constexpr int kTY = tile_rows3<T>(), kHY = kTY + 2, RPT = kTY / 8;
   // plane buffers: z (stencil), z+1 (its z+ neighbour), z+2 .. z+kZAhead (in flight)
   __shared__ cplx<T> tile[NS][kZBuf][kHY][kHX];
   const int nchunk = (c.nz + kZChunk - 1) / kZChunk;
@@ -706,18 +718,18 @@ __global__ void __launch_bounds__(256) k_stream3d(OpCoef c, OP op, const KScal* 
   const int chunk = (int)(blockIdx.z - (unsigned)j * nchunk);
   if (c.prof != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && chunk == 0 && threadIdx.x == 0)
     atomicAdd(c.prof + op.kid, op.bytes);
+  // each thread owns column tx of rows ty (and ty + 8 in a 16-row tile)
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool inside = x < c.nx && y < c.ny;
+  const int x = x0 + tx;
   const long long plane = (long long)c.nx * c.ny;
   const int z0 = chunk * kZChunk, z1 = min(c.nz, z0 + kZChunk);
   const cplx<T>* src[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) src[k] = op.src(k, j);
-  // each thread copies the same (at most two) halo-tile elements of every plane
-  long long qoff[2];
-  int hoff[2];
+  // each thread copies the same (at most three) halo-tile elements of every plane
+  long long qoff[3];
+  int hoff[3];
   int ne = 0;
   for (int e = threadIdx.x; e < kHX * kHY; e += 256, ++ne) {
     const int hy = e / kHX, hx = e - hy * kHX;
@@ -731,10 +743,17 @@ __global__ void __launch_bounds__(256) k_stream3d(OpCoef c, OP op, const KScal* 
       for (int k = 0; k < NS; ++k) cp_async_elem<T>(&tile[k][buf][0][0] + hoff[i], src[k] + zo + qoff[i]);
     asm volatile("cp.async.commit_group;\n" ::);
   };
-  const long long pxy = (long long)(inside ? y : 0) * c.nx + (inside ? x : 0);
-  cplx<T> zm[NS];
+  bool inside[RPT];
+  long long pxy[RPT];
+  cplx<T> zm[RPT][NS];
 #pragma unroll
-  for (int k = 0; k < NS; ++k) zm[k] = src[k][(long long)wrapi(z0 - 1, c.nz) * plane + pxy];
+  for (int r = 0; r < RPT; ++r) {
+    const int y = y0 + ty + 8 * r;
+    inside[r] = x < c.nx && y < c.ny;
+    pxy[r] = (long long)(inside[r] ? y : 0) * c.nx + (inside[r] ? x : 0);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) zm[r][k] = src[k][(long long)wrapi(z0 - 1, c.nz) * plane + pxy[r]];
+  }
 #pragma unroll
   for (int a = 0; a < kZAhead; ++a) issue_tile(a, z0 + a);
   int cb = 0;
@@ -745,20 +764,24 @@ __global__ void __launch_bounds__(256) k_stream3d(OpCoef c, OP op, const KScal* 
     issue_tile(fb, z + kZAhead);  // into a buffer no plane in use occupies
     asm volatile("cp.async.wait_group %0;\n" ::"n"(kZAhead - 1));  // planes z and z+1 have landed
     __syncthreads();
-    if (inside) {
-      N7<T> n[NS];
 #pragma unroll
-      for (int k = 0; k < NS; ++k) {
-        n[k].c = tile[k][cb][ty + 1][tx + 1];
-        n[k].xm = tile[k][cb][ty + 1][tx];
-        n[k].xp = tile[k][cb][ty + 1][tx + 2];
-        n[k].ym = tile[k][cb][ty][tx + 1];
-        n[k].yp = tile[k][cb][ty + 2][tx + 1];
-        n[k].zm = zm[k];
-        n[k].zp = tile[k][nb][ty + 1][tx + 1];
-        zm[k] = n[k].c;
+    for (int r = 0; r < RPT; ++r) {
+      if (inside[r]) {
+        const int ly = ty + 8 * r + 1;
+        N7<T> n[NS];
+#pragma unroll
+        for (int k = 0; k < NS; ++k) {
+          n[k].c = tile[k][cb][ly][tx + 1];
+          n[k].xm = tile[k][cb][ly][tx];
+          n[k].xp = tile[k][cb][ly][tx + 2];
+          n[k].ym = tile[k][cb][ly - 1][tx + 1];
+          n[k].yp = tile[k][cb][ly + 1][tx + 1];
+          n[k].zm = zm[r][k];
+          n[k].zp = tile[k][nb][ly][tx + 1];
+          zm[r][k] = n[k].c;
+        }
+        op.apply(j, (long long)z * plane + pxy[r], n, c);
       }
-      op.apply(j, (long long)z * plane + pxy, n, c);
     }
     __syncthreads();  // buffer cb is refilled two planes later
     cb = nb;
@@ -927,8 +950,9 @@ struct OpResRefine3 {
   }
 };
 
+template <typename T>
 inline dim3 grid_stream3d(const OpCoef& c) {
-  return dim3((unsigned)((c.nx + kTX - 1) / kTX), (unsigned)((c.ny + kTY - 1) / kTY),
+  return dim3((unsigned)((c.nx + kTX - 1) / kTX), (unsigned)((c.ny + tile_rows3<T>() - 1) / tile_rows3<T>()),
               (unsigned)(c.J * ((c.nz + kZChunk - 1) / kZChunk)));
 }
 
@@ -1234,7 +1258,7 @@ void launch_apply_A(const cplx<T>* x, cplx<T>* y, const OpCoef& c, const KScal* 
   if (c.dim == 3) {
     ProfScope ps3_(kid_of<T>(KID_APPLY_A), s);
     OpA3<T> op{x, y, c.pts, kid_of<T>(KID_APPLY_A), 4ull * (unsigned long long)c.pts * sizeof(cplx<T>)};
-    k_stream3d<T, OpA3<T>><<<grid_stream3d(c), 256, 0, s>>>(c, op, act);
+    k_stream3d<T, OpA3<T>><<<grid_stream3d<T>(c), 256, 0, s>>>(c, op, act);
     return;
   }
   ProfScope ps_(kid_of<T>(KID_APPLY_A), s);
@@ -1245,7 +1269,7 @@ void launch_residual(const cplx<T>* b, const cplx<T>* x, cplx<T>* r, cplx<T>* rh
   if (c.dim == 3) {
     ProfScope ps3_(kid_of<T>(KID_RESIDUAL), s);
     OpRes3<T> op{x, b, r, rhat, c.pts, kid_of<T>(KID_RESIDUAL), 8ull * (unsigned long long)c.pts * sizeof(cplx<T>)};
-    k_stream3d<T, OpRes3<T>><<<grid_stream3d(c), 256, 0, s>>>(c, op, nullptr);
+    k_stream3d<T, OpRes3<T>><<<grid_stream3d<T>(c), 256, 0, s>>>(c, op, nullptr);
     return;
   }
   ProfScope ps_(kid_of<T>(KID_RESIDUAL), s);
@@ -1256,7 +1280,7 @@ void launch_pc_rhs(const cplx<T>* beta, FieldRef<T> f, const OpCoef& c, const KS
   if (c.dim == 3) {
     ProfScope ps3_(kid_of<T>(KID_PC_RHS), s);
     OpPcRhs3<T> op{beta, f, c.pts, kid_of<T>(KID_PC_RHS), 3ull * (unsigned long long)c.pts * sizeof(cplx<T>)};
-    k_stream3d<T, OpPcRhs3<T>><<<grid_stream3d(c), 256, 0, s>>>(c, op, act);
+    k_stream3d<T, OpPcRhs3<T>><<<grid_stream3d<T>(c), 256, 0, s>>>(c, op, act);
     return;
   }
   ProfScope ps_(kid_of<T>(KID_PC_RHS), s);
@@ -1273,7 +1297,7 @@ void launch_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T>
   if (c.dim == 3) {
     ProfScope ps3_(kid_of<T>(KID_CHEB_FIRST), s);
     OpChebFirst3<T> op{f, X, R, Dn, w, last, kid_of<T>(KID_CHEB_FIRST), (last ? 2ull : 4ull) * (unsigned long long)c.pts * sizeof(cplx<T>)};
-    k_stream3d<T, OpChebFirst3<T>><<<grid_stream3d(c), 256, 0, s>>>(c, op, act);
+    k_stream3d<T, OpChebFirst3<T>><<<grid_stream3d<T>(c), 256, 0, s>>>(c, op, act);
     return;
   }
   ProfScope ps_(kid_of<T>(KID_CHEB_FIRST), s);
@@ -1285,7 +1309,7 @@ void launch_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, FieldRef<T
   if (c.dim == 3) {
     ProfScope ps3_(kid_of<T>(KID_CHEB_SWEEP), s);
     OpChebSweep3<T> op{Dd, X, R, Dn, w, last, kid_of<T>(KID_CHEB_SWEEP), (last ? 4ull : 6ull) * (unsigned long long)c.pts * sizeof(cplx<T>)};
-    k_stream3d<T, OpChebSweep3<T>><<<grid_stream3d(c), 256, 0, s>>>(c, op, act);
+    k_stream3d<T, OpChebSweep3<T>><<<grid_stream3d<T>(c), 256, 0, s>>>(c, op, act);
     return;
   }
   ProfScope ps_(kid_of<T>(KID_CHEB_SWEEP), s);
@@ -1331,7 +1355,7 @@ void launch_zeta(double2* x, const OpCoef& c, cudaStream_t s) {
   if (c.dim == 3) {
     ProfScope ps3_(KID_ZETA, s);
     OpZeta3 op{x, c.pts, KID_ZETA, 2ull * (unsigned long long)c.pts * sizeof(double2)};
-    k_stream3d<double, OpZeta3><<<grid_stream3d(c), 256, 0, s>>>(c, op, nullptr);
+    k_stream3d<double, OpZeta3><<<grid_stream3d<double>(c), 256, 0, s>>>(c, op, nullptr);
     return;
   }
   ProfScope ps_(KID_ZETA, s);
@@ -1353,7 +1377,7 @@ void launch_residual_refine3d(const double2* b, const double2* x, float2* r32, d
   ProfScope ps_(KID_RESID_REFINE, s);
   OpResRefine3 op{x, b, r32, r64, c.pts, KID_RESID_REFINE,
                   (unsigned long long)c.pts * ((r64 ? 6 : 4) * sizeof(double2) + 2 * sizeof(float2))};
-  k_stream3d<double, OpResRefine3><<<grid_stream3d(c), 256, 0, s>>>(c, op, nullptr);
+  k_stream3d<double, OpResRefine3><<<grid_stream3d<double>(c), 256, 0, s>>>(c, op, nullptr);
 }
 void launch_rhs_resid(const double2* x, double2* b, const double2* b_prev, const double2* r_prev, float2* r32,
                       double* partials, const OpCoef& c, const NonlinTable& nt, cudaStream_t s,
