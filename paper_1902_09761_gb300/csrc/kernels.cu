@@ -659,10 +659,12 @@ __global__ void k_sum_partials(const double* __restrict__ partials, int n, doubl
 constexpr int kZChunk = 64;
 constexpr int kZBuf = 6, kZAhead = 4;  // plane buffers and planes fetched ahead
 constexpr int kTX = 32, kHX = kTX + 2;
-// tile rows: FP32 passes take two rows per thread (32 x 16 tiles: more work per barrier,
-// less halo); FP64 passes (arithmetic-bound, twice the shared memory) keep 32 x 8
+// FP64 passes: 32 x 8 tiles, one point per thread (k_stream3d).  FP32 passes: 64 x 8
+// tiles, two adjacent points per thread (k_stream3d_pair).
 template <typename T>
-__host__ __device__ constexpr int tile_rows3() { return sizeof(T) == 4 ? 16 : 8; }
+__host__ __device__ constexpr int tile_rows3() { return 8; }
+template <typename T>
+__host__ __device__ constexpr int tile_cols3() { return sizeof(T) == 4 ? 64 : 32; }
 
 template <typename T>
 struct N7 {
@@ -950,9 +952,110 @@ struct OpResRefine3 {
   }
 };
 
+
+// FP32 variant of k_stream3d: each thread owns two adjacent points (x, x+1) of a row of a
+// 64 x 8 tile.  The plane tile (one-point halo) sits at local column x - x0 + 2, so the
+// pair and its y- and z-neighbour pairs are 16-byte shared-memory loads: half the
+// shared-memory instructions of one point per thread, the pipe that limited the
+// single-point kernel (short-scoreboard stalls).
+constexpr int kPX = 64, kPY = 8, kPW = kPX + 4;  // tile columns, rows, row stride (2 + 64 + 2)
+template <class OP>
+__global__ void __launch_bounds__(256) k_stream3d_pair(OpCoef c, OP op, const KScal* act) {
+  using T = float;
+  constexpr int NS = OP::NS;
+  constexpr int kHYp = kPY + 2, kNE = (kPX + 2) * kHYp;  // elements fetched per plane
+  __shared__ __align__(16) float2 tile[NS][kZBuf][kHYp][kPW];
+  const int nchunk = (c.nz + kZChunk - 1) / kZChunk;
+  const int j = (int)(blockIdx.z / (unsigned)nchunk);
+  if (act != nullptr && act[j].active == 0) return;
+  const int chunk = (int)(blockIdx.z - (unsigned)j * nchunk);
+  if (c.prof != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && chunk == 0 && threadIdx.x == 0)
+    atomicAdd(c.prof + op.kid, op.bytes);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kPY;
+  const int xa = x0 + 2 * tx, y = y0 + ty;
+  const long long plane = (long long)c.nx * c.ny;
+  const int z0 = chunk * kZChunk, z1 = min(c.nz, z0 + kZChunk);
+  const float2* src[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) src[k] = op.src(k, j);
+  // each thread copies the same (at most three) halo-tile elements of every plane
+  long long qoff[3];
+  int hoff[3];
+  int ne = 0;
+  for (int e = threadIdx.x; e < kNE; e += 256, ++ne) {
+    const int hy = e / (kPX + 2), li = e - hy * (kPX + 2);
+    qoff[ne] = (long long)wrapi(y0 - 1 + hy, c.ny) * c.nx + wrapi(x0 - 1 + li, c.nx);
+    hoff[ne] = hy * kPW + li + 1;
+  }
+  auto issue_tile = [&](int buf, int z) {
+    const long long zo = (long long)wrapi(z, c.nz) * plane;
+    for (int i = 0; i < ne; ++i)
+#pragma unroll
+      for (int k = 0; k < NS; ++k) cp_async_elem<T>(&tile[k][buf][0][0] + hoff[i], src[k] + zo + qoff[i]);
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+  const bool in0 = xa < c.nx && y < c.ny, in1 = xa + 1 < c.nx && y < c.ny;
+  const long long p0 = (long long)(in0 ? y : 0) * c.nx + (in0 ? xa : 0);
+  const long long p1 = in1 ? p0 + 1 : p0;
+  float2 zm0[NS], zm1[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const long long zo = (long long)wrapi(z0 - 1, c.nz) * plane;
+    zm0[k] = src[k][zo + p0];
+    zm1[k] = src[k][zo + p1];
+  }
+#pragma unroll
+  for (int a = 0; a < kZAhead; ++a) issue_tile(a, z0 + a);
+  const int lc = 2 * tx + 2;  // local column of xa: even, so the pair is 16-byte aligned
+  int cb = 0;
+  for (int z = z0; z < z1; ++z) {
+    const int nb = cb + 1 == kZBuf ? 0 : cb + 1;
+    int fb = cb + kZAhead;
+    if (fb >= kZBuf) fb -= kZBuf;
+    issue_tile(fb, z + kZAhead);  // into a buffer no plane in use occupies
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(kZAhead - 1));  // planes z and z+1 have landed
+    __syncthreads();
+    if (in0) {
+      N7<T> n0[NS], n1[NS];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        const float4 cc = *reinterpret_cast<const float4*>(&tile[k][cb][ty + 1][lc]);
+        const float4 ym = *reinterpret_cast<const float4*>(&tile[k][cb][ty][lc]);
+        const float4 yp = *reinterpret_cast<const float4*>(&tile[k][cb][ty + 2][lc]);
+        const float4 zp = *reinterpret_cast<const float4*>(&tile[k][nb][ty + 1][lc]);
+        const float2 xm = tile[k][cb][ty + 1][lc - 1], xp = tile[k][cb][ty + 1][lc + 2];
+        n0[k].c = make_float2(cc.x, cc.y);
+        n0[k].xm = xm;
+        n0[k].xp = make_float2(cc.z, cc.w);
+        n0[k].ym = make_float2(ym.x, ym.y);
+        n0[k].yp = make_float2(yp.x, yp.y);
+        n0[k].zm = zm0[k];
+        n0[k].zp = make_float2(zp.x, zp.y);
+        n1[k].c = make_float2(cc.z, cc.w);
+        n1[k].xm = make_float2(cc.x, cc.y);
+        n1[k].xp = xp;
+        n1[k].ym = make_float2(ym.z, ym.w);
+        n1[k].yp = make_float2(yp.z, yp.w);
+        n1[k].zm = zm1[k];
+        n1[k].zp = make_float2(zp.z, zp.w);
+        zm0[k] = n0[k].c;
+        zm1[k] = n1[k].c;
+      }
+      const long long zo = (long long)z * plane;
+      op.apply(j, zo + p0, n0, c);
+      if (in1) op.apply(j, zo + p1, n1, c);
+    }
+    __syncthreads();  // buffer cb is refilled two planes later
+    cb = nb;
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
 template <typename T>
 inline dim3 grid_stream3d(const OpCoef& c) {
-  return dim3((unsigned)((c.nx + kTX - 1) / kTX), (unsigned)((c.ny + tile_rows3<T>() - 1) / tile_rows3<T>()),
+  return dim3((unsigned)((c.nx + tile_cols3<T>() - 1) / tile_cols3<T>()),
+              (unsigned)((c.ny + tile_rows3<T>() - 1) / tile_rows3<T>()),
               (unsigned)(c.J * ((c.nz + kZChunk - 1) / kZChunk)));
 }
 
@@ -1248,6 +1351,15 @@ __global__ void __launch_bounds__(256) k_rotation(const double2* __restrict__ x,
   }
 }
 
+// FP32 passes take the two-point kernel, FP64 passes the one-point kernel.
+template <typename T, class OP>
+void stream3d(const OpCoef& c, const OP& op, const KScal* act, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4)
+    k_stream3d_pair<OP><<<grid_stream3d<T>(c), 256, 0, s>>>(c, op, act);
+  else
+    k_stream3d<T, OP><<<grid_stream3d<T>(c), 256, 0, s>>>(c, op, act);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -1258,7 +1370,7 @@ void launch_apply_A(const cplx<T>* x, cplx<T>* y, const OpCoef& c, const KScal* 
   if (c.dim == 3) {
     ProfScope ps3_(kid_of<T>(KID_APPLY_A), s);
     OpA3<T> op{x, y, c.pts, kid_of<T>(KID_APPLY_A), 4ull * (unsigned long long)c.pts * sizeof(cplx<T>)};
-    k_stream3d<T, OpA3<T>><<<grid_stream3d<T>(c), 256, 0, s>>>(c, op, act);
+    stream3d<T, OpA3<T>>(c, op, act, s);
     return;
   }
   ProfScope ps_(kid_of<T>(KID_APPLY_A), s);
@@ -1269,7 +1381,7 @@ void launch_residual(const cplx<T>* b, const cplx<T>* x, cplx<T>* r, cplx<T>* rh
   if (c.dim == 3) {
     ProfScope ps3_(kid_of<T>(KID_RESIDUAL), s);
     OpRes3<T> op{x, b, r, rhat, c.pts, kid_of<T>(KID_RESIDUAL), 8ull * (unsigned long long)c.pts * sizeof(cplx<T>)};
-    k_stream3d<T, OpRes3<T>><<<grid_stream3d<T>(c), 256, 0, s>>>(c, op, nullptr);
+    stream3d<T, OpRes3<T>>(c, op, nullptr, s);
     return;
   }
   ProfScope ps_(kid_of<T>(KID_RESIDUAL), s);
@@ -1280,7 +1392,7 @@ void launch_pc_rhs(const cplx<T>* beta, FieldRef<T> f, const OpCoef& c, const KS
   if (c.dim == 3) {
     ProfScope ps3_(kid_of<T>(KID_PC_RHS), s);
     OpPcRhs3<T> op{beta, f, c.pts, kid_of<T>(KID_PC_RHS), 3ull * (unsigned long long)c.pts * sizeof(cplx<T>)};
-    k_stream3d<T, OpPcRhs3<T>><<<grid_stream3d<T>(c), 256, 0, s>>>(c, op, act);
+    stream3d<T, OpPcRhs3<T>>(c, op, act, s);
     return;
   }
   ProfScope ps_(kid_of<T>(KID_PC_RHS), s);
@@ -1297,7 +1409,7 @@ void launch_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T>
   if (c.dim == 3) {
     ProfScope ps3_(kid_of<T>(KID_CHEB_FIRST), s);
     OpChebFirst3<T> op{f, X, R, Dn, w, last, kid_of<T>(KID_CHEB_FIRST), (last ? 2ull : 4ull) * (unsigned long long)c.pts * sizeof(cplx<T>)};
-    k_stream3d<T, OpChebFirst3<T>><<<grid_stream3d<T>(c), 256, 0, s>>>(c, op, act);
+    stream3d<T, OpChebFirst3<T>>(c, op, act, s);
     return;
   }
   ProfScope ps_(kid_of<T>(KID_CHEB_FIRST), s);
@@ -1309,7 +1421,7 @@ void launch_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, FieldRef<T
   if (c.dim == 3) {
     ProfScope ps3_(kid_of<T>(KID_CHEB_SWEEP), s);
     OpChebSweep3<T> op{Dd, X, R, Dn, w, last, kid_of<T>(KID_CHEB_SWEEP), (last ? 4ull : 6ull) * (unsigned long long)c.pts * sizeof(cplx<T>)};
-    k_stream3d<T, OpChebSweep3<T>><<<grid_stream3d<T>(c), 256, 0, s>>>(c, op, act);
+    stream3d<T, OpChebSweep3<T>>(c, op, act, s);
     return;
   }
   ProfScope ps_(kid_of<T>(KID_CHEB_SWEEP), s);
