@@ -671,25 +671,57 @@ struct N7 {
   cplx<T> c, xm, xp, ym, yp, zm, zp;
 };
 
+// Operator coefficients of amplitude j in the arithmetic precision T, formed once per
+// block (converting the FP64 coefficients at every point kept the FP32 passes bound by
+// the FP64 pipe).
 template <typename T>
-__device__ __forceinline__ cplx<T> lap7(const N7<T>& n, const OpCoef& c) {
-  const T c0 = (T)c.c0, ix = (T)c.ih2[0], iy = (T)c.ih2[1], iz = (T)c.ih2[2];
+struct Coef7 {
+  T c0, ih2[3], kh[3], kt, a, it, sD, mu, c1, c2;
+};
+template <typename T>
+__device__ __forceinline__ Coef7<T> coef7(const OpCoef& c, int j) {
+  Coef7<T> q;
+  q.c0 = (T)c.c0;
+  for (int d = 0; d < 3; ++d) {
+    q.ih2[d] = (T)c.ih2[d];
+    q.kh[d] = (T)c.kh[j][d];
+  }
+  q.kt = (T)c.kt[j];
+  q.a = (T)c.a[j];
+  q.it = (T)c.inv_theta[j];
+  q.sD = (T)c.sD[j];
+  q.mu = (T)c.mu[j];
+  q.c1 = q.c2 = (T)0;
+  return q;
+}
+// (2,2) block at point p: a_j plus the Jacobian diagonal of a Picard iteration
+template <typename T>
+__device__ __forceinline__ T a7(const Coef7<T>& q, const OpCoef& c, int j, long long p) {
+  if (c.jd == nullptr) return q.a;
+  if constexpr (sizeof(T) == 4) {
+    if (c.jd32 != nullptr) return q.a + c.jd32[(long long)j * c.pts + p].x;
+  }
+  return q.a + (T)c.jd[(long long)j * c.pts + p];
+}
+
+template <typename T>
+__device__ __forceinline__ cplx<T> lap7(const N7<T>& n, const Coef7<T>& q) {
+  const T c0 = q.c0, ix = q.ih2[0], iy = q.ih2[1], iz = q.ih2[2];
   return mkc<T>(c0 * n.c.x + ix * (n.xm.x + n.xp.x) + iy * (n.ym.x + n.yp.x) + iz * (n.zm.x + n.zp.x),
                 c0 * n.c.y + ix * (n.xm.y + n.xp.y) + iy * (n.ym.y + n.yp.y) + iz * (n.zm.y + n.zp.y));
 }
 template <typename T>
-__device__ __forceinline__ cplx<T> G7(const N7<T>& n, const OpCoef& c, int j) {
-  const cplx<T> L = lap7(n, c);
-  const T kx = (T)c.kh[j][0], ky = (T)c.kh[j][1], kz = (T)c.kh[j][2];
+__device__ __forceinline__ cplx<T> G7(const N7<T>& n, const Coef7<T>& q) {
+  const cplx<T> L = lap7(n, q);
+  const T kx = q.kh[0], ky = q.kh[1], kz = q.kh[2];
   const T ar = kx * (n.xp.x - n.xm.x) + ky * (n.yp.x - n.ym.x) + kz * (n.zp.x - n.zm.x);
   const T ai = kx * (n.xp.y - n.xm.y) + ky * (n.yp.y - n.ym.y) + kz * (n.zp.y - n.zm.y);
   return mkc<T>(L.x - ai, L.y + ar);
 }
 template <typename T>
-__device__ __forceinline__ cplx<T> D7(const N7<T>& n, const OpCoef& c, int j) {
-  const cplx<T> L = lap7(n, c);
-  const T sD = (T)c.sD[j], mu = (T)c.mu[j];
-  return mkc<T>(sD * n.c.x - mu * L.x, sD * n.c.y - mu * L.y);
+__device__ __forceinline__ cplx<T> D7(const N7<T>& n, const Coef7<T>& q) {
+  const cplx<T> L = lap7(n, q);
+  return mkc<T>(q.sD * n.c.x - q.mu * L.x, q.sD * n.c.y - q.mu * L.y);
 }
 
 __device__ __forceinline__ int wrapi(int v, int n) {
@@ -720,6 +752,8 @@ __global__ void __launch_bounds__(256) k_stream3d(OpCoef c, OP op, const KScal* 
   const int chunk = (int)(blockIdx.z - (unsigned)j * nchunk);
   if (c.prof != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && chunk == 0 && threadIdx.x == 0)
     atomicAdd(c.prof + op.kid, op.bytes);
+  Coef7<T> q = coef7<T>(c, j);
+  op.coef(q, j);
   // each thread owns column tx of rows ty (and ty + 8 in a 16-row tile)
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
@@ -782,7 +816,7 @@ __global__ void __launch_bounds__(256) k_stream3d(OpCoef c, OP op, const KScal* 
           n[k].zp = tile[k][nb][ly][tx + 1];
           zm[r][k] = n[k].c;
         }
-        op.apply(j, (long long)z * plane + pxy[r], n, c);
+        op.apply(j, (long long)z * plane + pxy[r], n, c, q);
       }
     }
     __syncthreads();  // buffer cb is refilled two planes later
@@ -800,10 +834,12 @@ struct OpA3 {
   long long pts;
   int kid;
   unsigned long long bytes;
+  template <typename Q>
+  __device__ void coef(Q&, int) const {}
   __device__ const cplx<T>* src(int k, int j) const { return x + (2LL * j + k) * pts; }
-  __device__ void apply(int j, long long p, const N7<T> (&n)[2], const OpCoef& c) const {
-    const cplx<T> gz = G7(n[0], c, j), ge = G7(n[1], c, j);
-    const T kt = (T)c.kt[j], a = (T)a_at(c, j, p);
+  __device__ void apply(int j, long long p, const N7<T> (&n)[2], const OpCoef& c, const Coef7<T>& q) const {
+    const cplx<T> gz = G7(n[0], q), ge = G7(n[1], q);
+    const T kt = q.kt, a = a7(q, c, j, p);
     cplx<T>* y1 = y + 2LL * j * pts;
     y1[p] = mkc<T>(n[0].c.x - ge.x, n[0].c.y - ge.y);
     y1[pts + p] = mkc<T>(kt * gz.x + a * n[1].c.x, kt * gz.y + a * n[1].c.y);
@@ -821,10 +857,12 @@ struct OpRes3 {
   long long pts;
   int kid;
   unsigned long long bytes;
+  template <typename Q>
+  __device__ void coef(Q&, int) const {}
   __device__ const cplx<T>* src(int k, int j) const { return x + (2LL * j + k) * pts; }
-  __device__ void apply(int j, long long p, const N7<T> (&n)[2], const OpCoef& c) const {
-    const cplx<T> gz = G7(n[0], c, j), ge = G7(n[1], c, j);
-    const T kt = (T)c.kt[j], a = (T)a_at(c, j, p);
+  __device__ void apply(int j, long long p, const N7<T> (&n)[2], const OpCoef& c, const Coef7<T>& q) const {
+    const cplx<T> gz = G7(n[0], q), ge = G7(n[1], q);
+    const T kt = q.kt, a = a7(q, c, j, p);
     const long long o = 2LL * j * pts;
     const cplx<T> b1 = b[o + p], b2 = b[o + pts + p];
     const cplx<T> r1 = mkc<T>(b1.x - (n[0].c.x - ge.x), b1.y - (n[0].c.y - ge.y));
@@ -845,11 +883,13 @@ struct OpPcRhs3 {
   long long pts;
   int kid;
   unsigned long long bytes;
+  template <typename Q>
+  __device__ void coef(Q&, int) const {}
   __device__ const cplx<T>* src(int, int j) const { return beta + 2LL * j * pts; }
-  __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c) const {
-    const cplx<T> g = G7(n[0], c, j);
+  __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c, const Coef7<T>& q) const {
+    const cplx<T> g = G7(n[0], q);
     const cplx<T> b2 = beta[2LL * j * pts + pts + p];
-    const T kt = (T)c.kt[j];
+    const T kt = q.kt;
     f.at(j)[p] = mkc<T>(b2.x - kt * g.x, b2.y - kt * g.y);
   }
 };
@@ -864,13 +904,18 @@ struct OpChebFirst3 {
   int last;
   int kid;
   unsigned long long bytes;
+  template <typename Q>
+  __device__ void coef(Q& q, int j) const {
+    q.c1 = (T)w.c1[j];
+    q.c2 = (T)w.c2[j];
+  }
   __device__ const cplx<T>* src(int, int j) const { return f.at(j); }
-  __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c) const {
-    const T it = (T)c.inv_theta[j];
-    const cplx<T> Df = D7(n[0], c, j);
+  __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c, const Coef7<T>& q) const {
+    const T it = q.it;
+    const cplx<T> Df = D7(n[0], q);
     const cplx<T> d0 = mkc<T>(it * n[0].c.x, it * n[0].c.y);
     const cplx<T> r1 = mkc<T>(n[0].c.x - it * Df.x, n[0].c.y - it * Df.y);
-    const T c1 = (T)w.c1[j], c2 = (T)w.c2[j];
+    const T c1 = q.c1, c2 = q.c2;
     const cplx<T> d1 = mkc<T>(c1 * d0.x + c2 * r1.x, c1 * d0.y + c2 * r1.y);
     if (last) {
       X.at(j)[p] = mkc<T>(d0.x + d1.x, d0.y + d1.y);
@@ -892,14 +937,19 @@ struct OpChebSweep3 {
   int last;
   int kid;
   unsigned long long bytes;
+  template <typename Q>
+  __device__ void coef(Q& q, int j) const {
+    q.c1 = (T)w.c1[j];
+    q.c2 = (T)w.c2[j];
+  }
   __device__ const cplx<T>* src(int, int j) const { return Dd.at(j); }
-  __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c) const {
-    const cplx<T> DD = D7(n[0], c, j);
+  __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c, const Coef7<T>& q) const {
+    const cplx<T> DD = D7(n[0], q);
     const cplx<T> d = n[0].c;
     const cplx<T> x = X.at(j)[p], r = R.at(j)[p];
     const cplx<T> xn = mkc<T>(x.x + d.x, x.y + d.y);
     const cplx<T> rn = mkc<T>(r.x - DD.x, r.y - DD.y);
-    const T c1 = (T)w.c1[j], c2 = (T)w.c2[j];
+    const T c1 = q.c1, c2 = q.c2;
     const cplx<T> dn = mkc<T>(c1 * d.x + c2 * rn.x, c1 * d.y + c2 * rn.y);
     if (last) {
       X.at(j)[p] = mkc<T>(xn.x + dn.x, xn.y + dn.y);
@@ -918,9 +968,11 @@ struct OpZeta3 {
   long long pts;
   int kid;
   unsigned long long bytes;
+  template <typename Q>
+  __device__ void coef(Q&, int) const {}
   __device__ const double2* src(int, int j) const { return x + (2LL * j + 1) * pts; }
-  __device__ void apply(int j, long long p, const N7<double> (&n)[1], const OpCoef& c) const {
-    x[2LL * j * pts + p] = G7(n[0], c, j);
+  __device__ void apply(int j, long long p, const N7<double> (&n)[1], const OpCoef& c, const Coef7<double>& q) const {
+    x[2LL * j * pts + p] = G7(n[0], q);
   }
 };
 
@@ -935,10 +987,12 @@ struct OpResRefine3 {
   long long pts;
   int kid;
   unsigned long long bytes;
+  template <typename Q>
+  __device__ void coef(Q&, int) const {}
   __device__ const double2* src(int k, int j) const { return x + (2LL * j + k) * pts; }
-  __device__ void apply(int j, long long p, const N7<double> (&n)[2], const OpCoef& c) const {
-    const double2 gz = G7(n[0], c, j), ge = G7(n[1], c, j);
-    const double kt = c.kt[j], a = a_at(c, j, p);
+  __device__ void apply(int j, long long p, const N7<double> (&n)[2], const OpCoef& c, const Coef7<double>& q) const {
+    const double2 gz = G7(n[0], q), ge = G7(n[1], q);
+    const double kt = q.kt, a = a7(q, c, j, p);
     const long long o = 2LL * j * pts;
     const double2 b1 = b[o + p], b2 = b[o + pts + p];
     const double r1x = (b1.x - n[0].c.x) + ge.x, r1y = (b1.y - n[0].c.y) + ge.y;
@@ -971,6 +1025,8 @@ __global__ void __launch_bounds__(256) k_stream3d_pair(OpCoef c, OP op, const KS
   const int chunk = (int)(blockIdx.z - (unsigned)j * nchunk);
   if (c.prof != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && chunk == 0 && threadIdx.x == 0)
     atomicAdd(c.prof + op.kid, op.bytes);
+  Coef7<T> q = coef7<T>(c, j);
+  op.coef(q, j);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kPY;
   const int xa = x0 + 2 * tx, y = y0 + ty;
@@ -1043,8 +1099,8 @@ __global__ void __launch_bounds__(256) k_stream3d_pair(OpCoef c, OP op, const KS
         zm1[k] = n1[k].c;
       }
       const long long zo = (long long)z * plane;
-      op.apply(j, zo + p0, n0, c);
-      if (in1) op.apply(j, zo + p1, n1, c);
+      op.apply(j, zo + p0, n0, c, q);
+      if (in1) op.apply(j, zo + p1, n1, c, q);
     }
     __syncthreads();  // buffer cb is refilled two planes later
     cb = nb;
