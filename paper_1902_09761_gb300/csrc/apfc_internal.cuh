@@ -222,23 +222,43 @@ template <typename T>
 void launch_pc_rhs(const cplx<T>* beta, FieldRef<T> f, const OpCoef& c, const KScal* act, cudaStream_t s);
 template <typename T>
 void launch_cheb_zero(CFieldRef<T> f, FieldRef<T> X, const OpCoef& c, const KScal* act, cudaStream_t s);
-template <typename T>
-void launch_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
-                       const OpCoef& c, const KScal* act, cudaStream_t s);
-template <typename T>
-void launch_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
-                       const OpCoef& c, const KScal* act, cudaStream_t s);
+
 template <typename T>
 void launch_pc_final(const cplx<T>* beta, CFieldRef<T> b2p, cplx<T>* chi, const OpCoef& c, const KScal* act,
                      cudaStream_t s);
 template <typename T>
 void launch_p_update(const cplx<T>* r, cplx<T>* p, const cplx<T>* v, const OpCoef& c, const KScal* k,
                      cudaStream_t s);
+// partials != nullptr: the inner products of the updated vectors, (s, s) for the s-update
+// and (rhat, r), (r, r) for the r-update, in the k_dots layout [J][kDotSlots][kDotBlocks]
 template <typename T>
 void launch_s_update(cplx<T>* r, const cplx<T>* v, cplx<T>* u, const cplx<T>* p, const OpCoef& c, const KScal* k,
-                     cudaStream_t s);
+                     cudaStream_t s, void* partials = nullptr);
 template <typename T>
-void launch_r_update(cplx<T>* r, const cplx<T>* t, cplx<T>* u, const OpCoef& c, const KScal* k, cudaStream_t s);
+void launch_r_update(cplx<T>* r, const cplx<T>* t, cplx<T>* u, const OpCoef& c, const KScal* k, cudaStream_t s,
+                     const cplx<T>* rhat = nullptr, void* partials = nullptr);
+// 3D grids: y = A x with inner products of y in the same pass: nd = 1 gives (du, y),
+// nd = 2 gives (y, du) and (y, y).  Partials use the layout [J][kDotSlots][npart] with
+// npart = stream3d_parts(c, sizeof(cplx<T>)) (one per block of the pass).
+template <typename T>
+void launch_apply_A_dots(const cplx<T>* x, cplx<T>* y, const cplx<T>* du, int nd, void* partials, const OpCoef& c,
+                         const KScal* act, cudaStream_t s);
+int stream3d_parts(const OpCoef& c, int elem_bytes);
+// Step 4 of P^{-1} folded into the last Chebyshev pass of the second diffusion solve
+// (3D grids): chi1 = beta1 + (beta2' - sD chi2) / mu, from the chi2 just computed.
+template <typename T>
+struct PcFin {
+  CFieldRef<T> b1;   // beta1 (stride 2 pts)
+  CFieldRef<T> b2p;  // beta2'
+  FieldRef<T> chi1;  // chi1 (stride 2 pts)
+};
+// fin != nullptr (3D grids, last pass only): also step 4 of P^{-1}, see PcFin
+template <typename T>
+void launch_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
+                       const OpCoef& c, const KScal* act, cudaStream_t s, const PcFin<T>* fin = nullptr);
+template <typename T>
+void launch_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
+                       const OpCoef& c, const KScal* act, cudaStream_t s, const PcFin<T>* fin = nullptr);
 template <typename T>
 void launch_add_to(const cplx<T>* d, double2* x, const OpCoef& c, cudaStream_t s);
 

@@ -257,6 +257,14 @@ apfc_status alloc_work(apfc_ctx* ctx, Work<T>& w) {
         for (int rows : {32, 64, 128, 256, 512, 1024, ctx->opts.tile_rows})
           if (rows > 0) cap = std::max(cap, fused2d_npart(g, m, rows, (int)sizeof(cplx<T>), tile));
   }
+  if (ctx->dim == 3) {
+    OpCoef g{};
+    g.nx = ctx->grid.n[0];
+    g.ny = ctx->grid.n[1];
+    g.nz = ctx->grid.n[2];
+    g.J = ctx->J;
+    cap = std::max(cap, stream3d_parts(g, (int)sizeof(cplx<T>)));
+  }
   w.npart_cap = cap;
   CK(cudaMalloc(&w.partials, 16ull * kDotSlots * cap * ctx->J));
   CK(cudaMalloc(&w.ks, sizeof(KScal) * ctx->J));
@@ -489,21 +497,28 @@ void apply_pinv(apfc_ctx* ctx, Work<T>& w, const cplx<T>* beta, cplx<T>* chi, co
   FieldRef<T> D[2] = {{w.fld[3], P}, {w.fld[4], P}};
   FieldRef<T> chi2{chi + P, 2 * P};
   const int m = ctx->opts.cheb_degree;
-  auto cheb = [&](CFieldRef<T> src, FieldRef<T> X) {
+  auto cheb = [&](CFieldRef<T> src, FieldRef<T> X, const PcFin<T>* fin) {
     if (m == 0) {
       launch_cheb_zero<T>(src, X, c, act, ctx->stream);
       return;
     }
-    launch_cheb_first<T>(src, X, R, D[0], cw[0], m == 1, c, act, ctx->stream);
+    launch_cheb_first<T>(src, X, R, D[0], cw[0], m == 1, c, act, ctx->stream, fin);
     int cur = 0;
     for (int k = 1; k < m; ++k) {
-      launch_cheb_sweep<T>(CFieldRef<T>{D[cur].p, P}, X, R, D[1 - cur], cw[k], k == m - 1, c, act, ctx->stream);
+      launch_cheb_sweep<T>(CFieldRef<T>{D[cur].p, P}, X, R, D[1 - cur], cw[k], k == m - 1, c, act, ctx->stream,
+                           fin);
       cur = 1 - cur;
     }
   };
   launch_pc_rhs<T>(beta, f, c, act, ctx->stream);
-  cheb(CFieldRef<T>{f.p, P}, b2p);
-  cheb(CFieldRef<T>{b2p.p, P}, chi2);
+  cheb(CFieldRef<T>{f.p, P}, b2p, nullptr);
+  if (c.dim == 3 && m > 0) {
+    // step 4 rides on the last pass of the second solve
+    const PcFin<T> fin{CFieldRef<T>{beta, 2 * P}, CFieldRef<T>{b2p.p, P}, FieldRef<T>{chi, 2 * P}};
+    cheb(CFieldRef<T>{b2p.p, P}, chi2, &fin);
+    return;
+  }
+  cheb(CFieldRef<T>{b2p.p, P}, chi2, nullptr);
   launch_pc_final<T>(beta, CFieldRef<T>{b2p.p, P}, chi, c, act, ctx->stream);
 }
 
@@ -600,6 +615,7 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
     // the t-kernel is latency-bound: its own tile (less look-ahead, more blocks per SM)
     const int tile_t = ctx->opts.tile_t >= 0 ? ctx->opts.tile_t : tile;
     const int npart_t = fused ? fused2d_npart(c, m, rows, (int)sizeof(cplx<T>), tile_t) : kDotBlocks;
+    const int npart3 = c.dim == 3 ? stream3d_parts(c, (int)sizeof(cplx<T>)) : kDotBlocks;
     cplx<T>* pp[2] = {p, w.blk[8]};
     cplx<T>* vv[2] = {v, w.blk[9]};
     cplx<T>* rr[2] = {r, w.blk[10]};
@@ -627,33 +643,33 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
           cur = 1 - cur;
           continue;
         }
+        // unfused iteration; the inner products come out of the passes that produce
+        // their vectors (on 3D grids also those of A P^{-1})
         launch_p_update<T>(r, p, v, c, w.ks, s);
         apply_pinv<T>(ctx, w, p, z, w.ks, cw);
-        launch_apply_A<T>(z, v, c, w.ks, s);
-        {
+        if (c.dim == 3) {
+          launch_apply_A_dots<T>(z, v, rhat, 1, w.partials, c, w.ks, s);  // (rhat, v)
+          launch_finalize<T>(1, w.partials, w.ks, OP_ALPHA, ctx->J, s, npart3);
+        } else {
+          launch_apply_A<T>(z, v, c, w.ks, s);
           DotPairs<T> d{{rhat, nullptr, nullptr}, {v, nullptr, nullptr}};
           launch_dots<T>(1, d, w.partials, c, w.ks, s);
           launch_finalize<T>(1, w.partials, w.ks, OP_ALPHA, ctx->J, s);
         }
-        launch_s_update<T>(r, v, u, p, c, w.ks, s);
-        {
-          DotPairs<T> d{{r, nullptr, nullptr}, {r, nullptr, nullptr}};
-          launch_dots<T>(1, d, w.partials, c, w.ks, s);
-          launch_finalize<T>(1, w.partials, w.ks, OP_SNORM, ctx->J, s);
-        }
+        launch_s_update<T>(r, v, u, p, c, w.ks, s, w.partials);  // (s, s)
+        launch_finalize<T>(1, w.partials, w.ks, OP_SNORM, ctx->J, s);
         apply_pinv<T>(ctx, w, r, z, w.ks, cw);
-        launch_apply_A<T>(z, t, c, w.ks, s);
-        {
-          DotPairs<T> d{{t, t, nullptr}, {r, t, nullptr}};
+        if (c.dim == 3) {
+          launch_apply_A_dots<T>(z, t, r, 2, w.partials, c, w.ks, s);  // (t, s), (t, t)
+          launch_finalize<T>(2, w.partials, w.ks, OP_OMEGA, ctx->J, s, npart3);
+        } else {
+          launch_apply_A<T>(z, t, c, w.ks, s);
+          DotPairs<T> d{{t, t, nullptr}, {r, t, nullptr}};  // (t, s), (t, t)
           launch_dots<T>(2, d, w.partials, c, w.ks, s);
           launch_finalize<T>(2, w.partials, w.ks, OP_OMEGA, ctx->J, s);
         }
-        launch_r_update<T>(r, t, u, c, w.ks, s);
-        {
-          DotPairs<T> d{{rhat, r, nullptr}, {r, r, nullptr}};
-          launch_dots<T>(2, d, w.partials, c, w.ks, s);
-          launch_finalize<T>(2, w.partials, w.ks, OP_RHO, ctx->J, s);
-        }
+        launch_r_update<T>(r, t, u, c, w.ks, s, rhat, w.partials);  // (rhat, r), (r, r)
+        launch_finalize<T>(2, w.partials, w.ks, OP_RHO, ctx->J, s);
       }
       st = sync_scalars(ctx, w);
       if (st != APFC_OK) return st;

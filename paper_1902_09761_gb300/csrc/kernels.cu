@@ -7,6 +7,7 @@
 //   D u    = sD u - mu L_h u                                      (diffusion part of Eq. preconditioner)
 #include <algorithm>
 
+#include "acc.cuh"
 #include "apfc_internal.cuh"
 
 namespace apfc {
@@ -264,57 +265,77 @@ __global__ void k_pc_final(const cplx<T>* __restrict__ beta, CFieldRef<T> b2p, c
   chi[o + p] = mkc<T>(b1.x + im * (bp.x - sD * x2.x), b1.y + im * (bp.y - sD * x2.y));
 }
 
-// BiCGStab updates on block vectors (scalars from the device KScal array).
+// BiCGStab updates on block vectors (scalars from the device KScal array).  Each
+// amplitude takes kDotBlocks blocks striding over its 2 pts values, so the FP64 scalars
+// are converted once per thread, and the inner products of the updated vectors come
+// out of the same pass with the traversal (and so the partial sums) of k_dots.
 template <typename T>
 __global__ void k_p_update(const cplx<T>* __restrict__ r, cplx<T>* __restrict__ p_, const cplx<T>* __restrict__ v,
                            OpCoef c, const KScal* k) {
   const int j = blockIdx.y;
   if (!k[j].active) return;
   prof_add(c, kid_of<T>(KID_P_UPDATE), 8ull * (unsigned long long)c.pts * sizeof(cplx<T>));
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * c.pts) return;
-  const long long q = 2LL * j * c.pts + i;
-  const double2 beta = k[j].beta, omega = k[j].omega;
-  const cplx<T> pv = p_[q], vv = v[q], rv = r[q];
-  const cplx<T> w = cmul<T>(omega, vv);
-  const cplx<T> t = mkc<T>(pv.x - w.x, pv.y - w.y);
-  const cplx<T> bt = cmul<T>(beta, t);
-  p_[q] = mkc<T>(rv.x + bt.x, rv.y + bt.y);
+  const long long n = 2LL * c.pts, o = 2LL * j * c.pts;
+  const T br = (T)k[j].beta.x, bi = (T)k[j].beta.y, wr = (T)k[j].omega.x, wi = (T)k[j].omega.y;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const cplx<T> pv = p_[o + i], vv = v[o + i], rv = r[o + i];
+    const T tx = pv.x - (wr * vv.x - wi * vv.y), ty = pv.y - (wr * vv.y + wi * vv.x);
+    p_[o + i] = mkc<T>(rv.x + (br * tx - bi * ty), rv.y + (br * ty + bi * tx));
+  }
 }
 
-// s = r - alpha v (in place in r); u += alpha p.
+// s = r - alpha v (in place in r); u += alpha p; partials != nullptr: (s, s) in slot 0.
 template <typename T>
 __global__ void k_s_update(cplx<T>* __restrict__ r, const cplx<T>* __restrict__ v, cplx<T>* __restrict__ u,
-                           const cplx<T>* __restrict__ p_, OpCoef c, const KScal* k) {
+                           const cplx<T>* __restrict__ p_, OpCoef c, const KScal* k, void* partials) {
   const int j = blockIdx.y;
   if (!k[j].active) return;
   prof_add(c, kid_of<T>(KID_S_UPDATE), 12ull * (unsigned long long)c.pts * sizeof(cplx<T>));
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * c.pts) return;
-  const long long q = 2LL * j * c.pts + i;
-  const double2 al = k[j].alpha;
-  const cplx<T> av = cmul<T>(al, v[q]), ap = cmul<T>(al, p_[q]);
-  const cplx<T> rv = r[q], uv = u[q];
-  r[q] = mkc<T>(rv.x - av.x, rv.y - av.y);
-  u[q] = mkc<T>(uv.x + ap.x, uv.y + ap.y);
+  const long long n = 2LL * c.pts, o = 2LL * j * c.pts;
+  const T ar = (T)k[j].alpha.x, ai = (T)k[j].alpha.y;
+  Acc<T> acc;
+  acc.zero();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const cplx<T> vv = v[o + i], pv = p_[o + i], rv = r[o + i], uv = u[o + i];
+    const cplx<T> sv = mkc<T>(rv.x - (ar * vv.x - ai * vv.y), rv.y - (ar * vv.y + ai * vv.x));
+    r[o + i] = sv;
+    u[o + i] = mkc<T>(uv.x + (ar * pv.x - ai * pv.y), uv.y + (ar * pv.y + ai * pv.x));
+    acc.add(sv, sv);
+  }
+  if (partials == nullptr) return;
+  block_reduce<T>(acc);
+  if (threadIdx.x == 0) acc.store(partials, (long long)(j * kDotSlots) * kDotBlocks + blockIdx.x);
 }
 
-// u += omega s; r = s - omega t (s held in r).
+// u += omega s; r = s - omega t (s held in r); partials != nullptr: (rhat, r), (r, r)
+// in slots 0 and 1.
 template <typename T>
-__global__ void k_r_update(cplx<T>* __restrict__ r, const cplx<T>* __restrict__ t, cplx<T>* __restrict__ u, OpCoef c,
-                           const KScal* k) {
+__global__ void k_r_update(cplx<T>* __restrict__ r, const cplx<T>* __restrict__ t, cplx<T>* __restrict__ u,
+                           const cplx<T>* __restrict__ rhat, OpCoef c, const KScal* k, void* partials) {
   const int j = blockIdx.y;
   if (!k[j].active) return;
-  prof_add(c, kid_of<T>(KID_R_UPDATE), 10ull * (unsigned long long)c.pts * sizeof(cplx<T>));
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= 2 * c.pts) return;
-  const long long q = 2LL * j * c.pts + i;
-  const double2 om = k[j].omega;
-  const cplx<T> s = r[q];
-  const cplx<T> os = cmul<T>(om, s), ot = cmul<T>(om, t[q]);
-  const cplx<T> uv = u[q];
-  u[q] = mkc<T>(uv.x + os.x, uv.y + os.y);
-  r[q] = mkc<T>(s.x - ot.x, s.y - ot.y);
+  prof_add(c, kid_of<T>(KID_R_UPDATE),
+           (partials != nullptr ? 12ull : 10ull) * (unsigned long long)c.pts * sizeof(cplx<T>));
+  const long long n = 2LL * c.pts, o = 2LL * j * c.pts;
+  const T wr = (T)k[j].omega.x, wi = (T)k[j].omega.y;
+  Acc<T> a0, a1;
+  a0.zero();
+  a1.zero();
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const cplx<T> sv = r[o + i], tv = t[o + i], uv = u[o + i];
+    u[o + i] = mkc<T>(uv.x + (wr * sv.x - wi * sv.y), uv.y + (wr * sv.y + wi * sv.x));
+    const cplx<T> rn = mkc<T>(sv.x - (wr * tv.x - wi * tv.y), sv.y - (wr * tv.y + wi * tv.x));
+    r[o + i] = rn;
+    if (partials != nullptr) {
+      a0.add(rhat[o + i], rn);
+      a1.add(rn, rn);
+    }
+  }
+  if (partials == nullptr) return;
+  block_reduce<T>(a0);
+  if (threadIdx.x == 0) a0.store(partials, (long long)(j * kDotSlots) * kDotBlocks + blockIdx.x);
+  block_reduce<T>(a1);
+  if (threadIdx.x == 0) a1.store(partials, (long long)(j * kDotSlots + 1) * kDotBlocks + blockIdx.x);
 }
 
 template <typename T>
@@ -676,7 +697,7 @@ struct N7 {
 // the FP64 pipe).
 template <typename T>
 struct Coef7 {
-  T c0, ih2[3], kh[3], kt, a, it, sD, mu, c1, c2;
+  T c0, ih2[3], kh[3], kt, a, it, sD, mu, im, c1, c2;
 };
 template <typename T>
 __device__ __forceinline__ Coef7<T> coef7(const OpCoef& c, int j) {
@@ -691,6 +712,7 @@ __device__ __forceinline__ Coef7<T> coef7(const OpCoef& c, int j) {
   q.it = (T)c.inv_theta[j];
   q.sD = (T)c.sD[j];
   q.mu = (T)c.mu[j];
+  q.im = (T)c.inv_mu[j];
   q.c1 = q.c2 = (T)0;
   return q;
 }
@@ -740,6 +762,11 @@ __device__ __forceinline__ void cp_async_elem(cplx<T>* dst, const cplx<T>* src) 
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
 }
 
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src));
+}
+
 template <typename T, class OP>
 __global__ void __launch_bounds__(256) k_stream3d(OpCoef c, OP op, const KScal* act) {
   constexpr int NS = OP::NS;
@@ -754,6 +781,9 @@ __global__ void __launch_bounds__(256) k_stream3d(OpCoef c, OP op, const KScal* 
     atomicAdd(c.prof + op.kid, op.bytes);
   Coef7<T> q = coef7<T>(c, j);
   op.coef(q, j);
+  Acc<T> acc[OP::ND > 0 ? OP::ND : 1];
+#pragma unroll
+  for (int d = 0; d < (OP::ND > 0 ? OP::ND : 1); ++d) acc[d].zero();
   // each thread owns column tx of rows ty (and ty + 8 in a 16-row tile)
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
@@ -816,40 +846,81 @@ __global__ void __launch_bounds__(256) k_stream3d(OpCoef c, OP op, const KScal* 
           n[k].zp = tile[k][nb][ly][tx + 1];
           zm[r][k] = n[k].c;
         }
-        op.apply(j, (long long)z * plane + pxy[r], n, c, q);
+        const long long pz = (long long)z * plane + pxy[r];
+        cplx<T> pv[OP::NQ > 0 ? OP::NQ : 1];
+#pragma unroll
+        for (int k = 0; k < OP::NQ; ++k) {
+          const cplx<T>* qs = op.qsrc(k, j);
+          pv[k] = qs != nullptr ? qs[pz] : cplx<T>{};
+        }
+        op.apply(j, pz, n, c, q, acc, pv);
       }
     }
+#pragma unroll
+    for (int d = 0; d < OP::ND; ++d) acc[d].flush();
     __syncthreads();  // buffer cb is refilled two planes later
     cb = nb;
   }
   asm volatile("cp.async.wait_group 0;\n" ::);
+  if constexpr (OP::ND > 0) {
+    const long long npart = (long long)gridDim.x * gridDim.y * nchunk;
+    const long long bid = ((long long)chunk * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int d = 0; d < OP::ND; ++d) {
+      block_reduce<T>(acc[d]);
+      if (threadIdx.x == 0) acc[d].store(op.partials, (long long)(j * kDotSlots + d) * npart + bid);
+    }
+  }
 }
 
-// y = A x (both parts of x are stencil inputs)
-template <typename T>
+// Pass interface of k_stream3d / k_stream3d_pair:
+//   NS stencil inputs src(k, j) (read with a one-point halo), NQ pointwise inputs
+//   qsrc(k, j) (their values at p arrive in pv[k]; a null qsrc is not read), ND inner
+//   products accumulated in acc, MINB blocks per SM for the two-point kernel, and
+//   apply(j, p, nbh[NS], c, q, acc, pv) doing the pointwise work and the stores.
+
+// y = A x (both parts of x are stencil inputs); ND inner products of y accumulated on
+// the way: ND = 1 (du, y), ND = 2 (y, du) and (y, y), with (u, v) = sum conj(u) v
+template <typename T, int ND_ = 0>
 struct OpA3 {
-  static constexpr int NS = 2;
+  static constexpr int NS = 2, ND = ND_, NQ = ND_ > 0 ? 2 : 0, MINB = ND_ > 0 ? 2 : 3;
   const cplx<T>* x;
   cplx<T>* y;
   long long pts;
   int kid;
   unsigned long long bytes;
+  const cplx<T>* du = nullptr;
+  void* partials = nullptr;
   template <typename Q>
   __device__ void coef(Q&, int) const {}
   __device__ const cplx<T>* src(int k, int j) const { return x + (2LL * j + k) * pts; }
-  __device__ void apply(int j, long long p, const N7<T> (&n)[2], const OpCoef& c, const Coef7<T>& q) const {
+  __device__ const cplx<T>* qsrc(int k, int j) const { return du + (2LL * j + k) * pts; }
+  __device__ void apply(int j, long long p, const N7<T> (&n)[2], const OpCoef& c, const Coef7<T>& q, Acc<T>* acc,
+                        const cplx<T>* pv) const {
     const cplx<T> gz = G7(n[0], q), ge = G7(n[1], q);
     const T kt = q.kt, a = a7(q, c, j, p);
-    cplx<T>* y1 = y + 2LL * j * pts;
-    y1[p] = mkc<T>(n[0].c.x - ge.x, n[0].c.y - ge.y);
-    y1[pts + p] = mkc<T>(kt * gz.x + a * n[1].c.x, kt * gz.y + a * n[1].c.y);
+    const long long o = 2LL * j * pts;
+    const cplx<T> y1 = mkc<T>(n[0].c.x - ge.x, n[0].c.y - ge.y);
+    const cplx<T> y2 = mkc<T>(kt * gz.x + a * n[1].c.x, kt * gz.y + a * n[1].c.y);
+    y[o + p] = y1;
+    y[o + pts + p] = y2;
+    // plain FP32 runs, folded into the compensated sums once per plane (Acc::flush)
+    if constexpr (ND == 1) {
+      acc[0].add_run(pv[0], y1);
+      acc[0].add_run(pv[1], y2);
+    } else if constexpr (ND == 2) {
+      acc[0].add_run(y1, pv[0]);
+      acc[0].add_run(y2, pv[1]);
+      acc[1].add_run(y1, y1);
+      acc[1].add_run(y2, y2);
+    }
   }
 };
 
 // r = b - A x, rhat = r
 template <typename T>
 struct OpRes3 {
-  static constexpr int NS = 2;
+  static constexpr int NS = 2, ND = 0, NQ = 2, MINB = 2;
   const cplx<T>* x;
   const cplx<T>* b;
   cplx<T>* r;
@@ -860,11 +931,13 @@ struct OpRes3 {
   template <typename Q>
   __device__ void coef(Q&, int) const {}
   __device__ const cplx<T>* src(int k, int j) const { return x + (2LL * j + k) * pts; }
-  __device__ void apply(int j, long long p, const N7<T> (&n)[2], const OpCoef& c, const Coef7<T>& q) const {
+  __device__ const cplx<T>* qsrc(int k, int j) const { return b + (2LL * j + k) * pts; }
+  __device__ void apply(int j, long long p, const N7<T> (&n)[2], const OpCoef& c, const Coef7<T>& q, Acc<T>*,
+                        const cplx<T>* pv) const {
     const cplx<T> gz = G7(n[0], q), ge = G7(n[1], q);
     const T kt = q.kt, a = a7(q, c, j, p);
     const long long o = 2LL * j * pts;
-    const cplx<T> b1 = b[o + p], b2 = b[o + pts + p];
+    const cplx<T> b1 = pv[0], b2 = pv[1];
     const cplx<T> r1 = mkc<T>(b1.x - (n[0].c.x - ge.x), b1.y - (n[0].c.y - ge.y));
     const cplx<T> r2 = mkc<T>(b2.x - (kt * gz.x + a * n[1].c.x), b2.y - (kt * gz.y + a * n[1].c.y));
     r[o + p] = r1;
@@ -877,7 +950,7 @@ struct OpRes3 {
 // f = beta2 - kt G beta1
 template <typename T>
 struct OpPcRhs3 {
-  static constexpr int NS = 1;
+  static constexpr int NS = 1, ND = 0, NQ = 1, MINB = 4;
   const cplx<T>* beta;
   FieldRef<T> f;
   long long pts;
@@ -886,22 +959,32 @@ struct OpPcRhs3 {
   template <typename Q>
   __device__ void coef(Q&, int) const {}
   __device__ const cplx<T>* src(int, int j) const { return beta + 2LL * j * pts; }
-  __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c, const Coef7<T>& q) const {
+  __device__ const cplx<T>* qsrc(int, int j) const { return beta + (2LL * j + 1) * pts; }
+  __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c, const Coef7<T>& q, Acc<T>*,
+                        const cplx<T>* pv) const {
     const cplx<T> g = G7(n[0], q);
-    const cplx<T> b2 = beta[2LL * j * pts + pts + p];
+    const cplx<T> b2 = pv[0];
     const T kt = q.kt;
     f.at(j)[p] = mkc<T>(b2.x - kt * g.x, b2.y - kt * g.y);
   }
 };
 
-// first Chebyshev application (see k_cheb_first)
+// step 4 of P^{-1} at point p: chi1 = beta1 + (beta2' - sD chi2) / mu
+template <typename T>
+__device__ __forceinline__ void finish_pc(const PcFin<T>& f, int j, long long p, cplx<T> b1, cplx<T> bp, cplx<T> x2,
+                                          const Coef7<T>& q) {
+  f.chi1.at(j)[p] = mkc<T>(b1.x + q.im * (bp.x - q.sD * x2.x), b1.y + q.im * (bp.y - q.sD * x2.y));
+}
+
+// first Chebyshev application (see k_cheb_first); pointwise input: beta1 with fin
 template <typename T>
 struct OpChebFirst3 {
-  static constexpr int NS = 1;
+  static constexpr int NS = 1, ND = 0, NQ = 1, MINB = 3;
   CFieldRef<T> f;
   FieldRef<T> X, R, Dn;
   ChebStep w;
   int last;
+  PcFin<T> fin;  // fin.chi1.p != nullptr: also chi1 = beta1 + (beta2' - sD chi2) / mu
   int kid;
   unsigned long long bytes;
   template <typename Q>
@@ -910,7 +993,9 @@ struct OpChebFirst3 {
     q.c2 = (T)w.c2[j];
   }
   __device__ const cplx<T>* src(int, int j) const { return f.at(j); }
-  __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c, const Coef7<T>& q) const {
+  __device__ const cplx<T>* qsrc(int, int j) const { return fin.chi1.p != nullptr ? fin.b1.at(j) : nullptr; }
+  __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c, const Coef7<T>& q, Acc<T>*,
+                        const cplx<T>* pv) const {
     const T it = q.it;
     const cplx<T> Df = D7(n[0], q);
     const cplx<T> d0 = mkc<T>(it * n[0].c.x, it * n[0].c.y);
@@ -918,7 +1003,10 @@ struct OpChebFirst3 {
     const T c1 = q.c1, c2 = q.c2;
     const cplx<T> d1 = mkc<T>(c1 * d0.x + c2 * r1.x, c1 * d0.y + c2 * r1.y);
     if (last) {
-      X.at(j)[p] = mkc<T>(d0.x + d1.x, d0.y + d1.y);
+      const cplx<T> x2 = mkc<T>(d0.x + d1.x, d0.y + d1.y);
+      X.at(j)[p] = x2;
+      // the source of the second solve is beta2'
+      if (fin.chi1.p != nullptr) finish_pc(fin, j, p, pv[0], n[0].c, x2, q);
     } else {
       X.at(j)[p] = d0;
       R.at(j)[p] = r1;
@@ -927,14 +1015,16 @@ struct OpChebFirst3 {
   }
 };
 
-// later Chebyshev application (see k_cheb_sweep)
+// later Chebyshev application (see k_cheb_sweep); pointwise inputs X, R and, with fin,
+// beta1 and beta2'
 template <typename T>
 struct OpChebSweep3 {
-  static constexpr int NS = 1;
+  static constexpr int NS = 1, ND = 0, NQ = 4, MINB = 3;
   CFieldRef<T> Dd;
   FieldRef<T> X, R, Dn;
   ChebStep w;
   int last;
+  PcFin<T> fin;  // fin.chi1.p != nullptr: also chi1 = beta1 + (beta2' - sD chi2) / mu
   int kid;
   unsigned long long bytes;
   template <typename Q>
@@ -943,16 +1033,24 @@ struct OpChebSweep3 {
     q.c2 = (T)w.c2[j];
   }
   __device__ const cplx<T>* src(int, int j) const { return Dd.at(j); }
-  __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c, const Coef7<T>& q) const {
+  __device__ const cplx<T>* qsrc(int k, int j) const {
+    if (k < 2) return k == 0 ? X.at(j) : R.at(j);
+    if (fin.chi1.p == nullptr) return nullptr;
+    return k == 2 ? fin.b1.at(j) : fin.b2p.at(j);
+  }
+  __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c, const Coef7<T>& q, Acc<T>*,
+                        const cplx<T>* pv) const {
     const cplx<T> DD = D7(n[0], q);
     const cplx<T> d = n[0].c;
-    const cplx<T> x = X.at(j)[p], r = R.at(j)[p];
+    const cplx<T> x = pv[0], r = pv[1];
     const cplx<T> xn = mkc<T>(x.x + d.x, x.y + d.y);
     const cplx<T> rn = mkc<T>(r.x - DD.x, r.y - DD.y);
     const T c1 = q.c1, c2 = q.c2;
     const cplx<T> dn = mkc<T>(c1 * d.x + c2 * rn.x, c1 * d.y + c2 * rn.y);
     if (last) {
-      X.at(j)[p] = mkc<T>(xn.x + dn.x, xn.y + dn.y);
+      const cplx<T> x2 = mkc<T>(xn.x + dn.x, xn.y + dn.y);
+      X.at(j)[p] = x2;
+      if (fin.chi1.p != nullptr) finish_pc(fin, j, p, pv[2], pv[3], x2, q);
     } else {
       X.at(j)[p] = xn;
       R.at(j)[p] = rn;
@@ -963,7 +1061,7 @@ struct OpChebSweep3 {
 
 // zeta-part of the state = G_h (eta-part), FP64
 struct OpZeta3 {
-  static constexpr int NS = 1;
+  static constexpr int NS = 1, ND = 0, NQ = 0, MINB = 3;
   double2* x;
   long long pts;
   int kid;
@@ -971,7 +1069,9 @@ struct OpZeta3 {
   template <typename Q>
   __device__ void coef(Q&, int) const {}
   __device__ const double2* src(int, int j) const { return x + (2LL * j + 1) * pts; }
-  __device__ void apply(int j, long long p, const N7<double> (&n)[1], const OpCoef& c, const Coef7<double>& q) const {
+  __device__ const double2* qsrc(int, int) const { return nullptr; }
+  __device__ void apply(int j, long long p, const N7<double> (&n)[1], const OpCoef& c, const Coef7<double>& q,
+                        Acc<double>*, const double2*) const {
     x[2LL * j * pts + p] = G7(n[0], q);
   }
 };
@@ -979,7 +1079,7 @@ struct OpZeta3 {
 // FP64 outer residual on 3D grids: r = b - A x (x, b FP64), written as FP32 and, if
 // r64 != nullptr, as FP64.
 struct OpResRefine3 {
-  static constexpr int NS = 2;
+  static constexpr int NS = 2, ND = 0, NQ = 2, MINB = 3;
   const double2* x;
   const double2* b;
   float2* r32;
@@ -990,11 +1090,13 @@ struct OpResRefine3 {
   template <typename Q>
   __device__ void coef(Q&, int) const {}
   __device__ const double2* src(int k, int j) const { return x + (2LL * j + k) * pts; }
-  __device__ void apply(int j, long long p, const N7<double> (&n)[2], const OpCoef& c, const Coef7<double>& q) const {
+  __device__ const double2* qsrc(int k, int j) const { return b + (2LL * j + k) * pts; }
+  __device__ void apply(int j, long long p, const N7<double> (&n)[2], const OpCoef& c, const Coef7<double>& q,
+                        Acc<double>*, const double2* pv) const {
     const double2 gz = G7(n[0], q), ge = G7(n[1], q);
     const double kt = q.kt, a = a7(q, c, j, p);
     const long long o = 2LL * j * pts;
-    const double2 b1 = b[o + p], b2 = b[o + pts + p];
+    const double2 b1 = pv[0], b2 = pv[1];
     const double r1x = (b1.x - n[0].c.x) + ge.x, r1y = (b1.y - n[0].c.y) + ge.y;
     const double r2x = b2.x - fma(kt, gz.x, a * n[1].c.x), r2y = b2.y - fma(kt, gz.y, a * n[1].c.y);
     r32[o + p] = make_float2((float)r1x, (float)r1y);
@@ -1014,11 +1116,16 @@ struct OpResRefine3 {
 // single-point kernel (short-scoreboard stalls).
 constexpr int kPX = 64, kPY = 8, kPW = kPX + 4;  // tile columns, rows, row stride (2 + 64 + 2)
 template <class OP>
-__global__ void __launch_bounds__(256) k_stream3d_pair(OpCoef c, OP op, const KScal* act) {
+__global__ void __launch_bounds__(256, OP::MINB) k_stream3d_pair(OpCoef c, OP op, const KScal* act) {
   using T = float;
   constexpr int NS = OP::NS;
   constexpr int kHYp = kPY + 2, kNE = (kPX + 2) * kHYp;  // elements fetched per plane
   __shared__ __align__(16) float2 tile[NS][kZBuf][kHYp][kPW];
+  // pointwise inputs (up to two) ride on the same copy groups: each thread fetches its own
+  // pair of every plane kZAhead planes ahead into a ring of kZAhead + 1 buffers
+  constexpr bool QS = OP::NQ > 0 && OP::NQ <= 2;
+  constexpr int NQS = QS ? OP::NQ : 1, kQB = QS ? kZAhead + 1 : 1;
+  __shared__ __align__(16) float2 qt[NQS][kQB][kPY][kPX];
   const int nchunk = (c.nz + kZChunk - 1) / kZChunk;
   const int j = (int)(blockIdx.z / (unsigned)nchunk);
   if (act != nullptr && act[j].active == 0) return;
@@ -1027,6 +1134,9 @@ __global__ void __launch_bounds__(256) k_stream3d_pair(OpCoef c, OP op, const KS
     atomicAdd(c.prof + op.kid, op.bytes);
   Coef7<T> q = coef7<T>(c, j);
   op.coef(q, j);
+  Acc<T> acc[OP::ND > 0 ? OP::ND : 1];
+#pragma unroll
+  for (int d = 0; d < (OP::ND > 0 ? OP::ND : 1); ++d) acc[d].zero();
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kPY;
   const int xa = x0 + 2 * tx, y = y0 + ty;
@@ -1044,16 +1154,35 @@ __global__ void __launch_bounds__(256) k_stream3d_pair(OpCoef c, OP op, const KS
     qoff[ne] = (long long)wrapi(y0 - 1 + hy, c.ny) * c.nx + wrapi(x0 - 1 + li, c.nx);
     hoff[ne] = hy * kPW + li + 1;
   }
-  auto issue_tile = [&](int buf, int z) {
+  const bool in0 = xa < c.nx && y < c.ny, in1 = xa + 1 < c.nx && y < c.ny;
+  const long long p0 = (long long)(in0 ? y : 0) * c.nx + (in0 ? xa : 0);
+  const long long p1 = in1 ? p0 + 1 : p0;
+  const float2* qs[OP::NQ > 0 ? OP::NQ : 1];
+#pragma unroll
+  for (int k = 0; k < OP::NQ; ++k) qs[k] = op.qsrc(k, j);
+  auto issue_tile = [&](int buf, int qb, int z) {
     const long long zo = (long long)wrapi(z, c.nz) * plane;
     for (int i = 0; i < ne; ++i)
 #pragma unroll
       for (int k = 0; k < NS; ++k) cp_async_elem<T>(&tile[k][buf][0][0] + hoff[i], src[k] + zo + qoff[i]);
+    if constexpr (QS) {
+      if (z < z1 && in0) {
+#pragma unroll
+        for (int k = 0; k < NQS; ++k) {
+          if (qs[k] == nullptr) continue;
+          const float2* g = qs[k] + zo + p0;
+          float2* d = &qt[k][qb][ty][2 * tx];
+          if (in1 && (reinterpret_cast<unsigned long long>(g) & 15ull) == 0) {
+            cp_async16(d, g);
+          } else {
+            cp_async_elem<T>(d, g);
+            if (in1) cp_async_elem<T>(d + 1, g + 1);
+          }
+        }
+      }
+    }
     asm volatile("cp.async.commit_group;\n" ::);
   };
-  const bool in0 = xa < c.nx && y < c.ny, in1 = xa + 1 < c.nx && y < c.ny;
-  const long long p0 = (long long)(in0 ? y : 0) * c.nx + (in0 ? xa : 0);
-  const long long p1 = in1 ? p0 + 1 : p0;
   float2 zm0[NS], zm1[NS];
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
@@ -1062,14 +1191,15 @@ __global__ void __launch_bounds__(256) k_stream3d_pair(OpCoef c, OP op, const KS
     zm1[k] = src[k][zo + p1];
   }
 #pragma unroll
-  for (int a = 0; a < kZAhead; ++a) issue_tile(a, z0 + a);
+  for (int a = 0; a < kZAhead; ++a) issue_tile(a, a, z0 + a);
   const int lc = 2 * tx + 2;  // local column of xa: even, so the pair is 16-byte aligned
-  int cb = 0;
+  int cb = 0, qc = 0;
   for (int z = z0; z < z1; ++z) {
     const int nb = cb + 1 == kZBuf ? 0 : cb + 1;
     int fb = cb + kZAhead;
     if (fb >= kZBuf) fb -= kZBuf;
-    issue_tile(fb, z + kZAhead);  // into a buffer no plane in use occupies
+    const int qf = qc == 0 ? kQB - 1 : qc - 1;  // (qc + kZAhead) mod kQB
+    issue_tile(fb, QS ? qf : 0, z + kZAhead);  // into buffers no plane in use occupies
     asm volatile("cp.async.wait_group %0;\n" ::"n"(kZAhead - 1));  // planes z and z+1 have landed
     __syncthreads();
     if (in0) {
@@ -1099,13 +1229,37 @@ __global__ void __launch_bounds__(256) k_stream3d_pair(OpCoef c, OP op, const KS
         zm1[k] = n1[k].c;
       }
       const long long zo = (long long)z * plane;
-      op.apply(j, zo + p0, n0, c, q);
-      if (in1) op.apply(j, zo + p1, n1, c, q);
+      float2 pv0[OP::NQ > 0 ? OP::NQ : 1], pv1[OP::NQ > 0 ? OP::NQ : 1];
+#pragma unroll
+      for (int k = 0; k < OP::NQ; ++k) {
+        if constexpr (QS) {
+          const float4 v = *reinterpret_cast<const float4*>(&qt[k][qc][ty][2 * tx]);
+          pv0[k] = make_float2(v.x, v.y);
+          pv1[k] = make_float2(v.z, v.w);
+        } else {
+          pv0[k] = qs[k] != nullptr ? qs[k][zo + p0] : make_float2(0.f, 0.f);
+          pv1[k] = qs[k] != nullptr ? qs[k][zo + p1] : make_float2(0.f, 0.f);
+        }
+      }
+      op.apply(j, zo + p0, n0, c, q, acc, pv0);
+      if (in1) op.apply(j, zo + p1, n1, c, q, acc, pv1);
+#pragma unroll
+      for (int d = 0; d < OP::ND; ++d) acc[d].flush();
     }
     __syncthreads();  // buffer cb is refilled two planes later
     cb = nb;
+    qc = qc + 1 == kQB ? 0 : qc + 1;
   }
   asm volatile("cp.async.wait_group 0;\n" ::);
+  if constexpr (OP::ND > 0) {
+    const long long npart = (long long)gridDim.x * gridDim.y * nchunk;
+    const long long bid = ((long long)chunk * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int d = 0; d < OP::ND; ++d) {
+      block_reduce<T>(acc[d]);
+      if (threadIdx.x == 0) acc[d].store(op.partials, (long long)(j * kDotSlots + d) * npart + bid);
+    }
+  }
 }
 
 template <typename T>
@@ -1119,9 +1273,6 @@ inline dim3 grid_pts3(const OpCoef& c) {
   return dim3((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8), (unsigned)(c.nz * c.J));
 }
 
-inline dim3 grid_pts(const OpCoef& c, long long n) {
-  return dim3((unsigned)((n + kThreads - 1) / kThreads), (unsigned)c.J);
-}
 
 
 // ---------------------------------------------------------------------------
@@ -1432,6 +1583,23 @@ void launch_apply_A(const cplx<T>* x, cplx<T>* y, const OpCoef& c, const KScal* 
   ProfScope ps_(kid_of<T>(KID_APPLY_A), s);
   k_apply_A<T><<<grid_pts3(c), kThreads, 0, s>>>(x, y, c, act);
 }
+int stream3d_parts(const OpCoef& c, int elem_bytes) {
+  const dim3 g = elem_bytes == 8 ? grid_stream3d<float>(c) : grid_stream3d<double>(c);
+  return (int)(g.x * g.y * (unsigned)((c.nz + kZChunk - 1) / kZChunk));
+}
+template <typename T>
+void launch_apply_A_dots(const cplx<T>* x, cplx<T>* y, const cplx<T>* du, int nd, void* partials, const OpCoef& c,
+                         const KScal* act, cudaStream_t s) {
+  ProfScope ps3_(kid_of<T>(KID_APPLY_A), s);
+  const unsigned long long b = 6ull * (unsigned long long)c.pts * sizeof(cplx<T>);
+  if (nd == 1) {
+    OpA3<T, 1> op{x, y, c.pts, kid_of<T>(KID_APPLY_A), b, du, partials};
+    stream3d<T, OpA3<T, 1>>(c, op, act, s);
+  } else {
+    OpA3<T, 2> op{x, y, c.pts, kid_of<T>(KID_APPLY_A), b, du, partials};
+    stream3d<T, OpA3<T, 2>>(c, op, act, s);
+  }
+}
 template <typename T>
 void launch_residual(const cplx<T>* b, const cplx<T>* x, cplx<T>* r, cplx<T>* rhat, const OpCoef& c, cudaStream_t s) {
   if (c.dim == 3) {
@@ -1460,50 +1628,69 @@ void launch_cheb_zero(CFieldRef<T> f, FieldRef<T> X, const OpCoef& c, const KSca
   k_cheb_zero<T><<<grid_pts3(c), kThreads, 0, s>>>(f, X, c, act);
 }
 template <typename T>
-void launch_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
-                       const OpCoef& c, const KScal* act, cudaStream_t s) {
-  if (c.dim == 3) {
-    ProfScope ps3_(kid_of<T>(KID_CHEB_FIRST), s);
-    OpChebFirst3<T> op{f, X, R, Dn, w, last, kid_of<T>(KID_CHEB_FIRST), (last ? 2ull : 4ull) * (unsigned long long)c.pts * sizeof(cplx<T>)};
-    stream3d<T, OpChebFirst3<T>>(c, op, act, s);
-    return;
-  }
-  ProfScope ps_(kid_of<T>(KID_CHEB_FIRST), s);
-  k_cheb_first<T><<<grid_pts3(c), kThreads, 0, s>>>(f, X, R, Dn, w, last, c, act);
-}
-template <typename T>
-void launch_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
-                       const OpCoef& c, const KScal* act, cudaStream_t s) {
-  if (c.dim == 3) {
-    ProfScope ps3_(kid_of<T>(KID_CHEB_SWEEP), s);
-    OpChebSweep3<T> op{Dd, X, R, Dn, w, last, kid_of<T>(KID_CHEB_SWEEP), (last ? 4ull : 6ull) * (unsigned long long)c.pts * sizeof(cplx<T>)};
-    stream3d<T, OpChebSweep3<T>>(c, op, act, s);
-    return;
-  }
-  ProfScope ps_(kid_of<T>(KID_CHEB_SWEEP), s);
-  k_cheb_sweep<T><<<grid_pts3(c), kThreads, 0, s>>>(Dd, X, R, Dn, w, last, c, act);
-}
-template <typename T>
 void launch_pc_final(const cplx<T>* beta, CFieldRef<T> b2p, cplx<T>* chi, const OpCoef& c, const KScal* act,
                      cudaStream_t s) {
   ProfScope ps_(kid_of<T>(KID_PC_FINAL), s);
   k_pc_final<T><<<grid_pts3(c), kThreads, 0, s>>>(beta, b2p, chi, c, act);
 }
 template <typename T>
+void launch_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
+                       const OpCoef& c, const KScal* act, cudaStream_t s, const PcFin<T>* fin) {
+  const bool fold = fin != nullptr && last;
+  if (c.dim == 3) {
+    ProfScope ps3_(kid_of<T>(KID_CHEB_FIRST), s);
+    OpChebFirst3<T> op{f,    X,
+                       R,    Dn,
+                       w,    last,
+                       fold ? *fin : PcFin<T>{},
+                       kid_of<T>(KID_CHEB_FIRST),
+                       (last ? (fold ? 4ull : 2ull) : 4ull) * (unsigned long long)c.pts * sizeof(cplx<T>)};
+    stream3d<T, OpChebFirst3<T>>(c, op, act, s);
+    return;
+  }
+  {
+    ProfScope ps_(kid_of<T>(KID_CHEB_FIRST), s);
+    k_cheb_first<T><<<grid_pts3(c), kThreads, 0, s>>>(f, X, R, Dn, w, last, c, act);
+  }
+  if (fold) launch_pc_final<T>(fin->b1.p, fin->b2p, fin->chi1.p, c, act, s);
+}
+template <typename T>
+void launch_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
+                       const OpCoef& c, const KScal* act, cudaStream_t s, const PcFin<T>* fin) {
+  const bool fold = fin != nullptr && last;
+  if (c.dim == 3) {
+    ProfScope ps3_(kid_of<T>(KID_CHEB_SWEEP), s);
+    OpChebSweep3<T> op{Dd,   X,
+                       R,    Dn,
+                       w,    last,
+                       fold ? *fin : PcFin<T>{},
+                       kid_of<T>(KID_CHEB_SWEEP),
+                       (last ? (fold ? 7ull : 4ull) : 6ull) * (unsigned long long)c.pts * sizeof(cplx<T>)};
+    stream3d<T, OpChebSweep3<T>>(c, op, act, s);
+    return;
+  }
+  {
+    ProfScope ps_(kid_of<T>(KID_CHEB_SWEEP), s);
+    k_cheb_sweep<T><<<grid_pts3(c), kThreads, 0, s>>>(Dd, X, R, Dn, w, last, c, act);
+  }
+  if (fold) launch_pc_final<T>(fin->b1.p, fin->b2p, fin->chi1.p, c, act, s);
+}
+template <typename T>
 void launch_p_update(const cplx<T>* r, cplx<T>* p, const cplx<T>* v, const OpCoef& c, const KScal* k, cudaStream_t s) {
   ProfScope ps_(kid_of<T>(KID_P_UPDATE), s);
-  k_p_update<T><<<grid_pts(c, 2 * c.pts), kThreads, 0, s>>>(r, p, v, c, k);
+  k_p_update<T><<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(r, p, v, c, k);
 }
 template <typename T>
 void launch_s_update(cplx<T>* r, const cplx<T>* v, cplx<T>* u, const cplx<T>* p, const OpCoef& c, const KScal* k,
-                     cudaStream_t s) {
+                     cudaStream_t s, void* partials) {
   ProfScope ps_(kid_of<T>(KID_S_UPDATE), s);
-  k_s_update<T><<<grid_pts(c, 2 * c.pts), kThreads, 0, s>>>(r, v, u, p, c, k);
+  k_s_update<T><<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(r, v, u, p, c, k, partials);
 }
 template <typename T>
-void launch_r_update(cplx<T>* r, const cplx<T>* t, cplx<T>* u, const OpCoef& c, const KScal* k, cudaStream_t s) {
+void launch_r_update(cplx<T>* r, const cplx<T>* t, cplx<T>* u, const OpCoef& c, const KScal* k, cudaStream_t s,
+                     const cplx<T>* rhat, void* partials) {
   ProfScope ps_(kid_of<T>(KID_R_UPDATE), s);
-  k_r_update<T><<<grid_pts(c, 2 * c.pts), kThreads, 0, s>>>(r, t, u, c, k);
+  k_r_update<T><<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(r, t, u, rhat, c, k, partials);
 }
 template <typename T>
 void launch_add_to(const cplx<T>* d, double2* x, const OpCoef& c, cudaStream_t s) {
@@ -1593,16 +1780,19 @@ void launch_rhs_picard(const double2* x, const double2* eta_prev, double2* b, do
   template void launch_pc_rhs<T>(const cplx<T>*, FieldRef<T>, const OpCoef&, const KScal*, cudaStream_t);           \
   template void launch_cheb_zero<T>(CFieldRef<T>, FieldRef<T>, const OpCoef&, const KScal*, cudaStream_t);          \
   template void launch_cheb_first<T>(CFieldRef<T>, FieldRef<T>, FieldRef<T>, FieldRef<T>, const ChebStep&, int,     \
-                                     const OpCoef&, const KScal*, cudaStream_t);                                    \
+                                     const OpCoef&, const KScal*, cudaStream_t, const PcFin<T>*);                   \
   template void launch_cheb_sweep<T>(CFieldRef<T>, FieldRef<T>, FieldRef<T>, FieldRef<T>, const ChebStep&, int,     \
-                                     const OpCoef&, const KScal*, cudaStream_t);                                    \
+                                     const OpCoef&, const KScal*, cudaStream_t, const PcFin<T>*);                   \
+  template void launch_apply_A_dots<T>(const cplx<T>*, cplx<T>*, const cplx<T>*, int, void*, const OpCoef&,         \
+                                       const KScal*, cudaStream_t);                                                 \
   template void launch_pc_final<T>(const cplx<T>*, CFieldRef<T>, cplx<T>*, const OpCoef&, const KScal*,             \
                                    cudaStream_t);                                                                   \
   template void launch_p_update<T>(const cplx<T>*, cplx<T>*, const cplx<T>*, const OpCoef&, const KScal*,           \
                                    cudaStream_t);                                                                   \
   template void launch_s_update<T>(cplx<T>*, const cplx<T>*, cplx<T>*, const cplx<T>*, const OpCoef&, const KScal*, \
-                                   cudaStream_t);                                                                   \
-  template void launch_r_update<T>(cplx<T>*, const cplx<T>*, cplx<T>*, const OpCoef&, const KScal*, cudaStream_t);  \
+                                   cudaStream_t, void*);                                                            \
+  template void launch_r_update<T>(cplx<T>*, const cplx<T>*, cplx<T>*, const OpCoef&, const KScal*, cudaStream_t,   \
+                                   const cplx<T>*, void*);                                                          \
   template void launch_add_to<T>(const cplx<T>*, double2*, const OpCoef&, cudaStream_t);
 
 APFC_INST(double)
