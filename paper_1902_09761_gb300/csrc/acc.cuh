@@ -171,15 +171,19 @@ __device__ __forceinline__ void scalar_update(KScal& k, int op, const double2* d
       }
       break;
     }
+    // unfused iteration: u += alpha p + omega s is one pass after OP_OMEGA, so an
+    // amplitude that stops at OP_SNORM or OP_OMEGA still owes u += alpha p (just_done)
     case OP_SNORM: {  // d0 = (s, s)
       if (!isfinite(d[0].x)) {
         k.status = KS_NAN;
         k.active = 0;
+        k.just_done = 1;
       } else if (d[0].x <= k.tol2) {
         k.rnorm2 = d[0].x;
         k.iters += 1;
         k.status = KS_CONVERGED;
         k.active = 0;
+        k.just_done = 1;
       }
       break;
     }
@@ -187,9 +191,11 @@ __device__ __forceinline__ void scalar_update(KScal& k, int op, const double2* d
       if (!finite2(d[0]) || !isfinite(d[1].x)) {
         k.status = KS_NAN;
         k.active = 0;
+        k.just_done = 1;
       } else if (d[1].x == 0.0 || cabs2(d[0]) == 0.0) {
         k.status = KS_BREAKDOWN;
         k.active = 0;
+        k.just_done = 1;
       } else {
         k.omega = make_double2(d[0].x / d[1].x, d[0].y / d[1].x);
       }

@@ -196,7 +196,7 @@ struct KScal {
   double2 rho, alpha, omega, beta;
   double bnorm2, rnorm2, tol2, tolrel2;
   int active, iters, status, max_iter;
-  int just_done;  // merged iteration: stopped in this iteration, its last update still pending
+  int just_done;  // stopped in this iteration, its last update of u still pending
   int pad;
 };
 
@@ -229,14 +229,15 @@ void launch_pc_final(const cplx<T>* beta, CFieldRef<T> b2p, cplx<T>* chi, const 
 template <typename T>
 void launch_p_update(const cplx<T>* r, cplx<T>* p, const cplx<T>* v, const OpCoef& c, const KScal* k,
                      cudaStream_t s);
-// partials != nullptr: the inner products of the updated vectors, (s, s) for the s-update
-// and (rhat, r), (r, r) for the r-update, in the k_dots layout [J][kDotSlots][kDotBlocks]
+// s = r - alpha v (in r); then u += alpha p + omega s, r = s - omega t.  partials !=
+// nullptr: the inner products of the updated vectors, (s, s) for the s-update and
+// (rhat, r), (r, r) for the r-update, in the k_dots layout [J][kDotSlots][kDotBlocks]
 template <typename T>
-void launch_s_update(cplx<T>* r, const cplx<T>* v, cplx<T>* u, const cplx<T>* p, const OpCoef& c, const KScal* k,
-                     cudaStream_t s, void* partials = nullptr);
+void launch_s_update(cplx<T>* r, const cplx<T>* v, const OpCoef& c, const KScal* k, cudaStream_t s,
+                     void* partials = nullptr);
 template <typename T>
-void launch_r_update(cplx<T>* r, const cplx<T>* t, cplx<T>* u, const OpCoef& c, const KScal* k, cudaStream_t s,
-                     const cplx<T>* rhat = nullptr, void* partials = nullptr);
+void launch_r_update(cplx<T>* r, const cplx<T>* t, cplx<T>* u, const cplx<T>* p, const OpCoef& c, const KScal* k,
+                     cudaStream_t s, const cplx<T>* rhat = nullptr, void* partials = nullptr);
 // 3D grids: y = A x with inner products of y in the same pass: nd = 1 gives (du, y),
 // nd = 2 gives (y, du) and (y, y).  Partials use the layout [J][kDotSlots][npart] with
 // npart = stream3d_parts(c, sizeof(cplx<T>)) (one per block of the pass).

@@ -656,7 +656,7 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
           launch_dots<T>(1, d, w.partials, c, w.ks, s);
           launch_finalize<T>(1, w.partials, w.ks, OP_ALPHA, ctx->J, s);
         }
-        launch_s_update<T>(r, v, u, p, c, w.ks, s, w.partials);  // (s, s)
+        launch_s_update<T>(r, v, c, w.ks, s, w.partials);  // (s, s)
         launch_finalize<T>(1, w.partials, w.ks, OP_SNORM, ctx->J, s);
         apply_pinv<T>(ctx, w, r, z, w.ks, cw);
         if (c.dim == 3) {
@@ -668,7 +668,7 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
           launch_dots<T>(2, d, w.partials, c, w.ks, s);
           launch_finalize<T>(2, w.partials, w.ks, OP_OMEGA, ctx->J, s);
         }
-        launch_r_update<T>(r, t, u, c, w.ks, s, rhat, w.partials);  // (rhat, r), (r, r)
+        launch_r_update<T>(r, t, u, p, c, w.ks, s, rhat, w.partials);  // u += alpha p + omega s; (rhat, r), (r, r)
         launch_finalize<T>(2, w.partials, w.ks, OP_RHO, ctx->J, s);
       }
       st = sync_scalars(ctx, w);

@@ -284,22 +284,21 @@ __global__ void k_p_update(const cplx<T>* __restrict__ r, cplx<T>* __restrict__ 
   }
 }
 
-// s = r - alpha v (in place in r); u += alpha p; partials != nullptr: (s, s) in slot 0.
+// s = r - alpha v (in place in r); partials != nullptr: (s, s) in slot 0.
 template <typename T>
-__global__ void k_s_update(cplx<T>* __restrict__ r, const cplx<T>* __restrict__ v, cplx<T>* __restrict__ u,
-                           const cplx<T>* __restrict__ p_, OpCoef c, const KScal* k, void* partials) {
+__global__ void k_s_update(cplx<T>* __restrict__ r, const cplx<T>* __restrict__ v, OpCoef c, const KScal* k,
+                           void* partials) {
   const int j = blockIdx.y;
   if (!k[j].active) return;
-  prof_add(c, kid_of<T>(KID_S_UPDATE), 12ull * (unsigned long long)c.pts * sizeof(cplx<T>));
+  prof_add(c, kid_of<T>(KID_S_UPDATE), 6ull * (unsigned long long)c.pts * sizeof(cplx<T>));
   const long long n = 2LL * c.pts, o = 2LL * j * c.pts;
   const T ar = (T)k[j].alpha.x, ai = (T)k[j].alpha.y;
   Acc<T> acc;
   acc.zero();
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const cplx<T> vv = v[o + i], pv = p_[o + i], rv = r[o + i], uv = u[o + i];
+    const cplx<T> vv = v[o + i], rv = r[o + i];
     const cplx<T> sv = mkc<T>(rv.x - (ar * vv.x - ai * vv.y), rv.y - (ar * vv.y + ai * vv.x));
     r[o + i] = sv;
-    u[o + i] = mkc<T>(uv.x + (ar * pv.x - ai * pv.y), uv.y + (ar * pv.y + ai * pv.x));
     acc.add(sv, sv);
   }
   if (partials == nullptr) return;
@@ -307,23 +306,37 @@ __global__ void k_s_update(cplx<T>* __restrict__ r, const cplx<T>* __restrict__ 
   if (threadIdx.x == 0) acc.store(partials, (long long)(j * kDotSlots) * kDotBlocks + blockIdx.x);
 }
 
-// u += omega s; r = s - omega t (s held in r); partials != nullptr: (rhat, r), (r, r)
-// in slots 0 and 1.
+// u += alpha p + omega s; r = s - omega t (s held in r); partials != nullptr: (rhat, r),
+// (r, r) in slots 0 and 1.  An amplitude that stopped at the s-check or at omega (not
+// active, just_done) only takes its owed u += alpha p.
 template <typename T>
 __global__ void k_r_update(cplx<T>* __restrict__ r, const cplx<T>* __restrict__ t, cplx<T>* __restrict__ u,
-                           const cplx<T>* __restrict__ rhat, OpCoef c, const KScal* k, void* partials) {
+                           const cplx<T>* __restrict__ p_, const cplx<T>* __restrict__ rhat, OpCoef c,
+                           const KScal* k, void* partials) {
   const int j = blockIdx.y;
-  if (!k[j].active) return;
-  prof_add(c, kid_of<T>(KID_R_UPDATE),
-           (partials != nullptr ? 12ull : 10ull) * (unsigned long long)c.pts * sizeof(cplx<T>));
+  const bool act = k[j].active != 0;
+  if (!act && k[j].just_done == 0) return;
   const long long n = 2LL * c.pts, o = 2LL * j * c.pts;
+  const T ar = (T)k[j].alpha.x, ai = (T)k[j].alpha.y;
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, di = (long long)gridDim.x * blockDim.x;
+  if (!act) {
+    prof_add(c, kid_of<T>(KID_R_UPDATE), 6ull * (unsigned long long)c.pts * sizeof(cplx<T>));
+    for (long long i = i0; i < n; i += di) {
+      const cplx<T> pv = p_[o + i], uv = u[o + i];
+      u[o + i] = mkc<T>(uv.x + (ar * pv.x - ai * pv.y), uv.y + (ar * pv.y + ai * pv.x));
+    }
+    return;
+  }
+  prof_add(c, kid_of<T>(KID_R_UPDATE),
+           (partials != nullptr ? 14ull : 12ull) * (unsigned long long)c.pts * sizeof(cplx<T>));
   const T wr = (T)k[j].omega.x, wi = (T)k[j].omega.y;
   Acc<T> a0, a1;
   a0.zero();
   a1.zero();
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const cplx<T> sv = r[o + i], tv = t[o + i], uv = u[o + i];
-    u[o + i] = mkc<T>(uv.x + (wr * sv.x - wi * sv.y), uv.y + (wr * sv.y + wi * sv.x));
+  for (long long i = i0; i < n; i += di) {
+    const cplx<T> sv = r[o + i], tv = t[o + i], uv = u[o + i], pv = p_[o + i];
+    u[o + i] = mkc<T>(uv.x + (ar * pv.x - ai * pv.y) + (wr * sv.x - wi * sv.y),
+                      uv.y + (ar * pv.y + ai * pv.x) + (wr * sv.y + wi * sv.x));
     const cplx<T> rn = mkc<T>(sv.x - (wr * tv.x - wi * tv.y), sv.y - (wr * tv.y + wi * tv.x));
     r[o + i] = rn;
     if (partials != nullptr) {
@@ -1681,16 +1694,15 @@ void launch_p_update(const cplx<T>* r, cplx<T>* p, const cplx<T>* v, const OpCoe
   k_p_update<T><<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(r, p, v, c, k);
 }
 template <typename T>
-void launch_s_update(cplx<T>* r, const cplx<T>* v, cplx<T>* u, const cplx<T>* p, const OpCoef& c, const KScal* k,
-                     cudaStream_t s, void* partials) {
+void launch_s_update(cplx<T>* r, const cplx<T>* v, const OpCoef& c, const KScal* k, cudaStream_t s, void* partials) {
   ProfScope ps_(kid_of<T>(KID_S_UPDATE), s);
-  k_s_update<T><<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(r, v, u, p, c, k, partials);
+  k_s_update<T><<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(r, v, c, k, partials);
 }
 template <typename T>
-void launch_r_update(cplx<T>* r, const cplx<T>* t, cplx<T>* u, const OpCoef& c, const KScal* k, cudaStream_t s,
-                     const cplx<T>* rhat, void* partials) {
+void launch_r_update(cplx<T>* r, const cplx<T>* t, cplx<T>* u, const cplx<T>* p, const OpCoef& c, const KScal* k,
+                     cudaStream_t s, const cplx<T>* rhat, void* partials) {
   ProfScope ps_(kid_of<T>(KID_R_UPDATE), s);
-  k_r_update<T><<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(r, t, u, rhat, c, k, partials);
+  k_r_update<T><<<dim3(kDotBlocks, c.J), kThreads, 0, s>>>(r, t, u, p, rhat, c, k, partials);
 }
 template <typename T>
 void launch_add_to(const cplx<T>* d, double2* x, const OpCoef& c, cudaStream_t s) {
@@ -1789,10 +1801,9 @@ void launch_rhs_picard(const double2* x, const double2* eta_prev, double2* b, do
                                    cudaStream_t);                                                                   \
   template void launch_p_update<T>(const cplx<T>*, cplx<T>*, const cplx<T>*, const OpCoef&, const KScal*,           \
                                    cudaStream_t);                                                                   \
-  template void launch_s_update<T>(cplx<T>*, const cplx<T>*, cplx<T>*, const cplx<T>*, const OpCoef&, const KScal*, \
-                                   cudaStream_t, void*);                                                            \
-  template void launch_r_update<T>(cplx<T>*, const cplx<T>*, cplx<T>*, const OpCoef&, const KScal*, cudaStream_t,   \
-                                   const cplx<T>*, void*);                                                          \
+  template void launch_s_update<T>(cplx<T>*, const cplx<T>*, const OpCoef&, const KScal*, cudaStream_t, void*);     \
+  template void launch_r_update<T>(cplx<T>*, const cplx<T>*, cplx<T>*, const cplx<T>*, const OpCoef&, const KScal*, \
+                                   cudaStream_t, const cplx<T>*, void*);                                            \
   template void launch_add_to<T>(const cplx<T>*, double2*, const OpCoef&, cudaStream_t);
 
 APFC_INST(double)
