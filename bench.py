@@ -108,11 +108,11 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
-    """Hash of the sources the fused pipeline kernels compile from."""
+def kernel_source_hash(names=("fused2d.cu", "acc.cuh")):
+    """Hash of the sources a kernel compiles from (default: the fused 2D pipeline's)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1902_09761_gb300", "csrc")
-    for name in ("fused2d.cu", "acc.cuh"):
+    for name in names:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -127,7 +127,7 @@ def ncu_traffic(kernel, algorithmic_bytes_per_launch):
         with open(path) as f:
             d = json.load(f)
         e = d[kernel]
-        if e.get("source_hash") != kernel_source_hash():
+        if e.get("source_hash") != kernel_source_hash(tuple(e.get("sources", ("fused2d.cu", "acc.cuh")))):
             return None
         return float(e["dram_over_algorithmic"]) * float(algorithmic_bytes_per_launch)
     except Exception:
@@ -1101,7 +1101,7 @@ def run_bcc(args):
                  "ms_per_step": ms64 / args.fp64_steps, "steps": args.fp64_steps},
         "speedup_fp32_refined_vs_fp64": (ms64 / args.fp64_steps) / (ms / args.steps),
         "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak, "peak_source": peak_src,
-                     "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": ncu_traffic(top, bpl),
                      "algorithmic_bytes_per_launch": bpl, "avg_launch_ms": avg_ms, "launches": per[top]["launches"]},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": eta0.nbytes, "d2h_bytes_per_step": eta0.nbytes},
