@@ -252,8 +252,8 @@ def test_separate_t_kernel_tile_parity(tile_t):
 
 @pytest.mark.parametrize("prec", [A.APFC_FP64, A.APFC_FP32_REFINED])
 def test_bcc_multi_tile_multi_chunk_parity(prec):
-    # 3D grids stream through z in 16-plane chunks over 32 x 8 (x, y) tiles: 40 x 12 x 20
-    # spans two tiles in x and y and two chunks in z, all ragged.
+    # 3D grids stream through z in 64-plane chunks over (x, y) tiles of 32 x 8 (FP64) or
+    # 64 x 8 (FP32) points: 40 x 12 x 20 spans two FP64 tiles in x and two tiles in y, ragged.
     shape, h = (20, 12, 40), (1.0, 1.3, 0.9)
     ctx, L = context("bcc", shape, h)
     x = inputs.random_amplitudes(12, shape, seed=31, scale=1.0).reshape((6, 2) + shape)
@@ -263,3 +263,23 @@ def test_bcc_multi_tile_multi_chunk_parity(prec):
         assert _max_rel(y[j, 0], y1) < 1e-13 and _max_rel(y[j, 1], y2) < 1e-13
     eta0 = inputs.random_amplitudes(6, shape, seed=32, scale=0.1)
     _trajectory_parity("bcc", eta0, shape, h, 2, dt=0.5, tol=1e-13, precision=prec, cheb_degree=2)
+
+
+@pytest.mark.parametrize("m", [1, 2])
+@pytest.mark.parametrize("prec", [A.APFC_FP64, A.APFC_FP32_REFINED])
+def test_bcc_chunks_tiles_odd_width(prec, m):
+    # 67 x 13 x 70: two 64-plane z-chunks (the second ragged), two FP32 / three FP64 tiles in
+    # x and two tiles in y, all ragged; the odd row length puts half of the point pairs of
+    # the FP32 passes off 16-byte alignment (their pointwise operands then arrive as single
+    # 8-byte copies) and leaves a lone last column.  m = 1 folds step 4 of P^-1 into the
+    # first Chebyshev pass, m = 2 into a later one; the inner products come out of the
+    # A passes and the vector updates.
+    shape, h = (70, 13, 67), (1.0, 1.3, 0.9)
+    ctx, L = context("bcc", shape, h, cheb_degree=m)
+    x = inputs.random_amplitudes(12, shape, seed=34, scale=1.0).reshape((6, 2) + shape)
+    y = ctx.apply_operator(0.7, x)
+    for j in range(6):
+        y1, y2 = O.apply_A(x[j, 0], x[j, 1], L.k[j], 0.7, P, h)
+        assert _max_rel(y[j, 0], y1) < 1e-13 and _max_rel(y[j, 1], y2) < 1e-13
+    eta0 = inputs.random_amplitudes(6, shape, seed=33, scale=0.1)
+    _trajectory_parity("bcc", eta0, shape, h, 2, dt=0.5, tol=1e-13, precision=prec, cheb_degree=m)
