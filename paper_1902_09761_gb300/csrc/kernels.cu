@@ -371,11 +371,12 @@ __device__ __forceinline__ double2 cm(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 
-// N_j at one point from amplitudes held in shared memory (column threadIdx.x of se): the
-// triangular closed form, or eta_j sum_m wdiag[j][m] |eta_m|^2 plus the remaining table
-// monomials.  Shared memory keeps the table's run-time amplitude indices off local memory.
-__device__ __forceinline__ double2 nonlin_shared(const double2 (*se)[kThreads], int j, int J, double A2,
-                                                 const NonlinTable& nt) {
+// N_j at one point from amplitudes held in shared memory (column threadIdx.x of se, with
+// |eta_m|^2 in sn): the triangular closed form, or eta_j sum_m wdiag[j][m] |eta_m|^2 plus the
+// remaining table monomials.  Shared memory keeps the table's run-time amplitude indices off
+// local memory; the first factor of a monomial scales its real coefficient.
+__device__ __forceinline__ double2 nonlin_shared(const double2 (*se)[kThreads], const double (*sn)[kThreads], int j,
+                                                 int J, double A2, const NonlinTable& nt) {
   const int t = threadIdx.x;
   const double2 ej = se[j][t];
   if (nt.hex) {
@@ -387,15 +388,15 @@ __device__ __forceinline__ double2 nonlin_shared(const double2 (*se)[kThreads], 
     return make_double2(s * ej.x - 2.0 * nt.t * pr.x, s * ej.y - 2.0 * nt.t * pr.y);
   }
   double w = 0.0;
-  for (int m = 0; m < J; ++m) {
-    const double2 em = se[m][t];
-    w += nt.wdiag[j][m] * (em.x * em.x + em.y * em.y);
-  }
+  for (int m = 0; m < J; ++m) w += nt.wdiag[j][m] * sn[m][t];
   double2 N = make_double2(w * ej.x, w * ej.y);
   for (int i = nt.rstart[j]; i < nt.rstart[j + 1]; ++i) {
     const int q = nt.ridx[i];
-    double2 prod = make_double2(nt.coef[q], 0.0);
-    for (int f = 0; f < nt.nf[q]; ++f) {
+    const int c0 = nt.f[q][0];
+    const double2 e0 = se[c0 >> 1][t];
+    const double cf = nt.coef[q];
+    double2 prod = make_double2(cf * e0.x, (c0 & 1) ? -cf * e0.y : cf * e0.y);
+    for (int f = 1; f < nt.nf[q]; ++f) {
       const int code = nt.f[q][f];
       const double2 e = se[code >> 1][t];
       prod = cm(prod, (code & 1) ? cconj(e) : e);
@@ -404,6 +405,20 @@ __device__ __forceinline__ double2 nonlin_shared(const double2 (*se)[kThreads], 
     N.y += prod.y;
   }
   return N;
+}
+
+// Load the amplitudes of point p into shared memory (se, and |eta_m|^2 into sn); returns A^2.
+__device__ __forceinline__ double load_point(const double2* __restrict__ x, long long pts, long long p, int J,
+                                             double2 (*se)[kThreads], double (*sn)[kThreads]) {
+  double A2 = 0.0;
+  for (int j = 0; j < J; ++j) {
+    const double2 e = x[(2LL * j + 1) * pts + p];
+    se[j][threadIdx.x] = e;
+    const double n2 = e.x * e.x + e.y * e.y;
+    sn[j][threadIdx.x] = n2;
+    A2 += n2;
+  }
+  return 2.0 * A2;
 }
 
 // Batched runs (rg != nullptr): blockIdx.y selects the run.
@@ -420,16 +435,11 @@ __global__ void k_rhs(const double2* __restrict__ x, double2* __restrict__ b, co
     atomicAdd(c.prof + KID_RHS, 2ull * c.J * (unsigned long long)pts * sizeof(double2));
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   __shared__ double2 se[kMaxJ][kThreads];
+  __shared__ double sn[kMaxJ][kThreads];
   if (p >= pts) return;
-  double A2 = 0.0;
+  const double A2 = load_point(x, pts, p, c.J, se, sn);
   for (int j = 0; j < c.J; ++j) {
-    const double2 e = x[(2LL * j + 1) * pts + p];
-    se[j][threadIdx.x] = e;
-    A2 += e.x * e.x + e.y * e.y;
-  }
-  A2 *= 2.0;
-  for (int j = 0; j < c.J; ++j) {
-    const double2 N = nonlin_shared(se, j, c.J, A2, nt);
+    const double2 N = nonlin_shared(se, sn, j, c.J, A2, nt);
     const double2 ej = se[j][threadIdx.x];
     const double kap = c.kap[j];
     b[(2LL * j + 1) * pts + p] = make_double2(ej.x * c.inv_dt - kap * N.x, ej.y * c.inv_dt - kap * N.y);
@@ -590,20 +600,15 @@ __global__ void __launch_bounds__(256) k_rhs_resid(const double2* __restrict__ x
   if (c.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
     atomicAdd(c.prof + KID_RHS, (unsigned long long)c.J * pts * (5 * sizeof(double2) + 2 * sizeof(float2)));
   __shared__ double2 se[kMaxJ][kThreads];
+  __shared__ double sn[kMaxJ][kThreads];
   float accf[2 * kMaxJ];
 #pragma unroll
   for (int i = 0; i < 2 * kMaxJ; ++i) accf[i] = 0.f;
   for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < pts;
        p += (long long)gridDim.x * blockDim.x) {
-    double A2 = 0.0;
+    const double A2 = load_point(x, pts, p, c.J, se, sn);
     for (int j = 0; j < c.J; ++j) {
-      const double2 e = x[(2LL * j + 1) * pts + p];
-      se[j][threadIdx.x] = e;
-      A2 += e.x * e.x + e.y * e.y;
-    }
-    A2 *= 2.0;
-    for (int j = 0; j < c.J; ++j) {
-      const double2 N = nonlin_shared(se, j, c.J, A2, nt);
+      const double2 N = nonlin_shared(se, sn, j, c.J, A2, nt);
       const double2 ej = se[j][threadIdx.x];
       const double kap = c.kap[j];
       const long long q1 = 2LL * j * pts + p, q2 = q1 + pts;
@@ -783,6 +788,7 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 template <typename T, class OP>
 __global__ void __launch_bounds__(256) k_stream3d(OpCoef c, OP op, const KScal* act) {
   constexpr int NS = OP::NS;
+  static_assert(OP::MINB >= 1 && OP::MINB <= 8, "blocks per SM of the two-point kernel");
   constexpr int kTY = tile_rows3<T>(), kHY = kTY + 2, RPT = kTY / 8;
   // plane buffers: z (stencil), z+1 (its z+ neighbour), z+2 .. z+kZAhead (in flight)
   __shared__ cplx<T> tile[NS][kZBuf][kHY][kHX];
