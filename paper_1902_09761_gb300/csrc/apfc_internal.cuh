@@ -253,6 +253,22 @@ struct PcFin {
   CFieldRef<T> b2p;  // beta2'
   FieldRef<T> chi1;  // chi1 (stride 2 pts)
 };
+// 3D grids (stream3d.cu): the passes behind launch_apply_A, launch_residual, launch_pc_rhs,
+// launch_cheb_first / _sweep (fin: step 4 of P^{-1} in this last pass) and launch_zeta.
+template <typename T>
+void launch3d_apply_A(const cplx<T>* x, cplx<T>* y, const OpCoef& c, const KScal* act, cudaStream_t s);
+template <typename T>
+void launch3d_residual(const cplx<T>* b, const cplx<T>* x, cplx<T>* r, cplx<T>* rhat, const OpCoef& c,
+                       cudaStream_t s);
+template <typename T>
+void launch3d_pc_rhs(const cplx<T>* beta, FieldRef<T> f, const OpCoef& c, const KScal* act, cudaStream_t s);
+template <typename T>
+void launch3d_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
+                         const OpCoef& c, const KScal* act, cudaStream_t s, const PcFin<T>* fin);
+template <typename T>
+void launch3d_cheb_sweep(CFieldRef<T> Dd, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
+                         const OpCoef& c, const KScal* act, cudaStream_t s, const PcFin<T>* fin);
+void launch3d_zeta(double2* x, const OpCoef& c, cudaStream_t s);
 // fin != nullptr (3D grids, last pass only): also step 4 of P^{-1}, see PcFin
 template <typename T>
 void launch_cheb_first(CFieldRef<T> f, FieldRef<T> X, FieldRef<T> R, FieldRef<T> Dn, const ChebStep& w, int last,
