@@ -956,7 +956,7 @@ def bcc_config(args):
         "tol": TOL,
         "tol_inner": TOL_INNER,
         "cheb_degree": CHEB,
-        "kernels": "one kernel per stencil pass, z-streaming 32x8 tiles",
+        "kernels": "one kernel per stencil pass, z-streaming (x, y) tiles: FP32 64x8 (two points per thread), FP64 32x8",
         "l2": f"inputs larger than L2 (FP64 state {16 * 12 * n ** 3 / 1e9:.1f} GB); no flush",
     }
 
