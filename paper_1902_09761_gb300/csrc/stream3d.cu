@@ -22,6 +22,7 @@ namespace {
 // ---------------------------------------------------------------------------
 constexpr int kZChunk = 64;
 constexpr int kZBuf = 6, kZAhead = 4;  // plane buffers and planes fetched ahead
+static_assert(kZBuf - kZAhead >= 2, "the passes rely on two spare plane buffers instead of a second barrier");
 constexpr int kTX = 32, kHX = kTX + 2;
 // FP64 passes: 32 x 8 tiles, one point per thread (k_stream3d).  FP32 passes: 64 x 8
 // tiles, two adjacent points per thread (k_stream3d_pair).
@@ -202,7 +203,9 @@ __global__ void __launch_bounds__(256) k_stream3d(OpCoef c, OP op, const KScal* 
     }
 #pragma unroll
     for (int d = 0; d < OP::ND; ++d) acc[d].flush();
-    __syncthreads();  // buffer cb is refilled two planes later
+    // no barrier here: the ring keeps kZBuf - kZAhead = 2 spare planes, so the buffer a thread
+    // refills at plane z + 1 was last read at plane z - 1, which every thread finished before
+    // the barrier of plane z that this thread has passed
     cb = nb;
   }
   asm volatile("cp.async.wait_group 0;\n" ::);
@@ -590,7 +593,9 @@ __global__ void __launch_bounds__(256, OP::MINB) k_stream3d_pair(OpCoef c, OP op
 #pragma unroll
       for (int d = 0; d < OP::ND; ++d) acc[d].flush();
     }
-    __syncthreads();  // buffer cb is refilled two planes later
+    // no barrier here: the ring keeps kZBuf - kZAhead = 2 spare planes, so the buffer a thread
+    // refills at plane z + 1 was last read at plane z - 1, which every thread finished before
+    // the barrier of plane z that this thread has passed
     cb = nb;
     qc = qc + 1 == kQB ? 0 : qc + 1;
   }
