@@ -211,7 +211,8 @@ struct DotPairs {
 };
 
 // ---------------------------------------------------------------------------
-// kernels.cu
+// kernels.cu (per-pass 2D kernels, nonlinear terms, vector updates, diagnostics;
+// their 3D branches and the launch*3d / stream3d_parts entries: stream3d.cu)
 // ---------------------------------------------------------------------------
 template <typename T>
 void launch_apply_A(const cplx<T>* x, cplx<T>* y, const OpCoef& c, const KScal* act, cudaStream_t s);
