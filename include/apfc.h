@@ -137,7 +137,10 @@ apfc_status apfc_uniform_amplitude(const apfc_lattice* lat, const apfc_params* p
  * builds per-amplitude stencil coefficients and the nonlinear-term table, and
  * allocates all device memory it needs (the context owns it).  stream: a
  * cudaStream_t (NULL = legacy default stream) used for every launch.  opts may
- * be NULL (defaults).  Amplitudes start unset (apfc_step returns ESTATE). */
+ * be NULL (defaults).  Amplitudes start unset (apfc_step returns ESTATE).
+ * On failure *ctx is NULL and apfc_last_error(NULL) describes the failure
+ * (per calling thread): EINVAL for arguments, ECUDA without a usable CUDA
+ * device or for a failed CUDA call, ENOMEM when device or host memory runs out. */
 apfc_status apfc_init(apfc_ctx** ctx, const apfc_lattice* lat, const apfc_params* p,
                       const apfc_grid* g, const apfc_opts* opts, void* stream);
 

@@ -217,9 +217,10 @@ def apfc_uniform_amplitude(lattice: Lattice, params: Params) -> float:
     return phi.value
 
 
-def _check(status, ctx=None):
+def _check(status, ctx=None, init=False):
     if status != APFC_OK:
-        msg = load().apfc_last_error(ctx).decode() if ctx else ""
+        # a failed apfc_init has no context: the library keeps this thread's init failure
+        msg = load().apfc_last_error(ctx).decode() if (ctx or init) else ""
         raise ApfcError(status, msg)
 
 
@@ -268,7 +269,7 @@ class Context:
             C.byref(handle), C.byref(self.lattice), C.byref(self.params), C.byref(self.grid), C.byref(self.opts),
             C.c_void_p(stream) if stream else None,
         )
-        _check(st)
+        _check(st, init=True)
         self._h = handle
 
     # -- lifecycle ---------------------------------------------------------

@@ -1109,22 +1109,39 @@ apfc_status apfc_uniform_amplitude(const apfc_lattice* lat, const apfc_params* p
   return APFC_OK;
 }
 
+// Why the last apfc_init of this thread failed (apfc_last_error(NULL)).
+static thread_local std::string g_init_err;
+
+static apfc_status init_fail(apfc_status s, const std::string& msg) {
+  g_init_err = msg;
+  return s;
+}
+
 apfc_status apfc_init(apfc_ctx** out, const apfc_lattice* lat, const apfc_params* p, const apfc_grid* g,
                       const apfc_opts* opts, void* stream) {
-  if (!out || !lat || !p || !g) return APFC_EINVAL;
+  g_init_err.clear();
+  if (!out || !lat || !p || !g) return init_fail(APFC_EINVAL, "null argument");
   *out = nullptr;
-  if (!valid_problem(*lat, *p)) return APFC_EINVAL;
+  if (!valid_problem(*lat, *p)) return init_fail(APFC_EINVAL, "invalid lattice or parameters");
   for (int d = 0; d < lat->dim; ++d)
-    if (g->n[d] < 3 || !(g->h[d] > 0.0) || !std::isfinite(g->h[d])) return APFC_EINVAL;
-  if (lat->dim == 2 && g->n[2] != 1) return APFC_EINVAL;
+    if (g->n[d] < 3 || !(g->h[d] > 0.0) || !std::isfinite(g->h[d]))
+      return init_fail(APFC_EINVAL, "grid sizes must be >= 3 and spacings positive and finite");
+  if (lat->dim == 2 && g->n[2] != 1) return init_fail(APFC_EINVAL, "2D grids take n[2] = 1");
   apfc_opts o;
   apfc_default_opts(&o);
   if (opts) o = *opts;
   std::string e;
-  if (!valid_opts(o, e)) return APFC_EINVAL;
+  if (!valid_opts(o, e)) return init_fail(APFC_EINVAL, "invalid option: " + e);
+  {
+    int ndev = 0;
+    const cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce != cudaSuccess || ndev == 0)
+      return init_fail(APFC_ECUDA, std::string("no CUDA device: ") +
+                                       (ce != cudaSuccess ? cudaGetErrorString(ce) : "device count 0"));
+  }
 
   apfc_ctx* ctx = new (std::nothrow) apfc_ctx();
-  if (!ctx) return APFC_ENOMEM;
+  if (!ctx) return init_fail(APFC_ENOMEM, "host allocation of the context failed");
   ctx->lat = *lat;
   ctx->par = *p;
   ctx->grid = *g;
@@ -1142,24 +1159,35 @@ apfc_status apfc_init(apfc_ctx** out, const apfc_lattice* lat, const apfc_params
   ctx->pts = (long long)g->n[0] * g->n[1] * (lat->dim == 3 ? g->n[2] : 1);
   if (!build_tables(*lat, *p, ctx->nt, ctx->et, e)) {
     delete ctx;
-    return APFC_EINVAL;
+    return init_fail(APFC_EINVAL, "nonlinear-term table: " + e);
   }
-  auto cleanup = [&](apfc_status s) {
+  // an allocation that fails for lack of memory is ENOMEM, any other CUDA failure ECUDA
+  auto check = [&](cudaError_t ce, const char* what) {
+    if (ce == cudaSuccess) return APFC_OK;
+    g_init_err = std::string(what) + ": " + cudaGetErrorString(ce);
     apfc_destroy(ctx);
-    return s;
+    return ce == cudaErrorMemoryAllocation ? APFC_ENOMEM : APFC_ECUDA;
   };
   const size_t blk = sizeof(double2) * 2ull * ctx->J * ctx->pts;
-  if (cudaMalloc(&ctx->x64, blk) != cudaSuccess) return cleanup(APFC_ENOMEM);
-  if (cudaMalloc(&ctx->b64, blk) != cudaSuccess) return cleanup(APFC_ENOMEM);
-  if (cudaMalloc(&ctx->epart, sizeof(double) * kDotBlocks) != cudaSuccess) return cleanup(APFC_ENOMEM);
-  if (cudaMalloc(&ctx->eout, sizeof(double)) != cudaSuccess) return cleanup(APFC_ENOMEM);
-  if (cudaMallocHost(&ctx->eout_host, sizeof(double)) != cudaSuccess) return cleanup(APFC_ENOMEM);
-  if (cudaMalloc(&ctx->ks64, sizeof(KScal) * ctx->J) != cudaSuccess) return cleanup(APFC_ENOMEM);
-  if (cudaMallocHost(&ctx->ks64_host, sizeof(KScal) * ctx->J) != cudaSuccess) return cleanup(APFC_ENOMEM);
-  if (cudaMalloc(&ctx->part64, 16ull * kDotSlots * kDotBlocks * ctx->J) != cudaSuccess) return cleanup(APFC_ENOMEM);
-  if (cudaMemsetAsync(ctx->b64, 0, blk, ctx->stream) != cudaSuccess) return cleanup(APFC_ECUDA);
-  if (cudaMemsetAsync(ctx->ks64, 0, sizeof(KScal) * ctx->J, ctx->stream) != cudaSuccess) return cleanup(APFC_ECUDA);
-  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cleanup(APFC_ECUDA);
+  apfc_status st = APFC_OK;
+  if ((st = check(cudaMalloc(&ctx->x64, blk), "cudaMalloc (state)")) != APFC_OK) return st;
+  if ((st = check(cudaMalloc(&ctx->b64, blk), "cudaMalloc (right-hand side)")) != APFC_OK) return st;
+  if ((st = check(cudaMalloc(&ctx->epart, sizeof(double) * kDotBlocks), "cudaMalloc (energy partials)")) != APFC_OK)
+    return st;
+  if ((st = check(cudaMalloc(&ctx->eout, sizeof(double)), "cudaMalloc (energy)")) != APFC_OK) return st;
+  if ((st = check(cudaMallocHost(&ctx->eout_host, sizeof(double)), "cudaMallocHost (energy)")) != APFC_OK) return st;
+  if ((st = check(cudaMalloc(&ctx->ks64, sizeof(KScal) * ctx->J), "cudaMalloc (Krylov scalars)")) != APFC_OK)
+    return st;
+  if ((st = check(cudaMallocHost(&ctx->ks64_host, sizeof(KScal) * ctx->J), "cudaMallocHost (Krylov scalars)")) !=
+      APFC_OK)
+    return st;
+  if ((st = check(cudaMalloc(&ctx->part64, 16ull * kDotSlots * kDotBlocks * ctx->J), "cudaMalloc (partials)")) !=
+      APFC_OK)
+    return st;
+  if ((st = check(cudaMemsetAsync(ctx->b64, 0, blk, ctx->stream), "cudaMemsetAsync")) != APFC_OK) return st;
+  if ((st = check(cudaMemsetAsync(ctx->ks64, 0, sizeof(KScal) * ctx->J, ctx->stream), "cudaMemsetAsync")) != APFC_OK)
+    return st;
+  if ((st = check(cudaStreamSynchronize(ctx->stream), "cudaStreamSynchronize")) != APFC_OK) return st;
   *out = ctx;
   return APFC_OK;
 }
@@ -1235,7 +1263,10 @@ apfc_status apfc_stats(const apfc_ctx* ctx, apfc_stats_t* out) {
   return APFC_OK;
 }
 
-const char* apfc_last_error(const apfc_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+const char* apfc_last_error(const apfc_ctx* ctx) {
+  if (ctx) return ctx->err.c_str();
+  return g_init_err.empty() ? "null context" : g_init_err.c_str();
+}
 
 void apfc_destroy(apfc_ctx* ctx) {
   if (!ctx) return;

@@ -124,6 +124,24 @@ def test_init_rejects_invalid_arguments_before_touching_cuda(lib, case):
     st = lib.apfc_init(C.byref(h_), C.byref(L), C.byref(prm), C.byref(G), C.byref(opts), None)
     assert st == A.APFC_EINVAL
     assert not h_.value
+    # without a context the failed init explains itself (per thread)
+    msg = lib.apfc_last_error(None).decode()
+    assert msg and msg != "null context", msg
+
+
+def test_init_failure_message_names_the_cause(lib):
+    k = O.hex_k()
+    with pytest.raises(A.ApfcError) as e:
+        A.Context(k, A.APFC_LATTICE_HEX2D, (P.dB, P.Bx, P.t, P.v), (2, 8), (1.0, 1.0))
+    assert e.value.status == A.APFC_EINVAL
+    assert "grid sizes" in str(e.value)
+    import torch
+
+    if not torch.cuda.is_available():
+        # a host without a usable GPU: ECUDA with the reason, never a CPU fallback
+        with pytest.raises(A.ApfcError) as e:
+            A.Context(k, A.APFC_LATTICE_HEX2D, (P.dB, P.Bx, P.t, P.v), (8, 8), (1.0, 1.0))
+        assert e.value.status == A.APFC_ECUDA and "no CUDA device" in str(e.value)
 
 
 def test_binding_fails_loudly_without_library(tmp_path):
