@@ -351,7 +351,9 @@ typedef struct apfc_batch apfc_batch;
  * 3 <= nx[r], ny[r] <= 2^20, opts: precision APFC_FP32_REFINED, fused 1,
  * cheb_degree 1..4; opts NULL = defaults with APFC_FP32_REFINED) and allocate.
  * EINVAL on bad arguments, ETOOBIG if a launch over all runs would exceed the
- * grid limit, ENOMEM if the device memory does not fit. */
+ * grid limit, ENOMEM if the device memory does not fit, ECUDA without a usable
+ * CUDA device.  On failure *b is NULL and apfc_batch_last_error(NULL)
+ * describes the failure (per calling thread). */
 apfc_status apfc_batch_init(apfc_batch** b, const apfc_lattice* lat, const apfc_params* p, int nruns,
                             const int* nx, const int* ny, double hx, double hy, const apfc_opts* opts,
                             int flags, void* stream);

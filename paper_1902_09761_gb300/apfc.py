@@ -224,9 +224,10 @@ def _check(status, ctx=None, init=False):
         raise ApfcError(status, msg)
 
 
-def _check_batch(status, h=None):
+def _check_batch(status, h=None, init=False):
     if status != APFC_OK:
-        msg = load().apfc_batch_last_error(h).decode() if h else ""
+        # a failed apfc_batch_init has no handle: the library keeps this thread's init failure
+        msg = load().apfc_batch_last_error(h).decode() if (h or init) else ""
         raise ApfcError(status, msg)
 
 
@@ -469,7 +470,7 @@ class Batch:
             C.byref(handle), C.byref(self.lattice), C.byref(self.params), self.R, nx, ny, float(h[1]), float(h[0]),
             C.byref(opts), APFC_BATCH_GRAPH if graph else 0, C.c_void_p(stream) if stream else None,
         )
-        _check_batch(st)
+        _check_batch(st, init=True)
         self._h = handle
 
     def close(self):

@@ -421,20 +421,31 @@ apfc_status check_run(apfc_batch* b, int run) {
 
 }  // namespace
 
+// Why the last apfc_batch_init of this thread failed (apfc_batch_last_error(NULL)).
+static thread_local std::string g_batch_init_err;
+
+static apfc_status bfail(apfc_status s, const std::string& msg) {
+  g_batch_init_err = msg;
+  return s;
+}
+
 extern "C" {
 
 apfc_status apfc_batch_init(apfc_batch** out, const apfc_lattice* lat, const apfc_params* p, int nruns, const int* nx,
                             const int* ny, double hx, double hy, const apfc_opts* opts, int flags, void* stream) {
-  if (!out || !lat || !p || !nx || !ny) return APFC_EINVAL;
+  g_batch_init_err.clear();
+  if (!out || !lat || !p || !nx || !ny) return bfail(APFC_EINVAL, "null argument");
   *out = nullptr;
-  if (!valid_problem(*lat, *p) || lat->dim != 2) return APFC_EINVAL;
-  if (nruns < 1 || nruns > kMaxRuns) return APFC_EINVAL;
-  if (!(hx > 0.0) || !(hy > 0.0) || !std::isfinite(hx) || !std::isfinite(hy)) return APFC_EINVAL;
-  if (flags & ~APFC_BATCH_GRAPH) return APFC_EINVAL;
+  if (!valid_problem(*lat, *p) || lat->dim != 2) return bfail(APFC_EINVAL, "invalid lattice or parameters (batches are 2D)");
+  if (nruns < 1 || nruns > kMaxRuns) return bfail(APFC_EINVAL, "run count out of range");
+  if (!(hx > 0.0) || !(hy > 0.0) || !std::isfinite(hx) || !std::isfinite(hy))
+    return bfail(APFC_EINVAL, "spacings must be positive and finite");
+  if (flags & ~APFC_BATCH_GRAPH) return bfail(APFC_EINVAL, "unknown flags");
   long long total = 0;
   int mx = 0, my = 0;
   for (int r = 0; r < nruns; ++r) {
-    if (nx[r] < 3 || ny[r] < 3 || nx[r] > (1 << 20) || ny[r] > (1 << 20)) return APFC_EINVAL;
+    if (nx[r] < 3 || ny[r] < 3 || nx[r] > (1 << 20) || ny[r] > (1 << 20))
+      return bfail(APFC_EINVAL, "run " + std::to_string(r) + ": grid sizes must be in [3, 2^20]");
     total += (long long)nx[r] * ny[r];
     mx = std::max(mx, nx[r]);
     my = std::max(my, ny[r]);
@@ -444,11 +455,18 @@ apfc_status apfc_batch_init(apfc_batch** out, const apfc_lattice* lat, const apf
   o.precision = APFC_FP32_REFINED;
   if (opts) o = *opts;
   std::string e;
-  if (!valid_batch_opts(o, e)) return APFC_EINVAL;
-  if (total * 2LL * lat->J > (1LL << 40)) return APFC_ETOOBIG;
+  if (!valid_batch_opts(o, e)) return bfail(APFC_EINVAL, "invalid option: " + e);
+  if (total * 2LL * lat->J > (1LL << 40)) return bfail(APFC_ETOOBIG, "too many points in the batch");
+  {
+    int ndev = 0;
+    const cudaError_t ce = cudaGetDeviceCount(&ndev);
+    if (ce != cudaSuccess || ndev == 0)
+      return bfail(APFC_ECUDA, std::string("no CUDA device: ") +
+                                   (ce != cudaSuccess ? cudaGetErrorString(ce) : "device count 0"));
+  }
 
   apfc_batch* b = new (std::nothrow) apfc_batch();
-  if (!b) return APFC_ENOMEM;
+  if (!b) return bfail(APFC_ENOMEM, "host allocation of the batch failed");
   b->lat = *lat;
   b->par = *p;
   b->opts = o;
@@ -467,10 +485,18 @@ apfc_status apfc_batch_init(apfc_batch** out, const apfc_lattice* lat, const apf
   b->has_state.assign(nruns, 0);
   b->stats.assign(nruns, apfc_stats_t{});
   auto cleanup = [&](apfc_status s) {
+    if (g_batch_init_err.empty())
+      g_batch_init_err = s == APFC_ENOMEM ? "device allocation failed"
+                         : s == APFC_ECUDA   ? std::string("CUDA call failed: ") + cudaGetErrorString(cudaGetLastError())
+                         : s == APFC_ETOOBIG ? "the batch exceeds the partial-sum table of the fused kernels"
+                                             : "invalid batch";
     free_batch(b);
     return s;
   };
-  if (!build_tables(*lat, *p, b->nt, b->et, e)) return cleanup(APFC_EINVAL);
+  if (!build_tables(*lat, *p, b->nt, b->et, e)) {
+    g_batch_init_err = "nonlinear-term table: " + e;
+    return cleanup(APFC_EINVAL);
+  }
   b->stream = static_cast<cudaStream_t>(stream);
   if ((flags & APFC_BATCH_GRAPH) && b->stream == nullptr) {
     // graph capture needs a stream other than the legacy default one
@@ -689,7 +715,10 @@ apfc_status apfc_batch_get_opts(const apfc_batch* b, apfc_opts* out) {
 
 long long apfc_batch_graph_replays(const apfc_batch* b) { return b ? b->graph_replays : -1; }
 
-const char* apfc_batch_last_error(const apfc_batch* b) { return b ? b->err.c_str() : "null batch"; }
+const char* apfc_batch_last_error(const apfc_batch* b) {
+  if (b) return b->err.c_str();
+  return g_batch_init_err.empty() ? "null batch" : g_batch_init_err.c_str();
+}
 
 void apfc_batch_destroy(apfc_batch* b) {
   if (b) free_batch(b);

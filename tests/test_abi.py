@@ -200,3 +200,16 @@ def test_batch_spec_draws_sizes_and_rotations():
     assert {n for n, _, _ in spec} <= {128, 256, 512, 1024} and len({n for n, _, _ in spec}) == 4
     assert all(-10 <= th <= 10 for _, th, _ in spec)
     assert spec == inputs.batch_spec(64, seed=7)
+
+
+def test_batch_init_failure_message_names_the_cause(lib):
+    k = O.hex_k()
+    with pytest.raises(A.ApfcError) as e:
+        A.Batch(k, A.APFC_LATTICE_HEX2D, (P.dB, P.Bx, P.t, P.v), [(8, 8), (2, 8)], (1.0, 1.0))
+    assert e.value.status == A.APFC_EINVAL and "run 1" in str(e.value)
+    import torch
+
+    if not torch.cuda.is_available():
+        with pytest.raises(A.ApfcError) as e:
+            A.Batch(k, A.APFC_LATTICE_HEX2D, (P.dB, P.Bx, P.t, P.v), [(8, 8)], (1.0, 1.0))
+        assert e.value.status == A.APFC_ECUDA and "no CUDA device" in str(e.value)
