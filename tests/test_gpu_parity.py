@@ -227,6 +227,30 @@ def test_full_size_voronoi_4096_one_step(prec):
     assert ctx.stats()["resid_last"] <= 1e-10
 
 
+@pytest.fixture(scope="module")
+def bcc_256_reference():
+    # the bcc benchmark workload (256^3 sphere) and one oracle step of it (about a minute)
+    phi = O.uniform_solid_bcc(P)
+    eta0 = inputs.bcc_sphere(phi, n=256)
+    ref, _ = O.step(eta0, 1.0, P, O.bcc_lattice(), (np.pi / 2,) * 3)
+    return eta0, ref
+
+
+@pytest.mark.parametrize("prec", [A.APFC_FP64, A.APFC_FP32_REFINED])
+def test_full_size_bcc_256_one_step(prec, bcc_256_reference):
+    # The 3D benchmark workload at the benchmark tolerance 1e-10 in the launch configuration
+    # the benchmark times: error vs the oracle within cond(S) * tol for every amplitude.
+    eta0, ref = bcc_256_reference
+    ctx, L = context("bcc", (256, 256, 256), (np.pi / 2,) * 3, tol=1e-10, precision=prec)
+    ctx.set_amplitudes(eta0)
+    ctx.step(1.0, 1)
+    errs = rel_l2_per_amp(ctx.get_amplitudes(), ref)
+    print(f"bcc 256^3 precision {prec}: rel L2 per amplitude {errs}, stats {ctx.stats()}")
+    assert max(errs) < 2e-9
+    assert ctx.stats()["resid_last"] <= 1e-10
+    ctx.close()
+
+
 @pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("rows", [32, 128])
 def test_tile_variants_parity(tile, rows):
