@@ -175,3 +175,33 @@ def test_batch_status_paths():
         assert b.try_step(1.0) == A.APFC_ENAN
         assert "run 1" in b.last_error()
         assert b.try_step(1.0) == A.APFC_ESTATE  # sticky
+
+
+def test_full_size_batch_64_runs_autotuned():
+    # The batched benchmark workload in its launch configuration: 64 runs with N drawn from
+    # {128, 256, 512, 1024}, tiles picked by the autotuner, Krylov blocks in CUDA graphs.
+    # One run of each size matches the same run alone (same options) bit for bit, and the
+    # smallest of them matches the FP64 oracle within cond(S) * tol.
+    phi = O.uniform_solid_hex(P)
+    spec = inputs.batch_spec(64, (128, 256, 512, 1024), seed=7)
+    states = [inputs.batch_run_state(phi, n, th, sd) for n, th, sd in spec]
+    shapes = [(n, n) for n, _, _ in spec]
+    opts = _opts(tol=1e-10)
+    steps, dt = 2, 1.0
+    with _batch(states, shapes, opts) as b:
+        b.autotune(dt)
+        o = b.opts
+        for r, e in enumerate(states):
+            b.set_amplitudes(r, e)
+        b.step(dt, steps)
+        picks = sorted({n: r for r, (n, _, _) in reversed(list(enumerate(spec)))}.items())
+        got = {r: b.get_amplitudes(r) for _, r in picks}
+        for _, r in picks:
+            assert b.stats(r)["resid_last"] <= 1e-10
+    assert [n for n, _ in picks] == [128, 256, 512, 1024]
+    for n, r in picks:
+        ref = _alone(states[r], shapes[r], steps, dt, o)[-1][0]
+        assert float(np.max(np.abs(got[r] - ref))) == 0.0, (r, n)
+    r = picks[0][1]
+    ref = O.run(states[r], dt, steps, P, O.hex_lattice(), H2)[-1]
+    assert max(rel_l2(got[r][j], ref[j]) for j in range(3)) <= 2e-9
