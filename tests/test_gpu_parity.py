@@ -159,6 +159,37 @@ def test_bcc_uniform_solid_fixed_point():
     assert np.max(np.abs(ctx.get_amplitudes() - phi)) < 1e-15
 
 
+@pytest.mark.parametrize("kind", ["hex", "bcc"])
+@pytest.mark.parametrize("prec", [A.APFC_FP64, A.APFC_FP32_REFINED])
+def test_step_commutes_with_grid_shift_and_displacement_phase(kind, prec):
+    # Periodic shifts and a uniform displacement u (eta_j -> eta_j exp(i k_j.u), which keeps
+    # every resonant monomial) commute with the exact step; the CUDA path, whose tiles,
+    # halos, wraps and reduction order all move with the data, must follow to the solver
+    # tolerance.  Ragged sizes: the shift crosses tile, strip and z-chunk boundaries.
+    if kind == "hex":
+        shape, h, shift = (70, 150), (1.2, 0.8), (17, -41)
+    else:
+        shape, h, shift = (70, 13, 67), (1.0, 1.3, 0.9), (9, 5, -30)
+    ctx, L = context(kind, shape, h, tol=1e-13, precision=prec)
+    axes = tuple(range(1, len(shape) + 1))
+    eta = inputs.random_amplitudes(L.J, shape, seed=41, scale=0.15)
+    rng = np.random.default_rng(42)
+    u = rng.uniform(-3.0, 3.0, size=len(shape))
+    ph = np.exp(1j * (L.k @ u)).reshape((L.J,) + (1,) * len(shape))
+
+    def step(e):
+        ctx.set_amplitudes(e)
+        ctx.step(0.7, 1)
+        return ctx.get_amplitudes()
+
+    base = step(eta)
+    scale = np.max(np.abs(base))
+    moved = step(np.roll(eta, shift, axis=axes))
+    assert np.max(np.abs(moved - np.roll(base, shift, axis=axes))) <= 1e-11 * scale
+    phased = step(eta * ph)
+    assert np.max(np.abs(phased - base * ph)) <= 1e-11 * scale
+
+
 def test_energy_decreases_on_gpu():
     eta0 = inputs.hex_grain_128(O.uniform_solid_hex(P))
     ctx, L = context("hex", (128, 128), H2)
