@@ -310,3 +310,145 @@ def test_chebyshev_preconditioner_tends_to_exact():
         ap = O.apply_Pinv(b[0], b[1], L.k[0], 1.0, P, H2, m)
         errs.append(max(np.abs(ap[0] - ex[0]).max(), np.abs(ap[1] - ex[1]).max()))
     assert errs[-1] < 1e-12 and all(b < a for a, b in zip(errs, errs[1:]))
+
+
+# --- the preconditioner against the paper's P on grid Fourier modes -------------
+#
+# Sec. II.B, Eq. preconditioner with M = I:
+#   P = [[I, 0], [kt G, D]] [[I, -K], [0, D]],   D = (1/sqrt(tau)) I + sqrt(kt) K,
+# where kt = |k_j|^2 Bx is the factor of G in the (2,1) block of A_j and
+# 1/tau = 1/dt + |k_j|^2 dB (tau_mode 'fold') or 1/dt ('plain').  Every block
+# is a translation-invariant stencil, so P acts on the grid mode e^{iq.r} as a
+# 2x2 matrix built from the scalar symbols of K = -L_h and G_h.  The symbols
+# below are the textbook ones of the 2d+1-point Laplacian and of the central
+# difference, and the coefficients come from the paper's formula, so none of
+# ``precond_coeffs``, ``apply_P`` or ``apply_Pinv`` enters the expected values.
+
+
+def _mode_symbols(kj, shape, h):
+    """(kK, g) at the FFT frequencies of ``shape``: K = -L_h and G_h = L_h + 2i k.D_h."""
+    dim = len(h)
+    kK = np.zeros(shape)
+    sk = np.zeros(shape)
+    for d in range(dim):
+        n = shape[dim - 1 - d]
+        q = 2 * np.pi * np.fft.fftfreq(n, d=h[d])
+        view = [1] * dim
+        view[dim - 1 - d] = n
+        q = q.reshape(view)
+        kK = kK + (2.0 - 2.0 * np.cos(q * h[d])) / (h[d] * h[d])
+        sk = sk + kj[d] * np.sin(q * h[d]) / h[d]
+    return kK, -kK - 2.0 * sk
+
+
+def _paper_P_symbol(kj, dt, p, shape, h, tau_mode):
+    kap = float(np.dot(kj, kj))
+    kt = kap * p.Bx
+    inv_tau = 1.0 / dt + (kap * p.dB if tau_mode == "fold" else 0.0)
+    kK, g = _mode_symbols(kj, shape, h)
+    dq = np.sqrt(inv_tau) + np.sqrt(kt) * kK
+    L = np.zeros(shape + (2, 2))
+    L[..., 0, 0] = 1.0
+    L[..., 1, 0] = kt * g
+    L[..., 1, 1] = dq
+    U = np.zeros(shape + (2, 2))
+    U[..., 0, 0] = 1.0
+    U[..., 0, 1] = -kK
+    U[..., 1, 1] = dq
+    return L @ U, dict(kt=kt, sD=np.sqrt(inv_tau), mu=np.sqrt(kt), kK=kK, g=g, dq=dq)
+
+
+def _block_symbol(apply2, shape):
+    """2x2 symbol of a translation-invariant block map: column b is the FFT of
+    its response to a unit impulse in block b (the response to e^{iq.r} is
+    e^{iq.r} times that FFT at q, numpy's sign convention)."""
+    dim = len(shape)
+    delta = np.zeros(shape, dtype=complex)
+    delta[(0,) * dim] = 1.0
+    zero = np.zeros(shape, dtype=complex)
+    S = np.empty(shape + (2, 2), dtype=complex)
+    for b, inp in enumerate(((delta, zero), (zero, delta))):
+        out = apply2(*inp)
+        for a in range(2):
+            S[..., a, b] = np.fft.fftn(out[a])
+    return S
+
+
+# Bx = 0.98 makes kt != sqrt(kt); the second set (dB = 0.3, dt = 0.7) separates
+# the two tau modes and 1/tau from 1/dt.
+_P_CASES = [
+    ("hex", 0, P, 1.0),
+    ("hex", 1, P, 1.0),
+    ("hex", 2, O.Params(dB=0.3, Bx=0.98, t=0.5, v=1 / 3), 0.7),
+    ("bcc", 3, O.Params(dB=0.3, Bx=0.6, t=0.5, v=1 / 3), 0.7),
+]
+
+
+def _case_grid(lat):
+    if lat == "hex":
+        return O.hex_k(), (10, 12), (np.pi / 2, 1.1)
+    return O.bcc_k(), (6, 5, 8), (np.pi / 2, 1.1, 0.9)
+
+
+@pytest.mark.parametrize("tau_mode", ["fold", "plain"])
+@pytest.mark.parametrize("lat,j,p,dt", _P_CASES)
+def test_apply_P_equals_paper_symbol(lat, j, p, dt, tau_mode):
+    ks, shape, h = _case_grid(lat)
+    want, _ = _paper_P_symbol(ks[j], dt, p, shape, h, tau_mode)
+    got = _block_symbol(lambda a, b: O.apply_P(a, b, ks[j], dt, p, h, tau_mode), shape)
+    np.testing.assert_allclose(got, want, atol=1e-12 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("tau_mode", ["fold", "plain"])
+@pytest.mark.parametrize("lat,j,p,dt", _P_CASES)
+def test_apply_Pinv_exact_equals_inverse_of_paper_symbol(lat, j, p, dt, tau_mode):
+    ks, shape, h = _case_grid(lat)
+    Pq, _ = _paper_P_symbol(ks[j], dt, p, shape, h, tau_mode)
+    want = np.linalg.inv(Pq)
+    got = _block_symbol(lambda a, b: O.apply_Pinv(a, b, ks[j], dt, p, h, None, tau_mode), shape)
+    np.testing.assert_allclose(got, want, atol=1e-12 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("m", [0, 1, 3])
+@pytest.mark.parametrize("lat,j,p,dt", _P_CASES[1:])
+def test_apply_Pinv_chebyshev_equals_four_steps_on_symbol(lat, j, p, dt, m):
+    # The four steps of Sec. II.B on one mode, with each diffusion solve D^{-1}
+    # replaced by the degree-m Chebyshev approximant r(d) = (1 - T_{m+1}((th - d)/de)
+    # / T_{m+1}(th/de)) / d on D's interval [sD, sD + sqrt(kt) max kK]:
+    #   b2' = r (b2 - kt g b1),  chi2 = r b2',  chi1 = b1 + (b2' - sD chi2) / sqrt(kt).
+    ks, shape, h = _case_grid(lat)
+    _, c = _paper_P_symbol(ks[j], dt, p, shape, h, "fold")
+    lmin, lmax = c["sD"], c["sD"] + c["mu"] * sum(4.0 / (hd * hd) for hd in h)
+    th, de = 0.5 * (lmax + lmin), 0.5 * (lmax - lmin)
+    T = np.polynomial.chebyshev.Chebyshev.basis(m + 1)
+    r = (1.0 - T((th - c["dq"]) / de) / T(th / de)) / c["dq"]
+    want = np.empty(shape + (2, 2), dtype=complex)
+    for b, (b1, b2) in enumerate(((1.0, 0.0), (0.0, 1.0))):
+        b2p = r * (b2 - c["kt"] * c["g"] * b1)
+        chi2 = r * b2p
+        want[..., 0, b] = b1 + (b2p - c["sD"] * chi2) / c["mu"]
+        want[..., 1, b] = chi2
+    got = _block_symbol(lambda a, b: O.apply_Pinv(a, b, ks[j], dt, p, h, m, "fold"), shape)
+    np.testing.assert_allclose(got, want, atol=1e-12 * np.abs(want).max())
+
+
+@pytest.mark.parametrize(
+    "j,tau_mode,lo,hi",
+    [(0, "plain", 0.1252, 1.956), (2, "plain", 0.1252, 1.956), (1, "plain", 0.166, 1.694),
+     (0, "fold", 0.1244, 1.935), (2, "fold", 0.1244, 1.935)],
+)
+def test_discrete_preconditioned_spectrum(j, tau_mode, lo, hi):
+    # Discrete counterpart of the paper's spectrum analysis (Sec. II.B): the
+    # eigenvalues of A_j(q) P_j(q)^{-1} for the hex k_j at h = pi/2, dt = 1,
+    # exact inner solves, over the frequencies of a 128^2 grid.  The interval
+    # ends are those of the 2x2 symbols of the discrete operators over the whole
+    # Brillouin zone (P(q) as in Eq. preconditioner, A(q) = [[1, -g], [kt g, a]]),
+    # rounded to 4 digits; the spectrum is real and positive.
+    k = O.hex_k()[j]
+    shape, h, dt = (128, 128), H2, 1.0
+    A = _block_symbol(lambda a, b: O.apply_A(a, b, k, dt, P, h), shape)
+    Pinv = _block_symbol(lambda a, b: O.apply_Pinv(a, b, k, dt, P, h, None, tau_mode), shape)
+    ev = np.linalg.eigvals(A @ Pinv)
+    assert np.abs(ev.imag).max() < 1e-9
+    assert ev.real.min() == pytest.approx(lo, abs=5e-4)
+    assert ev.real.max() == pytest.approx(hi, abs=5e-4)
