@@ -201,18 +201,27 @@ apfc_status apfc_nonlinear_rhs(apfc_ctx* ctx, double dt, const void* eta, void* 
  * framework that owns the allocator, a latency-critical path where cudaMalloc
  * would synchronise the device, a plugin handed buffers and a stream only).
  *
- * x = P_j^{-1} b for every amplitude, computed exactly as apfc_apply_preconditioner
- * computes it (same kernels, same Chebyshev polynomial of degree cheb_degree,
- * same tau_mode), but with no context: the caller passes lattice, parameters,
- * grid, dt, and DEVICE buffers b and x (block vectors [J][2][pts] complex128,
- * not aliased).  The five intermediate fields live in one file-scope device
- * array of 5 * APFC_STATIC_MAX_DOF complex128 (20 MB) that every GPU which
- * loads the library holds until the process exits; the call performs no
- * cudaMalloc/cudaFree and calls no allocating library routine.
+ * x = P_j^{-1} b for every amplitude: the same operator as
+ * apfc_apply_preconditioner (same coefficients, same Chebyshev polynomial of
+ * degree cheb_degree, same tau_mode), computed with the unfused FP64 per-pass
+ * kernels, so the two agree to rounding (not bit for bit: the context path may
+ * run the fused 2D pipeline or fold step 4 into the last 3D pass).  There is no
+ * context: the caller passes lattice, parameters, grid, dt, and DEVICE buffers
+ * b and x (block vectors [J][2][pts] complex128).  The five intermediate fields
+ * live in one file-scope device array of 5 * APFC_STATIC_MAX_DOF complex128
+ * (20 MB) that every GPU which loads the library holds until the process
+ * exits; the call performs no cudaMalloc/cudaFree and calls no allocating
+ * library routine.
  *
  * Limits and behaviour:
  *  - J * nx * ny * nz must be <= APFC_STATIC_MAX_DOF, else APFC_ETOOBIG
- *    (nothing is launched); other bad arguments give APFC_EINVAL.
+ *    (nothing is launched).  Bad arguments give APFC_EINVAL (nothing is
+ *    launched): the lattice, parameters, grid and dt checks of apfc_init and
+ *    of a step, and b and x overlapping (the last pass reads b while it writes
+ *    x, so the call cannot work in place).
+ *  - A CUDA error left pending by the caller's earlier work makes the call
+ *    return APFC_ECUDA without launching and without clearing that error;
+ *    otherwise APFC_ECUDA reports a failed launch of this call.
  *  - The first call on a device resolves the array's device address with
  *    cudaGetSymbolAddress (with that device current); make that first call
  *    before any stream capture.  stream must belong to the current device.

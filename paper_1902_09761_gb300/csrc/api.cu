@@ -293,12 +293,9 @@ void free_work(Work<T>& w) {
 // ---------------------------------------------------------------------------
 // Operator coefficients for a time step dt
 // ---------------------------------------------------------------------------
-bool apfc::make_coef(const apfc_lattice& lat, const apfc_params& par, const apfc_grid& grid, int tau_mode, double dt,
-                     OpCoef& o, std::string& err) {
-  if (!(dt > 0.0) || !std::isfinite(dt)) {
-    err = "dt must be positive and finite";
-    return false;
-  }
+const char* apfc::make_coef_into(const apfc_lattice& lat, const apfc_params& par, const apfc_grid& grid,
+                                 int tau_mode, double dt, OpCoef& o) {
+  if (!(dt > 0.0) || !std::isfinite(dt)) return "dt must be positive and finite";
   unsigned long long* prof = o.prof;
   std::memset(&o, 0, sizeof(o));
   o.prof = prof;
@@ -327,21 +324,31 @@ bool apfc::make_coef(const apfc_lattice& lat, const apfc_params& par, const apfc
     o.kt[j] = kap * par.Bx;
     o.a[j] = 1.0 / dt + kap * par.dB;
     const double inv_tau = 1.0 / dt + (tau_mode == APFC_TAU_FOLD ? kap * par.dB : 0.0);
-    if (!(o.a[j] > 0.0) || !(inv_tau > 0.0) || !(o.kt[j] > 0.0)) {
-      err = "need 1/dt + |k_j|^2 dB > 0 and |k_j|^2 Bx > 0";
-      return false;
-    }
+    if (!(o.a[j] > 0.0) || !(inv_tau > 0.0) || !(o.kt[j] > 0.0)) return "need 1/dt + |k_j|^2 dB > 0 and |k_j|^2 Bx > 0";
     o.sD[j] = std::sqrt(inv_tau);
     o.mu[j] = std::sqrt(o.kt[j]);
     o.inv_mu[j] = 1.0 / o.mu[j];
     const double lmin = o.sD[j], lmax = o.sD[j] + o.mu[j] * lapmax;
     o.inv_theta[j] = 2.0 / (lmax + lmin);
   }
-  return true;
+  return nullptr;
+}
+
+bool apfc::make_coef(const apfc_lattice& lat, const apfc_params& par, const apfc_grid& grid, int tau_mode, double dt,
+                     OpCoef& o, std::string& err) {
+  const char* e = make_coef_into(lat, par, grid, tau_mode, dt, o);
+  if (e) err = e;
+  return e == nullptr;
 }
 
 std::vector<ChebStep> apfc::cheb_weights_for(const OpCoef& c, const apfc_grid& grid, int m) {
   std::vector<ChebStep> w(std::max(m, 1));
+  cheb_weights_into(c, grid, m, w.data());
+  return w;
+}
+
+void apfc::cheb_weights_into(const OpCoef& c, const apfc_grid& grid, int m, ChebStep* w) {
+  std::memset(w, 0, sizeof(ChebStep) * std::max(m, 1));
   double lapmax = 0.0;
   for (int d = 0; d < c.dim; ++d) lapmax += 4.0 / (grid.h[d] * grid.h[d]);
   for (int j = 0; j < c.J; ++j) {
@@ -355,7 +362,6 @@ std::vector<ChebStep> apfc::cheb_weights_for(const OpCoef& c, const apfc_grid& g
       rho = rn;
     }
   }
-  return w;
 }
 
 namespace {

@@ -19,12 +19,18 @@ bool valid_opts(const apfc_opts& o, std::string& err);
 bool build_tables(const apfc_lattice& L, const apfc_params& P, NonlinTable& nt, EnergyTable& et, std::string& err);
 
 // Operator coefficients of the block system for a time step dt on grid (n, h).
+// make_coef_into returns nullptr on success, else a static message; it
+// allocates nothing.
+const char* make_coef_into(const apfc_lattice& lat, const apfc_params& par, const apfc_grid& grid, int tau_mode,
+                           double dt, OpCoef& o);
 bool make_coef(const apfc_lattice& lat, const apfc_params& par, const apfc_grid& grid, int tau_mode, double dt,
                OpCoef& o, std::string& err);
 
 // Chebyshev recurrence weights for m applications of D (Saad, Sec. 12.3); they
-// depend on the spacing only, not on the grid size.
+// depend on the spacing only, not on the grid size.  cheb_weights_into fills
+// max(m, 1) entries of w (zeroed first) and allocates nothing.
 std::vector<ChebStep> cheb_weights_for(const OpCoef& c, const apfc_grid& grid, int m);
+void cheb_weights_into(const OpCoef& c, const apfc_grid& grid, int m, ChebStep* w);
 
 // Measurement (see apfc_profile_start): dev receives the device byte counters.
 bool profiler_start(cudaStream_t s, int timed_id, unsigned long long** dev, std::string& err);

@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "apfc_internal.cuh"
+#include "host_common.h"
 
 using namespace apfc;
 
@@ -52,60 +53,30 @@ extern "C" apfc_status apfc_apply_preconditioner_static(const apfc_lattice* lat,
                                                         const apfc_grid* g, int cheb_degree, int tau_mode, double dt,
                                                         const void* b, void* x, void* stream) {
   if (!lat || !prm || !g || !b || !x) return APFC_EINVAL;
-  if ((lat->dim != 2 && lat->dim != 3) || lat->J < 1 || lat->J > kMaxJ) return APFC_EINVAL;
+  if (!valid_problem(*lat, *prm)) return APFC_EINVAL;
   if (cheb_degree < 0 || cheb_degree > kMaxCheb) return APFC_EINVAL;
   if (tau_mode != APFC_TAU_FOLD && tau_mode != APFC_TAU_PLAIN) return APFC_EINVAL;
-  if (!(dt > 0.0) || !std::isfinite(dt) || !(prm->Bx > 0.0) || !std::isfinite(prm->dB)) return APFC_EINVAL;
   for (int d = 0; d < lat->dim; ++d)
     if (g->n[d] < 3 || !(g->h[d] > 0.0) || !std::isfinite(g->h[d])) return APFC_EINVAL;
   if (lat->dim == 2 && g->n[2] != 1) return APFC_EINVAL;
   const long long pts = (long long)g->n[0] * g->n[1] * (lat->dim == 3 ? g->n[2] : 1);
   if (pts * lat->J > kStaticMaxDof) return APFC_ETOOBIG;
+  // b and x must not overlap: the last pass reads beta while it writes chi.
+  const unsigned long long bytes = (unsigned long long)lat->J * 2 * pts * sizeof(double2);
+  const unsigned long long pb = reinterpret_cast<unsigned long long>(b), px = reinterpret_cast<unsigned long long>(x);
+  if (pb < px + bytes && px < pb + bytes) return APFC_EINVAL;
 
-  // Operator coefficients (same definitions as the context path).
+  // Operator coefficients and Chebyshev weights: the builders the context uses
+  // (they write into the caller's stack and allocate nothing).
   OpCoef c;
   std::memset(&c, 0, sizeof(c));
-  c.J = lat->J;
-  c.dim = lat->dim;
-  c.nx = g->n[0];
-  c.ny = g->n[1];
-  c.nz = lat->dim == 3 ? g->n[2] : 1;
-  c.pts = pts;
-  double lapmax = 0.0;
-  for (int d = 0; d < lat->dim; ++d) {
-    c.ih2[d] = 1.0 / (g->h[d] * g->h[d]);
-    c.c0 -= 2.0 / (g->h[d] * g->h[d]);
-    lapmax += 4.0 / (g->h[d] * g->h[d]);
-  }
-  c.inv_dt = 1.0 / dt;
+  if (make_coef_into(*lat, *prm, *g, tau_mode, dt, c) != nullptr) return APFC_EINVAL;
   ChebStep w[kMaxCheb > 0 ? kMaxCheb : 1];
-  std::memset(w, 0, sizeof(w));
-  for (int j = 0; j < lat->J; ++j) {
-    double kap = 0.0;
-    for (int d = 0; d < lat->dim; ++d) {
-      c.kh[j][d] = lat->k[j][d] / g->h[d];
-      kap += lat->k[j][d] * lat->k[j][d];
-    }
-    c.kap[j] = kap;
-    c.kt[j] = kap * prm->Bx;
-    c.a[j] = 1.0 / dt + kap * prm->dB;
-    const double inv_tau = 1.0 / dt + (tau_mode == APFC_TAU_FOLD ? kap * prm->dB : 0.0);
-    if (!(inv_tau > 0.0) || !(c.kt[j] > 0.0)) return APFC_EINVAL;
-    c.sD[j] = std::sqrt(inv_tau);
-    c.mu[j] = std::sqrt(c.kt[j]);
-    c.inv_mu[j] = 1.0 / c.mu[j];
-    const double lmin = c.sD[j], lmax = c.sD[j] + c.mu[j] * lapmax;
-    const double theta = 0.5 * (lmax + lmin), delta = 0.5 * (lmax - lmin), sigma = theta / delta;
-    c.inv_theta[j] = 1.0 / theta;
-    double rho = 1.0 / sigma;
-    for (int k = 0; k < cheb_degree; ++k) {
-      const double rn = 1.0 / (2.0 * sigma - rho);
-      w[k].c1[j] = rn * rho;
-      w[k].c2[j] = 2.0 * rn / delta;
-      rho = rn;
-    }
-  }
+  cheb_weights_into(c, *g, cheb_degree, w);
 
+  // A CUDA error that the caller's own work left pending is not ours to report
+  // or to clear: refuse to launch rather than consume it below.
+  if (cudaPeekAtLastError() != cudaSuccess) return APFC_ECUDA;
   double2* scratch = nullptr;
   apfc_status st = scratch_on_current_device(&scratch);
   if (st != APFC_OK) return st;
@@ -133,5 +104,7 @@ extern "C" apfc_status apfc_apply_preconditioner_static(const apfc_lattice* lat,
   cheb(CFieldRef<double>{f.p, pts}, b2p);
   cheb(CFieldRef<double>{b2p.p, pts}, chi2);
   launch_pc_final<double>(beta, CFieldRef<double>{b2p.p, pts}, chi, c, nullptr, s);
+  // No error was pending before the launches, so whatever is pending now came
+  // from them.
   return cudaGetLastError() == cudaSuccess ? APFC_OK : APFC_ECUDA;
 }

@@ -158,7 +158,8 @@ def _fd_check(shape, n, every, prec, tol, ndir, bound, seed, h_fd=1e-6, phi_stat
 
 
 def test_autograd_matches_central_differences_small():
-    _fd_check((48, 64), 10, 4, A.APFC_FP64, 1e-13, 8, 5e-5, seed=20)
+    worst, err_dB, _ = _fd_check((48, 64), 10, 4, A.APFC_FP64, 1e-13, 8, 5e-5, seed=20)
+    print(f"48x64 x 10 steps: worst directional rel err {worst:.2e}, dB rel err {err_dB:.2e}")
 
 
 def test_autograd_complex64_input_gives_complex64_gradient():

@@ -198,10 +198,14 @@ def test_full_size_batch_64_runs_autotuned():
         got = {r: b.get_amplitudes(r) for _, r in picks}
         for _, r in picks:
             assert b.stats(r)["resid_last"] <= 1e-10
+        b_resid = b.stats(picks[0][1])["resid_last"]
     assert [n for n, _ in picks] == [128, 256, 512, 1024]
     for n, r in picks:
         ref = _alone(states[r], shapes[r], steps, dt, o)[-1][0]
         assert float(np.max(np.abs(got[r] - ref))) == 0.0, (r, n)
     r = picks[0][1]
     ref = O.run(states[r], dt, steps, P, O.hex_lattice(), H2)[-1]
-    assert max(rel_l2(got[r][j], ref[j]) for j in range(3)) <= 2e-9
+    errs = [rel_l2(got[r][j], ref[j]) for j in range(3)]
+    print(f"batch 64 runs: smallest run ({picks[0][0]}^2) rel L2 per amplitude vs oracle {errs}, "
+          f"resid {b_resid}")
+    assert max(errs) <= 2e-9
