@@ -258,6 +258,15 @@ apfc_status apfc_profile_read(apfc_ctx* ctx, int id, double* ms, long long* laun
                               long long* all_launches);
 apfc_status apfc_profile_stop(apfc_ctx* ctx);
 
+/* FMA throughput of the current device, for the arithmetic roofline of the FP64
+ * kernels (the paper has no counterpart; it reports no GPU rates).
+ * precision APFC_FP64 times FP64 FMAs, APFC_FP32_REFINED FP32 FMAs: independent
+ * FMA chains on 8 blocks of 256 threads per SM, best of three launches timed
+ * with CUDA events on stream (NULL = legacy default stream); *flops = 2 x FMAs /
+ * seconds.  Allocates and frees a small device buffer; synchronises the stream.
+ * EINVAL for another precision or a NULL output, ECUDA / ENOMEM on failure. */
+apfc_status apfc_measure_fma_rate(int precision, void* stream, double* flops);
+
 /* ---- parameters and the adjoint of the step ---------------------------------
  * Gradient convention: for a real loss L of complex fields, the gradient with
  * respect to a field eta is the complex field dL/dRe(eta) + i dL/dIm(eta) (twice

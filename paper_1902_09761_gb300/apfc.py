@@ -110,6 +110,7 @@ EXPORTS = {
          C.POINTER(C.c_longlong)],
     ),
     "apfc_profile_stop": (C.c_int, [C.c_void_p]),
+    "apfc_measure_fma_rate": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(C.c_double)]),
     "apfc_apply_preconditioner_static": (
         C.c_int,
         [C.POINTER(Lattice), C.POINTER(Params), C.POINTER(Grid), C.c_int, C.c_int, C.c_double, C.c_void_p,
@@ -556,6 +557,13 @@ class Batch:
 
     def profile_stop(self):
         _check_batch(load().apfc_batch_profile_stop(self._h), self._h)
+
+
+def measure_fma_rate(precision: int, stream: int | None = None) -> float:
+    """FMA throughput of the current GPU in FLOP/s (2 per FMA), FP64 (APFC_FP64) or FP32 (APFC_FP32_REFINED)."""
+    out = C.c_double()
+    _check(load().apfc_measure_fma_rate(int(precision), C.c_void_p(stream) if stream else None, C.byref(out)))
+    return out.value
 
 
 def kernel_ids() -> dict:
