@@ -74,6 +74,10 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="batch: launch the Krylov blocks without graphs")
     ap.add_argument("--no-autotune", action="store_true", help="batch: keep --tile / --rows")
     ap.add_argument("--alone-steps", type=int, default=4, help="batch: steps of each run alone (0: skip)")
+    ap.add_argument("--sub-steps", type=int, default=10,
+                    help="default run: timed steps of the bcc3d and batch sub-records (0: no sub-records)")
+    ap.add_argument("--oracle-workers", type=int, default=0,
+                    help="host processes of the oracle legs (0: one per core, as memory allows)")
     return ap.parse_args()
 
 
@@ -106,6 +110,27 @@ def measured_peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+# FP64-pipe instructions per amplitude value (DOF) of the FP64 kernels of the 2D hexagonal
+# FP32-refined step, counted from their source: (FP64 arithmetic, FP64 <-> FP32 conversions).
+#   residual_refine_f64 (k_residual_refine2d): two complex G_h stencils of 18 (4 neighbour
+#     sums/differences, 1 multiply and 4 FMAs per component), r1 4, r2 6; 4 conversions.
+#   rhs_f64 (k_rhs_resid, closed-form triangular N_j): per point 10 for A^2, per amplitude
+#     13 for N_j, 4 for eta/dt - kap N, 4 for the initial residual; 6 conversions per amplitude.
+FP64_PIPE_OPS = {"residual_refine_f64": (46.0, 4.0), "rhs_f64": ((10.0 + 3 * 21.0) / 3.0, 6.0)}
+
+
+def fp64_roofline(name, dof, rec, hbm_peak, alu):
+    """Roofline of an FP64 kernel: the larger of its FP64-pipe time (FMA-rate and conversion-rate
+    bound of its instruction count) and its HBM time, as a fraction of its measured time."""
+    n_ops, n_cvt = FP64_PIPE_OPS[name]
+    per_launch_ms = rec["ms"] / rec["launches"]
+    alu_ms = 1e3 * dof * (n_ops / (alu["fp64_fma_tflops"] * 1e12 / 2) + n_cvt / (alu["fp64_cvt_tops"] * 1e12))
+    hbm_ms = 1e3 * (rec["bytes"] / rec["launches"]) / (hbm_peak * 1e9)
+    bound = "alu" if alu_ms >= hbm_ms else "hbm"
+    return {"bound": bound, "fp64_ops_per_dof": n_ops, "cvt_per_dof": n_cvt, "alu_bound_ms": alu_ms,
+            "hbm_bound_ms": hbm_ms, "ms_per_launch": per_launch_ms, "frac": max(alu_ms, hbm_ms) / per_launch_ms}
 
 
 def kernel_source_hash(names=("fused2d.cu", "acc.cuh")):
@@ -225,32 +250,121 @@ def allmax(world, value, device=None):
 # ---------------------------------------------------------------------------
 
 
-def oracle_rate(n, steps, warmup=0):
-    """Time the oracle's step on an n x n sample of the workload; DOF-steps/s."""
+# Peak resident bytes per grid point of one oracle step (measured on the GPU machine:
+# 4.6 GB at 4096^2 hex, 8.5 GB at 256^3 bcc), used to size the host process pool.
+ORACLE_BYTES_PER_POINT = {"hex": 300, "bcc": 550}
+ORACLE_TIMEOUT_S = 1800
+
+
+def host_cores():
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+def _mem_available():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) * 1024
+    except Exception:
+        pass
+    return None
+
+
+def oracle_workers(kind, n, requested=0):
+    """One oracle process per host core, as many as 60% of the available memory holds."""
+    w = requested if requested > 0 else host_cores()
+    mem = _mem_available()
+    pts = n ** (2 if kind == "hex" else 3)
+    if mem:
+        w = min(w, max(1, int(0.6 * mem // (ORACLE_BYTES_PER_POINT[kind] * pts))))
+    return max(1, w)
+
+
+def _oracle_input(kind, n):
     import oracle as O
     from paper_1902_09761_gb300 import inputs
 
     P = O.params_from_paper(0.98, 0.01, 0.25, 0.5)
-    L = O.hex_lattice()
-    eta = inputs.hex_voronoi(O.uniform_solid_hex(P), n=n)
-    for _ in range(warmup):
-        eta, _ = O.step(eta, 1.0, P, L, (H, H))
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        eta, _ = O.step(eta, 1.0, P, L, (H, H))
-    dt = time.perf_counter() - t0
-    return 3.0 * n * n * steps / dt, dt
+    if kind == "hex":
+        return inputs.hex_voronoi(O.uniform_solid_hex(P), n=n), O.hex_lattice(), (H, H), P
+    return inputs.bcc_sphere(O.uniform_solid_bcc(P), n=n), O.bcc_lattice(), (H, H, H), P
+
+
+def _oracle_replica(idx, kind, n, steps, warmup, barrier, queue, save_dir):
+    """One host process: `warmup` untimed and `steps` timed oracle steps of its own replica."""
+    try:
+        import oracle as O
+
+        eta, L, h, P = _oracle_input(kind, n)
+        zeta = None
+        for _ in range(warmup):
+            eta, zeta = O.step(eta, 1.0, P, L, h)
+        barrier.wait()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            eta, zeta = O.step(eta, 1.0, P, L, h)
+        secs = time.perf_counter() - t0
+        if save_dir is not None and idx == 0:
+            np.save(os.path.join(save_dir, "eta.npy"), eta)
+            np.save(os.path.join(save_dir, "zeta.npy"), zeta)
+        queue.put((idx, secs, None))
+    except Exception as e:  # reported to the parent, which raises
+        try:
+            barrier.abort()
+        except Exception:
+            pass
+        queue.put((idx, None, repr(e)))
+
+
+def oracle_on_host(kind, n, steps, warmup=0, workers=0, save_dir=None):
+    """The oracle on the host cores: `workers` spawned processes (one per core), each stepping
+    its own replica of the n^d workload; a barrier aligns the timed regions.  Returns
+    (DOF-steps/s over all replicas, seconds of the slowest replica, workers).  Replica 0
+    saves its final (eta, zeta) under save_dir.  Spawned (not forked) processes are safe
+    after CUDA has been initialised in this one."""
+    import multiprocessing as mp
+    import queue as Q
+
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(k, "1")
+    w = oracle_workers(kind, n, workers)
+    mpc = mp.get_context("spawn")
+    bar = mpc.Barrier(w)
+    q = mpc.Queue()
+    procs = [mpc.Process(target=_oracle_replica, args=(i, kind, n, steps, warmup, bar, q, save_dir), daemon=True)
+             for i in range(w)]
+    for p in procs:
+        p.start()
+    res = []
+    try:
+        for _ in range(w):
+            res.append(q.get(timeout=ORACLE_TIMEOUT_S))
+    except Q.Empty:
+        raise RuntimeError("oracle host process timed out or died")
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.terminate()
+    errs = [e for _, _, e in res if e]
+    if errs:
+        raise RuntimeError("oracle host process failed: " + errs[0])
+    secs = max(t for _, t, _ in res)
+    J = 3 if kind == "hex" else 6
+    return w * J * n ** (2 if kind == "hex" else 3) * steps / secs, secs, w
 
 
 def run_reference(args):
     world, rank, local = init_dist(args)
     if rank != 0:
         return
-    n_sample = min(args.size, 2048)
-    rate, secs = oracle_rate(n_sample, args.steps, args.warmup)
+    n = args.size
+    rate, secs, w = oracle_on_host("hex", n, args.steps, args.warmup, args.oracle_workers)
     sample = (
-        f"oracle FP64 step (numpy, exact FFT Schur solve) on a {n_sample}x{n_sample} sample of the workload, "
-        f"{args.steps} timed steps after {args.warmup} warm-up"
+        f"{w} host processes (one per core), each stepping its own replica of the full {n}x{n} workload "
+        f"with the FP64 oracle (numpy, exact FFT Schur solve): {args.steps} timed steps after {args.warmup} "
+        f"warm-up, {secs:.1f} s for the slowest replica"
     )
     line = {
         "impl": "reference",
@@ -266,11 +380,18 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": workload_config(args.size, f"timed on a {n_sample}^2 sample"),
-        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "config": workload_config(n),
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": w, "kind": "oracle", "sample": sample},
         "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def rel_l2_fields(eta, zeta, o_eta, o_zeta):
+    """Relative L2 error per field (eta_j and zeta_j) against the oracle's result."""
+    f = lambda a, b: float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))  # noqa: E731
+    return {"eta": [f(eta[j], o_eta[j]) for j in range(eta.shape[0])],
+            "zeta": [f(zeta[j], o_zeta[j]) for j in range(zeta.shape[0])]}
 
 
 # ---------------------------------------------------------------------------
@@ -340,6 +461,15 @@ def run_ours(args):
     achieved = bytes_per_launch / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else None
     traffic = ncu_traffic(args.timed_kernel, bytes_per_launch)
 
+    # --- arithmetic peaks of this GPU (FP64 / FP32 FMA, FP64 <-> FP32 conversions) ----
+    alu = {
+        "fp64_fma_tflops": A.measure_alu_rate(A.APFC_ALU_FMA64, stream.cuda_stream) / 1e12,
+        "fp32_fma_tflops": A.measure_alu_rate(A.APFC_ALU_FMA32, stream.cuda_stream) / 1e12,
+        "fp64_cvt_tops": A.measure_alu_rate(A.APFC_ALU_CVT64, stream.cuda_stream) / 1e12,
+        "how": "independent FMA / conversion chains, 8 blocks of 256 threads per SM, best of 3 launches "
+               "(apfc_measure_alu_rate)",
+    }
+
     # --- per-kernel breakdown: every launch bracketed by events (separate pass) ----
     breakdown = None
     if args.breakdown_steps > 0:
@@ -363,6 +493,8 @@ def run_ours(args):
                     "launches_per_step": r["launches"] / args.breakdown_steps,
                     "gbs": (r["bytes"] / (r["ms"] * 1e-3) / 1e9) if r["ms"] > 0 else None,
                 }
+                if name in FP64_PIPE_OPS and r["ms"] > 0:
+                    per[name]["roofline"] = fp64_roofline(name, dof, r, peak, alu)
         ctx.profile_stop()
         breakdown = {
             "ms_per_step_wall": wall,
@@ -371,8 +503,9 @@ def run_ours(args):
         }
 
     # --- plain FP64 path at the same final residual ------------------------------
-    ctx.set_opts(A.apfc_default_opts(precision=A.APFC_FP64, tol=TOL, cheb_degree=args.cheb, tile_rows=args.rows,
-                                     picard_iters=args.picard, jacobian=int(args.jacobian)))
+    opts64 = A.apfc_default_opts(precision=A.APFC_FP64, tol=TOL, cheb_degree=args.cheb, tile_rows=args.rows,
+                                 picard_iters=args.picard, jacobian=int(args.jacobian))
+    ctx.set_opts(opts64)
     ms64, _ = timed_steps(args.fp64_steps)
     st64 = ctx.stats()
     value64 = world * dof * args.fp64_steps / (ms64 * 1e-3)
@@ -424,20 +557,52 @@ def run_ours(args):
         "wall_ms_per_call": r0.elapsed_time(r1) / reps,
     }
 
-    # --- CPU baseline: the oracle on this host's cores (rank 0, N = 1 only) -----
-    cpu = None
+    # --- one step from eta0 in both precisions: the error against the oracle ----------
+    first = {}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, secs = oracle_rate(n, 1)
+        for name, o in (("fp32_refined", opts), ("fp64", opts64)):
+            ctx.set_opts(o)
+            ctx.set_amplitudes(eta_dev)
+            ctx.step(1.0, 1)
+            first[name] = (ctx.get_amplitudes(), ctx.get_zeta(), ctx.stats()["resid_last"])
+        ctx.set_opts(opts)
+    ctx.close()
+    del eta_dev
+    torch.cuda.empty_cache()
+
+    # --- the other workloads, as sub-records of this line --------------------------
+    subs = {}
+    if args.sub_steps > 0:
+        sub_args = argparse.Namespace(**vars(args))
+        sub_args.steps, sub_args.warmup = args.sub_steps, min(args.warmup, 2)
+        sub_args.fp64_steps, sub_args.e2e_steps, sub_args.breakdown_steps = 2, 2, 1
+        subs["bcc3d"] = run_bcc(sub_args, world, rank, local, sub=True)
+        subs["batch"] = run_batch(sub_args, world, rank, local, sub=True)
+        adj_args = argparse.Namespace(**vars(sub_args))
+        adj_args.steps, adj_args.warmup = 1, 1
+        subs["adjoint"] = run_adjoint(adj_args, world, rank, local, sub=True)
+
+    # --- CPU baseline: the oracle on this host's cores (rank 0, N = 1 only), and the
+    # error of the first GPU step against the oracle's ------------------------------
+    cpu = None
+    err = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        with tempfile.TemporaryDirectory() as tmp:
+            rate, secs, w = oracle_on_host("hex", n, 1, 0, args.oracle_workers, save_dir=tmp)
+            o_eta, o_zeta = np.load(os.path.join(tmp, "eta.npy")), np.load(os.path.join(tmp, "zeta.npy"))
         cpu = {
             "value": rate,
             "unit": UNIT,
-            "cores": 1,
+            "cores": w,
             "kind": "oracle",
-            "sample": f"one oracle FP64 step (numpy, exact FFT Schur solve) of the full {n}x{n} workload, "
-            f"{secs:.1f} s; numpy FFT and elementwise ops run on one thread",
+            "sample": f"one FP64 oracle step (numpy, exact FFT Schur solve) of the full {n}x{n} workload from "
+            f"eta0 in each of {w} host processes (one per core, each its own replica), {secs:.1f} s",
         }
-
-    ctx.close()
+        err = {name: dict(rel_l2_fields(e, z, o_eta, o_zeta), resid=r) for name, (e, z, r) in first.items()}
+        err["note"] = ("first step from eta0 at tol 1e-10, relative L2 per field (eta_j, zeta_j) against the "
+                       "oracle's exact step; resid = the GPU solve's final relative residual")
+        if "bcc3d" in subs and subs["bcc3d"] is not None and not args.no_cpu_baseline:
+            bcc_oracle_leg(args, subs["bcc3d"])
     if rank != 0:
         return
     line = {
@@ -453,7 +618,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32 Krylov + f64 refinement",
         "data": "synthetic",
-        "config": dict(workload_config(n), parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
+        "config": dict(workload_config(n), **({"parallelism": f"replicas x{world}"} if world > 1 else {})),
         "iters_per_step_last": st["iters_last"],
         "refine_sweeps_last": st["refine_last"],
         "resid_last": st["resid_last"],
@@ -482,10 +647,16 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step},
         "gpu_launches": prof["all_launches"],
+        "error_vs_oracle": err,
+        "alu_peaks": alu,
         "breakdown": breakdown,
         "rotation_diagnostic": rotation,
         "clocks": clocks,
     }
+    for key, rec in subs.items():
+        if rec is not None:
+            rec.pop("_first", None)
+            line[key] = rec
     print(json.dumps(line), flush=True)
 
 
@@ -578,10 +749,12 @@ def run_batch_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
+def run_batch(args, world=None, rank=None, local=None, sub=False):
+    """The batched workload; sub: return its record (no print, no runs-alone comparison)."""
     import torch
 
-    world, rank, local = init_dist(args)
+    if world is None:
+        world, rank, local = init_dist(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
@@ -691,9 +864,10 @@ def run_batch(args):
                 total += e0.elapsed_time(e1) / nsteps
         return total
 
-    alone32 = alone(tuned_opts, args.alone_steps)
+    alone32 = alone(tuned_opts, 0 if sub else args.alone_steps)
     alone64 = alone(
-        A.apfc_default_opts(precision=A.APFC_FP64, tol=TOL, cheb_degree=args.cheb), min(args.alone_steps, args.fp64_steps)
+        A.apfc_default_opts(precision=A.APFC_FP64, tol=TOL, cheb_degree=args.cheb),
+        0 if sub else min(args.alone_steps, args.fp64_steps),
     )
 
     cpu = None
@@ -701,7 +875,7 @@ def run_batch(args):
         rate, secs, sample = oracle_batch_rate(spec, states)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
     if rank != 0:
-        return
+        return None
     ms_step = ms / args.steps
     per_n = {}
     for (n, _, _), st in zip(spec, stats):
@@ -719,7 +893,7 @@ def run_batch(args):
         "vs_baseline": None,
         "dtype": "f32 Krylov + f64 refinement",
         "data": "synthetic",
-        "config": dict(batch_config(args, spec, tuned), parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
+        "config": dict(batch_config(args, spec, tuned), **({"parallelism": f"replicas x{world}"} if world > 1 else {})),
         "per_run_ms_per_step": ms_step / len(spec),
         "iters_last_by_size": {n: max(v) for n, v in per_n.items()},
         "resid_last_max": max(st["resid_last"] for st in stats),
@@ -747,6 +921,8 @@ def run_batch(args):
         "gpu_launches": int(launches_per_step * args.steps),
         "clocks": clocks,
     }
+    if sub:
+        return line
     print(json.dumps(line), flush=True)
 
 
@@ -817,10 +993,12 @@ def run_adjoint_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_adjoint(args):
+def run_adjoint(args, world=None, rank=None, local=None, sub=False):
+    """The adjoint workload; sub: return its record (no print, no host baseline)."""
     import torch
 
-    world, rank, local = init_dist(args)
+    if world is None:
+        world, rank, local = init_dist(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_1902_09761_gb300 import apfc as A
@@ -907,18 +1085,18 @@ def run_adjoint(args):
     ro.close()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not sub:
         ns, ks = min(n, 512), min(K, 20)
         rate, secs = oracle_adjoint_rate(ns, ks)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"oracle rollout gradient (FFT-exact solves) on {ns}x{ns}, {ks} steps, {secs:.1f} s"}
     if rank != 0:
-        return
+        return None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 Krylov + f64 refinement", "data": "synthetic",
-        "config": dict(adjoint_config(args), parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
+        "config": dict(adjoint_config(args), **({"parallelism": f"replicas x{world}"} if world > 1 else {})),
         "ms_per_gradient": ms,
         "forward_ms_per_step": fwd_ms / K,
         "backward_ms_per_step": bwd_ms / K,
@@ -935,6 +1113,8 @@ def run_adjoint(args):
         "gpu_launches": prof["all_launches"],
         "clocks": clocks,
     }
+    if sub:
+        return line
     print(json.dumps(line), flush=True)
 
 
@@ -988,10 +1168,13 @@ def run_bcc_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_bcc(args):
+def run_bcc(args, world=None, rank=None, local=None, sub=False):
+    """The 3D bcc workload; sub: return its record (no print; the host-oracle leg and the
+    error against the oracle are added by bcc_oracle_leg)."""
     import torch
 
-    world, rank, local = init_dist(args)
+    if world is None:
+        world, rank, local = init_dist(args)
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     from paper_1902_09761_gb300 import apfc as A
@@ -1056,9 +1239,20 @@ def run_bcc(args):
     achieved = bpl / (avg_ms * 1e-3) / 1e9
 
     # plain FP64 at the same final residual
-    ctx.set_opts(A.apfc_default_opts(precision=A.APFC_FP64, tol=TOL, cheb_degree=args.cheb))
+    opts64 = A.apfc_default_opts(precision=A.APFC_FP64, tol=TOL, cheb_degree=args.cheb)
+    ctx.set_opts(opts64)
     ms64, _ = timed(args.fp64_steps)
     ctx.set_opts(opts)
+
+    # one step from eta0 in both precisions, for the error against the oracle
+    first = {}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        for name, o in (("fp32_refined", opts), ("fp64", opts64)):
+            ctx.set_opts(o)
+            ctx.set_amplitudes(eta_dev)
+            ctx.step(1.0, 1)
+            first[name] = (ctx.get_amplitudes(), ctx.get_zeta(), ctx.stats()["resid_last"])
+        ctx.set_opts(opts)
 
     # end to end: host-resident state copied in and out every step
     h_state = torch.empty(eta0.shape, dtype=torch.complex128).pin_memory()
@@ -1077,7 +1271,7 @@ def run_bcc(args):
     ctx.close()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not sub:
         import oracle as O
 
         P = O.params_from_paper(0.98, 0.01, 0.25, 0.5)
@@ -1089,12 +1283,12 @@ def run_bcc(args):
         cpu = {"value": 6.0 * ns ** 3 / secs, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"one oracle FP64 step (FFT exact solve) of a {ns}^3 bcc sphere, {secs:.2f} s"}
     if rank != 0:
-        return
+        return None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 Krylov + f64 refinement", "data": "synthetic",
-        "config": dict(bcc_config(args), parallelism=f"replicas x{world}" if world > 1 else "1 GPU"),
+        "config": dict(bcc_config(args), **({"parallelism": f"replicas x{world}"} if world > 1 else {})),
         "iters_per_step_last": st["iters_last"], "refine_sweeps_last": st["refine_last"],
         "resid_last": st["resid_last"],
         "fp64": {"value": world * dof * args.fp64_steps / (ms64 * 1e-3), "unit": UNIT,
@@ -1110,7 +1304,29 @@ def run_bcc(args):
                       for nm, v in sorted(per.items(), key=lambda kv: -kv[1]["ms_per_step"])},
         "clocks": clocks,
     }
+    if sub:
+        line["_first"] = first
+        return line
     print(json.dumps(line), flush=True)
+
+
+def bcc_oracle_leg(args, rec):
+    """Host-oracle leg of the bcc3d record: one oracle step of the full sphere workload from
+    eta0 in one host process per core (as memory allows); replica 0's result gives the error
+    of the GPU's first step in both precisions."""
+    first = rec.pop("_first", {})
+    n = args.bcc_size
+    with tempfile.TemporaryDirectory() as tmp:
+        rate, secs, w = oracle_on_host("bcc", n, 1, 0, args.oracle_workers, save_dir=tmp)
+        o_eta, o_zeta = np.load(os.path.join(tmp, "eta.npy")), np.load(os.path.join(tmp, "zeta.npy"))
+    rec["cpu_baseline"] = {
+        "value": rate, "unit": UNIT, "cores": w, "kind": "oracle",
+        "sample": f"one FP64 oracle step (exact FFT solve) of the full {n}^3 sphere from eta0 in each of {w} host "
+                  f"processes (one per core, each its own replica), {secs:.1f} s",
+    }
+    err = {name: dict(rel_l2_fields(e, z, o_eta, o_zeta), resid=r) for name, (e, z, r) in first.items()}
+    err["note"] = "first step from eta0 at tol 1e-10, relative L2 per field against the oracle's exact step"
+    rec["error_vs_oracle"] = err
 
 
 CHEB = 1

@@ -258,14 +258,16 @@ apfc_status apfc_profile_read(apfc_ctx* ctx, int id, double* ms, long long* laun
                               long long* all_launches);
 apfc_status apfc_profile_stop(apfc_ctx* ctx);
 
-/* FMA throughput of the current device, for the arithmetic roofline of the FP64
- * kernels (the paper has no counterpart; it reports no GPU rates).
- * precision APFC_FP64 times FP64 FMAs, APFC_FP32_REFINED FP32 FMAs: independent
- * FMA chains on 8 blocks of 256 threads per SM, best of three launches timed
- * with CUDA events on stream (NULL = legacy default stream); *flops = 2 x FMAs /
- * seconds.  Allocates and frees a small device buffer; synchronises the stream.
- * EINVAL for another precision or a NULL output, ECUDA / ENOMEM on failure. */
-apfc_status apfc_measure_fma_rate(int precision, void* stream, double* flops);
+/* Arithmetic rates of the current device, for the arithmetic roofline of the
+ * FP64 kernels (the paper has no counterpart; it reports no GPU rates).
+ * kind APFC_ALU_FMA64 / APFC_ALU_FMA32: independent FMA chains in FP64 / FP32,
+ * *rate = FLOP/s (2 per FMA); APFC_ALU_CVT64: FP64 -> FP32 -> FP64 conversion
+ * chains, *rate = conversions/s.  8 blocks of 256 threads per SM, best of three
+ * launches timed with CUDA events on stream (NULL = legacy default stream).
+ * Allocates and frees a small device buffer and synchronises the stream.
+ * EINVAL for another kind or a NULL output, ECUDA / ENOMEM on failure. */
+enum { APFC_ALU_FMA64 = 0, APFC_ALU_FMA32 = 1, APFC_ALU_CVT64 = 2 };
+apfc_status apfc_measure_alu_rate(int kind, void* stream, double* rate);
 
 /* ---- parameters and the adjoint of the step ---------------------------------
  * Gradient convention: for a real loss L of complex fields, the gradient with

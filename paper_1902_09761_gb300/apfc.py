@@ -27,6 +27,7 @@ APFC_BICGSTAB = 0
 APFC_TAU_FOLD, APFC_TAU_PLAIN = 0, 1
 APFC_MAX_J = 8
 APFC_BATCH_GRAPH = 1
+APFC_ALU_FMA64, APFC_ALU_FMA32, APFC_ALU_CVT64 = 0, 1, 2
 
 
 class ApfcError(RuntimeError):
@@ -110,7 +111,7 @@ EXPORTS = {
          C.POINTER(C.c_longlong)],
     ),
     "apfc_profile_stop": (C.c_int, [C.c_void_p]),
-    "apfc_measure_fma_rate": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(C.c_double)]),
+    "apfc_measure_alu_rate": (C.c_int, [C.c_int, C.c_void_p, C.POINTER(C.c_double)]),
     "apfc_apply_preconditioner_static": (
         C.c_int,
         [C.POINTER(Lattice), C.POINTER(Params), C.POINTER(Grid), C.c_int, C.c_int, C.c_double, C.c_void_p,
@@ -559,10 +560,11 @@ class Batch:
         _check_batch(load().apfc_batch_profile_stop(self._h), self._h)
 
 
-def measure_fma_rate(precision: int, stream: int | None = None) -> float:
-    """FMA throughput of the current GPU in FLOP/s (2 per FMA), FP64 (APFC_FP64) or FP32 (APFC_FP32_REFINED)."""
+def measure_alu_rate(kind: int, stream: int | None = None) -> float:
+    """Arithmetic rate of the current GPU: FLOP/s of FP64 (APFC_ALU_FMA64) or FP32 (APFC_ALU_FMA32)
+    FMAs, or FP64 <-> FP32 conversions/s (APFC_ALU_CVT64)."""
     out = C.c_double()
-    _check(load().apfc_measure_fma_rate(int(precision), C.c_void_p(stream) if stream else None, C.byref(out)))
+    _check(load().apfc_measure_alu_rate(int(kind), C.c_void_p(stream) if stream else None, C.byref(out)))
     return out.value
 
 

@@ -68,3 +68,22 @@ def test_reference_arm_under_torchrun_prints_one_line_from_rank_zero():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_oracle_host_pool_replicas_and_saved_step(tmp_path):
+    # bench.py's host-oracle legs: spawned processes, one replica each, aligned by a
+    # barrier; replica 0's result is the oracle's step of the same workload.
+    sys.path.insert(0, ROOT)
+    import bench
+    import numpy as np
+
+    import oracle as O
+
+    rate, secs, w = bench.oracle_on_host("hex", 32, 2, 1, workers=2, save_dir=str(tmp_path))
+    assert w == 2 and secs > 0
+    assert rate == pytest.approx(2 * 3 * 32 * 32 * 2 / secs, rel=1e-12)
+    eta, L, h, P = bench._oracle_input("hex", 32)
+    for _ in range(3):
+        eta, zeta = O.step(eta, 1.0, P, L, h)
+    assert np.array_equal(np.load(tmp_path / "eta.npy"), eta)
+    assert np.array_equal(np.load(tmp_path / "zeta.npy"), zeta)
