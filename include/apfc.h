@@ -60,6 +60,11 @@ typedef enum {
 
 enum { APFC_HOST = 0, APFC_DEVICE = 1 };
 
+/* Element type of an amplitude buffer of apfc_set_amplitudes / apfc_get_amplitudes:
+ * complex128 (interleaved doubles) or complex64 (interleaved floats; converted
+ * on the device to and from the FP64 state, rounding to nearest on the way out). */
+enum { APFC_C128 = 0, APFC_C64 = 1 };
+
 /* Lattices.  HEX2D: triangular lattice, J = 3, dim = 2, k_1 + k_2 + k_3 = 0,
  * nonlinear term in the closed form of Sec. II.  BCC3D / CUSTOM: the nonlinear
  * term is generated from k by keeping the resonant (zero-sum) wavevector
@@ -147,12 +152,15 @@ apfc_status apfc_init(apfc_ctx** ctx, const apfc_lattice* lat, const apfc_params
 /* Replace the solver options (precision, tolerances, degree). */
 apfc_status apfc_set_opts(apfc_ctx* ctx, const apfc_opts* opts);
 
-/* Copy amplitudes eta in ([J][nz][ny][nx] complex128) and set zeta = G_h eta
- * (the auxiliary field of Sec. II.A).  Clears a sticky error and the stats. */
-apfc_status apfc_set_amplitudes(apfc_ctx* ctx, const void* eta, int where);
+/* Copy amplitudes eta in ([J][nz][ny][nx], element type dtype: APFC_C128 or
+ * APFC_C64) and set zeta = G_h eta (the auxiliary field of Sec. II.A).  The
+ * state is FP64 either way.  Clears a sticky error and the stats.  EINVAL for
+ * another dtype. */
+apfc_status apfc_set_amplitudes(apfc_ctx* ctx, const void* eta, int where, int dtype);
 
-/* Copy the current amplitudes eta (or the auxiliary field zeta) out. */
-apfc_status apfc_get_amplitudes(apfc_ctx* ctx, void* eta, int where);
+/* Copy the current amplitudes eta out as dtype (APFC_C128 or APFC_C64), or the
+ * auxiliary field zeta (complex128). */
+apfc_status apfc_get_amplitudes(apfc_ctx* ctx, void* eta, int where, int dtype);
 apfc_status apfc_get_zeta(apfc_ctx* ctx, void* zeta, int where);
 
 /* Advance n steps of size dt (Alg. 1).  Default (picard_iters 1, jacobian 0):

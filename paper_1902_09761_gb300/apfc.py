@@ -21,6 +21,7 @@ APFC_OK, APFC_EINVAL, APFC_ENOMEM, APFC_ECUDA, APFC_ENOCONV, APFC_ENAN, APFC_EST
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "ENAN", 6: "ESTATE", 7: "ETOOBIG"}
 APFC_STATIC_MAX_DOF = 262144
 APFC_HOST, APFC_DEVICE = 0, 1
+APFC_C128, APFC_C64 = 0, 1
 APFC_LATTICE_CUSTOM, APFC_LATTICE_HEX2D, APFC_LATTICE_BCC3D = 0, 1, 2
 APFC_FP64, APFC_FP32_REFINED = 0, 1
 APFC_BICGSTAB = 0
@@ -91,8 +92,8 @@ EXPORTS = {
         [C.POINTER(C.c_void_p), C.POINTER(Lattice), C.POINTER(Params), C.POINTER(Grid), C.POINTER(Opts), C.c_void_p],
     ),
     "apfc_set_opts": (C.c_int, [C.c_void_p, C.POINTER(Opts)]),
-    "apfc_set_amplitudes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
-    "apfc_get_amplitudes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "apfc_set_amplitudes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
+    "apfc_get_amplitudes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "apfc_get_zeta": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "apfc_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     "apfc_energy": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
@@ -233,11 +234,13 @@ def _check_batch(status, h=None, init=False):
         raise ApfcError(status, msg)
 
 
-def _ptr(buf, writable=False):
-    """(pointer, where, keepalive) of a numpy array or torch tensor of complex128."""
+def _ptr(buf, writable=False, c64_ok=False):
+    """(pointer, where, keepalive) of a numpy array or torch tensor of complex128 (or, where
+    the entry point takes a dtype, complex64; see _dtype)."""
     if isinstance(buf, np.ndarray):
-        if buf.dtype != np.complex128 or not buf.flags["C_CONTIGUOUS"]:
-            raise TypeError("numpy buffers must be C-contiguous complex128")
+        ok = buf.dtype == np.complex128 or (c64_ok and buf.dtype == np.complex64)
+        if not ok or not buf.flags["C_CONTIGUOUS"]:
+            raise TypeError("numpy buffers must be C-contiguous complex128" + (" or complex64" if c64_ok else ""))
         if writable and not buf.flags["WRITEABLE"]:
             raise TypeError("output buffer is read-only")
         return buf.ctypes.data_as(C.c_void_p), APFC_HOST, buf
@@ -245,14 +248,20 @@ def _ptr(buf, writable=False):
 
     if not isinstance(buf, torch.Tensor):
         raise TypeError("buffer must be a numpy array or a torch tensor")
-    if buf.dtype != torch.complex128 or not buf.is_contiguous():
-        raise TypeError("torch buffers must be contiguous complex128")
+    ok = buf.dtype == torch.complex128 or (c64_ok and buf.dtype == torch.complex64)
+    if not ok or not buf.is_contiguous():
+        raise TypeError("torch buffers must be contiguous complex128" + (" or complex64" if c64_ok else ""))
     if buf.is_cuda:
         return C.c_void_p(buf.data_ptr()), APFC_DEVICE, buf
     if writable:
         raise TypeError("host output must be a numpy array")
     arr = buf.numpy()
     return arr.ctypes.data_as(C.c_void_p), APFC_HOST, arr
+
+
+def _dtype(buf) -> int:
+    """APFC_C64 for complex64 buffers, else APFC_C128."""
+    return APFC_C64 if str(buf.dtype).endswith("complex64") else APFC_C128
 
 
 class Context:
@@ -307,13 +316,15 @@ class Context:
         self.opts = opts
 
     def set_amplitudes(self, eta):
-        p, where, keep = _ptr(eta)
-        _check(load().apfc_set_amplitudes(self._h, p, where), self._h)
+        """Copy amplitudes in: complex128 or complex64 (converted on the device)."""
+        p, where, keep = _ptr(eta, c64_ok=True)
+        _check(load().apfc_set_amplitudes(self._h, p, where, _dtype(eta)), self._h)
 
-    def get_amplitudes(self, out=None):
-        out = np.empty(self.amp_shape, np.complex128) if out is None else out
-        p, where, keep = _ptr(out, True)
-        _check(load().apfc_get_amplitudes(self._h, p, where), self._h)
+    def get_amplitudes(self, out=None, dtype=np.complex128):
+        """Copy amplitudes out into `out` (complex128 or complex64), or a new host array of dtype."""
+        out = np.empty(self.amp_shape, dtype) if out is None else out
+        p, where, keep = _ptr(out, True, c64_ok=True)
+        _check(load().apfc_get_amplitudes(self._h, p, where, _dtype(out)), self._h)
         return out
 
     def get_zeta(self, out=None):

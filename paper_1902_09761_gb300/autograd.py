@@ -3,7 +3,8 @@
 ``Rollout(...)(eta0, dB)`` returns (eta^n, F(eta^n)) after n steps of size dt
 of the library's step (Alg. 1 with one nonlinear iterate, nonlinear term
 explicit), as a differentiable function of the initial amplitudes eta0
-(complex128 or complex64, host or CUDA tensor) and of dB (a real tensor).  The
+(complex128 or complex64, host or CUDA tensor; complex64 is converted by the
+library on the device) and of dB (a real tensor).  The
 backward pass is the library's checkpointed adjoint (``apfc_rollout_backward``:
 one adjoint solve per step with the Hermitian Schur complement, the adjoint of
 the nonlinear term with both Wirtinger derivatives, and the dB derivative
@@ -42,14 +43,19 @@ class Rollout:
     def _view(self, t: torch.Tensor):
         return t if t.is_cuda else t.numpy()
 
-    def _empty(self, like: torch.Tensor):
-        return torch.empty(self.shape, dtype=torch.complex128, device=like.device)
+    def _empty(self, like: torch.Tensor, dtype=torch.complex128):
+        return torch.empty(self.shape, dtype=dtype, device=like.device)
 
 
 class _RolloutFn(torch.autograd.Function):
     @staticmethod
     def forward(fctx, eta0, dB, ro: Rollout):
-        e0 = eta0.detach().to(torch.complex128).contiguous()
+        # complex64 and complex128 inputs go to the library as they are (it converts on the
+        # device); the output comes back in the input's type, and the final state in
+        # complex128 is kept for the energy gradient of the backward pass
+        e0 = eta0.detach().contiguous()
+        if e0.dtype not in (torch.complex64, torch.complex128):
+            raise TypeError("eta0 must be complex64 or complex128")
         if tuple(e0.shape) != tuple(ro.shape):
             raise ValueError(f"eta0 has shape {tuple(e0.shape)}, expected {tuple(ro.shape)}")
         p = ro.params
@@ -58,12 +64,16 @@ class _RolloutFn(torch.autograd.Function):
         ro.ctx.rollout_forward(ro.dt, ro.n, ro.every)
         etaN = ro._empty(e0)
         ro.ctx.get_amplitudes(ro._view(etaN))
+        out = etaN
+        if e0.dtype == torch.complex64:
+            out = ro._empty(e0, torch.complex64)
+            ro.ctx.get_amplitudes(ro._view(out))
         F = ro.ctx.energy()
         fctx.ro = ro
         fctx.in_dtype = eta0.dtype
         fctx.dB_meta = (dB.shape, dB.dtype, dB.device) if isinstance(dB, torch.Tensor) else None
         fctx.save_for_backward(etaN)
-        return etaN.to(eta0.dtype), torch.tensor(F, dtype=torch.float64, device=e0.device)
+        return out, torch.tensor(F, dtype=torch.float64, device=e0.device)
 
     @staticmethod
     def backward(fctx, g_eta, g_F):

@@ -863,9 +863,27 @@ apfc_status copy_out_block(apfc_ctx* ctx, void* dst, const double2* src_dev, int
 }
 
 // Copy one part (0 = zeta, 1 = eta) of the state block to/from [J][pts].
-apfc_status copy_part(apfc_ctx* ctx, void* plain, int where, int part, bool to_state) {
+apfc_status copy_part(apfc_ctx* ctx, void* plain, int where, int part, bool to_state, int dtype = APFC_C128) {
   const size_t row = sizeof(double2) * (size_t)ctx->pts;
   double2* base = ctx->x64 + (size_t)part * ctx->pts;
+  if (dtype == APFC_C64) {
+    // complex64: converted on the device (host buffers pass through the staging field)
+    const size_t bytes = sizeof(float2) * (size_t)ctx->pts * ctx->J;
+    const bool host = where == APFC_HOST;
+    if (host && !ctx->stage) CK(cudaMalloc(&ctx->stage, row * ctx->J));
+    float2* dev = host ? reinterpret_cast<float2*>(ctx->stage) : static_cast<float2*>(plain);
+    if (to_state) {
+      if (host) CK(cudaMemcpyAsync(dev, plain, bytes, cudaMemcpyHostToDevice, ctx->stream));
+      launch_c64_to_part(dev, ctx->x64, ctx->pts, ctx->J, part, ctx->stream);
+      CK(cudaGetLastError());
+    } else {
+      launch_part_to_c64(ctx->x64, dev, ctx->pts, ctx->J, part, ctx->stream);
+      CK(cudaGetLastError());
+      if (host) CK(cudaMemcpyAsync(plain, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return APFC_OK;
+  }
   cudaMemcpyKind k;
   if (to_state)
     k = where == APFC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
@@ -1208,12 +1226,13 @@ apfc_status apfc_set_opts(apfc_ctx* ctx, const apfc_opts* opts) {
   return APFC_OK;
 }
 
-apfc_status apfc_set_amplitudes(apfc_ctx* ctx, const void* eta, int where) {
+apfc_status apfc_set_amplitudes(apfc_ctx* ctx, const void* eta, int where, int dtype) {
   if (!ctx || !eta || (where != APFC_HOST && where != APFC_DEVICE)) return APFC_EINVAL;
+  if (dtype != APFC_C128 && dtype != APFC_C64) return APFC_EINVAL;
   ctx->failed = false;
   ctx->err.clear();
   ctx->have_prev = false;
-  apfc_status st = copy_part(ctx, const_cast<void*>(eta), where, 1, true);
+  apfc_status st = copy_part(ctx, const_cast<void*>(eta), where, 1, true, dtype);
   if (st != APFC_OK) return st;
   std::string e;
   if (ctx->coef_dt < 0 && !build_coef(ctx, 1.0, e)) return fail(ctx, APFC_EINVAL, e);
@@ -1225,10 +1244,11 @@ apfc_status apfc_set_amplitudes(apfc_ctx* ctx, const void* eta, int where) {
   return APFC_OK;
 }
 
-apfc_status apfc_get_amplitudes(apfc_ctx* ctx, void* eta, int where) {
+apfc_status apfc_get_amplitudes(apfc_ctx* ctx, void* eta, int where, int dtype) {
   if (!ctx || !eta || (where != APFC_HOST && where != APFC_DEVICE)) return APFC_EINVAL;
+  if (dtype != APFC_C128 && dtype != APFC_C64) return APFC_EINVAL;
   if (!ctx->has_state) return fail(ctx, APFC_ESTATE, "no amplitudes set");
-  return copy_part(ctx, eta, where, 1, false);
+  return copy_part(ctx, eta, where, 1, false, dtype);
 }
 
 apfc_status apfc_get_zeta(apfc_ctx* ctx, void* zeta, int where) {

@@ -25,6 +25,7 @@
 // result and accumulate inner products for the BiCGStab scalars.
 #include "acc.cuh"
 #include "apfc_internal.cuh"
+#include "dfloat.cuh"
 
 #include <algorithm>
 #include <cstring>
@@ -395,10 +396,17 @@ struct EpAddX {  // x64 += y (the Krylov correction P^{-1} u)
   __device__ const cplx<T>* ep(int) const { return nullptr; }
   __device__ void put(const cplx<T>*, int, long long p, cplx<T> y1, cplx<T> y2) {
     double2 a = x[off + p], b = x[off + pts + p];
-    a.x += (double)y1.x;
-    a.y += (double)y1.y;
-    b.x += (double)y2.x;
-    b.y += (double)y2.y;
+    if constexpr (sizeof(T) == 4) {  // exact widening by integer operations (no FP64 conversion)
+      a.x += f2d(y1.x);
+      a.y += f2d(y1.y);
+      b.x += f2d(y2.x);
+      b.y += f2d(y2.y);
+    } else {
+      a.x += y1.x;
+      a.y += y1.y;
+      b.x += y2.x;
+      b.y += y2.y;
+    }
     x[off + p] = a;
     x[off + pts + p] = b;
   }

@@ -9,6 +9,7 @@
 
 #include "acc.cuh"
 #include "apfc_internal.cuh"
+#include "dfloat.cuh"
 
 namespace apfc {
 
@@ -358,8 +359,13 @@ __global__ void k_add_to(const cplx<T>* __restrict__ d, double2* __restrict__ x,
   if (i >= n) return;
   const cplx<T> dv = d[i];
   double2 xv = x[i];
-  xv.x += (double)dv.x;
-  xv.y += (double)dv.y;
+  if constexpr (sizeof(T) == 4) {  // exact widening by integer operations (no FP64 conversion)
+    xv.x += f2d(dv.x);
+    xv.y += f2d(dv.y);
+  } else {
+    xv.x += dv.x;
+    xv.y += dv.y;
+  }
   x[i] = xv;
 }
 
@@ -510,65 +516,129 @@ __global__ void k_residual_refine(const double2* __restrict__ b, const double2* 
   }
 }
 
-// FP64 outer residual on 2D grids: r = b - A x with x, b FP64; writes r as FP32
-// (the inner solve's right-hand side) and, if r64 != nullptr, as FP64 (kept as
-// the previous residual of the next step).  32 x 8 point tiles, neighbours by
-// comparison (no division per point).  The partial ||r||^2 per amplitude is
-// accumulated from the FP32-rounded residual (it only decides convergence, where
-// a relative error of 1e-5 in the norm is immaterial); ||b||^2 is not
+// FP64-accurate outer residual on 2D grids, r = b - A x with x, b FP64 in memory,
+// evaluated without the FP64 pipe: every input double is split into an FP32 pair
+// (h, l) by integer operations and each component of r1 = b1 - zeta + G_h eta and
+// r2 = b2 - kt G_h zeta - a eta is one compensated sum of products (dfloat.cuh);
+// residuals to about 1e-14 of the terms' size, beneath the 1e-10 and 1e-13
+// tolerances of the refinement.  Writes r as FP32 (the inner solve's right-hand
+// side) and, if r64 != nullptr, as FP64 (kept as the previous residual of the
+// next step).  32 x 8 point tiles whose (zeta, eta) values and one-point halo are
+// split once into shared memory.  The partial ||r||^2 per amplitude is
+// accumulated from the FP32-rounded residual (it only decides convergence,
+// where a relative error of 1e-5 in the norm is immaterial); ||b||^2 is not
 // recomputed: b is fixed within a step.
+constexpr int kRTX = 32, kRTY = 8;
+__device__ __forceinline__ float4 pdf_pack(PDF v) { return make_float4(v.h.x, v.l.x, v.h.y, v.l.y); }
+__device__ __forceinline__ PDF pdf_unpack(float4 v) { return PDF{make_float2(v.x, v.z), make_float2(v.y, v.w)}; }
+__device__ __forceinline__ PDF pdf_swap(PDF v) {  // (re, im) -> (im, re)
+  return PDF{make_float2(v.h.y, v.h.x), make_float2(v.l.y, v.l.x)};
+}
+// lane coefficients (s0 c, s1 c) of a double-float c
+struct PCoef {
+  float2 h, l;
+};
+__device__ __forceinline__ PCoef pcoef(double c, float s0, float s1) {
+  const DF d = split_d(c);
+  return PCoef{make_float2(s0 * d.h, s1 * d.h), make_float2(s0 * d.l, s1 * d.l)};
+}
+
 __global__ void __launch_bounds__(256) k_residual_refine2d(const double2* __restrict__ b,
                                                            const double2* __restrict__ x, float2* __restrict__ r32,
                                                            double2* __restrict__ r64, double2* __restrict__ partials,
-                                                           OpCoef c, const RunGeom* rg) {
+                                                           const __grid_constant__ OpCoef c, const RunGeom* rg) {
   const int j = blockIdx.y;
-  if (rg != nullptr) {  // batched runs: blockIdx.z selects the run
-    const long long ro = select_run(rg, blockIdx.z, c);
-    b += ro;
-    x += ro;
-    r32 += ro;
-    if (r64 != nullptr) r64 += ro;
+  int nx = c.nx, ny = c.ny;
+  long long pts = c.pts;
+  if (rg != nullptr) {  // batched runs: blockIdx.z selects the run (the Jacobian is never on here)
+    const RunGeom& q = rg[blockIdx.z];
+    nx = q.nx;
+    ny = q.ny;
+    pts = q.pts;
+    b += q.elem_off;
+    x += q.elem_off;
+    r32 += q.elem_off;
+    if (r64 != nullptr) r64 += q.elem_off;
     partials += (long long)blockIdx.z * c.J * kDotSlots * kDotBlocks;
   }
-  prof_add(c, KID_RESID_REFINE,
-           (unsigned long long)c.pts * (4 * sizeof(double2) + 2 * sizeof(float2) + (r64 ? 2 * sizeof(double2) : 0)));
-  const long long o = 2LL * j * c.pts;
+  if (c.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
+    atomicAdd(c.prof + KID_RESID_REFINE, (unsigned long long)pts * (4 * sizeof(double2) + 2 * sizeof(float2) +
+                                                                   (r64 ? 2 * sizeof(double2) : 0)));
+  __shared__ float4 sz[kRTY + 2][kRTX + 2], se[kRTY + 2][kRTX + 2];
+  const long long o = 2LL * j * pts;
   const double2* z = x + o;
-  const double2* e = z + c.pts;
-  const double kt = c.kt[j], a = c.a[j];
-  const double c0 = c.c0, ihx = c.ih2[0], ihy = c.ih2[1], khx = c.kh[j][0], khy = c.kh[j][1];
-  const int nx = c.nx, ny = c.ny;
-  const int tx_count = (nx + 31) / 32, ntiles = tx_count * ((ny + 7) / 8);
+  const double2* e = z + pts;
+  // G_h: c0 at the centre, ih_d on the d-neighbours (both lanes), and the advection
+  // i (k_d / h_d)(u(+d) - u(-d)) as lane coefficients on swapped (im, re) values
+  const PCoef g0 = pcoef(c.c0, 1.f, 1.f), gx = pcoef(c.ih2[0], 1.f, 1.f), gy = pcoef(c.ih2[1], 1.f, 1.f);
+  const PCoef axp = pcoef(c.kh[j][0], -1.f, 1.f), axm = pcoef(c.kh[j][0], 1.f, -1.f);
+  const PCoef ayp = pcoef(c.kh[j][1], -1.f, 1.f), aym = pcoef(c.kh[j][1], 1.f, -1.f);
+  // -kt G_h for the (2,1) block
+  const double kt = c.kt[j];
+  const PCoef k0 = pcoef(kt * c.c0, -1.f, -1.f), kx = pcoef(kt * c.ih2[0], -1.f, -1.f);
+  const PCoef ky = pcoef(kt * c.ih2[1], -1.f, -1.f);
+  const PCoef kxp = pcoef(kt * c.kh[j][0], 1.f, -1.f), kxm = pcoef(kt * c.kh[j][0], -1.f, 1.f);
+  const PCoef kyp = pcoef(kt * c.kh[j][1], 1.f, -1.f), kym = pcoef(kt * c.kh[j][1], -1.f, 1.f);
+  PCoef ma = pcoef(c.a[j], -1.f, -1.f);
+  const int tx_count = (nx + kRTX - 1) / kRTX, ntiles = tx_count * ((ny + kRTY - 1) / kRTY);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   float rr = 0.f;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int ty0 = tile / tx_count;
-    const int xx = (tile - ty0 * tx_count) * 32 + tx, yy = ty0 * 8 + ty;
+    const int tyi = tile / tx_count;
+    const int x0 = (tile - tyi * tx_count) * kRTX, y0 = tyi * kRTY;
+    __syncthreads();  // the previous tile's shared values are no longer read
+    for (int i = threadIdx.x; i < (kRTX + 2) * (kRTY + 2); i += 256) {
+      const int ry = i / (kRTX + 2), rx = i - ry * (kRTX + 2);
+      int gxx = x0 - 1 + rx, gyy = y0 - 1 + ry;
+      gxx = gxx < 0 ? gxx + nx : (gxx >= nx ? gxx % nx : gxx);
+      gyy = gyy < 0 ? gyy + ny : (gyy >= ny ? gyy % ny : gyy);
+      const long long q = (long long)gyy * nx + gxx;
+      sz[ry][rx] = pdf_pack(pdf_split(z[q]));
+      se[ry][rx] = pdf_pack(pdf_split(e[q]));
+    }
+    __syncthreads();
+    const int xx = x0 + tx, yy = y0 + ty;
     if (xx >= nx || yy >= ny) continue;
-    const long long row = (long long)yy * nx;
-    const long long pc = row + xx;
-    const long long pl = row + (xx == 0 ? nx - 1 : xx - 1), pr = row + (xx + 1 == nx ? 0 : xx + 1);
-    const long long pu = (long long)(yy == 0 ? ny - 1 : yy - 1) * nx + xx;
-    const long long pd = (long long)(yy + 1 == ny ? 0 : yy + 1) * nx + xx;
-    // G_h u: 9 FP64 operations per component
-    auto G = [&](const double2* u) {
-      const double2 C = u[pc], L = u[pl], R = u[pr], U = u[pu], D = u[pd];
-      const double gx = fma(ihx, L.x + R.x, fma(ihy, U.x + D.x, fma(-khx, R.y - L.y, fma(-khy, D.y - U.y, c0 * C.x))));
-      const double gy = fma(ihx, L.y + R.y, fma(ihy, U.y + D.y, fma(khx, R.x - L.x, fma(khy, D.x - U.x, c0 * C.y))));
-      return make_double2(gx, gy);
-    };
-    const double2 gz = G(z), ge = G(e);
-    const double2 zc = z[pc], ec = e[pc];
-    const double2 b1 = b[o + pc], b2 = b[o + c.pts + pc];
-    const double r1x = (b1.x - zc.x) + ge.x, r1y = (b1.y - zc.y) + ge.y;
-    const double ap = c.jd == nullptr ? a : a_at(c, j, pc);
-    const double r2x = b2.x - fma(kt, gz.x, ap * ec.x), r2y = b2.y - fma(kt, gz.y, ap * ec.y);
-    const float2 f1 = make_float2((float)r1x, (float)r1y), f2 = make_float2((float)r2x, (float)r2y);
+    const long long pc = (long long)yy * nx + xx;
+    const PDF zc = pdf_unpack(sz[ty + 1][tx + 1]), zl = pdf_unpack(sz[ty + 1][tx]), zr = pdf_unpack(sz[ty + 1][tx + 2]);
+    const PDF zu = pdf_unpack(sz[ty][tx + 1]), zd = pdf_unpack(sz[ty + 2][tx + 1]);
+    const PDF ec = pdf_unpack(se[ty + 1][tx + 1]), el = pdf_unpack(se[ty + 1][tx]), er = pdf_unpack(se[ty + 1][tx + 2]);
+    const PDF eu = pdf_unpack(se[ty][tx + 1]), ed = pdf_unpack(se[ty + 2][tx + 1]);
+    // r1 = b1 - zeta + G_h eta
+    PAcc a1;
+    a1.init(pdf_split(b[o + pc]));
+    a1.add(zc, -1.f);
+    a1.fma(g0.h, g0.l, ec);
+    a1.fma(gx.h, gx.l, el);
+    a1.fma(gx.h, gx.l, er);
+    a1.fma(gy.h, gy.l, eu);
+    a1.fma(gy.h, gy.l, ed);
+    a1.fma(axp.h, axp.l, pdf_swap(er));
+    a1.fma(axm.h, axm.l, pdf_swap(el));
+    a1.fma(ayp.h, ayp.l, pdf_swap(ed));
+    a1.fma(aym.h, aym.l, pdf_swap(eu));
+    // r2 = b2 - kt G_h zeta - a eta
+    if (c.jd != nullptr) ma = pcoef(a_at(c, j, pc), -1.f, -1.f);
+    PAcc a2;
+    a2.init(pdf_split(b[o + pts + pc]));
+    a2.fma(k0.h, k0.l, zc);
+    a2.fma(kx.h, kx.l, zl);
+    a2.fma(kx.h, kx.l, zr);
+    a2.fma(ky.h, ky.l, zu);
+    a2.fma(ky.h, ky.l, zd);
+    a2.fma(kxp.h, kxp.l, pdf_swap(zr));
+    a2.fma(kxm.h, kxm.l, pdf_swap(zl));
+    a2.fma(kyp.h, kyp.l, pdf_swap(zd));
+    a2.fma(kym.h, kym.l, pdf_swap(zu));
+    a2.fma(ma.h, ma.l, ec);
+    float2 f1, l1, f2, l2;
+    a1.result(f1, l1);
+    a2.result(f2, l2);
     r32[o + pc] = f1;
-    r32[o + c.pts + pc] = f2;
+    r32[o + pts + pc] = f2;
     if (r64 != nullptr) {
-      r64[o + pc] = make_double2(r1x, r1y);
-      r64[o + c.pts + pc] = make_double2(r2x, r2y);
+      r64[o + pc] = make_double2(df_to_d(DF{f1.x, l1.x}), df_to_d(DF{f1.y, l1.y}));
+      r64[o + pts + pc] = make_double2(df_to_d(DF{f2.x, l2.x}), df_to_d(DF{f2.y, l2.y}));
     }
     rr = fmaf(f1.x, f1.x, fmaf(f1.y, f1.y, fmaf(f2.x, f2.x, fmaf(f2.y, f2.y, rr))));
   }
@@ -634,6 +704,83 @@ __global__ void __launch_bounds__(256) k_rhs_resid(const double2* __restrict__ x
   }
   __syncthreads();
   if (threadIdx.x < 2 * c.J) {
+    double v = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) v += sh[threadIdx.x][k];
+    const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
+    partials[(j * kDotSlots + which) * kDotBlocks + blockIdx.x] = make_double2(v, 0.0);
+  }
+}
+
+// The same for the triangular lattice (closed-form N_j) without the FP64 pipe:
+// amplitudes, b_prev and r_prev are split into FP32 pairs by integer operations
+// and rhs_j = eta_j/dt - kap_j N_j(eta), r0 = rhs - b_prev + r_prev are formed in
+// double-float arithmetic (about 2^-44 relative per operation, dfloat.cuh).  The
+// new right-hand side is stored as the nearest double.
+__global__ void __launch_bounds__(256) k_rhs_resid_hex(const double2* __restrict__ x, double2* __restrict__ b,
+                                                       const double2* __restrict__ b_prev,
+                                                       const double2* __restrict__ r_prev, float2* __restrict__ r32,
+                                                       double2* __restrict__ partials, const __grid_constant__ OpCoef c,
+                                                       const __grid_constant__ NonlinTable nt, const RunGeom* rg) {
+  long long pts = c.pts;
+  if (rg != nullptr) {  // batched runs: blockIdx.y selects the run
+    const RunGeom& q = rg[blockIdx.y];
+    pts = q.pts;
+    x += q.elem_off;
+    b += q.elem_off;
+    b_prev += q.elem_off;
+    r_prev += q.elem_off;
+    r32 += q.elem_off;
+    partials += (long long)blockIdx.y * 3 * kDotSlots * kDotBlocks;
+  }
+  if (c.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
+    atomicAdd(c.prof + KID_RHS, 3ull * pts * (5 * sizeof(double2) + 2 * sizeof(float2)));
+  const DF v3 = split_d(3.0 * nt.v), t2 = split_d(2.0 * nt.t), idt = split_d(c.inv_dt);
+  DF kap[3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) kap[j] = split_d(c.kap[j]);
+  float accf[6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) accf[i] = 0.f;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < pts;
+       p += (long long)gridDim.x * blockDim.x) {
+    CDF eta[3];
+    DF m2[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      eta[j] = cdf_split(x[(2LL * j + 1) * pts + p]);
+      m2[j] = cdf_abs2(eta[j]);
+    }
+    const DF A2 = df_scale2(df_add(df_add(m2[0], m2[1]), m2[2]));
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      // N_j = 3v (A^2 - |eta_j|^2) eta_j - 2t conj(eta_k eta_l)
+      const int k1 = j == 2 ? 0 : j + 1, k2 = j == 0 ? 2 : j - 1;
+      const DF sj = df_mul(v3, df_sub(A2, m2[j]));
+      const CDF N = cdf_sub(cdf_scale(sj, eta[j]), cdf_scale(t2, cdf_conj(cdf_mul(eta[k1], eta[k2]))));
+      const CDF bn = cdf_sub(cdf_scale(idt, eta[j]), cdf_scale(kap[j], N));
+      const long long q1 = 2LL * j * pts + p, q2 = q1 + pts;
+      b[q2] = cdf_to_d(bn);
+      const CDF r2 = cdf_add(cdf_sub(bn, cdf_split(b_prev[q2])), cdf_split(r_prev[q2]));
+      const DF p1x = split_d(r_prev[q1].x), p1y = split_d(r_prev[q1].y);
+      const float2 f1 = make_float2(__fadd_rn(p1x.h, p1x.l), __fadd_rn(p1y.h, p1y.l));
+      const float2 f2 = make_float2(r2.x.h, r2.y.h);
+      r32[q1] = f1;
+      r32[q2] = f2;
+      // norms only decide convergence: accumulated from FP32-rounded values
+      accf[2 * j] = fmaf(f1.x, f1.x, fmaf(f1.y, f1.y, fmaf(f2.x, f2.x, fmaf(f2.y, f2.y, accf[2 * j]))));
+      accf[2 * j + 1] = fmaf(bn.x.h, bn.x.h, fmaf(bn.y.h, bn.y.h, accf[2 * j + 1]));
+    }
+  }
+  __shared__ double sh[6][kThreads / 32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    double v = (double)accf[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (l == 0) sh[i][w] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
     double v = 0.0;
     for (int k = 0; k < kThreads / 32; ++k) v += sh[threadIdx.x][k];
     const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
@@ -1078,6 +1225,32 @@ void launch_rhs(const double2* x, double2* b, const OpCoef& c, const NonlinTable
   const dim3 g((unsigned)((c.pts + kThreads - 1) / kThreads), bl ? bl->R : 1);
   k_rhs<<<g, kThreads, 0, s>>>(x, b, c, nt, bl ? bl->dev : nullptr);
 }
+// complex64 amplitudes [J][pts] <-> part `part` of the FP64 state block [J][2][pts]
+__global__ void k_c64_to_part(const float2* __restrict__ src, double2* __restrict__ x, long long pts, int J,
+                              int part) {
+  const long long n = (long long)J * pts;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long j = i / pts, p = i - j * pts;
+    const float2 v = src[i];
+    x[(2 * j + part) * pts + p] = make_double2((double)v.x, (double)v.y);
+  }
+}
+__global__ void k_part_to_c64(const double2* __restrict__ x, float2* __restrict__ dst, long long pts, int J,
+                              int part) {
+  const long long n = (long long)J * pts;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long j = i / pts, p = i - j * pts;
+    const double2 v = x[(2 * j + part) * pts + p];
+    dst[i] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+  }
+}
+void launch_c64_to_part(const float2* src, double2* x, long long pts, int J, int part, cudaStream_t s) {
+  k_c64_to_part<<<4 * kDotBlocks, kThreads, 0, s>>>(src, x, pts, J, part);
+}
+void launch_part_to_c64(const double2* x, float2* dst, long long pts, int J, int part, cudaStream_t s) {
+  k_part_to_c64<<<4 * kDotBlocks, kThreads, 0, s>>>(x, dst, pts, J, part);
+}
+
 void launch_zeta(double2* x, const OpCoef& c, cudaStream_t s) {
   if (c.dim == 3) {
     launch3d_zeta(x, c, s);
@@ -1101,6 +1274,11 @@ void launch_rhs_resid(const double2* x, double2* b, const double2* b_prev, const
                       double* partials, const OpCoef& c, const NonlinTable& nt, cudaStream_t s,
                       const BatchLaunch* bl) {
   ProfScope ps_(KID_RHS, s);
+  if (nt.hex) {
+    k_rhs_resid_hex<<<dim3(kDotBlocks, bl ? bl->R : 1), kThreads, 0, s>>>(
+        x, b, b_prev, r_prev, r32, reinterpret_cast<double2*>(partials), c, nt, bl ? bl->dev : nullptr);
+    return;
+  }
   k_rhs_resid<<<dim3(kDotBlocks, bl ? bl->R : 1), kThreads, 0, s>>>(
       x, b, b_prev, r_prev, r32, reinterpret_cast<double2*>(partials), c, nt, bl ? bl->dev : nullptr);
 }

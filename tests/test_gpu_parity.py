@@ -8,6 +8,8 @@ grids (S_j's symbol spans [1/dt + dB, 1/dt + dB + Bx max g^2]), so parity
 runs use tol = 1e-13 and must match the oracle to relative L2 <= 1e-10 per
 step and per amplitude.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -341,3 +343,35 @@ def test_bcc_chunks_tiles_odd_width(prec, m):
         assert _max_rel(y[j, 0], y1) < 1e-13 and _max_rel(y[j, 1], y2) < 1e-13
     eta0 = inputs.random_amplitudes(6, shape, seed=33, scale=0.1)
     _trajectory_parity("bcc", eta0, shape, h, 2, dt=0.5, tol=1e-13, precision=prec, cheb_degree=m)
+
+
+@pytest.mark.parametrize("device", [False, True])
+def test_complex64_amplitudes_at_the_boundary(device):
+    # complex64 amplitudes in and out through the C ABI (converted on the device): a step
+    # from complex64 input equals the complex128 path from the same (rounded) values, and
+    # complex64 output is the complex128 state rounded to nearest.
+    torch = pytest.importorskip("torch")
+    shape = (40, 52)
+    eta = inputs.random_amplitudes(3, shape, seed=41, scale=0.2)
+    e64 = eta.astype(np.complex64)
+    outs = []
+    for src in (e64, e64.astype(np.complex128)):
+        ctx, L = context("hex", shape, H2, tol=1e-13)
+        ctx.set_amplitudes(torch.from_numpy(src).cuda() if device else src)
+        assert np.array_equal(ctx.get_amplitudes(), e64.astype(np.complex128))  # widening is exact
+        ctx.step(1.0, 2)
+        full = ctx.get_amplitudes()
+        if device:
+            low = torch.empty((3,) + shape, dtype=torch.complex64, device="cuda")
+            ctx.get_amplitudes(low)
+            low = low.cpu().numpy()
+        else:
+            low = ctx.get_amplitudes(dtype=np.complex64)
+        assert low.dtype == np.complex64
+        assert np.array_equal(low, full.astype(np.complex64))
+        outs.append(full)
+    assert np.array_equal(outs[0], outs[1])
+    ref = O.run(e64.astype(np.complex128), 1.0, 2, P, L, H2)[-1]
+    assert max(rel_l2_per_amp(outs[0], ref)) < 1e-10
+    # any other element type is rejected
+    assert A.load().apfc_set_amplitudes(ctx._h, e64.ctypes.data_as(ctypes.c_void_p), A.APFC_HOST, 7) == A.APFC_EINVAL
