@@ -112,13 +112,13 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-# FP64-pipe instructions per amplitude value (DOF) of the FP64 kernels of the 2D hexagonal
-# FP32-refined step, counted from their source: (FP64 arithmetic, FP64 <-> FP32 conversions).
-#   residual_refine_f64 (k_residual_refine2d): two complex G_h stencils of 18 (4 neighbour
-#     sums/differences, 1 multiply and 4 FMAs per component), r1 4, r2 6; 4 conversions.
-#   rhs_f64 (k_rhs_resid, closed-form triangular N_j): per point 10 for A^2, per amplitude
-#     13 for N_j, 4 for eta/dt - kap N, 4 for the initial residual; 6 conversions per amplitude.
-FP64_PIPE_OPS = {"residual_refine_f64": (46.0, 4.0), "rhs_f64": ((10.0 + 3 * 21.0) / 3.0, 6.0)}
+# FP64-pipe instructions per amplitude value (DOF) of the FP64-accurate kernels of the 2D
+# hexagonal FP32-refined step, counted from their source: (FP64 arithmetic, FP64 <-> FP32
+# conversions).  Both kernels do their arithmetic in FP32 on doubles split by integer
+# operations; only the FP64 outputs cost FP64 additions.
+#   residual_refine_f64 (k_resid2d_tma): r64 = f2d(hi) + f2d(lo), 4 per DOF.
+#   rhs_f64 (k_rhs_resid_hex): the new right-hand side as a double, 2 per DOF.
+FP64_PIPE_OPS = {"residual_refine_f64": (4.0, 0.0), "rhs_f64": (2.0, 0.0)}
 
 
 def fp64_roofline(name, dof, rec, hbm_peak, alu):

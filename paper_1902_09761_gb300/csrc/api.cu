@@ -712,7 +712,10 @@ double max_rel_resid(const KScal* k, int J) {
 }
 
 apfc_status status_of(apfc_ctx* ctx, int worst) {
-  if (worst == KS_NAN) return fail(ctx, APFC_ENAN, "residual norm is not finite (NaN/Inf in the state?)");
+  if (worst == KS_NAN) {
+    if (tma_timeouts() > 0) return fail(ctx, APFC_ECUDA, "a TMA tile load did not complete within its wait limit");
+    return fail(ctx, APFC_ENAN, "residual norm is not finite (NaN/Inf in the state?)");
+  }
   if (worst == KS_NOCONV || worst == KS_BREAKDOWN)
     return fail(ctx, APFC_ENOCONV, "Krylov solve did not reach the tolerance within max_iter");
   return APFC_OK;
@@ -760,7 +763,9 @@ apfc_status refine_solve(apfc_ctx* ctx, const double2* b, double2* x, double2* r
         launch_finalize64(1, ctx->part64, ctx->ks64, OP_BNORM, ctx->J, s);
       }
       if (ctx->dim == 2) {
-        launch_residual_refine2d(b, x, r32, r64_keep, part, ctx->coef, s);
+        const char* terr = nullptr;
+        if (!launch_residual_refine2d_tma(b, x, r32, r64_keep, part, ctx->coef, s, &terr))
+          return fail(ctx, APFC_ECUDA, terr ? terr : "TMA residual launch failed");
         launch_finalize64(1, ctx->part64, ctx->ks64, OP_RNORM, ctx->J, s);
       } else {
         launch_residual_refine3d(b, x, r32, r64_keep, ctx->coef, s);

@@ -375,3 +375,12 @@ def test_complex64_amplitudes_at_the_boundary(device):
     assert max(rel_l2_per_amp(outs[0], ref)) < 1e-10
     # any other element type is rejected
     assert A.load().apfc_set_amplitudes(ctx._h, e64.ctypes.data_as(ctypes.c_void_p), A.APFC_HOST, 7) == A.APFC_EINVAL
+
+
+@pytest.mark.parametrize("shape", [(5, 7), (9, 40), (33, 31), (17, 65)])
+def test_refined_step_on_grids_smaller_than_or_ragged_against_tiles(shape):
+    # The FP32-refined step's FP64-accurate residual stages 32 x 8 tiles with a one-point
+    # halo; grids narrower or shorter than a tile, or one point past a tile boundary, take
+    # most of their halo from the periodic image.
+    eta0 = inputs.random_amplitudes(3, shape, seed=51, scale=0.15)
+    _trajectory_parity("hex", eta0, shape, (1.1, 0.9), 2, dt=0.7, tol=1e-13, precision=A.APFC_FP32_REFINED)
