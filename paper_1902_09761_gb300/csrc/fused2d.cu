@@ -320,9 +320,13 @@ struct LoadPR {
 };
 
 // t = y with s = r - alpha v; (t, s), (t, t), (s, s), (rhat, s), (rhat, t).
+// Epilogues: put(raw, st, p, y1, y2, k1, k2) stores the output (y1, y2) at point p; raw
+// holds the operands named by ep(i) (stride st); (k1, k2) are the loader's outputs at the
+// same point (beta1, beta2: s for LoadS) in FP32 pipelines, zero otherwise.
 template <typename T>
 struct EpT5 {
-  static constexpr int NDOT = 5, NEP = 6;
+  static constexpr bool KEEP = sizeof(T) == 4;  // s = r - alpha v arrives from the loader
+  static constexpr int NDOT = 5, NEP = KEEP ? 2 : 6;
   cplx<T>* t;
   const cplx<T>* r;
   const cplx<T>* v;
@@ -343,10 +347,12 @@ struct EpT5 {
     off = 2LL * j * pts;
     alpha = to_c<T>(k[j].alpha);
   }
-  // raw order: r1 r2 v1 v2 rhat1 rhat2
-  __device__ const cplx<T>* ep(int i) const { return (i < 2 ? r : (i < 4 ? v : rhat)) + off + (i & 1) * pts; }
-  __device__ void one(long long q, cplx<T> y, cplx<T> rr, cplx<T> vv, cplx<T> hh) {
-    const cplx<T> s = csub(rr, cmulz(alpha, vv));
+  // raw order: rhat1 rhat2 (FP32), r1 r2 v1 v2 rhat1 rhat2 (FP64)
+  __device__ const cplx<T>* ep(int i) const {
+    if constexpr (KEEP) return rhat + off + i * pts;
+    return (i < 2 ? r : (i < 4 ? v : rhat)) + off + (i & 1) * pts;
+  }
+  __device__ void one(long long q, cplx<T> y, cplx<T> s, cplx<T> hh) {
     t[q] = y;
     acc[0].add_run(y, s);
     acc[1].add_run(y, y);
@@ -354,9 +360,14 @@ struct EpT5 {
     acc[3].add_run(hh, s);
     acc[4].add_run(hh, y);
   }
-  __device__ void put(const cplx<T>* raw, int st, long long p, cplx<T> y1, cplx<T> y2) {
-    one(off + p, y1, raw[0], raw[2 * st], raw[4 * st]);
-    one(off + pts + p, y2, raw[st], raw[3 * st], raw[5 * st]);
+  __device__ void put(const cplx<T>* raw, int st, long long p, cplx<T> y1, cplx<T> y2, cplx<T> k1, cplx<T> k2) {
+    if constexpr (KEEP) {
+      one(off + p, y1, k1, raw[0]);
+      one(off + pts + p, y2, k2, raw[st]);
+    } else {
+      one(off + p, y1, csub(raw[0], cmulz(alpha, raw[2 * st])), raw[4 * st]);
+      one(off + pts + p, y2, csub(raw[st], cmulz(alpha, raw[3 * st])), raw[5 * st]);
+    }
   }
 };
 
@@ -374,7 +385,7 @@ struct EpStore {  // out = y
   }
   __device__ void setup(int j, const KScal*) { off = 2LL * j * pts; }
   __device__ const cplx<T>* ep(int) const { return nullptr; }
-  __device__ void put(const cplx<T>*, int, long long p, cplx<T> y1, cplx<T> y2) {
+  __device__ void put(const cplx<T>*, int, long long p, cplx<T> y1, cplx<T> y2, cplx<T>, cplx<T>) {
     out[off + p] = y1;
     out[off + pts + p] = y2;
   }
@@ -394,7 +405,7 @@ struct EpAddX {  // x64 += y (the Krylov correction P^{-1} u)
   }
   __device__ void setup(int j, const KScal*) { off = 2LL * j * pts; }
   __device__ const cplx<T>* ep(int) const { return nullptr; }
-  __device__ void put(const cplx<T>*, int, long long p, cplx<T> y1, cplx<T> y2) {
+  __device__ void put(const cplx<T>*, int, long long p, cplx<T> y1, cplx<T> y2, cplx<T>, cplx<T>) {
     double2 a = x[off + p], b = x[off + pts + p];
     if constexpr (sizeof(T) == 4) {  // exact widening by integer operations (no FP64 conversion)
       a.x += f2d(y1.x);
@@ -428,7 +439,7 @@ struct EpV {  // v = y; (rhat, v)
   }
   __device__ void setup(int j, const KScal*) { off = 2LL * j * pts; }
   __device__ const cplx<T>* ep(int i) const { return rhat + off + i * pts; }
-  __device__ void put(const cplx<T>* raw, int st, long long p, cplx<T> y1, cplx<T> y2) {
+  __device__ void put(const cplx<T>* raw, int st, long long p, cplx<T> y1, cplx<T> y2, cplx<T>, cplx<T>) {
     v[off + p] = y1;
     v[off + pts + p] = y2;
     acc[0].add_run(raw[0], y1);
@@ -454,7 +465,8 @@ struct EpJ : EP {
 
 template <typename T>
 struct EpT {  // t = y; (t, s), (t, t), (s, s) with s = r - alpha v
-  static constexpr int NDOT = 3, NEP = 4;
+  static constexpr bool KEEP = sizeof(T) == 4;  // s arrives from the loader
+  static constexpr int NDOT = 3, NEP = KEEP ? 0 : 4;
   cplx<T>* t;
   const cplx<T>* r;
   const cplx<T>* v;
@@ -473,18 +485,22 @@ struct EpT {  // t = y; (t, s), (t, t), (s, s) with s = r - alpha v
     off = 2LL * j * pts;
     alpha = to_c<T>(k[j].alpha);
   }
-  // raw order: r1, r2, v1, v2
+  // raw order: r1, r2, v1, v2 (FP64)
   __device__ const cplx<T>* ep(int i) const { return (i < 2 ? r : v) + off + (i & 1) * pts; }
-  __device__ void one(long long q, cplx<T> y, cplx<T> rr, cplx<T> vv) {
-    const cplx<T> s = csub(rr, cmulz(alpha, vv));
+  __device__ void one(long long q, cplx<T> y, cplx<T> s) {
     t[q] = y;
     acc[0].add_run(y, s);
     acc[1].add_run(y, y);
     acc[2].add_run(s, s);
   }
-  __device__ void put(const cplx<T>* raw, int st, long long p, cplx<T> y1, cplx<T> y2) {
-    one(off + p, y1, raw[0], raw[2 * st]);
-    one(off + pts + p, y2, raw[st], raw[3 * st]);
+  __device__ void put(const cplx<T>* raw, int st, long long p, cplx<T> y1, cplx<T> y2, cplx<T> k1, cplx<T> k2) {
+    if constexpr (KEEP) {
+      one(off + p, y1, k1);
+      one(off + pts + p, y2, k2);
+    } else {
+      one(off + p, y1, csub(raw[0], cmulz(alpha, raw[2 * st])));
+      one(off + pts + p, y2, csub(raw[st], cmulz(alpha, raw[3 * st])));
+    }
   }
 };
 
@@ -528,11 +544,18 @@ struct PipeShape {
   static constexpr int DB = pow2_at_least<2 * M + 1>() < 4 ? 4 : pow2_at_least<2 * M + 1>();
   static constexpr int SCHI = 2 * M + 1;  // stage forming chi1 (step 4)
   static constexpr int SEP = S;           // stage calling the epilogue
-  static constexpr int NRAW = LD::NIN + LD::NRE + EP::NEP;
+  // FP32 pipelines keep the loader's outputs (beta1, beta2) of the last 2S + 1 rows of
+  // their own column in shared memory: step 4 and the epilogue read them there instead of
+  // fetching and re-forming them from the Krylov vectors again
+  static constexpr bool KEEP = sizeof(T) == 4;
+  static constexpr int KD = 2 * S + 1;
+  static constexpr int NRE_F = KEEP ? 0 : LD::NRE;  // re-form operands fetched per row
+  static constexpr int NRAW = LD::NIN + NRE_F + EP::NEP;
   static constexpr int NSLOT = PF > 0 ? PF + 1 : 0;
   static constexpr int NT = NT_;
   static constexpr size_t ring_elems = (size_t)((NRING - 1) * 4 + DB) * NT;
-  static constexpr size_t smem = sizeof(cplx<T>) * (ring_elems + (size_t)NSLOT * NRAW * NT);
+  static constexpr size_t keep_elems = KEEP ? (size_t)KD * 2 * NT : 0;
+  static constexpr size_t smem = sizeof(cplx<T>) * (ring_elems + keep_elems + (size_t)NSLOT * NRAW * NT);
   // element offset of ring q
   __host__ __device__ static constexpr int off(int qi) { return (qi <= QB ? qi * 4 : QB * 4 + DB + (qi - QB - 1) * 4) * NT; }
   __host__ __device__ static constexpr int depth(int qi) { return qi == QB ? DB : 4; }
@@ -580,10 +603,11 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
   constexpr int NT = SH::NT;
   constexpr int S = SH::S;
   constexpr int NRAW = SH::NRAW;
-  constexpr int OIN = 0, ORE = LD::NIN, OEP = LD::NIN + LD::NRE;  // raw offsets inside a slot
+  constexpr int OIN = 0, ORE = LD::NIN, OEP = LD::NIN + SH::NRE_F;  // raw offsets inside a slot
   extern __shared__ unsigned char smem_raw[];
   cplx<T>* sm = reinterpret_cast<cplx<T>*>(smem_raw);
-  cplx<T>* stage_buf = sm + SH::ring_elems;
+  cplx<T>* keep = sm + SH::ring_elems;  // [KD][2][NT]: loader outputs of the own column
+  cplx<T>* stage_buf = keep + SH::keep_elems;
 
   // work item: strip sx, row segment sy, amplitude j (of run blockIdx.y when batched)
   int sx, sy, j;
@@ -661,10 +685,12 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
 #pragma unroll
         for (int i = 0; i < LD::NIN; ++i) cp_async<T>(slot + (OIN + i) * NT, ld.in(i) + p);
       }
-      if (valid_at(SH::SCHI, tf - 2 * SH::SCHI)) {
-        const long long p = ptg(fy_re);
+      if constexpr (!SH::KEEP) {
+        if (valid_at(SH::SCHI, tf - 2 * SH::SCHI)) {
+          const long long p = ptg(fy_re);
 #pragma unroll
-        for (int i = 0; i < LD::NRE; ++i) cp_async<T>(slot + (ORE + i) * NT, ld.re(i) + p);
+          for (int i = 0; i < LD::NRE; ++i) cp_async<T>(slot + (ORE + i) * NT, ld.re(i) + p);
+        }
       }
       if constexpr (EP::NEP > 0) {
         if (need_ep(tf - 2 * SH::SEP)) {
@@ -792,7 +818,9 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
             const cplx<T> chi2 = cadd(X, dn);
             const long long p = ptg(gy_chi);
             cplx<T> b1;
-            if constexpr (PF > 0) {
+            if constexpr (SH::KEEP) {
+              b1 = keep[(lr % SH::KD) * 2 * NT + t];
+            } else if constexpr (PF > 0) {
               b1 = ld.form_re(raw + ORE * st, st);
             } else {
               cplx<T> rr[LD::NRE];
@@ -808,7 +836,11 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
               ring(s)[(lr & 3) * NT + t] = chi1;
               ring(s + 1)[(lr & 3) * NT + t] = chi2;
             } else {
-              if (col_own && row_own(lr)) ep.put(raw + OEP * st, st, p, chi1, chi2);
+              if (col_own && row_own(lr)) {
+                const cplx<T>* kp = keep + (lr % SH::KD) * 2 * NT + t;
+                const cplx<T> k1 = SH::KEEP ? kp[0] : zero, k2 = SH::KEEP ? kp[NT] : zero;
+                ep.put(raw + OEP * st, st, p, chi1, chi2, k1, k2);
+              }
             }
           }
         }
@@ -845,13 +877,15 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
           } else {
             y2 = caxpy(q.kt, g1, cscale(q.a, n2.c));
           }
+          const cplx<T>* kp = keep + (lr % SH::KD) * 2 * NT + t;
+          const cplx<T> k1 = SH::KEEP ? kp[0] : zero, k2 = SH::KEEP ? kp[NT] : zero;
           if constexpr (PF > 0) {
-            ep.put(raw + OEP * st, st, p, y1, y2);
+            ep.put(raw + OEP * st, st, p, y1, y2, k1, k2);
           } else {
             cplx<T> er[EP::NEP > 0 ? EP::NEP : 1];
 #pragma unroll
             for (int i = 0; i < EP::NEP; ++i) er[i] = ep.ep(i)[p];
-            ep.put(er, 1, p, y1, y2);
+            ep.put(er, 1, p, y1, y2, k1, k2);
           }
         }
       }
@@ -870,6 +904,11 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
           ld.form_in(ri, 1, p, col_own && row_own(rho), b1, b2);
         }
         ring(0)[(rho & 3) * NT + t] = b1;
+        if constexpr (SH::KEEP) {
+          cplx<T>* kp = keep + (rho % SH::KD) * 2 * NT + t;
+          kp[0] = b1;
+          kp[NT] = b2;
+        }
       }
       push(0, b1);
       b2dl[1] = b2dl[0];
