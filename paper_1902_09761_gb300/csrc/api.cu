@@ -347,6 +347,13 @@ std::vector<ChebStep> apfc::cheb_weights_for(const OpCoef& c, const apfc_grid& g
   return w;
 }
 
+double apfc::inner_tol(double tol, double tol_inner, double rnorm2, double bnorm2) {
+  if (!(bnorm2 > 0.0)) return tol_inner;
+  if (rnorm2 <= tol * tol * bnorm2) return 2.0;
+  const double want = 0.25 * tol * std::sqrt(bnorm2 / rnorm2);
+  return std::min(0.5, std::max(tol_inner, want));
+}
+
 void apfc::cheb_weights_into(const OpCoef& c, const apfc_grid& grid, int m, ChebStep* w) {
   std::memset(w, 0, sizeof(ChebStep) * std::max(m, 1));
   double lapmax = 0.0;
@@ -566,7 +573,7 @@ apfc_status sync_scalars(apfc_ctx* ctx, Work<T>& w) {
 // Returns the worst per-amplitude KStatus; iterations in *iters (max over j).
 template <typename T>
 apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, double tol, int max_iter, int* iters,
-                   int* worst) {
+                   int* worst, const double* tol_amp = nullptr) {
   const OpCoef& c = ctx->coef;
   cudaStream_t s = ctx->stream;
   cplx<T>*r = w.blk[0], *rhat = w.blk[1], *p = w.blk[2], *v = w.blk[3], *u = w.blk[4], *t = w.blk[5], *z = w.blk[6];
@@ -579,7 +586,8 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
   for (int attempt = 0;; ++attempt) {
     // init: r = b - A x0, rhat = r, p = v = u = 0
     for (int j = 0; j < ctx->J; ++j) {
-      w.ks_host[j].tolrel2 = tol * tol;
+      const double tj = tol_amp ? tol_amp[j] : tol;  // per-amplitude relative tolerance, if given
+      w.ks_host[j].tolrel2 = tj * tj;
       w.ks_host[j].max_iter = max_iter;
     }
     CK(cudaMemcpyAsync(w.ks, w.ks_host, sizeof(KScal) * ctx->J, cudaMemcpyHostToDevice, s));
@@ -797,8 +805,12 @@ apfc_status refine_solve(apfc_ctx* ctx, const double2* b, double2* x, double2* r
       worst = KS_NOCONV;
       break;
     }
+    // inner tolerance per amplitude: no further than the outer tolerance needs
+    double tin[kMaxJ];
+    for (int j = 0; j < ctx->J; ++j)
+      tin[j] = inner_tol(ctx->opts.tol, ctx->opts.tol_inner, ctx->ks64_host[j].rnorm2, ctx->ks64_host[j].bnorm2);
     int it = 0, w = 0;
-    st = krylov<float>(ctx, ctx->w32, r32, x, ctx->opts.tol_inner, ctx->opts.max_iter, &it, &w);
+    st = krylov<float>(ctx, ctx->w32, r32, x, ctx->opts.tol_inner, ctx->opts.max_iter, &it, &w, tin);
     if (st != APFC_OK) return st;
     total += it;
     if (w == KS_NAN) {

@@ -214,16 +214,24 @@ apfc_status sync_ks(apfc_batch* b, KScal* dev, KScal* host) {
 }
 
 // Start a BiCGStab solve of A P^{-1} u = r32 for every (run, amplitude); runs with
-// skip[r] start converged.  Leaves the scalars on the host; *any: some are active.
-apfc_status krylov_init(apfc_batch* b, const std::vector<char>& skip, double tol, int max_iter, bool* any) {
+// skip[r] start converged.  fixed_tol >= 0: that relative tolerance for all; else the
+// refinement's per-amplitude choice (inner_tol) from the outer residual norms.
+// Leaves the scalars on the host; *any: some are active.
+apfc_status krylov_init(apfc_batch* b, const std::vector<char>& skip, int max_iter, bool* any,
+                        double fixed_tol = -1.0) {
   const Vecs x = vecs(b);
   cudaStream_t s = b->stream;
   const size_t bytes = sizeof(float2) * (size_t)b->elems;
   for (int r = 0; r < b->R; ++r)
     for (int j = 0; j < b->J; ++j) {
       KScal& k = b->ks_host[r * b->J + j];
+      // r0 = b: a relative tolerance >= 1 stops at once; otherwise the run alone's choice
+      const KScal& o = b->ks64_host[r * b->J + j];
+      const double tj = skip[r]           ? 2.0
+                        : fixed_tol >= 0.0 ? fixed_tol
+                                           : inner_tol(b->opts.tol, b->opts.tol_inner, o.rnorm2, o.bnorm2);
       std::memset(&k, 0, sizeof(k));
-      k.tolrel2 = skip[r] ? 4.0 : tol * tol;  // r0 = b: a relative tolerance >= 1 stops at once
+      k.tolrel2 = tj * tj;
       k.max_iter = max_iter;
     }
   BK(cudaMemcpyAsync(b->ks, b->ks_host, sizeof(KScal) * b->R * b->J, cudaMemcpyHostToDevice, s));
@@ -344,7 +352,7 @@ apfc_status batch_step(apfc_batch* b) {
         if (!done[r]) return bfail(b, APFC_ENOCONV, "run " + std::to_string(r) + ": refinement did not converge");
     }
     bool any = false;
-    st = krylov_init(b, done, b->opts.tol_inner, b->opts.max_iter, &any);
+    st = krylov_init(b, done, b->opts.max_iter, &any);
     if (st != APFC_OK) return st;
     if (any) {
       st = krylov_iterate(b, b->opts.max_iter, tile, rows, tile_t);
@@ -664,7 +672,7 @@ apfc_status apfc_batch_autotune(apfc_batch* b, double dt, int* tile_out, int* ro
     for (int rep = 0; rep < 2; ++rep) {  // the first pass warms up
       bool any = false;
       // a tolerance no solve reaches within kTuneIters iterations
-      if ((s2 = krylov_init(b, none, 1e-30, 1 << 20, &any)) != APFC_OK) return s2;
+      if ((s2 = krylov_init(b, none, 1 << 20, &any, 1e-30)) != APFC_OK) return s2;
       BK(cudaEventRecord(e0, s));
       if (!issue_block(b, 0, kTuneIters, tile, rows, tile_t))
         return bfail(b, APFC_EINVAL, "fused pipeline cannot run these options");

@@ -32,6 +32,12 @@ bool make_coef(const apfc_lattice& lat, const apfc_params& par, const apfc_grid&
 std::vector<ChebStep> cheb_weights_for(const OpCoef& c, const apfc_grid& grid, int m);
 void cheb_weights_into(const OpCoef& c, const apfc_grid& grid, int m, ChebStep* w);
 
+// Relative tolerance of the next FP32 inner solve of one amplitude in iterative
+// refinement: 2 (stop at once) if its outer residual already meets tol; otherwise
+// just enough to bring the outer residual to a quarter of tol, never tighter than
+// tol_inner nor looser than 1/2.
+double inner_tol(double tol, double tol_inner, double rnorm2, double bnorm2);
+
 // Measurement (see apfc_profile_start): dev receives the device byte counters.
 bool profiler_start(cudaStream_t s, int timed_id, unsigned long long** dev, std::string& err);
 bool profiler_read(cudaStream_t s, int id, double* ms, long long* launches, double* bytes, long long* all_launches,

@@ -181,8 +181,8 @@ def test_full_size_batch_64_runs_autotuned():
     # The batched benchmark workload in its launch configuration: 64 runs with N drawn from
     # {128, 256, 512, 1024}, tiles picked by the autotuner, Krylov blocks in CUDA graphs.
     # One run of each size matches the same run alone (same options) bit for bit, and the
-    # smallest of them matches the FP64 oracle within the FP32-refined path's stated 1e-12
-    # relative L2 per amplitude (measured 8.9e-14).
+    # smallest of them matches the FP64 oracle to the contract's 1e-10 relative L2 per
+    # amplitude (the runs stop at relative residual <= 1e-10).
     phi = O.uniform_solid_hex(P)
     spec = inputs.batch_spec(64, (128, 256, 512, 1024), seed=7)
     states = [inputs.batch_run_state(phi, n, th, sd) for n, th, sd in spec]
@@ -209,4 +209,4 @@ def test_full_size_batch_64_runs_autotuned():
     errs = [rel_l2(got[r][j], ref[j]) for j in range(3)]
     print(f"batch 64 runs: smallest run ({picks[0][0]}^2) rel L2 per amplitude vs oracle {errs}, "
           f"resid {b_resid}")
-    assert max(errs) <= 1e-12
+    assert max(errs) <= 1e-10
