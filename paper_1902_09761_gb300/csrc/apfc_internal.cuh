@@ -293,15 +293,13 @@ void launch_residual_refine(const double2* b, const double2* x, float2* r32, dou
 // 2D only: FP64 residual with FP32 (and optional FP64) output
 void launch_residual_refine2d(const double2* b, const double2* x, float2* r32, double2* r64, double* partials,
                               const OpCoef& c, cudaStream_t s, const BatchLaunch* bl = nullptr);
-// 2D, one grid: the same residual with its tiles staged by TMA (resid2d.cu); false, with
-// *err set, if the tensor maps cannot be built (nothing is launched then)
-bool launch_residual_refine2d_tma(const double2* b, const double2* x, float2* r32, double2* r64, double* partials,
-                                  const OpCoef& c, cudaStream_t s, const char** err);
+// One 2D or 3D grid: the residual with its tiles staged by TMA and the partial ||r||^2
+// per amplitude (resid2d.cu); false, with *err set, if the tensor maps cannot be built
+// (nothing is launched then)
+bool launch_residual_refine_tma(const double2* b, const double2* x, float2* r32, double2* r64, double* partials,
+                                const OpCoef& c, cudaStream_t s, const char** err);
 // bounded waits of the TMA kernels that gave up since the library was loaded
 unsigned long long tma_timeouts();
-// 3D: FP64 residual with FP32 and FP64 output (norm taken separately)
-void launch_residual_refine3d(const double2* b, const double2* x, float2* r32, double2* r64, const OpCoef& c,
-                              cudaStream_t s);
 // new RHS and initial residual r0 = b - b_prev + r_prev (pointwise)
 void launch_rhs_resid(const double2* x, double2* b, const double2* b_prev, const double2* r_prev, float2* r32,
                       double* partials, const OpCoef& c, const NonlinTable& nt, cudaStream_t s,

@@ -770,16 +770,11 @@ apfc_status refine_solve(apfc_ctx* ctx, const double2* b, double2* x, double2* r
         launch_dots<double>(1, d, ctx->part64, ctx->coef, nullptr, s);
         launch_finalize64(1, ctx->part64, ctx->ks64, OP_BNORM, ctx->J, s);
       }
-      if (ctx->dim == 2) {
+      {
         const char* terr = nullptr;
-        if (!launch_residual_refine2d_tma(b, x, r32, r64_keep, part, ctx->coef, s, &terr))
+        if (!launch_residual_refine_tma(b, x, r32, r64_keep, part, ctx->coef, s, &terr))
           return fail(ctx, APFC_ECUDA, terr ? terr : "TMA residual launch failed");
         launch_finalize64(1, ctx->part64, ctx->ks64, OP_RNORM, ctx->J, s);
-      } else {
-        launch_residual_refine3d(b, x, r32, r64_keep, ctx->coef, s);
-        DotPairs<float> d{{r32, nullptr, nullptr}, {r32, nullptr, nullptr}};
-        launch_dots<float>(1, d, ctx->w32.partials, ctx->coef, nullptr, s);
-        launch_finalize<float>(1, ctx->w32.partials, ctx->ks64, OP_RNORM, ctx->J, s);
       }
       stencil = true;
     }

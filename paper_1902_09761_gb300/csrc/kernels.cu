@@ -649,73 +649,12 @@ __global__ void __launch_bounds__(256) k_residual_refine2d(const double2* __rest
 
 // New right-hand side plus the initial outer residual of the step without a
 // stencil: with the previous step's final residual r_prev = b_prev - A x0,
-// r0 = b - A x0 = b - b_prev + r_prev (exact algebra, pointwise in FP64).
-// Writes b (eta-parts), r0 as FP32, and partials ||r0||^2, ||b||^2.
-__global__ void __launch_bounds__(256) k_rhs_resid(const double2* __restrict__ x, double2* __restrict__ b,
-                                                   const double2* __restrict__ b_prev,
-                                                   const double2* __restrict__ r_prev, float2* __restrict__ r32,
-                                                   double2* __restrict__ partials, const __grid_constant__ OpCoef c,
-                                                   const __grid_constant__ NonlinTable nt, const RunGeom* rg) {
-  long long pts = c.pts;  // the run's own size when batched (c stays untouched: no local copy)
-  if (rg != nullptr) {  // batched runs: blockIdx.y selects the run
-    const RunGeom& q = rg[blockIdx.y];
-    pts = q.pts;
-    x += q.elem_off;
-    b += q.elem_off;
-    b_prev += q.elem_off;
-    r_prev += q.elem_off;
-    r32 += q.elem_off;
-    partials += (long long)blockIdx.y * c.J * kDotSlots * kDotBlocks;
-  }
-  if (c.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
-    atomicAdd(c.prof + KID_RHS, (unsigned long long)c.J * pts * (5 * sizeof(double2) + 2 * sizeof(float2)));
-  __shared__ double2 se[kMaxJ][kThreads];
-  __shared__ double sn[kMaxJ][kThreads];
-  float accf[2 * kMaxJ];
-#pragma unroll
-  for (int i = 0; i < 2 * kMaxJ; ++i) accf[i] = 0.f;
-  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < pts;
-       p += (long long)gridDim.x * blockDim.x) {
-    const double A2 = load_point(x, pts, p, c.J, se, sn);
-    for (int j = 0; j < c.J; ++j) {
-      const double2 N = nonlin_shared(se, sn, j, c.J, A2, nt);
-      const double2 ej = se[j][threadIdx.x];
-      const double kap = c.kap[j];
-      const long long q1 = 2LL * j * pts + p, q2 = q1 + pts;
-      const double2 bn = make_double2(ej.x * c.inv_dt - kap * N.x, ej.y * c.inv_dt - kap * N.y);
-      b[q2] = bn;
-      const double2 bp = b_prev[q2], rp2 = r_prev[q2], rp1 = r_prev[q1];
-      const double r2x = (bn.x - bp.x) + rp2.x, r2y = (bn.y - bp.y) + rp2.y;
-      const float2 f1 = make_float2((float)rp1.x, (float)rp1.y), f2 = make_float2((float)r2x, (float)r2y);
-      r32[q1] = f1;
-      r32[q2] = f2;
-      // norms only decide convergence: accumulated from FP32-rounded values
-      const float2 fb = make_float2((float)bn.x, (float)bn.y);
-      accf[2 * j] = fmaf(f1.x, f1.x, fmaf(f1.y, f1.y, fmaf(f2.x, f2.x, fmaf(f2.y, f2.y, accf[2 * j]))));
-      accf[2 * j + 1] = fmaf(fb.x, fb.x, fmaf(fb.y, fb.y, accf[2 * j + 1]));
-    }
-  }
-  __shared__ double sh[2 * kMaxJ][kThreads / 32];
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  for (int i = 0; i < 2 * c.J; ++i) {
-    double v = (double)accf[i];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (l == 0) sh[i][w] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 2 * c.J) {
-    double v = 0.0;
-    for (int k = 0; k < kThreads / 32; ++k) v += sh[threadIdx.x][k];
-    const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
-    partials[(j * kDotSlots + which) * kDotBlocks + blockIdx.x] = make_double2(v, 0.0);
-  }
-}
-
-// The same for the triangular lattice (closed-form N_j) without the FP64 pipe:
-// amplitudes, b_prev and r_prev are split into FP32 pairs by integer operations
-// and rhs_j = eta_j/dt - kap_j N_j(eta), r0 = rhs - b_prev + r_prev are formed in
-// double-float arithmetic (about 2^-44 relative per operation, dfloat.cuh).  The
-// new right-hand side is stored as the nearest double.
+// r0 = b - A x0 = b - b_prev + r_prev (exact algebra, pointwise).  Writes b
+// (eta-parts, the nearest doubles), r0 as FP32, and partials ||r0||^2, ||b||^2.
+// Triangular lattice (closed-form N_j), without the FP64 pipe: amplitudes, b_prev
+// and r_prev are split into FP32 pairs by integer operations and rhs_j = eta_j/dt -
+// kap_j N_j(eta) and r0 are formed in double-float arithmetic (about 2^-44
+// relative per operation, dfloat.cuh).
 __global__ void __launch_bounds__(256) k_rhs_resid_hex(const double2* __restrict__ x, double2* __restrict__ b,
                                                        const double2* __restrict__ b_prev,
                                                        const double2* __restrict__ r_prev, float2* __restrict__ r32,
@@ -784,6 +723,113 @@ __global__ void __launch_bounds__(256) k_rhs_resid_hex(const double2* __restrict
     double v = 0.0;
     for (int k = 0; k < kThreads / 32; ++k) v += sh[threadIdx.x][k];
     const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
+    partials[(j * kDotSlots + which) * kDotBlocks + blockIdx.x] = make_double2(v, 0.0);
+  }
+}
+
+// Table lattices (bcc, custom), the same (new right-hand side and r0 = rhs - b_prev +
+// r_prev) without the FP64 pipe: rhs_j = eta_j/dt -
+// kap_j N_j(eta) with N_j = eta_j sum_m wdiag[j][m] |eta_m|^2 + the remaining resonance
+// monomials (coefficient times a product of amplitudes and conjugates), all in
+// double-float arithmetic (about 2^-44 relative per operation,
+// dfloat.cuh).  The split amplitudes of a point sit in shared memory (the table indexes
+// them at run time), the table's coefficients as FP32 pairs too.
+__global__ void __launch_bounds__(256) k_rhs_resid_tab(const double2* __restrict__ x, double2* __restrict__ b,
+                                                       const double2* __restrict__ b_prev,
+                                                       const double2* __restrict__ r_prev, float2* __restrict__ r32,
+                                                       double2* __restrict__ partials, const __grid_constant__ OpCoef c,
+                                                       const __grid_constant__ NonlinTable nt, const RunGeom* rg) {
+  long long pts = c.pts;
+  if (rg != nullptr) {  // batched runs: blockIdx.y selects the run
+    const RunGeom& q = rg[blockIdx.y];
+    pts = q.pts;
+    x += q.elem_off;
+    b += q.elem_off;
+    b_prev += q.elem_off;
+    r_prev += q.elem_off;
+    r32 += q.elem_off;
+    partials += (long long)blockIdx.y * c.J * kDotSlots * kDotBlocks;
+  }
+  const int J = c.J, t = threadIdx.x;
+  if (c.prof != nullptr && blockIdx.x == 0 && t == 0)
+    atomicAdd(c.prof + KID_RHS, (unsigned long long)J * pts * (5 * sizeof(double2) + 2 * sizeof(float2)));
+  __shared__ float4 se4[kMaxJ][kThreads];  // split amplitudes of each thread's point (re h, re l, im h, im l)
+  __shared__ float2 sn2[kMaxJ][kThreads];  // |eta_m|^2 as (h, l)
+  __shared__ float2 swd[kMaxJ][kMaxJ];
+  __shared__ float2 scf[kMaxTerms];
+  __shared__ float2 skap[kMaxJ];
+  for (int i = t; i < J * J; i += blockDim.x) {
+    const DF d = split_d(nt.wdiag[i / J][i % J]);
+    swd[i / J][i % J] = make_float2(d.h, d.l);
+  }
+  for (int i = t; i < kMaxTerms; i += blockDim.x) {
+    const DF d = split_d(nt.coef[i]);
+    scf[i] = make_float2(d.h, d.l);
+  }
+  if (t < J) {
+    const DF d = split_d(c.kap[t]);
+    skap[t] = make_float2(d.h, d.l);
+  }
+  __syncthreads();
+  const DF idt = split_d(c.inv_dt);
+  auto eta_of = [&](int code) {  // amplitude code >> 1, conjugated if code & 1
+    const float4 v = se4[code >> 1][t];
+    return (code & 1) ? CDF{DF{v.x, v.y}, DF{-v.z, -v.w}} : CDF{DF{v.x, v.y}, DF{v.z, v.w}};
+  };
+  float accf[2 * kMaxJ];
+#pragma unroll
+  for (int i = 0; i < 2 * kMaxJ; ++i) accf[i] = 0.f;
+  for (long long p = (long long)blockIdx.x * blockDim.x + t; p < pts; p += (long long)gridDim.x * blockDim.x) {
+    for (int m = 0; m < J; ++m) {
+      const CDF e = cdf_split(x[(2LL * m + 1) * pts + p]);
+      se4[m][t] = make_float4(e.x.h, e.x.l, e.y.h, e.y.l);
+      const DF a = cdf_abs2(e);
+      sn2[m][t] = make_float2(a.h, a.l);
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxJ; ++j) {
+      if (j >= J) break;
+      DF w{0.f, 0.f};
+      for (int m = 0; m < J; ++m) {
+        const float2 wd = swd[j][m], n2 = sn2[m][t];
+        w = df_add(w, df_mul(DF{wd.x, wd.y}, DF{n2.x, n2.y}));
+      }
+      const CDF ej = eta_of(2 * j);
+      CDF N = cdf_scale(w, ej);
+      for (int i = nt.rstart[j]; i < nt.rstart[j + 1]; ++i) {
+        const int q = nt.ridx[i];
+        const float2 cf = scf[q];
+        CDF prod = cdf_scale(DF{cf.x, cf.y}, eta_of(nt.f[q][0]));
+        for (int f = 1; f < nt.nf[q]; ++f) prod = cdf_mul(prod, eta_of(nt.f[q][f]));
+        N = cdf_add(N, prod);
+      }
+      const float2 kp = skap[j];
+      const CDF bn = cdf_sub(cdf_scale(idt, ej), cdf_scale(DF{kp.x, kp.y}, N));
+      const long long q1 = 2LL * j * pts + p, q2 = q1 + pts;
+      b[q2] = cdf_to_d(bn);
+      const CDF r2 = cdf_add(cdf_sub(bn, cdf_split(b_prev[q2])), cdf_split(r_prev[q2]));
+      const DF p1x = split_d(r_prev[q1].x), p1y = split_d(r_prev[q1].y);
+      const float2 f1 = make_float2(__fadd_rn(p1x.h, p1x.l), __fadd_rn(p1y.h, p1y.l));
+      const float2 f2 = make_float2(r2.x.h, r2.y.h);
+      r32[q1] = f1;
+      r32[q2] = f2;
+      // norms only decide convergence: accumulated from FP32-rounded values
+      accf[2 * j] = fmaf(f1.x, f1.x, fmaf(f1.y, f1.y, fmaf(f2.x, f2.x, fmaf(f2.y, f2.y, accf[2 * j]))));
+      accf[2 * j + 1] = fmaf(bn.x.h, bn.x.h, fmaf(bn.y.h, bn.y.h, accf[2 * j + 1]));
+    }
+  }
+  __shared__ double sh[2 * kMaxJ][kThreads / 32];
+  const int w = t >> 5, l = t & 31;
+  for (int i = 0; i < 2 * J; ++i) {
+    double v = (double)accf[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (l == 0) sh[i][w] = v;
+  }
+  __syncthreads();
+  if (t < 2 * J) {
+    double v = 0.0;
+    for (int k = 0; k < kThreads / 32; ++k) v += sh[t][k];
+    const int j = t >> 1, which = t & 1;
     partials[(j * kDotSlots + which) * kDotBlocks + blockIdx.x] = make_double2(v, 0.0);
   }
 }
@@ -1279,7 +1325,7 @@ void launch_rhs_resid(const double2* x, double2* b, const double2* b_prev, const
         x, b, b_prev, r_prev, r32, reinterpret_cast<double2*>(partials), c, nt, bl ? bl->dev : nullptr);
     return;
   }
-  k_rhs_resid<<<dim3(kDotBlocks, bl ? bl->R : 1), kThreads, 0, s>>>(
+  k_rhs_resid_tab<<<dim3(kDotBlocks, bl ? bl->R : 1), kThreads, 0, s>>>(
       x, b, b_prev, r_prev, r32, reinterpret_cast<double2*>(partials), c, nt, bl ? bl->dev : nullptr);
 }
 void launch_energy(const double2* x, double* partials, double* out, const OpCoef& c, const EnergyTable& et, double Bx,

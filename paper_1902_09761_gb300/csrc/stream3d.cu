@@ -423,39 +423,6 @@ struct OpZeta3 {
   }
 };
 
-// FP64 outer residual on 3D grids: r = b - A x (x, b FP64), written as FP32 and, if
-// r64 != nullptr, as FP64.
-struct OpResRefine3 {
-  static constexpr int NS = 2, ND = 0, NQ = 2, MINB = 3;
-  const double2* x;
-  const double2* b;
-  float2* r32;
-  double2* r64;
-  long long pts;
-  int kid;
-  unsigned long long bytes;
-  template <typename Q>
-  __device__ void coef(Q&, int) const {}
-  __device__ const double2* src(int k, int j) const { return x + (2LL * j + k) * pts; }
-  __device__ const double2* qsrc(int k, int j) const { return b + (2LL * j + k) * pts; }
-  __device__ void apply(int j, long long p, const N7<double> (&n)[2], const OpCoef& c, const Coef7<double>& q,
-                        Acc<double>*, const double2* pv) const {
-    const double2 gz = G7(n[0], q), ge = G7(n[1], q);
-    const double kt = q.kt, a = a7(q, c, j, p);
-    const long long o = 2LL * j * pts;
-    const double2 b1 = pv[0], b2 = pv[1];
-    const double r1x = (b1.x - n[0].c.x) + ge.x, r1y = (b1.y - n[0].c.y) + ge.y;
-    const double r2x = b2.x - fma(kt, gz.x, a * n[1].c.x), r2y = b2.y - fma(kt, gz.y, a * n[1].c.y);
-    r32[o + p] = make_float2((float)r1x, (float)r1y);
-    r32[o + pts + p] = make_float2((float)r2x, (float)r2y);
-    if (r64 != nullptr) {
-      r64[o + p] = make_double2(r1x, r1y);
-      r64[o + pts + p] = make_double2(r2x, r2y);
-    }
-  }
-};
-
-
 // FP32 variant of k_stream3d: each thread owns two adjacent points (x, x+1) of a row of a
 // 64 x 8 tile.  The plane tile (one-point halo) sits at local column x - x0 + 2, so the
 // pair and its y- and z-neighbour pairs are 16-byte shared-memory loads: half the
@@ -699,14 +666,6 @@ void launch3d_zeta(double2* x, const OpCoef& c, cudaStream_t s) {
   OpZeta3 op{x, c.pts, KID_ZETA, 2ull * (unsigned long long)c.pts * sizeof(double2)};
   k_stream3d<double, OpZeta3><<<grid_stream3d<double>(c), 256, 0, s>>>(c, op, nullptr);
 }
-void launch_residual_refine3d(const double2* b, const double2* x, float2* r32, double2* r64, const OpCoef& c,
-                              cudaStream_t s) {
-  ProfScope ps_(KID_RESID_REFINE, s);
-  OpResRefine3 op{x, b, r32, r64, c.pts, KID_RESID_REFINE,
-                  (unsigned long long)c.pts * ((r64 ? 6 : 4) * sizeof(double2) + 2 * sizeof(float2))};
-  k_stream3d<double, OpResRefine3><<<grid_stream3d<double>(c), 256, 0, s>>>(c, op, nullptr);
-}
-
 #define APFC_INST3(T)                                                                                                \
   template void launch3d_apply_A<T>(const cplx<T>*, cplx<T>*, const OpCoef&, const KScal*, cudaStream_t);           \
   template void launch_apply_A_dots<T>(const cplx<T>*, cplx<T>*, const cplx<T>*, int, void*, const OpCoef&,         \

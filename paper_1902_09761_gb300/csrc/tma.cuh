@@ -26,6 +26,9 @@ namespace apfc {
 // TMA or rejects the arguments.
 bool tma_encode_f64(CUtensorMap* map, const void* base, const unsigned long long dims[3],
                     const unsigned long long strides[2], const unsigned box[3], const char** err);
+// The same with rank 4 (strides[0..2]: byte strides of dims 1..3).
+bool tma_encode_f64_4d(CUtensorMap* map, const void* base, const unsigned long long dims[4],
+                       const unsigned long long strides[3], const unsigned box[4], const char** err);
 
 // Number of TMA waits that timed out since the library was loaded (all devices).
 unsigned long long tma_timeouts();
@@ -83,6 +86,16 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
       "[%5];\n" ::"r"(smem_u32(dst)),
       "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 4D tiled box load (coordinates innermost first; x * 8 bytes a multiple of 16).
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, unsigned long long* bar, int x, int y,
+                                            int z, int w) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(smem_u32(bar))
       : "memory");
 }
 
