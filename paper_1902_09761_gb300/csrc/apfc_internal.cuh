@@ -43,13 +43,13 @@ template <typename T>
 struct FieldRef {
   cplx<T>* p;
   long long ld;  // elements between amplitude j and j+1
-  __device__ __forceinline__ cplx<T>* at(int j) const { return p + (long long)j * ld; }
+  __host__ __device__ __forceinline__ cplx<T>* at(int j) const { return p + (long long)j * ld; }
 };
 template <typename T>
 struct CFieldRef {
   const cplx<T>* p;
   long long ld;
-  __device__ __forceinline__ const cplx<T>* at(int j) const { return p + (long long)j * ld; }
+  __host__ __device__ __forceinline__ const cplx<T>* at(int j) const { return p + (long long)j * ld; }
 };
 
 // ---------------------------------------------------------------------------
@@ -299,7 +299,9 @@ void launch_residual_refine2d(const double2* b, const double2* x, float2* r32, d
 bool launch_residual_refine_tma(const double2* b, const double2* x, float2* r32, double2* r64, double* partials,
                                 const OpCoef& c, cudaStream_t s, const char** err);
 // bounded waits of the TMA kernels that gave up since the library was loaded
+// (stream3d_timeouts: those of the 3D passes alone)
 unsigned long long tma_timeouts();
+unsigned long long stream3d_timeouts();
 // new RHS and initial residual r0 = b - b_prev + r_prev (pointwise)
 void launch_rhs_resid(const double2* x, double2* b, const double2* b_prev, const double2* r_prev, float2* r32,
                       double* partials, const OpCoef& c, const NonlinTable& nt, cudaStream_t s,

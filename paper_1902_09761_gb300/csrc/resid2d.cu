@@ -290,13 +290,18 @@ bool tma_encode_f64(CUtensorMap* map, const void* base, const unsigned long long
 
 bool tma_encode_f64_4d(CUtensorMap* map, const void* base, const unsigned long long dims[4],
                        const unsigned long long strides[3], const unsigned box[4], const char** err) {
+  return tma_encode_4d(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, base, dims, strides, box, err);
+}
+
+bool tma_encode_4d(CUtensorMap* map, CUtensorMapDataType type, const void* base, const unsigned long long dims[4],
+                   const unsigned long long strides[3], const unsigned box[4], const char** err) {
   PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn(err);
   if (!fn) return false;
   const cuuint64_t gd[4] = {dims[0], dims[1], dims[2], dims[3]};
   const cuuint64_t gs[3] = {strides[0], strides[1], strides[2]};
   const cuuint32_t bd[4] = {box[0], box[1], box[2], box[3]};
   const cuuint32_t es[4] = {1, 1, 1, 1};
-  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, const_cast<void*>(base), gd, gs, bd, es,
+  const CUresult r = fn(map, type, 4, const_cast<void*>(base), gd, gs, bd, es,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
@@ -308,8 +313,8 @@ bool tma_encode_f64_4d(CUtensorMap* map, const void* base, const unsigned long l
 
 unsigned long long tma_timeouts() {
   unsigned long long v = 0;
-  if (cudaMemcpyFromSymbol(&v, g_timeouts, sizeof(v)) != cudaSuccess) return 0;
-  return v;
+  if (cudaMemcpyFromSymbol(&v, g_timeouts, sizeof(v)) != cudaSuccess) v = 0;
+  return v + stream3d_timeouts();
 }
 
 namespace {

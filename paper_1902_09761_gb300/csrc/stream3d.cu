@@ -5,9 +5,11 @@
 // streams (x, y) tiles through chunks of z-planes.  The Krylov inner products of A P^{-1}
 // come out of the A passes.
 #include <algorithm>
+#include <cstring>
 
 #include "acc.cuh"
 #include "apfc_internal.cuh"
+#include "tma.cuh"
 
 namespace apfc {
 
@@ -240,8 +242,8 @@ struct OpA3 {
   void* partials = nullptr;
   template <typename Q>
   __device__ void coef(Q&, int) const {}
-  __device__ const cplx<T>* src(int k, int j) const { return x + (2LL * j + k) * pts; }
-  __device__ const cplx<T>* qsrc(int k, int j) const { return du + (2LL * j + k) * pts; }
+  __host__ __device__ const cplx<T>* src(int k, int j) const { return x + (2LL * j + k) * pts; }
+  __host__ __device__ const cplx<T>* qsrc(int k, int j) const { return du + (2LL * j + k) * pts; }
   __device__ void apply(int j, long long p, const N7<T> (&n)[2], const OpCoef& c, const Coef7<T>& q, Acc<T>* acc,
                         const cplx<T>* pv) const {
     const cplx<T> gz = G7(n[0], q), ge = G7(n[1], q);
@@ -277,8 +279,8 @@ struct OpRes3 {
   unsigned long long bytes;
   template <typename Q>
   __device__ void coef(Q&, int) const {}
-  __device__ const cplx<T>* src(int k, int j) const { return x + (2LL * j + k) * pts; }
-  __device__ const cplx<T>* qsrc(int k, int j) const { return b + (2LL * j + k) * pts; }
+  __host__ __device__ const cplx<T>* src(int k, int j) const { return x + (2LL * j + k) * pts; }
+  __host__ __device__ const cplx<T>* qsrc(int k, int j) const { return b + (2LL * j + k) * pts; }
   __device__ void apply(int j, long long p, const N7<T> (&n)[2], const OpCoef& c, const Coef7<T>& q, Acc<T>*,
                         const cplx<T>* pv) const {
     const cplx<T> gz = G7(n[0], q), ge = G7(n[1], q);
@@ -305,8 +307,8 @@ struct OpPcRhs3 {
   unsigned long long bytes;
   template <typename Q>
   __device__ void coef(Q&, int) const {}
-  __device__ const cplx<T>* src(int, int j) const { return beta + 2LL * j * pts; }
-  __device__ const cplx<T>* qsrc(int, int j) const { return beta + (2LL * j + 1) * pts; }
+  __host__ __device__ const cplx<T>* src(int, int j) const { return beta + 2LL * j * pts; }
+  __host__ __device__ const cplx<T>* qsrc(int, int j) const { return beta + (2LL * j + 1) * pts; }
   __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c, const Coef7<T>& q, Acc<T>*,
                         const cplx<T>* pv) const {
     const cplx<T> g = G7(n[0], q);
@@ -339,8 +341,8 @@ struct OpChebFirst3 {
     q.c1 = (T)w.c1[j];
     q.c2 = (T)w.c2[j];
   }
-  __device__ const cplx<T>* src(int, int j) const { return f.at(j); }
-  __device__ const cplx<T>* qsrc(int, int j) const { return fin.chi1.p != nullptr ? fin.b1.at(j) : nullptr; }
+  __host__ __device__ const cplx<T>* src(int, int j) const { return f.at(j); }
+  __host__ __device__ const cplx<T>* qsrc(int, int j) const { return fin.chi1.p != nullptr ? fin.b1.at(j) : nullptr; }
   __device__ void apply(int j, long long p, const N7<T> (&n)[1], const OpCoef& c, const Coef7<T>& q, Acc<T>*,
                         const cplx<T>* pv) const {
     const T it = q.it;
@@ -379,8 +381,8 @@ struct OpChebSweep3 {
     q.c1 = (T)w.c1[j];
     q.c2 = (T)w.c2[j];
   }
-  __device__ const cplx<T>* src(int, int j) const { return Dd.at(j); }
-  __device__ const cplx<T>* qsrc(int k, int j) const {
+  __host__ __device__ const cplx<T>* src(int, int j) const { return Dd.at(j); }
+  __host__ __device__ const cplx<T>* qsrc(int k, int j) const {
     if (k < 2) return k == 0 ? X.at(j) : R.at(j);
     if (fin.chi1.p == nullptr) return nullptr;
     return k == 2 ? fin.b1.at(j) : fin.b2p.at(j);
@@ -415,8 +417,8 @@ struct OpZeta3 {
   unsigned long long bytes;
   template <typename Q>
   __device__ void coef(Q&, int) const {}
-  __device__ const double2* src(int, int j) const { return x + (2LL * j + 1) * pts; }
-  __device__ const double2* qsrc(int, int) const { return nullptr; }
+  __host__ __device__ const double2* src(int, int j) const { return x + (2LL * j + 1) * pts; }
+  __host__ __device__ const double2* qsrc(int, int) const { return nullptr; }
   __device__ void apply(int j, long long p, const N7<double> (&n)[1], const OpCoef& c, const Coef7<double>& q,
                         Acc<double>*, const double2*) const {
     x[2LL * j * pts + p] = G7(n[0], q);
@@ -578,6 +580,218 @@ __global__ void __launch_bounds__(256, OP::MINB) k_stream3d_pair(OpCoef c, OP op
   }
 }
 
+// ---------------------------------------------------------------------------
+// The FP32 passes with every plane moved by the tensor memory accelerator (grids with
+// nx % 64 == 0 and ny % 8 == 0): the same 64 x 8 tiles, two points per thread and
+// 64-plane z-chunks as k_stream3d_pair.  Per plane, one thread issues for every stencil
+// input one box of the tile with its one-point halo (columns x0 - 2 .. x0 + 65, rows
+// y0 - 1 .. y0 + 8) and for every pointwise input one box of the tile, kTAhead planes
+// ahead into a ring of kTBuf planes, completing on that plane's mbarrier.  Periodic
+// x and y: TMA fills halo cells beyond the grid with zeros, so tiles at the boundary
+// also load the wrapped column (x = nx - 2 .. nx - 1, or 0 .. 1) or row (y = ny - 1,
+// or 0) as side boxes, and the stencil takes those neighbours from there.  The z
+// coordinate of every box is wrapped on issue.
+// ---------------------------------------------------------------------------
+constexpr int kTBuf = 4, kTAhead = 2;                 // plane buffers, planes in flight
+constexpr int kTQB = kTAhead + 2;                     // pointwise-input buffers
+constexpr int kMainF = 688;                           // 10 x 68 float2 (5440 B), padded to 5504 B
+constexpr int kRowF = 80, kColF = 32;                 // 68 and 2 x 10 float2, padded to 640 and 256 B
+constexpr int kSlotF = kMainF + 2 * kRowF + 2 * kColF;  // one plane of one stencil input (7296 B)
+constexpr int kQF = kPX * kPY;                        // one plane of one pointwise input (4096 B)
+struct Maps3 {
+  CUtensorMap main[2], row[2], col[2], q[2];
+};
+template <class OP>
+constexpr size_t tma3_smem() {
+  constexpr bool QS = OP::NQ > 0 && OP::NQ <= 2;
+  return sizeof(float2) * ((size_t)OP::NS * kTBuf * kSlotF + (QS ? (size_t)OP::NQ * kTQB * kQF : 0)) + 128;
+}
+
+__device__ unsigned long long g_timeouts3;
+
+template <class OP>
+__global__ void __launch_bounds__(256, OP::MINB) k_stream3d_tma(const __grid_constant__ OpCoef c, OP op,
+                                                                const KScal* act, const __grid_constant__ Maps3 mp) {
+  using T = float;
+  constexpr int NS = OP::NS;
+  constexpr bool QS = OP::NQ > 0 && OP::NQ <= 2;
+  constexpr int NQS = QS ? OP::NQ : 1;
+  extern __shared__ __align__(128) unsigned char dsm_raw[];
+  __shared__ unsigned long long bar[kTBuf];
+  __shared__ int s_fail;
+  float2* sbase = reinterpret_cast<float2*>(dsm_raw + ((128u - (smem_u32(dsm_raw) & 127u)) & 127u));
+  auto mainb = [&](int k, int b) { return sbase + (k * kTBuf + b) * kSlotF; };
+  auto rowb = [&](int k, int b, int side) { return mainb(k, b) + kMainF + side * kRowF; };
+  auto colb = [&](int k, int b, int side) { return mainb(k, b) + kMainF + 2 * kRowF + side * kColF; };
+  float2* qbase = sbase + NS * kTBuf * kSlotF;
+  auto qbuf = [&](int k, int qb) { return qbase + (k * kTQB + qb) * kQF; };
+
+  const int nchunk = (c.nz + kZChunk - 1) / kZChunk;
+  const int j = (int)(blockIdx.z / (unsigned)nchunk);
+  if (act != nullptr && act[j].active == 0) return;
+  const int chunk = (int)(blockIdx.z - (unsigned)j * nchunk);
+  if (c.prof != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && chunk == 0 && threadIdx.x == 0)
+    atomicAdd(c.prof + op.kid, op.bytes);
+  Coef7<T> q = coef7<T>(c, j);
+  op.coef(q, j);
+  Acc<T> acc[OP::ND > 0 ? OP::ND : 1];
+#pragma unroll
+  for (int d = 0; d < (OP::ND > 0 ? OP::ND : 1); ++d) acc[d].zero();
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int x0 = blockIdx.x * kPX, y0 = blockIdx.y * kPY;
+  const int xa = x0 + 2 * tx, y = y0 + ty;
+  const long long plane = (long long)c.nx * c.ny;
+  const int z0 = chunk * kZChunk, z1 = min(c.nz, z0 + kZChunk);
+  // sides of this tile at the periodic boundary (a one-tile-wide grid has both)
+  const bool wl = x0 == 0, wr = x0 + kPX == c.nx, wt = y0 == 0, wb = y0 + kPY == c.ny;
+  const float2* qs[NQS];
+  int nql = 0;
+#pragma unroll
+  for (int k = 0; k < NQS; ++k) {
+    qs[k] = QS ? op.qsrc(k, j) : nullptr;
+    nql += qs[k] != nullptr ? 1 : 0;
+  }
+  const unsigned side_b = (wt ? 544u : 0u) + (wb ? 544u : 0u) + (wl ? 160u : 0u) + (wr ? 160u : 0u);
+  auto issue = [&](int b, int qb, int z) {  // thread 0
+    const int zw = wrapi(z, c.nz);
+    const bool wq = QS && z < z1;
+    fence_proxy_async();
+    mbar_arrive_expect_tx(&bar[b], NS * (5440u + side_b) + (wq ? 4096u * nql : 0u));
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      tma_load_4d(mainb(k, b), &mp.main[k], &bar[b], 2 * (x0 - 2), y0 - 1, zw, j);
+      if (wt) tma_load_4d(rowb(k, b, 0), &mp.row[k], &bar[b], 2 * (x0 - 2), c.ny - 1, zw, j);
+      if (wb) tma_load_4d(rowb(k, b, 1), &mp.row[k], &bar[b], 2 * (x0 - 2), 0, zw, j);
+      if (wl) tma_load_4d(colb(k, b, 0), &mp.col[k], &bar[b], 2 * (c.nx - 2), y0 - 1, zw, j);
+      if (wr) tma_load_4d(colb(k, b, 1), &mp.col[k], &bar[b], 0, y0 - 1, zw, j);
+    }
+    if (wq) {
+#pragma unroll
+      for (int k = 0; k < NQS; ++k)
+        if (qs[k] != nullptr) tma_load_4d(qbuf(k, qb), &mp.q[k], &bar[b], 2 * x0, y0, zw, j);
+    }
+  };
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) tma_prefetch_map(&mp.main[k]);
+    for (int b = 0; b < kTBuf; ++b) mbar_init(&bar[b], 1);
+    fence_mbar_init();
+    s_fail = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int a = 0; a < kTAhead && z0 + a <= z1; ++a) issue(a, a, z0 + a);
+  const bool in0 = xa < c.nx && y < c.ny, in1 = xa + 1 < c.nx && y < c.ny;
+  const long long p0 = (long long)(in0 ? y : 0) * c.nx + (in0 ? xa : 0);
+  const long long p1 = in1 ? p0 + 1 : p0;
+  float2 zm0[NS], zm1[NS];
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const float2* src = op.src(k, j);
+    const long long zo = (long long)wrapi(z0 - 1, c.nz) * plane;
+    zm0[k] = src[zo + p0];
+    zm1[k] = src[zo + p1];
+  }
+  unsigned ph = 0;  // parity of the next wait of each barrier
+  auto wait_buf = [&](int b) {
+    const bool ok = mbar_wait(&bar[b], (ph >> b) & 1u);
+    ph ^= 1u << b;
+    return ok;
+  };
+  if (!wait_buf(0)) s_fail = 1;
+  const int lc = 2 * tx + 2;  // local column of xa: even, so the pair is 16-byte aligned
+  int cb = 0, qc = 0;
+  int z = z0;
+  for (; z < z1; ++z) {
+    const int nb = cb + 1 == kTBuf ? 0 : cb + 1;
+    int fb = cb + kTAhead;
+    if (fb >= kTBuf) fb -= kTBuf;
+    int qf = qc + kTAhead;
+    if (qf >= kTQB) qf -= kTQB;
+    // into buffers that held planes z - 2 (and their inputs), which every thread finished
+    // before the barrier of plane z - 1 that this thread has passed
+    if (threadIdx.x == 0 && z + kTAhead <= z1) issue(fb, qf, z + kTAhead);
+    if (!wait_buf(nb)) s_fail = 1;  // plane z + 1 (the z+ neighbours)
+    __syncthreads();
+    if (s_fail) break;
+    if (in0) {
+      N7<T> n0[NS], n1[NS];
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        const float2* m = mainb(k, cb);
+        const float4 cc = *reinterpret_cast<const float4*>(m + (ty + 1) * kPW + lc);
+        const float2* ymr = (ty == 0 && wt) ? rowb(k, cb, 0) + lc : m + ty * kPW + lc;
+        const float2* ypr = (ty == kPY - 1 && wb) ? rowb(k, cb, 1) + lc : m + (ty + 2) * kPW + lc;
+        const float4 ym = *reinterpret_cast<const float4*>(ymr);
+        const float4 yp = *reinterpret_cast<const float4*>(ypr);
+        const float4 zp = *reinterpret_cast<const float4*>(mainb(k, nb) + (ty + 1) * kPW + lc);
+        const float2 xm = (tx == 0 && wl) ? colb(k, cb, 0)[(ty + 1) * 2 + 1] : m[(ty + 1) * kPW + lc - 1];
+        const float2 xp = (tx == 31 && wr) ? colb(k, cb, 1)[(ty + 1) * 2] : m[(ty + 1) * kPW + lc + 2];
+        n0[k].c = make_float2(cc.x, cc.y);
+        n0[k].xm = xm;
+        n0[k].xp = make_float2(cc.z, cc.w);
+        n0[k].ym = make_float2(ym.x, ym.y);
+        n0[k].yp = make_float2(yp.x, yp.y);
+        n0[k].zm = zm0[k];
+        n0[k].zp = make_float2(zp.x, zp.y);
+        n1[k].c = make_float2(cc.z, cc.w);
+        n1[k].xm = make_float2(cc.x, cc.y);
+        n1[k].xp = xp;
+        n1[k].ym = make_float2(ym.z, ym.w);
+        n1[k].yp = make_float2(yp.z, yp.w);
+        n1[k].zm = zm1[k];
+        n1[k].zp = make_float2(zp.z, zp.w);
+        zm0[k] = n0[k].c;
+        zm1[k] = n1[k].c;
+      }
+      const long long zo = (long long)z * plane;
+      float2 pv0[OP::NQ > 0 ? OP::NQ : 1], pv1[OP::NQ > 0 ? OP::NQ : 1];
+#pragma unroll
+      for (int k = 0; k < OP::NQ; ++k) {
+        if constexpr (QS) {
+          if (qs[k] != nullptr) {
+            const float4 v = *reinterpret_cast<const float4*>(qbuf(k, qc) + ty * kPX + 2 * tx);
+            pv0[k] = make_float2(v.x, v.y);
+            pv1[k] = make_float2(v.z, v.w);
+          } else {
+            pv0[k] = pv1[k] = make_float2(0.f, 0.f);
+          }
+        } else {
+          const float2* g = op.qsrc(k, j);
+          pv0[k] = g != nullptr ? g[zo + p0] : make_float2(0.f, 0.f);
+          pv1[k] = g != nullptr ? g[zo + p1] : make_float2(0.f, 0.f);
+        }
+      }
+      op.apply(j, zo + p0, n0, c, q, acc, pv0);
+      if (in1) op.apply(j, zo + p1, n1, c, q, acc, pv1);
+#pragma unroll
+      for (int d = 0; d < OP::ND; ++d) acc[d].flush();
+    }
+    cb = nb;
+    qc = qc + 1 == kTQB ? 0 : qc + 1;
+  }
+  if (s_fail) {
+    // a plane never arrived: bounded waits for the copies still in flight, then count the
+    // timeout (the host checks the count after the solve) and make the products NaN
+    if (threadIdx.x == 0) {
+      for (int b = 0; b < kTBuf; ++b) (void)wait_buf(b);
+      atomicAdd(&g_timeouts3, 1ull);
+    }
+#pragma unroll
+    for (int d = 0; d < (OP::ND > 0 ? OP::ND : 1); ++d) acc[d].add(make_float2(__int_as_float(0x7fc00000), 0.f),
+                                                                  make_float2(1.f, 0.f));
+  }
+  if constexpr (OP::ND > 0) {
+    const long long npart = (long long)gridDim.x * gridDim.y * nchunk;
+    const long long bid = ((long long)chunk * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+#pragma unroll
+    for (int d = 0; d < OP::ND; ++d) {
+      block_reduce<T>(acc[d]);
+      if (threadIdx.x == 0) acc[d].store(op.partials, (long long)(j * kDotSlots + d) * npart + bid);
+    }
+  }
+}
+
 template <typename T>
 inline dim3 grid_stream3d(const OpCoef& c) {
   return dim3((unsigned)((c.nx + tile_cols3<T>() - 1) / tile_cols3<T>()),
@@ -586,17 +800,68 @@ inline dim3 grid_stream3d(const OpCoef& c) {
 }
 
 
-// FP32 passes take the two-point kernel, FP64 passes the one-point kernel.
+// Tensor maps of the FP32 pass inputs for k_stream3d_tma: every input is a sequence of
+// J plane-major [nz][ny][nx] fields with a constant stride between amplitudes (taken from
+// src(k, 0) and src(k, 1)).  False if the grid or a buffer does not meet the TMA rules
+// (the pass then takes k_stream3d_pair).
+template <class OP>
+bool maps3(const OpCoef& c, const OP& op, Maps3& mp) {
+  if (c.nx % kPX != 0 || c.ny % kPY != 0) return false;
+  auto enc = [&](CUtensorMap* m, const float2* a, const float2* b, unsigned bx, unsigned by) {
+    if (a == nullptr) return true;
+    if ((reinterpret_cast<unsigned long long>(a) & 15ull) != 0) return false;
+    const long long ld = c.J > 1 ? (long long)(b - a) : c.pts;
+    if (ld <= 0 || (ld & 1)) return false;
+    const unsigned long long dims[4] = {2ull * c.nx, (unsigned long long)c.ny, (unsigned long long)c.nz,
+                                        (unsigned long long)c.J};
+    const unsigned long long st[3] = {8ull * c.nx, 8ull * c.nx * c.ny, 8ull * (unsigned long long)ld};
+    const unsigned box[4] = {bx, by, 1, 1};
+    return tma_encode_4d(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, a, dims, st, box, nullptr);
+  };
+  std::memset(&mp, 0, sizeof(mp));
+  for (int k = 0; k < OP::NS; ++k) {
+    const float2* a = op.src(k, 0);
+    const float2* b = op.src(k, c.J > 1 ? 1 : 0);
+    if (!enc(&mp.main[k], a, b, 2 * (kPX + 4), kPY + 2) || !enc(&mp.row[k], a, b, 2 * (kPX + 4), 1) ||
+        !enc(&mp.col[k], a, b, 4, kPY + 2))
+      return false;
+  }
+  if constexpr (OP::NQ > 0 && OP::NQ <= 2) {
+    for (int k = 0; k < OP::NQ; ++k)
+      if (!enc(&mp.q[k], op.qsrc(k, 0), op.qsrc(k, c.J > 1 ? 1 : 0), 2 * kPX, kPY)) return false;
+  }
+  return true;
+}
+
+// FP32 passes take the TMA kernel where the grid allows it, else the two-point kernel;
+// FP64 passes the one-point kernel.
 template <typename T, class OP>
 void stream3d(const OpCoef& c, const OP& op, const KScal* act, cudaStream_t s) {
-  if constexpr (sizeof(T) == 4)
+  if constexpr (sizeof(T) == 4) {
+    Maps3 mp;
+    if (maps3(c, op, mp)) {
+      static bool attr = false;
+      if (!attr) {
+        cudaFuncSetAttribute(k_stream3d_tma<OP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma3_smem<OP>());
+        attr = true;
+      }
+      k_stream3d_tma<OP><<<grid_stream3d<T>(c), 256, tma3_smem<OP>(), s>>>(c, op, act, mp);
+      return;
+    }
     k_stream3d_pair<OP><<<grid_stream3d<T>(c), 256, 0, s>>>(c, op, act);
-  else
+  } else {
     k_stream3d<T, OP><<<grid_stream3d<T>(c), 256, 0, s>>>(c, op, act);
+  }
 }
 
 
 }  // namespace
+
+unsigned long long stream3d_timeouts() {
+  unsigned long long v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_timeouts3, sizeof(v)) != cudaSuccess) return 0;
+  return v;
+}
 
 int stream3d_parts(const OpCoef& c, int elem_bytes) {
   const dim3 g = elem_bytes == 8 ? grid_stream3d<float>(c) : grid_stream3d<double>(c);

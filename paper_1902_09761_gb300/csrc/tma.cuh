@@ -30,6 +30,10 @@ bool tma_encode_f64(CUtensorMap* map, const void* base, const unsigned long long
 bool tma_encode_f64_4d(CUtensorMap* map, const void* base, const unsigned long long dims[4],
                        const unsigned long long strides[3], const unsigned box[4], const char** err);
 
+// Rank-4 tiled tensor map of any element type (box[0] * element bytes a multiple of 16).
+bool tma_encode_4d(CUtensorMap* map, CUtensorMapDataType type, const void* base, const unsigned long long dims[4],
+                   const unsigned long long strides[3], const unsigned box[4], const char** err);
+
 // Number of TMA waits that timed out since the library was loaded (all devices).
 unsigned long long tma_timeouts();
 

@@ -384,3 +384,13 @@ def test_refined_step_on_grids_smaller_than_or_ragged_against_tiles(shape):
     # most of their halo from the periodic image.
     eta0 = inputs.random_amplitudes(3, shape, seed=51, scale=0.15)
     _trajectory_parity("hex", eta0, shape, (1.1, 0.9), 2, dt=0.7, tol=1e-13, precision=A.APFC_FP32_REFINED)
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 128), (12, 8, 64), (70, 24, 64)])
+def test_bcc_refined_on_tma_staged_passes(shape):
+    # FP32 3D passes move their planes by TMA on grids with nx % 64 == 0 and ny % 8 == 0;
+    # the periodic x and y halos of boundary tiles come from side boxes (a one-tile-wide
+    # grid wraps on both sides), z wraps by coordinate; 70 planes span two z-chunks.
+    eta0 = inputs.random_amplitudes(6, shape, seed=61, scale=0.1)
+    _trajectory_parity("bcc", eta0, shape, (1.0, 1.3, 0.9), 2, dt=0.5, tol=1e-13, precision=A.APFC_FP32_REFINED,
+                       cheb_degree=2)
