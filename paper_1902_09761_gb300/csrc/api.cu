@@ -849,6 +849,8 @@ apfc_status step_refined(apfc_ctx* ctx) {
   bool stencil_last = false;
   st = refine_solve(ctx, ctx->b64, ctx->x64, ctx->r64_prev, resid_ready, &total_it, &sweeps, &worst, &stencil_last);
   if (st != APFC_OK) return st;
+  // a TMA wait that gave up leaves its kernel's results incomplete: fail the step
+  if (tma_timeouts() != 0) return fail(ctx, APFC_ECUDA, "a TMA tile load did not complete within its wait limit");
   if (worst == KS_CONVERGED) {
     // after at least one sweep the last check was a stencil residual of the final
     // state, kept in r64_prev: it seeds the next step's initial residual
