@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=4)
     ap.add_argument("--timed-kernel", default="fused_apinv_f32")
     ap.add_argument("--tile", type=int, default=3)
-    ap.add_argument("--tile-t", type=int, default=0, help="tile variant of the t-kernel (-1: same as --tile)")
+    ap.add_argument("--tile-t", type=int, default=1, help="tile variant of the t-kernel (-1: same as --tile)")
     ap.add_argument("--rows", type=int, default=0)
     ap.add_argument("--cheb", type=int, default=1, help="Chebyshev applications per diffusion solve")
     ap.add_argument("--tol-inner", type=float, default=1e-4, help="relative tolerance of each FP32 inner solve")

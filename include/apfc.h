@@ -116,7 +116,7 @@ typedef struct {
   int jacobian;              /* 1: linearise N_j with D_j = dN_j/d eta_j (the
                                 paper's J^j, h^j) in every Picard iteration        */
   int tile_t;                /* variant 0..5 of the fused kernel t = A P^{-1} s of
-                                the merged iteration (-1: same as tile), default 0 */
+                                the merged iteration (-1: same as tile), default 1 */
 } apfc_opts;
 
 typedef struct {
@@ -129,7 +129,7 @@ typedef struct {
 
 /* Fill *o with defaults: FP64, BiCGStab, tol 1e-10, max_iter 500,
  * cheb_degree 1, tau fold, max_refine 10, tol_inner 1e-4, check_every 4, fused 1,
- * tile 3, tile_rows 0 (automatic), picard_iters 1, jacobian 0, tile_t 0. */
+ * tile 3, tile_rows 0 (automatic), picard_iters 1, jacobian 0, tile_t 1. */
 apfc_status apfc_default_opts(apfc_opts* o);
 
 /* Relaxed-solid amplitude phi of a uniform crystal (eta_j = phi for all j):

@@ -1125,7 +1125,7 @@ apfc_status apfc_default_opts(apfc_opts* o) {
   o->tile_rows = 0;
   o->picard_iters = 1;
   o->jacobian = 0;
-  o->tile_t = 0;
+  o->tile_t = 1;
   return APFC_OK;
 }
 

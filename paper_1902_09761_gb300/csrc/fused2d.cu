@@ -553,11 +553,15 @@ struct PipeShape {
   static constexpr int NRAW = LD::NIN + NRE_F + EP::NEP;
   static constexpr int NSLOT = PF > 0 ? PF + 1 : 0;
   static constexpr int NT = NT_;
-  static constexpr size_t ring_elems = (size_t)((NRING - 1) * 4 + DB) * NT;
+  // ring 0 (beta1, the input of stage 1) is the keep ring's first component when KEEP
+  static constexpr int R0 = KEEP ? 0 : 4;
+  static constexpr size_t ring_elems = (size_t)((NRING - 1) * 4 + DB - (4 - R0)) * NT;
   static constexpr size_t keep_elems = KEEP ? (size_t)KD * 2 * NT : 0;
   static constexpr size_t smem = sizeof(cplx<T>) * (ring_elems + keep_elems + (size_t)NSLOT * NRAW * NT);
-  // element offset of ring q
-  __host__ __device__ static constexpr int off(int qi) { return (qi <= QB ? qi * 4 : QB * 4 + DB + (qi - QB - 1) * 4) * NT; }
+  // element offset of ring q (q >= 1 when KEEP)
+  __host__ __device__ static constexpr int off(int qi) {
+    return qi == 0 ? 0 : ((qi <= QB ? qi * 4 : QB * 4 + DB + (qi - QB - 1) * 4) - (4 - R0)) * NT;
+  }
   __host__ __device__ static constexpr int depth(int qi) { return qi == QB ? DB : 4; }
 };
 
@@ -651,7 +655,7 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
     atomicAdd(c.prof + kid, (unsigned long long)fields * (unsigned long long)g.pts * sizeof(cplx<T>));
 
   // zero the rings (garbage in invalid halo columns must stay finite)
-  for (int i = t; i < (int)SH::ring_elems; i += NT) sm[i] = mkc<T>((T)0, (T)0);
+  for (int i = t; i < (int)(SH::ring_elems + SH::keep_elems); i += NT) sm[i] = mkc<T>((T)0, (T)0);
 
   const int x_first = sx * g.wv - S;  // global column of thread 0 (unwrapped)
   int gx = (x_first + t) % g.nx;
@@ -736,7 +740,13 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
   auto nbh = [&](int qi, int lr) {
     if constexpr (HIST) {
       const cplx<T>* rq = ring(qi);
-      const int sc = lr & (SH::depth(qi) - 1);
+      int sc = lr & (SH::depth(qi) - 1);
+      if constexpr (SH::KEEP) {
+        if (qi == 0) {  // beta1 of row lr from the keep ring (component 0 of its slot)
+          rq = keep;
+          sc = (lr % SH::KD) * 2;
+        }
+      }
       Nbh<T> n;
       n.c = H[qi][1];
       n.u = H[qi][2];
@@ -903,7 +913,7 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
           for (int i = 0; i < LD::NIN; ++i) ri[i] = ld.in(i)[p];
           ld.form_in(ri, 1, p, col_own && row_own(rho), b1, b2);
         }
-        ring(0)[(rho & 3) * NT + t] = b1;
+        if constexpr (!SH::KEEP) ring(0)[(rho & 3) * NT + t] = b1;
         if constexpr (SH::KEEP) {
           cplx<T>* kp = keep + (rho % SH::KD) * 2 * NT + t;
           kp[0] = b1;

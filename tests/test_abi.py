@@ -41,7 +41,7 @@ def test_default_opts(lib):
     o = A.apfc_default_opts()
     assert o.precision == A.APFC_FP64 and o.krylov == A.APFC_BICGSTAB
     assert o.tol == 1e-10 and o.max_iter == 500 and o.cheb_degree == 1 and o.tile == 3
-    assert o.picard_iters == 1 and o.jacobian == 0 and o.tile_t == 0
+    assert o.picard_iters == 1 and o.jacobian == 0 and o.tile_t == 1
     assert o.tau_mode == A.APFC_TAU_FOLD and 0 < o.tol_inner < 1 and o.check_every >= 1
 
 
