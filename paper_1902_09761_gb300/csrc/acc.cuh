@@ -39,6 +39,7 @@ struct Acc<double> {
     im += u.x * v.y - u.y * v.x;
   }
   __device__ __forceinline__ void add_run(double2 u, double2 v) { add(u, v); }
+  __device__ __forceinline__ void add_run_self(double2 u) { re += u.x * u.x + u.y * u.y; }  // (u, u) is real
   __device__ __forceinline__ void flush() {}
   __device__ __forceinline__ void shfl_merge(int o) {
     re += __shfl_xor_sync(0xffffffffu, re, o);
@@ -79,6 +80,8 @@ struct Acc<float> {
     run_re = fmaf(u.x, v.x, fmaf(u.y, v.y, run_re));
     run_im = fmaf(u.x, v.y, fmaf(-u.y, v.x, run_im));
   }
+  // (u, u): real, the imaginary run stays zero
+  __device__ __forceinline__ void add_run_self(float2 u) { run_re = fmaf(u.x, u.x, fmaf(u.y, u.y, run_re)); }
   __device__ __forceinline__ void flush() {
     cf_add(re, run_re);
     cf_add(im, run_im);

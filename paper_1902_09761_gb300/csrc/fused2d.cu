@@ -355,8 +355,8 @@ struct EpT5 {
   __device__ void one(long long q, cplx<T> y, cplx<T> s, cplx<T> hh) {
     t[q] = y;
     acc[0].add_run(y, s);
-    acc[1].add_run(y, y);
-    acc[2].add_run(s, s);
+    acc[1].add_run_self(y);
+    acc[2].add_run_self(s);
     acc[3].add_run(hh, s);
     acc[4].add_run(hh, y);
   }
@@ -490,8 +490,8 @@ struct EpT {  // t = y; (t, s), (t, t), (s, s) with s = r - alpha v
   __device__ void one(long long q, cplx<T> y, cplx<T> s) {
     t[q] = y;
     acc[0].add_run(y, s);
-    acc[1].add_run(y, y);
-    acc[2].add_run(s, s);
+    acc[1].add_run_self(y);
+    acc[2].add_run_self(s);
   }
   __device__ void put(const cplx<T>* raw, int st, long long p, cplx<T> y1, cplx<T> y2, cplx<T> k1, cplx<T> k2) {
     if constexpr (KEEP) {
@@ -647,6 +647,9 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
     c1[k] = (T)cw.c1[k][j];
     c2[k] = (T)cw.c2[k][j];
   }
+  // M = 1: x = it f + c1 it f + c2 (f - it D f) = pa1 f + pb1 D f
+  const T pa1 = (T)(c.inv_theta[j] * (1.0 + cw.c1[0][j]) + cw.c2[0][j]);
+  const T pb1 = (T)(-cw.c2[0][j] * c.inv_theta[j]);
   ld.setup(j, act);
   ep.setup(j, act);
 #pragma unroll
@@ -808,7 +811,11 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
         if (valid) {
           const Nbh<T>& n = nb[s];
           const cplx<T> Dd = opD<T>(n, q);
-          if constexpr (k == 0) {
+          if constexpr (M == 1) {
+            // one application of D: the Chebyshev approximant of D^{-1} is the polynomial
+            // pa + pb D (the recurrence below, collapsed); X holds the result, dn = 0
+            X = caxpy(pb1, Dd, cscale(pa1, n.c));
+          } else if constexpr (k == 0) {
             const cplx<T> d0 = cscale(q.it, n.c);
             X = d0;
             R = csub(n.c, cscale(q.it, Dd));
@@ -822,10 +829,10 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
             out1 = dn;
             ring(s)[(lr & 3) * NT + t] = dn;
           } else if constexpr (solve1) {
-            out1 = cadd(X, dn);  // beta2'
+            out1 = M == 1 ? X : cadd(X, dn);  // beta2'
             ring(s)[(lr & (SH::DB - 1)) * NT + t] = out1;
           } else {
-            const cplx<T> chi2 = cadd(X, dn);
+            const cplx<T> chi2 = M == 1 ? X : cadd(X, dn);
             const long long p = ptg(gy_chi);
             cplx<T> b1;
             if constexpr (SH::KEEP) {
