@@ -74,8 +74,11 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="batch: launch the Krylov blocks without graphs")
     ap.add_argument("--no-autotune", action="store_true", help="batch: keep --tile / --rows")
     ap.add_argument("--alone-steps", type=int, default=4, help="batch: steps of each run alone (0: skip)")
+    ap.add_argument("--guess", type=int, default=0, help="initial guess: 0 previous state, 1 extrapolated")
     ap.add_argument("--sub-steps", type=int, default=10,
-                    help="default run: timed steps of the bcc3d and batch sub-records (0: no sub-records)")
+                    help="default run: timed steps of the bcc3d sub-record (0: no sub-records)")
+    ap.add_argument("--sub-steps-batch", type=int, default=100,
+                    help="default run: timed steps of the batch sub-record (its early steps are the slow ones)")
     ap.add_argument("--oracle-workers", type=int, default=0,
                     help="host processes of the oracle legs (0: one per core, as memory allows)")
     return ap.parse_args()
@@ -423,6 +426,7 @@ def run_ours(args):
     opts = A.apfc_default_opts(
         precision=A.APFC_FP32_REFINED, tol=TOL, cheb_degree=args.cheb, tol_inner=args.tol_inner, tile=args.tile,
         tile_rows=args.rows, picard_iters=args.picard, jacobian=int(args.jacobian), tile_t=args.tile_t,
+        guess=args.guess,
     )
     ctx = A.Context(k, A.APFC_LATTICE_HEX2D, prm, (n, n), (H, H), opts, stream=stream.cuda_stream)
     eta_dev = torch.from_numpy(eta0).to(dev)
@@ -574,12 +578,14 @@ def run_ours(args):
     subs = {}
     if args.sub_steps > 0:
         sub_args = argparse.Namespace(**vars(args))
-        sub_args.steps, sub_args.warmup = args.sub_steps, min(args.warmup, 2)
+        sub_args.steps = args.sub_steps
         sub_args.fp64_steps, sub_args.e2e_steps, sub_args.breakdown_steps = 2, 2, 1
         subs["bcc3d"] = run_bcc(sub_args, world, rank, local, sub=True)
-        subs["batch"] = run_batch(sub_args, world, rank, local, sub=True)
+        batch_args = argparse.Namespace(**vars(sub_args))
+        batch_args.steps = args.sub_steps_batch
+        subs["batch"] = run_batch(batch_args, world, rank, local, sub=True)
         adj_args = argparse.Namespace(**vars(sub_args))
-        adj_args.steps, adj_args.warmup = 1, 1
+        adj_args.steps = 1
         subs["adjoint"] = run_adjoint(adj_args, world, rank, local, sub=True)
 
     # --- CPU baseline: the oracle on this host's cores (rank 0, N = 1 only), and the
@@ -821,6 +827,23 @@ def run_batch(args, world=None, rank=None, local=None, sub=False):
     b.step(1.0, max(args.breakdown_steps, 1))
     prof = b.profile_read(args.timed_kernel)
     b.profile_stop()
+
+    # --- per-kernel device time (every launch timed, graphs off while measuring) against
+    # the graph-replayed wall time of the same steps (same start, same iterations) ------
+    nb_steps = max(args.breakdown_steps, 1)
+    ms_nb, _ = timed(nb_steps)
+    reset()
+    b.step(1.0, args.warmup)
+    b.profile_start("all")
+    torch.cuda.synchronize(dev)
+    b.step(1.0, nb_steps)
+    per = {}
+    for name in A.kernel_ids():
+        r = b.profile_read(name)
+        if r["launches"]:
+            per[name] = {"ms_per_step": r["ms"] / nb_steps, "launches_per_step": r["launches"] / nb_steps}
+    b.profile_stop()
+    kernels_ms = sum(v["ms_per_step"] for v in per.values())
     peak, peak_src = measured_peaks()
     avg_ms = prof["ms"] / max(prof["launches"], 1)
     bytes_per_launch = prof["bytes"] / max(prof["launches"], 1)
@@ -919,6 +942,16 @@ def run_batch(args, world=None, rank=None, local=None, sub=False):
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": bytes_step, "d2h_bytes_per_step": bytes_step},
         "gpu_launches_per_step": launches_per_step,
         "gpu_launches": int(launches_per_step * args.steps),
+        "breakdown": {
+            "steps": nb_steps,
+            "ms_per_step_graph": ms_nb / nb_steps,
+            "ms_per_step_kernels": kernels_ms,
+            "launch_gaps_ms_per_step": ms_nb / nb_steps - kernels_ms,
+            "note": "the first steps after the warm-up, twice: graph-replayed as in the timed region "
+                    "(wall time), and with every launch timed (graphs off; kernel device times summed); "
+                    "the difference is the time between kernels that fewer launches could save",
+            "kernels": dict(sorted(per.items(), key=lambda kv: -kv[1]["ms_per_step"])),
+        },
         "clocks": clocks,
     }
     if sub:

@@ -117,7 +117,12 @@ typedef struct {
                                 paper's J^j, h^j) in every Picard iteration        */
   int tile_t;                /* variant 0..5 of the fused kernel t = A P^{-1} s of
                                 the merged iteration (-1: same as tile), default 1 */
+  int guess;                 /* initial guess of each explicit step's solve:
+                                APFC_GUESS_PREV (the previous state, Alg. 1) or
+                                APFC_GUESS_EXTRAP (2 x^n - x^(n-1), after a
+                                completed step of the same dt; else the previous state) */
 } apfc_opts;
+enum { APFC_GUESS_PREV = 0, APFC_GUESS_EXTRAP = 1 };
 
 typedef struct {
   long long steps;           /* steps taken since apfc_set_amplitudes             */

@@ -29,6 +29,7 @@ APFC_TAU_FOLD, APFC_TAU_PLAIN = 0, 1
 APFC_MAX_J = 8
 APFC_BATCH_GRAPH = 1
 APFC_ALU_FMA64, APFC_ALU_FMA32, APFC_ALU_CVT64 = 0, 1, 2
+APFC_GUESS_PREV, APFC_GUESS_EXTRAP = 0, 1
 
 
 class ApfcError(RuntimeError):
@@ -66,6 +67,7 @@ class Opts(C.Structure):
         ("picard_iters", C.c_int),
         ("jacobian", C.c_int),
         ("tile_t", C.c_int),
+        ("guess", C.c_int),
     ]
 
 

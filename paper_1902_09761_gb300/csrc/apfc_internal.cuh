@@ -110,6 +110,7 @@ enum KernelId {
   KID_ADJ_NONLIN,
   KID_ENERGY_GRAD,
   KID_ROTATION,
+  KID_EXTRAP,
   KID_COUNT
 };
 template <typename T>
@@ -285,6 +286,8 @@ void launch_add_to(const cplx<T>* d, double2* x, const OpCoef& c, cudaStream_t s
 void launch_rhs(const double2* x, double2* b, const OpCoef& c, const NonlinTable& nt, cudaStream_t s,
                 const BatchLaunch* bl = nullptr);
 void launch_zeta(double2* x, const OpCoef& c, cudaStream_t s);
+// x <- 2 x - xp, xp <- x over the state block (the extrapolated initial guess)
+void launch_extrapolate(double2* x, double2* xp, const OpCoef& c, cudaStream_t s);
 // complex64 [J][pts] <-> part (0 zeta, 1 eta) of the FP64 state block, rounding to nearest
 void launch_c64_to_part(const float2* src, double2* x, long long pts, int J, int part, cudaStream_t s);
 void launch_part_to_c64(const double2* x, float2* dst, long long pts, int J, int part, cudaStream_t s);

@@ -175,6 +175,10 @@ struct apfc_ctx {
   double2* r64_prev = nullptr;
   bool have_prev = false;
   double prev_dt = 0.0;
+  // APFC_GUESS_EXTRAP: the state before the last completed explicit step of step size xprev_dt
+  double2* x_prev = nullptr;
+  bool have_xprev = false;
+  double xprev_dt = 0.0;
   double* epart = nullptr;
   double* eout = nullptr;
   double* eout_host = nullptr;
@@ -730,14 +734,46 @@ apfc_status status_of(apfc_ctx* ctx, int worst) {
 }
 
 // One step in FP64.
+// APFC_GUESS_EXTRAP, after the right-hand side has been formed from the state: replace the
+// state by the extrapolated guess 2 x^n - x^(n-1) (keeping x^n) when the history is that of
+// a completed step of the same size; else keep x^n as the guess and start the history.
+// Returns whether the guess was extrapolated.
+apfc_status guess_prepare(apfc_ctx* ctx, bool* extrapolated) {
+  *extrapolated = false;
+  if (ctx->opts.guess != APFC_GUESS_EXTRAP) return APFC_OK;
+  const size_t blk = sizeof(double2) * 2ull * ctx->J * ctx->pts;
+  if (!ctx->x_prev) {
+    CK(cudaMalloc(&ctx->x_prev, blk));
+    ctx->have_xprev = false;
+  }
+  if (ctx->have_xprev && ctx->xprev_dt == ctx->coef_dt) {
+    launch_extrapolate(ctx->x64, ctx->x_prev, ctx->coef, ctx->stream);
+    *extrapolated = true;
+  } else {
+    CK(cudaMemcpyAsync(ctx->x_prev, ctx->x64, blk, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  CK(cudaGetLastError());
+  ctx->have_xprev = false;  // valid again once this step has converged
+  return APFC_OK;
+}
+void guess_done(apfc_ctx* ctx, int worst) {
+  if (ctx->opts.guess == APFC_GUESS_EXTRAP && worst == KS_CONVERGED) {
+    ctx->have_xprev = true;
+    ctx->xprev_dt = ctx->coef_dt;
+  }
+}
+
 apfc_status step_fp64(apfc_ctx* ctx) {
   ctx->have_prev = false;
   apfc_status st = alloc_work<double>(ctx, ctx->w64);
   if (st != APFC_OK) return st;
   launch_rhs(ctx->x64, ctx->b64, ctx->coef, ctx->nt, ctx->stream);
+  bool ex = false;
+  if ((st = guess_prepare(ctx, &ex)) != APFC_OK) return st;
   int iters = 0, worst = 0;
   st = krylov<double>(ctx, ctx->w64, ctx->b64, ctx->x64, ctx->opts.tol, ctx->opts.max_iter, &iters, &worst);
   if (st != APFC_OK) return st;
+  guess_done(ctx, worst);
   ctx->stats.iters_last = iters;
   ctx->stats.iters_total += iters;
   ctx->stats.refine_last = 0;
@@ -845,10 +881,14 @@ apfc_status step_refined(apfc_ctx* ctx) {
     launch_rhs(ctx->x64, ctx->b64, ctx->coef, ctx->nt, s);
   }
   ctx->have_prev = false;
+  bool ex = false;
+  if ((st = guess_prepare(ctx, &ex)) != APFC_OK) return st;
+  if (ex) resid_ready = false;  // the pointwise r0 belongs to the guess x^n: take a stencil residual
   int total_it = 0, sweeps = 0, worst = KS_CONVERGED;
   bool stencil_last = false;
   st = refine_solve(ctx, ctx->b64, ctx->x64, ctx->r64_prev, resid_ready, &total_it, &sweeps, &worst, &stencil_last);
   if (st != APFC_OK) return st;
+  guess_done(ctx, worst);
   // a TMA wait that gave up leaves its kernel's results incomplete: fail the step
   if (tma_timeouts() != 0) return fail(ctx, APFC_ECUDA, "a TMA tile load did not complete within its wait limit");
   if (worst == KS_CONVERGED) {
@@ -956,6 +996,7 @@ apfc_status load_state(apfc_ctx* ctx, const double2* eta) {
   launch_zeta(ctx->x64, ctx->coef, ctx->stream);
   CK(cudaGetLastError());
   ctx->have_prev = false;
+  ctx->have_xprev = false;
   return APFC_OK;
 }
 
@@ -1034,6 +1075,7 @@ apfc_status step_picard(apfc_ctx* ctx) {
   apfc_status st = block_to_field(ctx, ctx->eta_step, ctx->x64, 1);
   if (st != APFC_OK) return st;
   ctx->have_prev = false;
+  ctx->have_xprev = false;
   int total = 0;
   for (int k = 0; k < ctx->opts.picard_iters; ++k) {
     // b and kap D from eta^(k-1), the eta-parts of the state; solve from x^(k-1)
@@ -1081,6 +1123,7 @@ bool apfc::valid_opts(const apfc_opts& o, std::string& e) {
   else if (o.tile_rows < 0 || o.tile_rows > 65536) e = "tile_rows";
   else if (o.picard_iters < 1 || o.picard_iters > 100) e = "picard_iters";
   else if (o.jacobian != 0 && o.jacobian != 1) e = "jacobian";
+  else if (o.guess != APFC_GUESS_PREV && o.guess != APFC_GUESS_EXTRAP) e = "guess";
   else if (!(o.tol > 0.0) || !(o.tol_inner > 0.0) || !(o.tol_inner < 1.0)) e = "tol";
   else return true;
   e = "invalid option: " + e;
@@ -1126,6 +1169,7 @@ apfc_status apfc_default_opts(apfc_opts* o) {
   o->picard_iters = 1;
   o->jacobian = 0;
   o->tile_t = 1;
+  o->guess = APFC_GUESS_PREV;
   return APFC_OK;
 }
 
@@ -1237,6 +1281,7 @@ apfc_status apfc_set_opts(apfc_ctx* ctx, const apfc_opts* opts) {
   ctx->opts = *opts;
   ctx->coef_dt = -1.0;  // tau_mode may have changed
   ctx->have_prev = false;
+  ctx->have_xprev = false;
   return APFC_OK;
 }
 
@@ -1246,6 +1291,7 @@ apfc_status apfc_set_amplitudes(apfc_ctx* ctx, const void* eta, int where, int d
   ctx->failed = false;
   ctx->err.clear();
   ctx->have_prev = false;
+  ctx->have_xprev = false;
   apfc_status st = copy_part(ctx, const_cast<void*>(eta), where, 1, true, dtype);
   if (st != APFC_OK) return st;
   std::string e;
@@ -1315,6 +1361,7 @@ void apfc_destroy(apfc_ctx* ctx) {
   cudaFree(ctx->b64);
   cudaFree(ctx->b64_prev);
   cudaFree(ctx->r64_prev);
+  cudaFree(ctx->x_prev);
   cudaFree(ctx->epart);
   cudaFree(ctx->eout);
   if (ctx->eout_host) cudaFreeHost(ctx->eout_host);
@@ -1339,7 +1386,7 @@ void apfc_destroy(apfc_ctx* ctx) {
 static const char* kKernelNames[KID_COUNT] = {
     "apply_A", "residual", "pc_rhs", "cheb_zero", "cheb_first", "cheb_sweep", "pc_final", "p_update", "s_update",
     "r_update", "add_to", "dots", "finalize", "rhs", "zeta", "residual_refine", "energy", "fused_apinv",
-    "fused_pinv", "bicg_update", "fused_apinv_t", "adj_nonlin", "energy_grad", "rotation"};
+    "fused_pinv", "bicg_update", "fused_apinv_t", "adj_nonlin", "energy_grad", "rotation", "extrapolate"};
 
 int apfc_kernel_count(void) { return 2 * KID_COUNT; }
 
@@ -1452,6 +1499,7 @@ apfc_status apfc_set_params(apfc_ctx* ctx, const apfc_params* p) {
   ctx->et = et;
   ctx->coef_dt = -1.0;  // a and the preconditioner's shift depend on dB
   ctx->have_prev = false;
+  ctx->have_xprev = false;
   ctx->r_ready = false;
   return APFC_OK;
 }

@@ -395,6 +395,7 @@ bool valid_batch_opts(const apfc_opts& o, std::string& e) {
   if (o.precision != APFC_FP32_REFINED) e = "batched runs use precision APFC_FP32_REFINED";
   else if (o.fused != 1) e = "batched runs use the fused pipeline (fused = 1)";
   else if (o.picard_iters != 1 || o.jacobian != 0) e = "batched runs take the explicit step (picard_iters 1, jacobian 0)";
+  else if (o.guess != APFC_GUESS_PREV) e = "batched runs start each solve from the previous state (guess 0)";
   else if (o.cheb_degree < 1 || o.cheb_degree > fused2d_max_degree((int)sizeof(float2))) e = "cheb_degree";
   else return true;
   return false;

@@ -1297,6 +1297,21 @@ void launch_part_to_c64(const double2* x, float2* dst, long long pts, int J, int
   k_part_to_c64<<<4 * kDotBlocks, kThreads, 0, s>>>(x, dst, pts, J, part);
 }
 
+// Linear extrapolation of the state history: x <- 2 x - xp (the next solve's initial
+// guess) and xp <- x (the state it came from), elementwise over n complex values.
+__global__ void k_extrapolate(double2* __restrict__ x, double2* __restrict__ xp, long long n, OpCoef c) {
+  prof_add(c, KID_EXTRAP, (unsigned long long)n * 4 * sizeof(double2));
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double2 a = x[i], b = xp[i];
+    xp[i] = a;
+    x[i] = make_double2(fma(2.0, a.x, -b.x), fma(2.0, a.y, -b.y));
+  }
+}
+void launch_extrapolate(double2* x, double2* xp, const OpCoef& c, cudaStream_t s) {
+  ProfScope ps_(KID_EXTRAP, s);
+  k_extrapolate<<<4 * kDotBlocks, kThreads, 0, s>>>(x, xp, 2LL * c.J * c.pts, c);
+}
+
 void launch_zeta(double2* x, const OpCoef& c, cudaStream_t s) {
   if (c.dim == 3) {
     launch3d_zeta(x, c, s);

@@ -76,6 +76,7 @@ def test_uniform_amplitude_matches_closed_forms(lib):
         "jac2",
         "tile_t5",
         "tile_t_neg2",
+        "guess2",
     ],
 )
 def test_init_rejects_invalid_arguments_before_touching_cuda(lib, case):
@@ -118,6 +119,8 @@ def test_init_rejects_invalid_arguments_before_touching_cuda(lib, case):
         opts.tile_t = 6
     elif case == "tile_t_neg2":
         opts.tile_t = -2
+    elif case == "guess2":
+        opts.guess = 2
     import ctypes as C
 
     h_ = C.c_void_p()
@@ -154,7 +157,7 @@ def test_binding_fails_loudly_without_library(tmp_path):
         A._lib = saved
 
 
-@pytest.mark.parametrize("case", ["nruns0", "nx2", "bcc", "fp64", "unfused", "flags", "hx0", "cheb5", "picard", "jac"])
+@pytest.mark.parametrize("case", ["nruns0", "nx2", "bcc", "fp64", "unfused", "flags", "hx0", "cheb5", "picard", "jac", "guess"])
 def test_batch_init_rejects_invalid_arguments_before_touching_cuda(lib, case):
     import ctypes as C
 
@@ -182,6 +185,8 @@ def test_batch_init_rejects_invalid_arguments_before_touching_cuda(lib, case):
         opts.picard_iters = 2
     elif case == "jac":
         opts.jacobian = 1
+    elif case == "guess":
+        opts.guess = A.APFC_GUESS_EXTRAP
     L = A.make_lattice(k, kind)
     h_ = C.c_void_p()
     st = lib.apfc_batch_init(

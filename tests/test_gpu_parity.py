@@ -17,7 +17,7 @@ import oracle as O
 from paper_1902_09761_gb300 import apfc as A
 from paper_1902_09761_gb300 import inputs
 
-from gpu_common import H2, H3, P, context, ensure_built, rel_l2, rel_l2_per_amp
+from gpu_common import H2, H3, P, context, ensure_built, lattice, rel_l2, rel_l2_per_amp
 
 pytestmark = pytest.mark.gpu
 
@@ -394,3 +394,16 @@ def test_bcc_refined_on_tma_staged_passes(shape):
     eta0 = inputs.random_amplitudes(6, shape, seed=61, scale=0.1)
     _trajectory_parity("bcc", eta0, shape, (1.0, 1.3, 0.9), 2, dt=0.5, tol=1e-13, precision=A.APFC_FP32_REFINED,
                        cheb_degree=2)
+
+
+@pytest.mark.parametrize("prec", [A.APFC_FP64, A.APFC_FP32_REFINED])
+@pytest.mark.parametrize("kind,shape,h", [("hex", (64, 80), H2), ("bcc", (12, 16, 64), (1.0, 1.3, 0.9))])
+def test_extrapolated_initial_guess_same_trajectory(prec, kind, shape, h):
+    # APFC_GUESS_EXTRAP starts each solve from 2 x^n - x^(n-1): the converged steps are the
+    # oracle's (the solution of the block system is unique); 4 steps cover the first step
+    # (no history), the extrapolated ones and, in the refined path, the stencil residual
+    # that replaces the pointwise initial residual.
+    L, _ = lattice(kind)
+    phi = O.uniform_solid_hex(P) if kind == "hex" else O.uniform_solid_bcc(P)
+    eta0 = inputs.single_grain(L.k, phi, shape, h, 0.3 * min(shape) * min(h), 6.0, seed=71, noise=1e-3)
+    _trajectory_parity(kind, eta0, shape, h, 4, dt=1.0, tol=1e-13, precision=prec, guess=A.APFC_GUESS_EXTRAP)
