@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libapfc.so")
-SOURCES = ["kernels.cu", "stream3d.cu", "reduce.cu", "fused2d.cu", "api.cu", "batch.cu", "noalloc.cu", "probe.cu", "resid2d.cu"]
+SOURCES = ["fused2d_v.cu", "fused2d_t.cu", "fused2d.cu", "kernels.cu", "stream3d.cu", "reduce.cu", "api.cu", "batch.cu", "noalloc.cu", "probe.cu", "resid2d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

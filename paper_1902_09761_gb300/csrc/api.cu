@@ -949,10 +949,16 @@ apfc_status copy_part(apfc_ctx* ctx, void* plain, int where, int part, bool to_s
     if (!ctx->stage) CK(cudaMalloc(&ctx->stage, row * ctx->J));
     CK(cudaMemcpyAsync(ctx->stage, plain, row * ctx->J, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpy2DAsync(base, 2 * row, ctx->stage, row, row, ctx->J, cudaMemcpyDeviceToDevice, ctx->stream));
-  } else if (to_state)
+  } else if (to_state) {
     CK(cudaMemcpy2DAsync(base, 2 * row, plain, row, row, ctx->J, k, ctx->stream));
-  else
+  } else if (where == APFC_HOST) {
+    // the same on the way out: the strided copy on the device, then one contiguous copy
+    if (!ctx->stage) CK(cudaMalloc(&ctx->stage, row * ctx->J));
+    CK(cudaMemcpy2DAsync(ctx->stage, row, base, 2 * row, row, ctx->J, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(plain, ctx->stage, row * ctx->J, cudaMemcpyDeviceToHost, ctx->stream));
+  } else {
     CK(cudaMemcpy2DAsync(plain, row, base, 2 * row, row, ctx->J, k, ctx->stream));
+  }
   CK(cudaStreamSynchronize(ctx->stream));
   return APFC_OK;
 }

@@ -10,6 +10,7 @@
 #include "acc.cuh"
 #include "apfc_internal.cuh"
 #include "dfloat.cuh"
+#include "resid_point.cuh"
 
 namespace apfc {
 
@@ -529,21 +530,7 @@ __global__ void k_residual_refine(const double2* __restrict__ b, const double2* 
 // where a relative error of 1e-5 in the norm is immaterial); ||b||^2 is not
 // recomputed: b is fixed within a step.
 constexpr int kRTX = 32, kRTY = 8;
-__device__ __forceinline__ float4 pdf_pack(PDF v) { return make_float4(v.h.x, v.l.x, v.h.y, v.l.y); }
-__device__ __forceinline__ PDF pdf_unpack(float4 v) { return PDF{make_float2(v.x, v.z), make_float2(v.y, v.w)}; }
-__device__ __forceinline__ PDF pdf_swap(PDF v) {  // (re, im) -> (im, re)
-  return PDF{make_float2(v.h.y, v.h.x), make_float2(v.l.y, v.l.x)};
-}
-// lane coefficients (s0 c, s1 c) of a double-float c
-struct PCoef {
-  float2 h, l;
-};
-__device__ __forceinline__ PCoef pcoef(double c, float s0, float s1) {
-  const DF d = split_d(c);
-  return PCoef{make_float2(s0 * d.h, s1 * d.h), make_float2(s0 * d.l, s1 * d.l)};
-}
-
-__global__ void __launch_bounds__(256) k_residual_refine2d(const double2* __restrict__ b,
+__global__ void __launch_bounds__(256, 3) k_residual_refine2d(const double2* __restrict__ b,
                                                            const double2* __restrict__ x, float2* __restrict__ r32,
                                                            double2* __restrict__ r64, double2* __restrict__ partials,
                                                            const __grid_constant__ OpCoef c, const RunGeom* rg) {
@@ -568,18 +555,8 @@ __global__ void __launch_bounds__(256) k_residual_refine2d(const double2* __rest
   const long long o = 2LL * j * pts;
   const double2* z = x + o;
   const double2* e = z + pts;
-  // G_h: c0 at the centre, ih_d on the d-neighbours (both lanes), and the advection
-  // i (k_d / h_d)(u(+d) - u(-d)) as lane coefficients on swapped (im, re) values
-  const PCoef g0 = pcoef(c.c0, 1.f, 1.f), gx = pcoef(c.ih2[0], 1.f, 1.f), gy = pcoef(c.ih2[1], 1.f, 1.f);
-  const PCoef axp = pcoef(c.kh[j][0], -1.f, 1.f), axm = pcoef(c.kh[j][0], 1.f, -1.f);
-  const PCoef ayp = pcoef(c.kh[j][1], -1.f, 1.f), aym = pcoef(c.kh[j][1], 1.f, -1.f);
-  // -kt G_h for the (2,1) block
-  const double kt = c.kt[j];
-  const PCoef k0 = pcoef(kt * c.c0, -1.f, -1.f), kx = pcoef(kt * c.ih2[0], -1.f, -1.f);
-  const PCoef ky = pcoef(kt * c.ih2[1], -1.f, -1.f);
-  const PCoef kxp = pcoef(kt * c.kh[j][0], 1.f, -1.f), kxm = pcoef(kt * c.kh[j][0], -1.f, 1.f);
-  const PCoef kyp = pcoef(kt * c.kh[j][1], 1.f, -1.f), kym = pcoef(kt * c.kh[j][1], -1.f, 1.f);
-  PCoef ma = pcoef(c.a[j], -1.f, -1.f);
+  const ResidCoef<2> q = resid_coef<2>(c, j);
+  LaneC ma = lane_c(c.a[j], -1.f, -1.f);
   const int tx_count = (nx + kRTX - 1) / kRTX, ntiles = tx_count * ((ny + kRTY - 1) / kRTY);
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   float rr = 0.f;
@@ -600,40 +577,14 @@ __global__ void __launch_bounds__(256) k_residual_refine2d(const double2* __rest
     const int xx = x0 + tx, yy = y0 + ty;
     if (xx >= nx || yy >= ny) continue;
     const long long pc = (long long)yy * nx + xx;
-    const PDF zc = pdf_unpack(sz[ty + 1][tx + 1]), zl = pdf_unpack(sz[ty + 1][tx]), zr = pdf_unpack(sz[ty + 1][tx + 2]);
-    const PDF zu = pdf_unpack(sz[ty][tx + 1]), zd = pdf_unpack(sz[ty + 2][tx + 1]);
-    const PDF ec = pdf_unpack(se[ty + 1][tx + 1]), el = pdf_unpack(se[ty + 1][tx]), er = pdf_unpack(se[ty + 1][tx + 2]);
-    const PDF eu = pdf_unpack(se[ty][tx + 1]), ed = pdf_unpack(se[ty + 2][tx + 1]);
-    // r1 = b1 - zeta + G_h eta
-    PAcc a1;
-    a1.init(pdf_split(b[o + pc]));
-    a1.add(zc, -1.f);
-    a1.fma(g0.h, g0.l, ec);
-    a1.fma(gx.h, gx.l, el);
-    a1.fma(gx.h, gx.l, er);
-    a1.fma(gy.h, gy.l, eu);
-    a1.fma(gy.h, gy.l, ed);
-    a1.fma(axp.h, axp.l, pdf_swap(er));
-    a1.fma(axm.h, axm.l, pdf_swap(el));
-    a1.fma(ayp.h, ayp.l, pdf_swap(ed));
-    a1.fma(aym.h, aym.l, pdf_swap(eu));
-    // r2 = b2 - kt G_h zeta - a eta
-    if (c.jd != nullptr) ma = pcoef(a_at(c, j, pc), -1.f, -1.f);
-    PAcc a2;
-    a2.init(pdf_split(b[o + pts + pc]));
-    a2.fma(k0.h, k0.l, zc);
-    a2.fma(kx.h, kx.l, zl);
-    a2.fma(kx.h, kx.l, zr);
-    a2.fma(ky.h, ky.l, zu);
-    a2.fma(ky.h, ky.l, zd);
-    a2.fma(kxp.h, kxp.l, pdf_swap(zr));
-    a2.fma(kxm.h, kxm.l, pdf_swap(zl));
-    a2.fma(kyp.h, kyp.l, pdf_swap(zd));
-    a2.fma(kym.h, kym.l, pdf_swap(zu));
-    a2.fma(ma.h, ma.l, ec);
+    const PDF zn[2][2] = {{pdf_unpack(sz[ty + 1][tx]), pdf_unpack(sz[ty + 1][tx + 2])},
+                          {pdf_unpack(sz[ty][tx + 1]), pdf_unpack(sz[ty + 2][tx + 1])}};
+    const PDF en[2][2] = {{pdf_unpack(se[ty + 1][tx]), pdf_unpack(se[ty + 1][tx + 2])},
+                          {pdf_unpack(se[ty][tx + 1]), pdf_unpack(se[ty + 2][tx + 1])}};
+    if (c.jd != nullptr) ma = lane_c(a_at(c, j, pc), -1.f, -1.f);
     float2 f1, l1, f2, l2;
-    a1.result(f1, l1);
-    a2.result(f2, l2);
+    resid_point<2>(q, ma, pdf_split(b[o + pc]), pdf_split(b[o + pts + pc]), pdf_unpack(sz[ty + 1][tx + 1]),
+                   pdf_unpack(se[ty + 1][tx + 1]), zn, en, f1, l1, f2, l2);
     r32[o + pc] = f1;
     r32[o + pts + pc] = f2;
     if (r64 != nullptr) {

@@ -16,12 +16,13 @@
 // stage's mbarrier.  TMA fills boxes beyond the grid with zeros; on tiles at the
 // grid's edge those cells are re-read from the periodic image with plain loads.
 // The raw doubles of a tile are split once into FP32 pairs in shared memory,
-// then every thread evaluates its point's residual.
+// then every thread evaluates its point's residual (resid_point.cuh).
 #include <cstring>
 #include <mutex>
 
 #include "apfc_internal.cuh"
 #include "dfloat.cuh"
+#include "resid_point.cuh"
 #include "tma.cuh"
 
 #include <cudaTypedefs.h>
@@ -50,16 +51,6 @@ constexpr size_t resid_smem() {
   return kStages * RLay<DIM>::stage + 2 * kHalo * sizeof(float4) + 128;
 }
 
-__device__ __forceinline__ float4 pack4(PDF v) { return make_float4(v.h.x, v.l.x, v.h.y, v.l.y); }
-__device__ __forceinline__ PDF unpack4(float4 v) { return PDF{make_float2(v.x, v.z), make_float2(v.y, v.w)}; }
-__device__ __forceinline__ PDF swap_ri(PDF v) { return PDF{make_float2(v.h.y, v.h.x), make_float2(v.l.y, v.l.x)}; }
-struct LaneC {
-  float2 h, l;
-};
-__device__ __forceinline__ LaneC lane_c(double c, float s0, float s1) {
-  const DF d = split_d(c);
-  return LaneC{make_float2(s0 * d.h, s1 * d.h), make_float2(s0 * d.l, s1 * d.l)};
-}
 
 // Grid (blocks per amplitude, J); each block walks the tiles blockIdx.x + k gridDim.x of
 // its amplitude (tiles: 32 x 8 points of one plane, planes slowest).  mx: the state block
@@ -67,7 +58,7 @@ __device__ __forceinline__ LaneC lane_c(double c, float s0, float s1) {
 // mxc: the same tensor with a 32 x 8 box (3D only: planes z -+ 1); mb: the right-hand
 // side block with a 32 x 8 box.
 template <int DIM>
-__global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ CUtensorMap mx,
+__global__ void __launch_bounds__(256, DIM == 2 ? 3 : 2) k_resid_tma(const __grid_constant__ CUtensorMap mx,
                                                    const __grid_constant__ CUtensorMap mxc,
                                                    const __grid_constant__ CUtensorMap mb,
                                                    const double2* __restrict__ x, float2* __restrict__ r32,
@@ -87,20 +78,7 @@ __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ CUten
   if (c.prof != nullptr && blockIdx.x == 0 && t == 0)
     atomicAdd(c.prof + KID_RESID_REFINE,
               (unsigned long long)pts * (4 * sizeof(double2) + 2 * sizeof(float2) + (r64 ? 2 * sizeof(double2) : 0)));
-  // G_h: c0 at the centre, 1/h_d^2 on the d-neighbours, the advection i (k_d/h_d)(u(+d) - u(-d))
-  // as lane coefficients on (im, re)-swapped values; the (2,1) block carries -kt G_h
-  const double kt = c.kt[j];
-  const LaneC g0 = lane_c(c.c0, 1.f, 1.f), k0 = lane_c(kt * c.c0, -1.f, -1.f);
-  LaneC gl[DIM], gp[DIM], gm[DIM], kl[DIM], kp[DIM], km[DIM];
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    gl[d] = lane_c(c.ih2[d], 1.f, 1.f);
-    gp[d] = lane_c(c.kh[j][d], -1.f, 1.f);
-    gm[d] = lane_c(c.kh[j][d], 1.f, -1.f);
-    kl[d] = lane_c(kt * c.ih2[d], -1.f, -1.f);
-    kp[d] = lane_c(kt * c.kh[j][d], 1.f, -1.f);
-    km[d] = lane_c(kt * c.kh[j][d], -1.f, 1.f);
-  }
+  const ResidCoef<DIM> q = resid_coef<DIM>(c, j);
   LaneC ma = lane_c(c.a[j], -1.f, -1.f);
 
   const int txc = (nx + TX - 1) / TX, tpl = txc * ((ny + TY - 1) / TY), ntiles = tpl * nz;
@@ -171,8 +149,8 @@ __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ CUten
     __syncthreads();
     if (s_fail) break;
     for (int i = t; i < kHalo; i += blockDim.x) {
-      sz[i] = pack4(pdf_split(rz[i]));
-      se[i] = pack4(pdf_split(re[i]));
+      sz[i] = pdf_pack(pdf_split(rz[i]));
+      se[i] = pdf_pack(pdf_split(re[i]));
     }
     __syncthreads();
     // the stage is consumed: refill it two tiles ahead
@@ -183,55 +161,24 @@ __global__ void __launch_bounds__(256) k_resid_tma(const __grid_constant__ CUten
     const int cc = (ty + 1) * HX + tx + 1;
     // neighbours of the point per dimension: (-, +)
     PDF zn_[DIM][2], en_[DIM][2];
-    zn_[0][0] = unpack4(sz[cc - 1]);
-    zn_[0][1] = unpack4(sz[cc + 1]);
-    zn_[1][0] = unpack4(sz[cc - HX]);
-    zn_[1][1] = unpack4(sz[cc + HX]);
-    en_[0][0] = unpack4(se[cc - 1]);
-    en_[0][1] = unpack4(se[cc + 1]);
-    en_[1][0] = unpack4(se[cc - HX]);
-    en_[1][1] = unpack4(se[cc + HX]);
+    zn_[0][0] = pdf_unpack(sz[cc - 1]);
+    zn_[0][1] = pdf_unpack(sz[cc + 1]);
+    zn_[1][0] = pdf_unpack(sz[cc - HX]);
+    zn_[1][1] = pdf_unpack(sz[cc + HX]);
+    en_[0][0] = pdf_unpack(se[cc - 1]);
+    en_[0][1] = pdf_unpack(se[cc + 1]);
+    en_[1][0] = pdf_unpack(se[cc - HX]);
+    en_[1][1] = pdf_unpack(se[cc + HX]);
     if constexpr (DIM == 3) {
       zn_[2][0] = pdf_split(zmv);
       zn_[2][1] = pdf_split(zpv);
       en_[2][0] = pdf_split(emv);
       en_[2][1] = pdf_split(epv);
     }
-    const PDF zc = unpack4(sz[cc]), ec = unpack4(se[cc]);
-    PAcc a1;  // r1 = b1 - zeta + G_h eta
-    a1.init(pdf_split(b1v));
-    a1.add(zc, -1.f);
-    // term order: centre, Laplacian neighbours, advection (the batched kernel's order, so
-    // that a run alone and in a batch round alike)
-    a1.fma(g0.h, g0.l, ec);
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      a1.fma(gl[d].h, gl[d].l, en_[d][0]);
-      a1.fma(gl[d].h, gl[d].l, en_[d][1]);
-    }
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      a1.fma(gp[d].h, gp[d].l, swap_ri(en_[d][1]));
-      a1.fma(gm[d].h, gm[d].l, swap_ri(en_[d][0]));
-    }
     if (c.jd != nullptr) ma = lane_c(a_at(c, j, pc), -1.f, -1.f);
-    PAcc a2;  // r2 = b2 - kt G_h zeta - a eta
-    a2.init(pdf_split(b2v));
-    a2.fma(k0.h, k0.l, zc);
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      a2.fma(kl[d].h, kl[d].l, zn_[d][0]);
-      a2.fma(kl[d].h, kl[d].l, zn_[d][1]);
-    }
-#pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-      a2.fma(kp[d].h, kp[d].l, swap_ri(zn_[d][1]));
-      a2.fma(km[d].h, km[d].l, swap_ri(zn_[d][0]));
-    }
-    a2.fma(ma.h, ma.l, ec);
     float2 f1, l1, f2, l2;
-    a1.result(f1, l1);
-    a2.result(f2, l2);
+    resid_point<DIM>(q, ma, pdf_split(b1v), pdf_split(b2v), pdf_unpack(sz[cc]), pdf_unpack(se[cc]), zn_, en_, f1, l1,
+                     f2, l2);
     r32[o + pc] = f1;
     r32[o + pts + pc] = f2;
     if (r64 != nullptr) {

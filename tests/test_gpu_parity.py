@@ -288,10 +288,11 @@ def test_full_size_bcc_256_one_step(prec, bcc_256_reference):
 
 
 @pytest.mark.parametrize("tile", [0, 1, 2, 3, 4, 5])
-@pytest.mark.parametrize("rows", [32, 128])
+@pytest.mark.parametrize("rows", [32, 128, 179])
 def test_tile_variants_parity(tile, rows):
     # Every FP32 variant of the fused pipeline (strip width, look-ahead depth, rows per
-    # segment) gives the same converged step: 530 columns span 3-5 strips, 300 rows 3-10 segments.
+    # segment) gives the same converged step: 530 columns span 3-5 strips, 300 rows 2-10 segments
+    # (rows 179: a segment height that is not a power of two).
     eta0 = inputs.random_amplitudes(3, (300, 530), seed=8, scale=0.1)
     _trajectory_parity(
         "hex", eta0, (300, 530), (1.2, 0.8), 2, dt=0.5, tol=1e-13, precision=A.APFC_FP32_REFINED, cheb_degree=1,
