@@ -167,6 +167,7 @@ struct PipeGeom {
 // ---------------------------------------------------------------------------
 template <typename T>
 struct LoadPlain {
+  static constexpr bool PHASED = false;
   static constexpr int NIN = 2, NRE = 1;
   const cplx<T>* b;
   long long pts;
@@ -189,6 +190,7 @@ struct LoadPlain {
 // p = r + beta (p_old - omega v_old), written to p_new at the points this block owns.
 template <typename T>
 struct LoadP {
+  static constexpr bool PHASED = true;
   static constexpr int NIN = 6, NRE = 3;
   const cplx<T>* r;
   const cplx<T>* po;
@@ -233,6 +235,7 @@ struct LoadP {
 // s = r - alpha v.
 template <typename T>
 struct LoadS {
+  static constexpr bool PHASED = false;
   static constexpr int NIN = 4, NRE = 2;
   const cplx<T>* r;
   const cplx<T>* v;
@@ -264,6 +267,7 @@ struct LoadS {
 // store r', p' and apply the previous iteration's update u += alpha p + omega (r - alpha v).
 template <typename T>
 struct LoadPR {
+  static constexpr bool PHASED = true;
   static constexpr int NIN = 10, NRE = 4;
   const cplx<T>* r;
   const cplx<T>* v;
@@ -574,7 +578,15 @@ struct PipeShape {
   static constexpr int KD = 2 * S + 1;
   static constexpr int NRE_F = KEEP ? 0 : LD::NRE;  // re-form operands fetched per row
   static constexpr int NRAW = LD::NIN + NRE_F + EP::NEP;
-  static constexpr int NSLOT = PF > 0 ? PF + 1 : 0;
+  // The v-kernels (FP32, one Chebyshev application, A) run their row loop in phases of
+  // PERIOD = 9 rows, a multiple of every ring depth (stage rings 3, beta2' 3, keep 9, a
+  // staging ring of 3), so that every ring slot is a constant in each copy of the unrolled
+  // body: no slot or address arithmetic (measured 25.2 -> 24.8 ms per 4096^2 step).  The
+  // t-kernel, bound by instruction issue, lost more to the nine-fold body than it saved
+  // (13.9 -> 15.0 ms; with 3-row phases it needed 120 registers), so loaders opt in.
+  static constexpr bool PHASED = HIST && M == 1 && WITH_A && (PF == 1 || PF == 2) && LD::PHASED;
+  static constexpr int PERIOD = PHASED ? 9 : 1;
+  static constexpr int NSLOT = PF > 0 ? (PHASED ? 3 : PF + 1) : 0;
   static constexpr int NT = NT_;
   // ring 0 (beta1, the input of stage 1) is the keep ring's first component when KEEP
   static constexpr int R0 = KEEP ? 0 : RD;
@@ -586,6 +598,8 @@ struct PipeShape {
     return (qi == 0 ? 0 : (qi <= QB ? R0 + (qi - 1) * RD : R0 + (QB - 1) * RD + DB + (qi - QB - 1) * RD)) * NT;
   }
   __host__ __device__ static constexpr int depth(int qi) { return qi == QB ? DB : RD; }
+  static_assert(!PHASED || (PERIOD % RD == 0 && PERIOD % DB == 0 && PERIOD % KD == 0 && PERIOD % NSLOT == 0),
+                "the phase period must be a multiple of every ring depth");
 };
 
 template <typename T, int NT>
@@ -706,10 +720,10 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
   // rows of the next fetch, starting with the prologue's local time 0
   int fy_in = grow(0), fy_re = grow(-2 * SH::SCHI), fy_ep = grow(-2 * SH::SEP);
 
-  // asynchronous fetch of everything local time tf will consume (rows fy_*)
-  auto issue = [&](int tf) {
+  // asynchronous fetch of everything local time tf will consume (rows fy_*) into staging slot ns
+  auto issue = [&](int tf, int ns) {
     if constexpr (PF > 0) {
-      cplx<T>* slot = stage_buf + (size_t)(tf % SH::NSLOT) * NRAW * NT + t;
+      cplx<T>* slot = stage_buf + (size_t)ns * NRAW * NT + t;
       if (tf < rows_in) {
         const long long p = ptg(fy_in);
 #pragma unroll
@@ -788,20 +802,32 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
 
   if constexpr (PF > 0) {
 #pragma unroll
-    for (int tf = 0; tf < PF; ++tf) issue(tf);
+    for (int tf = 0; tf < PF; ++tf) issue(tf, tf % SH::NSLOT);
   }
   __syncthreads();
 
   // rho mod the depths of the rings, the beta2' ring and the keep ring
   int rm = 0, rq = 0, rk = 0;
-#pragma unroll(sizeof(T) == 4 ? 2 : 1)
-  for (int rho = 0; rho < steps; ++rho) {
+  constexpr int PER = SH::PERIOD;
+  // Phased pipelines: the outer loop takes PER rows at a time and the inner one is fully
+  // unrolled, so rm, rq, rk and the staging slots are constants in every copy of the body.
+#pragma unroll(PER == 1 && sizeof(T) == 4 ? 2 : 1)
+  for (int rho0 = 0; rho0 < steps; rho0 += PER) {
+#pragma unroll
+  for (int ph = 0; ph < PER; ++ph) {
+    const int rho = rho0 + ph;
+    if (PER > 1 && rho >= steps) break;
+    if constexpr (PER > 1) {
+      rm = ph % SH::RD;
+      rq = ph % SH::DB;
+      rk = ph % SH::KD;
+    }
     const cplx<T>* raw = nullptr;
     int st = 1;
     if constexpr (PF > 0) {
-      issue(rho + PF);
+      issue(rho + PF, PER > 1 ? (ph + PF) % SH::NSLOT : (rho + PF) % SH::NSLOT);
       cp_wait<PF>();
-      raw = stage_buf + (size_t)(rho % SH::NSLOT) * NRAW * NT + t;
+      raw = stage_buf + (size_t)(PER > 1 ? ph % SH::NSLOT : rho % SH::NSLOT) * NRAW * NT + t;
       st = NT;
     }
     Nbh<T> nb[S + 2];
@@ -978,6 +1004,7 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
       b2dl[0] = b2;
     }
     if constexpr (EP::NDOT > 0) {
+      // fold the plain FP32 runs into the compensated sums every 8 rows
       if ((rho & 7) == 7) {
 #pragma unroll
         for (int k = 0; k < EP::NDOT; ++k) ep.acc[k].flush();
@@ -986,10 +1013,13 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
     gy_in = wrap_inc(gy_in, g.ny);
     gy_chi = wrap_inc(gy_chi, g.ny);
     gy_ep = wrap_inc(gy_ep, g.ny);
-    rm = wrap_inc(rm, SH::RD);
-    rq = wrap_inc(rq, SH::DB);
-    rk = wrap_inc(rk, SH::KD);
+    if constexpr (PER == 1) {
+      rm = wrap_inc(rm, SH::RD);
+      rq = wrap_inc(rq, SH::DB);
+      rk = wrap_inc(rk, SH::KD);
+    }
     __syncthreads();
+  }
   }
   if constexpr (PF > 0) cp_wait<0>();
 
