@@ -7,6 +7,7 @@
 #pragma once
 
 #include "apfc_internal.cuh"
+#include "dfloat.cuh"
 
 namespace apfc {
 
@@ -63,11 +64,14 @@ struct Acc<double> {
 template <>
 struct Acc<float> {
   CF re, im;
-  float run_re, run_im;  // short plain FP32 runs, folded into (re, im) by flush()
+  // short plain FP32 runs, folded into (re, im) by flush(): packed lanes
+  // rr = sum (u.x v.x, u.y v.y) and ri = sum (u.x v.y, u.y v.x), so that one product
+  // term costs two packed FMAs (re = rr.x + rr.y, im = ri.x - ri.y)
+  float2 rr, ri;
   __device__ __forceinline__ void zero() {
     re = CF{0.f, 0.f};
     im = CF{0.f, 0.f};
-    run_re = run_im = 0.f;
+    rr = ri = make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ void add(float2 u, float2 v) {
     cf_add(re, u.x * v.x + u.y * v.y);
@@ -77,15 +81,15 @@ struct Acc<float> {
   // FP32 and each run total enters the compensated sum (callers flush every
   // few products and before reducing).
   __device__ __forceinline__ void add_run(float2 u, float2 v) {
-    run_re = fmaf(u.x, v.x, fmaf(u.y, v.y, run_re));
-    run_im = fmaf(u.x, v.y, fmaf(-u.y, v.x, run_im));
+    rr = p_fma(u, v, rr);
+    ri = p_fma(u, make_float2(v.y, v.x), ri);
   }
   // (u, u): real, the imaginary run stays zero
-  __device__ __forceinline__ void add_run_self(float2 u) { run_re = fmaf(u.x, u.x, fmaf(u.y, u.y, run_re)); }
+  __device__ __forceinline__ void add_run_self(float2 u) { rr = p_fma(u, u, rr); }
   __device__ __forceinline__ void flush() {
-    cf_add(re, run_re);
-    cf_add(im, run_im);
-    run_re = run_im = 0.f;
+    cf_add(re, rr.x + rr.y);
+    cf_add(im, ri.x - ri.y);
+    rr = ri = make_float2(0.f, 0.f);
   }
   __device__ __forceinline__ void shfl_merge(int o) {
     CF r{__shfl_xor_sync(0xffffffffu, re.s, o), __shfl_xor_sync(0xffffffffu, re.c, o)};
