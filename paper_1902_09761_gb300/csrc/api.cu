@@ -1336,6 +1336,79 @@ apfc_status apfc_step(apfc_ctx* ctx, double dt, int n) {
   return APFC_OK;
 }
 
+apfc_status apfc_autotune(apfc_ctx* ctx, double dt, int* tile_rows, double* ms_per_step) {
+  if (!ctx) return APFC_EINVAL;
+  if (ctx->failed) return APFC_ESTATE;
+  if (!ctx->has_state) return fail(ctx, APFC_ESTATE, "no amplitudes set");
+  std::string e;
+  if (!build_coef(ctx, dt, e)) return fail(ctx, APFC_EINVAL, e);
+  const bool tunable = ctx->dim == 2 && ctx->opts.precision == APFC_FP32_REFINED &&
+                       use_fused(ctx, (int)sizeof(float2)) && ctx->opts.picard_iters == 1 && ctx->opts.jacobian == 0;
+  if (!tunable) {
+    if (tile_rows) *tile_rows = fused_rows(ctx);
+    if (ms_per_step) *ms_per_step = 0.0;
+    return APFC_OK;
+  }
+  // candidate heights: every ceil(ny / s) from 96 to 256 rows, and the automatic one
+  const int ny = ctx->grid.n[1];
+  const int saved_rows = ctx->opts.tile_rows;
+  std::vector<int> cand;
+  ctx->opts.tile_rows = 0;
+  cand.push_back(fused_rows(ctx));
+  for (int s = std::max(1, (ny + 255) / 256); s <= std::max(1, ny / 96); ++s) {
+    const int rows = (ny + s - 1) / s;
+    if (rows >= 32 && rows <= ny && std::find(cand.begin(), cand.end(), rows) == cand.end()) cand.push_back(rows);
+  }
+  const size_t blk = sizeof(double2) * 2 * (size_t)ctx->J * (size_t)ctx->pts;
+  double2* saved = nullptr;
+  if (cudaMalloc(&saved, blk) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->opts.tile_rows = saved_rows;
+    ctx->err = "autotune: no room for a copy of the state";  // the context stays usable
+    return APFC_ENOMEM;
+  }
+  const apfc_stats_t stats = ctx->stats;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  apfc_status st = APFC_OK;
+  int best_rows = cand[0];
+  double best = 1e300;
+  auto restore = [&]() -> cudaError_t {
+    ctx->have_prev = false;
+    ctx->have_xprev = false;
+    return cudaMemcpyAsync(ctx->x64, saved, blk, cudaMemcpyDeviceToDevice, ctx->stream);
+  };
+  if (cudaMemcpyAsync(saved, ctx->x64, blk, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    st = fail(ctx, APFC_ECUDA, "autotune: copy or event creation failed");
+  for (int i = -1; i < (int)cand.size() && st == APFC_OK; ++i) {  // i = -1: untimed warm-up
+    ctx->opts.tile_rows = cand[i < 0 ? 0 : i];
+    if (restore() != cudaSuccess || cudaEventRecord(e0, ctx->stream) != cudaSuccess) {
+      st = fail(ctx, APFC_ECUDA, "autotune: restore failed");
+      break;
+    }
+    if ((st = one_step(ctx)) != APFC_OK) break;
+    float ms = 0.f;
+    if (cudaEventRecord(e1, ctx->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+      st = fail(ctx, APFC_ECUDA, "autotune: timing failed");
+      break;
+    }
+    if (i >= 0 && ms < best) best = ms, best_rows = cand[i];
+  }
+  if (restore() != cudaSuccess && st == APFC_OK) st = fail(ctx, APFC_ECUDA, "autotune: restore failed");
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && st == APFC_OK)
+    st = fail(ctx, APFC_ECUDA, "autotune: synchronisation failed");
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(saved);
+  ctx->stats = stats;
+  ctx->opts.tile_rows = st == APFC_OK ? best_rows : saved_rows;
+  if (st != APFC_OK) return st;
+  if (tile_rows) *tile_rows = best_rows;
+  if (ms_per_step) *ms_per_step = best;
+  return APFC_OK;
+}
+
 apfc_status apfc_energy(apfc_ctx* ctx, double* F) {
   if (!ctx || !F) return APFC_EINVAL;
   if (!ctx->has_state) return fail(ctx, APFC_ESTATE, "no amplitudes set");

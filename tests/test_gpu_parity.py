@@ -408,3 +408,40 @@ def test_extrapolated_initial_guess_same_trajectory(prec, kind, shape, h):
     phi = O.uniform_solid_hex(P) if kind == "hex" else O.uniform_solid_bcc(P)
     eta0 = inputs.single_grain(L.k, phi, shape, h, 0.3 * min(shape) * min(h), 6.0, seed=71, noise=1e-3)
     _trajectory_parity(kind, eta0, shape, h, 4, dt=1.0, tol=1e-13, precision=prec, guess=A.APFC_GUESS_EXTRAP)
+
+
+def test_autotune_keeps_state_and_continues_the_trajectory():
+    # apfc_autotune times one step per candidate segment height from the same state and
+    # restores it: amplitudes, zeta and statistics unchanged, the chosen height one of the
+    # candidates (ceil(ny / s) within 96..256 rows, or the automatic one), and the next
+    # steps still the oracle's
+    shape, h, dt = (300, 530), (1.2, 0.8), 0.5
+    eta0 = inputs.random_amplitudes(3, shape, seed=21, scale=0.1)
+    ctx, L = context("hex", shape, h, precision=A.APFC_FP32_REFINED, tol=1e-13)
+    ctx.set_amplitudes(eta0)
+    ctx.step(dt, 1)
+    eta1, zeta1, st1 = ctx.get_amplitudes(), ctx.get_zeta(), ctx.stats()
+    tuned = ctx.autotune(dt)
+    assert np.array_equal(ctx.get_amplitudes(), eta1) and np.array_equal(ctx.get_zeta(), zeta1)
+    assert ctx.stats() == st1
+    ny = shape[1]
+    allowed = {-(-ny // s) for s in range(max(1, -(-ny // 256)), max(1, ny // 96) + 1)}
+    assert tuned["tile_rows"] in allowed | {128, 64, 32} and tuned["ms_per_step"] > 0
+    eta_o = eta1.copy()
+    for _ in range(2):
+        ctx.step(dt, 1)
+        eta_o, zeta_o = O.step(eta_o, dt, P, L, h)
+        assert max(rel_l2_per_amp(ctx.get_amplitudes(), eta_o)) <= 1e-10
+        assert max(rel_l2_per_amp(ctx.get_zeta(), zeta_o)) <= 1e-10
+    ctx.close()
+
+
+def test_autotune_is_a_no_op_off_the_fused_refined_path():
+    eta0 = inputs.random_amplitudes(3, (64, 64), seed=22, scale=0.1)
+    ctx, _ = context("hex", (64, 64), H2, precision=A.APFC_FP64, tol=1e-12)
+    ctx.set_amplitudes(eta0)
+    before = ctx.get_amplitudes()
+    tuned = ctx.autotune(1.0)
+    assert tuned["ms_per_step"] == 0.0 and np.array_equal(ctx.get_amplitudes(), before)
+    assert ctx.stats()["steps"] == 0
+    ctx.close()
