@@ -439,7 +439,7 @@ def run_ours(args):
         ctx.set_amplitudes(eta_dev)
         ctx.step(1.0, args.warmup)
         tuned = ctx.autotune(1.0)
-        opts.tile_rows = tuned["tile_rows"]
+        opts.tile_rows, opts.tile_t = tuned["tile_rows"], tuned["tile_t"]
 
     def timed_steps(nsteps, sampler=None, timed_kernel=None):
         ctx.set_amplitudes(eta_dev)

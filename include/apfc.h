@@ -181,16 +181,19 @@ apfc_status apfc_get_zeta(apfc_ctx* ctx, void* zeta, int where);
  * ENOCONV / ENAN if a solve failed (the state then holds the last iterate). */
 apfc_status apfc_step(apfc_ctx* ctx, double dt, int n);
 
-/* Choose the rows per segment of the fused 2D kernels (opts.tile_rows) by timing:
- * from the current state, one step of size dt per candidate height (every height
- * ceil(ny / s) between 96 and 256 rows, and the automatic one), each from the same
- * state, after one untimed step; keeps the fastest in the context's options.  The
- * state and the statistics are restored (the next step takes a stencil initial
- * residual).  Only the FP32-refined fused path on 2D grids has a choice to make:
- * other configurations return APFC_OK with their options unchanged.  tile_rows and
- * ms_per_step (nullable) receive the chosen height and its step time.  Allocates
- * one copy of the state block for the duration of the call; ENOMEM if it cannot. */
-apfc_status apfc_autotune(apfc_ctx* ctx, double dt, int* tile_rows, double* ms_per_step);
+/* Choose the rows per segment of the fused 2D kernels (opts.tile_rows) and the
+ * variant of the merged iteration's t-kernel (opts.tile_t) by timing: from the
+ * current state, one step of size dt per candidate, each from the same state,
+ * after one untimed step; first every height ceil(ny / s) between 96 and 256 rows
+ * and the automatic one (t-kernel variant as set), then every t-kernel variant at
+ * the best height.  Keeps the fastest in the context's options.  The state and the
+ * statistics are restored (the next step takes a stencil initial residual).  Only
+ * the FP32-refined fused path on 2D grids has a choice to make: other
+ * configurations return APFC_OK with their options unchanged and ms_per_step 0.
+ * tile_rows, tile_t and ms_per_step (nullable) receive the choice and its step
+ * time.  Allocates one copy of the state block for the duration of the call;
+ * ENOMEM (context still usable) if it cannot. */
+apfc_status apfc_autotune(apfc_ctx* ctx, double dt, int* tile_rows, int* tile_t, double* ms_per_step);
 
 /* Discrete free energy (Eq. energyamplitude with the gradient term scaled so
  * that its Wirtinger derivative is the flow's Bx G_h^2 eta_j):

@@ -98,7 +98,9 @@ EXPORTS = {
     "apfc_get_amplitudes": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int]),
     "apfc_get_zeta": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "apfc_step": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
-    "apfc_autotune": (C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "apfc_autotune": (
+        C.c_int, [C.c_void_p, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    ),
     "apfc_energy": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
     "apfc_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "apfc_last_error": (C.c_char_p, [C.c_void_p]),
@@ -344,10 +346,11 @@ class Context:
         return load().apfc_step(self._h, float(dt), int(n))
 
     def autotune(self, dt: float) -> dict:
-        """apfc_autotune: time one step per candidate segment height, keep the fastest."""
-        rows, ms = C.c_int(), C.c_double()
-        _check(load().apfc_autotune(self._h, float(dt), C.byref(rows), C.byref(ms)), self._h)
-        return {"tile_rows": rows.value, "ms_per_step": ms.value}
+        """apfc_autotune: time one step per candidate segment height and t-kernel variant,
+        keep the fastest."""
+        rows, tt, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(load().apfc_autotune(self._h, float(dt), C.byref(rows), C.byref(tt), C.byref(ms)), self._h)
+        return {"tile_rows": rows.value, "tile_t": tt.value, "ms_per_step": ms.value}
 
     def energy(self) -> float:
         F = C.c_double()

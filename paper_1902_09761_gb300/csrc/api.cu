@@ -1336,7 +1336,7 @@ apfc_status apfc_step(apfc_ctx* ctx, double dt, int n) {
   return APFC_OK;
 }
 
-apfc_status apfc_autotune(apfc_ctx* ctx, double dt, int* tile_rows, double* ms_per_step) {
+apfc_status apfc_autotune(apfc_ctx* ctx, double dt, int* tile_rows, int* tile_t, double* ms_per_step) {
   if (!ctx) return APFC_EINVAL;
   if (ctx->failed) return APFC_ESTATE;
   if (!ctx->has_state) return fail(ctx, APFC_ESTATE, "no amplitudes set");
@@ -1346,12 +1346,13 @@ apfc_status apfc_autotune(apfc_ctx* ctx, double dt, int* tile_rows, double* ms_p
                        use_fused(ctx, (int)sizeof(float2)) && ctx->opts.picard_iters == 1 && ctx->opts.jacobian == 0;
   if (!tunable) {
     if (tile_rows) *tile_rows = fused_rows(ctx);
+    if (tile_t) *tile_t = ctx->opts.tile_t;
     if (ms_per_step) *ms_per_step = 0.0;
     return APFC_OK;
   }
   // candidate heights: every ceil(ny / s) from 96 to 256 rows, and the automatic one
   const int ny = ctx->grid.n[1];
-  const int saved_rows = ctx->opts.tile_rows;
+  const int saved_rows = ctx->opts.tile_rows, saved_tt = ctx->opts.tile_t;
   std::vector<int> cand;
   ctx->opts.tile_rows = 0;
   cand.push_back(fused_rows(ctx));
@@ -1364,13 +1365,14 @@ apfc_status apfc_autotune(apfc_ctx* ctx, double dt, int* tile_rows, double* ms_p
   if (cudaMalloc(&saved, blk) != cudaSuccess) {
     cudaGetLastError();
     ctx->opts.tile_rows = saved_rows;
+    ctx->opts.tile_t = saved_tt;
     ctx->err = "autotune: no room for a copy of the state";  // the context stays usable
     return APFC_ENOMEM;
   }
   const apfc_stats_t stats = ctx->stats;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   apfc_status st = APFC_OK;
-  int best_rows = cand[0];
+  int best_rows = cand[0], best_tt = saved_tt;
   double best = 1e300;
   auto restore = [&]() -> cudaError_t {
     ctx->have_prev = false;
@@ -1380,8 +1382,13 @@ apfc_status apfc_autotune(apfc_ctx* ctx, double dt, int* tile_rows, double* ms_p
   if (cudaMemcpyAsync(saved, ctx->x64, blk, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess ||
       cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     st = fail(ctx, APFC_ECUDA, "autotune: copy or event creation failed");
-  for (int i = -1; i < (int)cand.size() && st == APFC_OK; ++i) {  // i = -1: untimed warm-up
-    ctx->opts.tile_rows = cand[i < 0 ? 0 : i];
+  // pass 1: the heights with the t-kernel variant as set; pass 2: every t-kernel variant at
+  // the best height
+  const int nrows = (int)cand.size(), ntt = fused2d_tiles();
+  for (int i = -1; i < nrows + ntt && st == APFC_OK; ++i) {  // i = -1: untimed warm-up
+    if (i >= nrows && i - nrows == (saved_tt < 0 ? ctx->opts.tile : saved_tt)) continue;  // timed in pass 1
+    ctx->opts.tile_rows = i < nrows ? cand[i < 0 ? 0 : i] : best_rows;
+    ctx->opts.tile_t = i < nrows ? saved_tt : i - nrows;
     if (restore() != cudaSuccess || cudaEventRecord(e0, ctx->stream) != cudaSuccess) {
       st = fail(ctx, APFC_ECUDA, "autotune: restore failed");
       break;
@@ -1393,7 +1400,7 @@ apfc_status apfc_autotune(apfc_ctx* ctx, double dt, int* tile_rows, double* ms_p
       st = fail(ctx, APFC_ECUDA, "autotune: timing failed");
       break;
     }
-    if (i >= 0 && ms < best) best = ms, best_rows = cand[i];
+    if (i >= 0 && ms < best) best = ms, best_rows = ctx->opts.tile_rows, best_tt = ctx->opts.tile_t;
   }
   if (restore() != cudaSuccess && st == APFC_OK) st = fail(ctx, APFC_ECUDA, "autotune: restore failed");
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess && st == APFC_OK)
@@ -1403,8 +1410,10 @@ apfc_status apfc_autotune(apfc_ctx* ctx, double dt, int* tile_rows, double* ms_p
   cudaFree(saved);
   ctx->stats = stats;
   ctx->opts.tile_rows = st == APFC_OK ? best_rows : saved_rows;
+  ctx->opts.tile_t = st == APFC_OK ? best_tt : saved_tt;
   if (st != APFC_OK) return st;
   if (tile_rows) *tile_rows = best_rows;
+  if (tile_t) *tile_t = best_tt;
   if (ms_per_step) *ms_per_step = best;
   return APFC_OK;
 }

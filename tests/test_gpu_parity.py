@@ -427,6 +427,7 @@ def test_autotune_keeps_state_and_continues_the_trajectory():
     ny = shape[1]
     allowed = {-(-ny // s) for s in range(max(1, -(-ny // 256)), max(1, ny // 96) + 1)}
     assert tuned["tile_rows"] in allowed | {128, 64, 32} and tuned["ms_per_step"] > 0
+    assert 0 <= tuned["tile_t"] < 6
     eta_o = eta1.copy()
     for _ in range(2):
         ctx.step(dt, 1)
