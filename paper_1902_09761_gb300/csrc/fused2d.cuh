@@ -167,7 +167,7 @@ struct PipeGeom {
 // ---------------------------------------------------------------------------
 template <typename T>
 struct LoadPlain {
-  static constexpr bool PHASED = false;
+  static constexpr int PERIOD = 1;  // row-loop phase (see PipeShape)
   static constexpr int NIN = 2, NRE = 1;
   const cplx<T>* b;
   long long pts;
@@ -190,7 +190,7 @@ struct LoadPlain {
 // p = r + beta (p_old - omega v_old), written to p_new at the points this block owns.
 template <typename T>
 struct LoadP {
-  static constexpr bool PHASED = true;
+  static constexpr int PERIOD = 9;
   static constexpr int NIN = 6, NRE = 3;
   const cplx<T>* r;
   const cplx<T>* po;
@@ -235,7 +235,7 @@ struct LoadP {
 // s = r - alpha v.
 template <typename T>
 struct LoadS {
-  static constexpr bool PHASED = false;
+  static constexpr int PERIOD = 1;
   static constexpr int NIN = 4, NRE = 2;
   const cplx<T>* r;
   const cplx<T>* v;
@@ -267,7 +267,7 @@ struct LoadS {
 // store r', p' and apply the previous iteration's update u += alpha p + omega (r - alpha v).
 template <typename T>
 struct LoadPR {
-  static constexpr bool PHASED = true;
+  static constexpr int PERIOD = 9;
   static constexpr int NIN = 10, NRE = 4;
   const cplx<T>* r;
   const cplx<T>* v;
@@ -578,14 +578,16 @@ struct PipeShape {
   static constexpr int KD = 2 * S + 1;
   static constexpr int NRE_F = KEEP ? 0 : LD::NRE;  // re-form operands fetched per row
   static constexpr int NRAW = LD::NIN + NRE_F + EP::NEP;
-  // The v-kernels (FP32, one Chebyshev application, A) run their row loop in phases of
-  // PERIOD = 9 rows, a multiple of every ring depth (stage rings 3, beta2' 3, keep 9, a
-  // staging ring of 3), so that every ring slot is a constant in each copy of the unrolled
-  // body: no slot or address arithmetic (measured 25.2 -> 24.8 ms per 4096^2 step).  The
-  // t-kernel, bound by instruction issue, lost more to the nine-fold body than it saved
-  // (13.9 -> 15.0 ms; with 3-row phases it needed 120 registers), so loaders opt in.
-  static constexpr bool PHASED = HIST && M == 1 && WITH_A && (PF == 1 || PF == 2) && LD::PHASED;
-  static constexpr int PERIOD = PHASED ? 9 : 1;
+  // FP32 pipelines with one Chebyshev application and A run their row loop in phases of
+  // PERIOD rows (the loader's choice), fully unrolled, so that the slots of every ring whose
+  // depth divides PERIOD are constants in each copy of the body: no slot or address
+  // arithmetic.  v-kernels take 9 rows (stage rings 3, beta2' 3, keep 9, staging 3; measured
+  // 25.2 -> 24.8 ms per 4096^2 step).  The t-kernel, bound by instruction issue, loses more to
+  // the longer body than it saves (9-row phases 13.9 -> 15.0 ms, 3-row phases with the
+  // keep-ring slot a counter 12.9 -> 15.2 ms), so it keeps the plain loop.
+  static constexpr bool PHASED = HIST && M == 1 && WITH_A && (PF == 1 || PF == 2) && LD::PERIOD > 1;
+  static constexpr int PERIOD = PHASED ? LD::PERIOD : 1;
+  static constexpr bool KEEP_CONST = PERIOD % KD == 0;  // keep-ring slot a constant too
   static constexpr int NSLOT = PF > 0 ? (PHASED ? 3 : PF + 1) : 0;
   static constexpr int NT = NT_;
   // ring 0 (beta1, the input of stage 1) is the keep ring's first component when KEEP
@@ -598,8 +600,8 @@ struct PipeShape {
     return (qi == 0 ? 0 : (qi <= QB ? R0 + (qi - 1) * RD : R0 + (QB - 1) * RD + DB + (qi - QB - 1) * RD)) * NT;
   }
   __host__ __device__ static constexpr int depth(int qi) { return qi == QB ? DB : RD; }
-  static_assert(!PHASED || (PERIOD % RD == 0 && PERIOD % DB == 0 && PERIOD % KD == 0 && PERIOD % NSLOT == 0),
-                "the phase period must be a multiple of every ring depth");
+  static_assert(!PHASED || (PERIOD % RD == 0 && PERIOD % DB == 0 && PERIOD % NSLOT == 0),
+                "the phase period must be a multiple of the stage, beta2' and staging ring depths");
 };
 
 template <typename T, int NT>
@@ -820,7 +822,7 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
     if constexpr (PER > 1) {
       rm = ph % SH::RD;
       rq = ph % SH::DB;
-      rk = ph % SH::KD;
+      if constexpr (SH::KEEP_CONST) rk = ph % SH::KD;
     }
     const cplx<T>* raw = nullptr;
     int st = 1;
@@ -1016,8 +1018,8 @@ __global__ void __launch_bounds__(NT_) k_pipe2d(OpCoef c, ChebAll cw, PipeGeom g
     if constexpr (PER == 1) {
       rm = wrap_inc(rm, SH::RD);
       rq = wrap_inc(rq, SH::DB);
-      rk = wrap_inc(rk, SH::KD);
     }
+    if constexpr (!SH::KEEP_CONST) rk = wrap_inc(rk, SH::KD);
     __syncthreads();
   }
   }
