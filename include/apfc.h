@@ -108,9 +108,11 @@ typedef struct {
   double tol_inner;          /* relative tolerance of each FP32 inner solve         */
   int tile;                  /* fused 2D kernel variant 0..5 (columns per block and
                                 rows of look-ahead), default 3                     */
-  int tile_rows;             /* rows per block of the fused 2D kernels; 0 (default):
-                                the tallest of 128, 64, 32 rows that gives the first
-                                fused kernel's launch >= 1.5 blocks per SM         */
+  int tile_rows;             /* rows per block of the fused 2D kernels of the Krylov
+                                iteration; 0 (default): the tallest of 128, 64, 32
+                                rows that gives the first fused kernel's launch
+                                >= 1.5 blocks per SM (x += P^{-1} u always takes
+                                that automatic height)                             */
   int picard_iters;          /* K of Alg. 1: Picard iterations per step, 1..100;
                                 1 (default) with jacobian 0 is the explicit step   */
   int jacobian;              /* 1: linearise N_j with D_j = dN_j/d eta_j (the

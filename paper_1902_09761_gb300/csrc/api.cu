@@ -539,12 +539,17 @@ void apply_pinv(apfc_ctx* ctx, Work<T>& w, const cplx<T>* beta, cplx<T>* chi, co
   launch_pc_final<T>(beta, CFieldRef<T>{b2p.p, P}, chi, c, act, ctx->stream);
 }
 
-// Rows per block segment of the fused kernels.  tile_rows 0: the tallest of 128, 64 and
-// 32 rows that still gives the v-kernel's launch about 1.5 blocks per SM (taller segments
-// waste less on the 3S-row pipeline fill, but on small grids they leave SMs idle:
-// 512^2 runs twice as fast with 32-row segments as with 128).
+// Rows per block segment of the merged iteration's fused kernels: opts.tile_rows, else the
+// automatic height, the tallest of 128, 64 and 32 rows that still gives the v-kernel's
+// launch about 1.5 blocks per SM (taller segments waste less on the 3S-row pipeline fill,
+// but on small grids they leave SMs idle: 512^2 runs twice as fast with 32-row segments as
+// with 128).  x += P^{-1} u always takes the automatic height.
+int fused_rows_auto(const apfc_ctx* ctx);
 int fused_rows(const apfc_ctx* ctx) {
   if (ctx->opts.tile_rows > 0) return ctx->opts.tile_rows;
+  return fused_rows_auto(ctx);
+}
+int fused_rows_auto(const apfc_ctx* ctx) {
   const int elem = ctx->opts.precision == APFC_FP64 ? (int)sizeof(double2) : (int)sizeof(float2);
   const int m = std::max(1, ctx->opts.cheb_degree);
   for (int rows : {kFusedRows, kFusedRows / 2}) {
@@ -696,7 +701,9 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
       if (!run) break;
     }
     // x += P^{-1} u
-    if (!fused || !launch_fused_pinv_add<T>(m, rows, tile, c, cw.data(), u, x64, s)) {
+    // x += P^{-1} u (three stages, no partial sums) keeps the automatic height: the taller
+    // segments that suit the merged iteration leave its launch with too few blocks
+    if (!fused || !launch_fused_pinv_add<T>(m, fused_rows_auto(ctx), tile, c, cw.data(), u, x64, s)) {
       apply_pinv<T>(ctx, w, u, z, nullptr, cw);
       launch_add_to<T>(z, x64, c, s);
     }
