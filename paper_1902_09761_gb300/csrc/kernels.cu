@@ -606,7 +606,10 @@ __global__ void __launch_bounds__(256, 3) k_residual_refine2d(const double2* __r
 // and r_prev are split into FP32 pairs by integer operations and rhs_j = eta_j/dt -
 // kap_j N_j(eta) and r0 are formed in double-float arithmetic (about 2^-44
 // relative per operation, dfloat.cuh).
-__global__ void __launch_bounds__(256) k_rhs_resid_hex(const double2* __restrict__ x, double2* __restrict__ b,
+// 384 threads per block: the kernel keeps one partial-sum slot per block (kDotBlocks blocks),
+// and 12 warps per block give each SM 24 resident warps to overlap its loads.
+constexpr int kRhsThreads = 384;
+__global__ void __launch_bounds__(kRhsThreads) k_rhs_resid_hex(const double2* __restrict__ x, double2* __restrict__ b,
                                                        const double2* __restrict__ b_prev,
                                                        const double2* __restrict__ r_prev, float2* __restrict__ r32,
                                                        double2* __restrict__ partials, const __grid_constant__ OpCoef c,
@@ -661,7 +664,7 @@ __global__ void __launch_bounds__(256) k_rhs_resid_hex(const double2* __restrict
       accf[2 * j + 1] = fmaf(bn.x.h, bn.x.h, fmaf(bn.y.h, bn.y.h, accf[2 * j + 1]));
     }
   }
-  __shared__ double sh[6][kThreads / 32];
+  __shared__ double sh[6][kRhsThreads / 32];
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
@@ -672,7 +675,7 @@ __global__ void __launch_bounds__(256) k_rhs_resid_hex(const double2* __restrict
   __syncthreads();
   if (threadIdx.x < 6) {
     double v = 0.0;
-    for (int k = 0; k < kThreads / 32; ++k) v += sh[threadIdx.x][k];
+    for (int k = 0; k < kRhsThreads / 32; ++k) v += sh[threadIdx.x][k];
     const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
     partials[(j * kDotSlots + which) * kDotBlocks + blockIdx.x] = make_double2(v, 0.0);
   }
@@ -1287,7 +1290,7 @@ void launch_rhs_resid(const double2* x, double2* b, const double2* b_prev, const
                       const BatchLaunch* bl) {
   ProfScope ps_(KID_RHS, s);
   if (nt.hex) {
-    k_rhs_resid_hex<<<dim3(kDotBlocks, bl ? bl->R : 1), kThreads, 0, s>>>(
+    k_rhs_resid_hex<<<dim3(kDotBlocks, bl ? bl->R : 1), kRhsThreads, 0, s>>>(
         x, b, b_prev, r_prev, r32, reinterpret_cast<double2*>(partials), c, nt, bl ? bl->dev : nullptr);
     return;
   }
