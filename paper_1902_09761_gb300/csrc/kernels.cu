@@ -454,12 +454,35 @@ __global__ void k_rhs(const double2* __restrict__ x, double2* __restrict__ b, co
 }
 
 // zeta-part of the state = G_h (eta-part)
-__global__ void k_zeta(double2* __restrict__ x, OpCoef c) {
+// zeta = G_h eta from the state's eta-parts, FP64-accurate without the FP64 pipe: the point
+// and its neighbours split into FP32 pairs and G_h as one compensated sum of products with
+// the residual's grouping (resid_point.cuh), rounded to the nearest double at the end.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_zeta(double2* __restrict__ x, const __grid_constant__ OpCoef c) {
   prof_add3(c, KID_ZETA, 2ull * (unsigned long long)c.pts * sizeof(double2));
   APFC_POINT_INDEX
   const double2* e = x + (2LL * j + 1) * c.pts;
   const Nb n = APFC_NEIGHBOURS;
-  x[2LL * j * c.pts + p] = opG<double>(e, n, c, j);
+  const ResidCoef<DIM> q = resid_coef<DIM>(c, j);
+  PDF en[DIM][2];
+  en[0][0] = pdf_split(e[n.xm]);
+  en[0][1] = pdf_split(e[n.xp]);
+  en[1][0] = pdf_split(e[n.ym]);
+  en[1][1] = pdf_split(e[n.yp]);
+  if constexpr (DIM == 3) {
+    en[2][0] = pdf_split(e[n.zm]);
+    en[2][1] = pdf_split(e[n.zp]);
+  }
+  PAcc a;
+  a.init(PDF{make_float2(0.f, 0.f), make_float2(0.f, 0.f)});
+  a.fma(q.g0.h, q.g0.l, pdf_split(e[p]));
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) a.fma(q.gl[d].h, q.gl[d].l, pdf_add(en[d][1], en[d][0]));
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) a.fma(q.ga[d].h, q.ga[d].l, pdf_swap(pdf_sub(en[d][1], en[d][0])));
+  float2 hi, lo;
+  a.result(hi, lo);
+  x[2LL * j * c.pts + p] = make_double2(df_to_d(DF{hi.x, lo.x}), df_to_d(DF{hi.y, lo.y}));
 }
 
 // ---------------------------------------------------------------------------
@@ -1272,7 +1295,10 @@ void launch_zeta(double2* x, const OpCoef& c, cudaStream_t s) {
     return;
   }
   ProfScope ps_(KID_ZETA, s);
-  k_zeta<<<grid_pts3(c), kThreads, 0, s>>>(x, c);
+  if (c.dim == 3)
+    k_zeta<3><<<grid_pts3(c), kThreads, 0, s>>>(x, c);
+  else
+    k_zeta<2><<<grid_pts3(c), kThreads, 0, s>>>(x, c);
 }
 void launch_residual_refine(const double2* b, const double2* x, float2* r32, double* partials, const OpCoef& c,
                             cudaStream_t s) {
