@@ -305,7 +305,8 @@ bool launch_residual_refine_tma(const double2* b, const double2* x, float2* r32,
 // (stream3d_timeouts: those of the 3D passes alone)
 unsigned long long tma_timeouts();
 unsigned long long stream3d_timeouts();
-// new RHS and initial residual r0 = b - b_prev + r_prev (pointwise)
+// new RHS and initial residual r0 = b - b_prev + r_prev (pointwise); b_prev = r_prev = null:
+// the RHS and the ||b||^2 partials only (the ||r0||^2 slot holds 0, r32 is not written)
 void launch_rhs_resid(const double2* x, double2* b, const double2* b_prev, const double2* r_prev, float2* r32,
                       double* partials, const OpCoef& c, const NonlinTable& nt, cudaStream_t s,
                       const BatchLaunch* bl = nullptr);

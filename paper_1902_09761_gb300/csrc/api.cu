@@ -793,8 +793,9 @@ apfc_status step_fp64(apfc_ctx* ctx) {
 // ||b||^2 are already in place (the pointwise initial residual of a step).
 // r64_keep != nullptr receives the FP64 residual b - A x of every stencil
 // residual sweep.  *stencil_last: the final check was such a sweep.
+// bnorm_ready: the partial sums hold ||b||^2 (slot 1) from the right-hand-side kernel
 apfc_status refine_solve(apfc_ctx* ctx, const double2* b, double2* x, double2* r64_keep, bool resid_ready,
-                         int* total_it, int* sweeps, int* worst_out, bool* stencil_last) {
+                         int* total_it, int* sweeps, int* worst_out, bool* stencil_last, bool bnorm_ready = false) {
   apfc_status st = alloc_work<float>(ctx, ctx->w32);
   if (st != APFC_OK) return st;
   cudaStream_t s = ctx->stream;
@@ -809,9 +810,13 @@ apfc_status refine_solve(apfc_ctx* ctx, const double2* b, double2* x, double2* r
       stencil = false;
     } else {
       if (sweep == 0) {  // ||b||^2 once per solve
-        DotPairs<double> d{{b, nullptr, nullptr}, {b, nullptr, nullptr}};
-        launch_dots<double>(1, d, ctx->part64, ctx->coef, nullptr, s);
-        launch_finalize64(1, ctx->part64, ctx->ks64, OP_BNORM, ctx->J, s);
+        if (bnorm_ready) {
+          launch_finalize64(2, ctx->part64, ctx->ks64, OP_NORMS, ctx->J, s);  // its ||r||^2 slot is 0
+        } else {
+          DotPairs<double> d{{b, nullptr, nullptr}, {b, nullptr, nullptr}};
+          launch_dots<double>(1, d, ctx->part64, ctx->coef, nullptr, s);
+          launch_finalize64(1, ctx->part64, ctx->ks64, OP_BNORM, ctx->J, s);
+        }
       }
       {
         const char* terr = nullptr;
@@ -877,7 +882,7 @@ apfc_status step_refined(apfc_ctx* ctx) {
   if (st != APFC_OK) return st;
   float2* r32 = ctx->w32.blk[7];
   double* part = reinterpret_cast<double*>(ctx->part64);
-  bool resid_ready = false;
+  bool resid_ready = false, bnorm_ready = false;
   if (ctx->have_prev && ctx->prev_dt == ctx->coef_dt) {
     // r0 = b - b_prev + r_prev with the previous step's final residual r_prev = b_prev - A x;
     // b_prev is the RHS that residual was taken against; the new RHS goes to the other buffer
@@ -885,7 +890,9 @@ apfc_status step_refined(apfc_ctx* ctx) {
     std::swap(ctx->b64, ctx->b64_prev);
     resid_ready = true;
   } else {
-    launch_rhs(ctx->x64, ctx->b64, ctx->coef, ctx->nt, s);
+    // no previous residual: the new RHS and its norm, the initial residual by stencil below
+    launch_rhs_resid(ctx->x64, ctx->b64, nullptr, nullptr, r32, part, ctx->coef, ctx->nt, s);
+    bnorm_ready = true;
   }
   ctx->have_prev = false;
   bool ex = false;
@@ -893,7 +900,8 @@ apfc_status step_refined(apfc_ctx* ctx) {
   if (ex) resid_ready = false;  // the pointwise r0 belongs to the guess x^n: take a stencil residual
   int total_it = 0, sweeps = 0, worst = KS_CONVERGED;
   bool stencil_last = false;
-  st = refine_solve(ctx, ctx->b64, ctx->x64, ctx->r64_prev, resid_ready, &total_it, &sweeps, &worst, &stencil_last);
+  st = refine_solve(ctx, ctx->b64, ctx->x64, ctx->r64_prev, resid_ready, &total_it, &sweeps, &worst, &stencil_last,
+                    bnorm_ready);
   if (st != APFC_OK) return st;
   guess_done(ctx, worst);
   // a TMA wait that gave up leaves its kernel's results incomplete: fail the step

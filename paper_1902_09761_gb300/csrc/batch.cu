@@ -300,14 +300,16 @@ apfc_status batch_step(apfc_batch* b) {
   const int tile = b->opts.tile, rows = rows_of(b->opts), tile_t = tile_t_of(b->opts);
   const Vecs x = vecs(b);
   double* part = reinterpret_cast<double*>(b->part_fix);
-  bool resid_ready = false;
+  bool resid_ready = false, bnorm_ready = false;
   if (b->have_prev && b->prev_dt == b->coef_dt) {
     // r0 = b - b_prev + r_prev; the new RHS goes to the other buffer
     launch_rhs_resid(b->x64, b->b64_prev, b->b64, b->r64_prev, x.r32, part, b->coef, b->nt, s, &b->bl);
     std::swap(b->b64, b->b64_prev);
     resid_ready = true;
   } else {
-    launch_rhs(b->x64, b->b64, b->coef, b->nt, s, &b->bl);
+    // the new RHS and ||b||^2 (the same kernel as a context alone), r0 by stencil below
+    launch_rhs_resid(b->x64, b->b64, nullptr, nullptr, x.r32, part, b->coef, b->nt, s, &b->bl);
+    bnorm_ready = true;
   }
   b->have_prev = false;
   const double tol2 = b->opts.tol * b->opts.tol;
@@ -319,9 +321,13 @@ apfc_status batch_step(apfc_batch* b) {
       launch_finalize_batch<double>(2, part, kDotBlocks, b->bl, b->J, b->ks64, OP_NORMS, s);
     } else {
       if (sweep == 0) {
-        DotPairs<double> d{{b->b64, nullptr, nullptr}, {b->b64, nullptr, nullptr}};
-        launch_dots<double>(1, d, part, b->coef, nullptr, s, &b->bl);
-        launch_finalize_batch<double>(1, part, kDotBlocks, b->bl, b->J, b->ks64, OP_BNORM, s);
+        if (bnorm_ready) {
+          launch_finalize_batch<double>(2, part, kDotBlocks, b->bl, b->J, b->ks64, OP_NORMS, s);
+        } else {
+          DotPairs<double> d{{b->b64, nullptr, nullptr}, {b->b64, nullptr, nullptr}};
+          launch_dots<double>(1, d, part, b->coef, nullptr, s, &b->bl);
+          launch_finalize_batch<double>(1, part, kDotBlocks, b->bl, b->J, b->ks64, OP_BNORM, s);
+        }
       }
       launch_residual_refine2d(b->b64, b->x64, x.r32, b->r64_prev, part, b->coef, s, &b->bl);
       launch_finalize_batch<double>(1, part, kDotBlocks, b->bl, b->J, b->ks64, OP_RNORM, s);

@@ -643,13 +643,15 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_resid_hex(const double2* __
     pts = q.pts;
     x += q.elem_off;
     b += q.elem_off;
-    b_prev += q.elem_off;
-    r_prev += q.elem_off;
+    if (b_prev != nullptr) {  // null: no previous step (kept null, not offset)
+      b_prev += q.elem_off;
+      r_prev += q.elem_off;
+    }
     r32 += q.elem_off;
     partials += (long long)blockIdx.y * 3 * kDotSlots * kDotBlocks;
   }
   if (c.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
-    atomicAdd(c.prof + KID_RHS, 3ull * pts * (5 * sizeof(double2) + 2 * sizeof(float2)));
+    atomicAdd(c.prof + KID_RHS, 3ull * pts * (b_prev ? 5 * sizeof(double2) + 2 * sizeof(float2) : 2 * sizeof(double2)));
   const DF v3 = split_d(3.0 * nt.v), t2 = split_d(2.0 * nt.t), idt = split_d(c.inv_dt);
   DF kap[3];
 #pragma unroll
@@ -676,14 +678,16 @@ __global__ void __launch_bounds__(kRhsThreads) k_rhs_resid_hex(const double2* __
       const CDF bn = cdf_sub(cdf_scale(idt, eta[j]), cdf_scale(kap[j], N));
       const long long q1 = 2LL * j * pts + p, q2 = q1 + pts;
       b[q2] = cdf_to_d(bn);
-      const CDF r2 = cdf_add(cdf_sub(bn, cdf_split(b_prev[q2])), cdf_split(r_prev[q2]));
-      const DF p1x = split_d(r_prev[q1].x), p1y = split_d(r_prev[q1].y);
-      const float2 f1 = make_float2(__fadd_rn(p1x.h, p1x.l), __fadd_rn(p1y.h, p1y.l));
-      const float2 f2 = make_float2(r2.x.h, r2.y.h);
-      r32[q1] = f1;
-      r32[q2] = f2;
-      // norms only decide convergence: accumulated from FP32-rounded values
-      accf[2 * j] = fmaf(f1.x, f1.x, fmaf(f1.y, f1.y, fmaf(f2.x, f2.x, fmaf(f2.y, f2.y, accf[2 * j]))));
+      if (b_prev != nullptr) {  // without a previous step: b and ||b||^2 only (r0 by stencil)
+        const CDF r2 = cdf_add(cdf_sub(bn, cdf_split(b_prev[q2])), cdf_split(r_prev[q2]));
+        const DF p1x = split_d(r_prev[q1].x), p1y = split_d(r_prev[q1].y);
+        const float2 f1 = make_float2(__fadd_rn(p1x.h, p1x.l), __fadd_rn(p1y.h, p1y.l));
+        const float2 f2 = make_float2(r2.x.h, r2.y.h);
+        r32[q1] = f1;
+        r32[q2] = f2;
+        // norms only decide convergence: accumulated from FP32-rounded values
+        accf[2 * j] = fmaf(f1.x, f1.x, fmaf(f1.y, f1.y, fmaf(f2.x, f2.x, fmaf(f2.y, f2.y, accf[2 * j]))));
+      }
       accf[2 * j + 1] = fmaf(bn.x.h, bn.x.h, fmaf(bn.y.h, bn.y.h, accf[2 * j + 1]));
     }
   }
@@ -722,14 +726,17 @@ __global__ void __launch_bounds__(256) k_rhs_resid_tab(const double2* __restrict
     pts = q.pts;
     x += q.elem_off;
     b += q.elem_off;
-    b_prev += q.elem_off;
-    r_prev += q.elem_off;
+    if (b_prev != nullptr) {  // null: no previous step (kept null, not offset)
+      b_prev += q.elem_off;
+      r_prev += q.elem_off;
+    }
     r32 += q.elem_off;
     partials += (long long)blockIdx.y * c.J * kDotSlots * kDotBlocks;
   }
   const int J = c.J, t = threadIdx.x;
   if (c.prof != nullptr && blockIdx.x == 0 && t == 0)
-    atomicAdd(c.prof + KID_RHS, (unsigned long long)J * pts * (5 * sizeof(double2) + 2 * sizeof(float2)));
+    atomicAdd(c.prof + KID_RHS, (unsigned long long)J * pts *
+                                    (b_prev ? 5 * sizeof(double2) + 2 * sizeof(float2) : 2 * sizeof(double2)));
   __shared__ float4 se4[kMaxJ][kThreads];  // split amplitudes of each thread's point (re h, re l, im h, im l)
   __shared__ float2 sn2[kMaxJ][kThreads];  // |eta_m|^2 as (h, l)
   __shared__ float2 swd[kMaxJ][kMaxJ];
@@ -784,14 +791,16 @@ __global__ void __launch_bounds__(256) k_rhs_resid_tab(const double2* __restrict
       const CDF bn = cdf_sub(cdf_scale(idt, ej), cdf_scale(DF{kp.x, kp.y}, N));
       const long long q1 = 2LL * j * pts + p, q2 = q1 + pts;
       b[q2] = cdf_to_d(bn);
-      const CDF r2 = cdf_add(cdf_sub(bn, cdf_split(b_prev[q2])), cdf_split(r_prev[q2]));
-      const DF p1x = split_d(r_prev[q1].x), p1y = split_d(r_prev[q1].y);
-      const float2 f1 = make_float2(__fadd_rn(p1x.h, p1x.l), __fadd_rn(p1y.h, p1y.l));
-      const float2 f2 = make_float2(r2.x.h, r2.y.h);
-      r32[q1] = f1;
-      r32[q2] = f2;
-      // norms only decide convergence: accumulated from FP32-rounded values
-      accf[2 * j] = fmaf(f1.x, f1.x, fmaf(f1.y, f1.y, fmaf(f2.x, f2.x, fmaf(f2.y, f2.y, accf[2 * j]))));
+      if (b_prev != nullptr) {  // without a previous step: b and ||b||^2 only (r0 by stencil)
+        const CDF r2 = cdf_add(cdf_sub(bn, cdf_split(b_prev[q2])), cdf_split(r_prev[q2]));
+        const DF p1x = split_d(r_prev[q1].x), p1y = split_d(r_prev[q1].y);
+        const float2 f1 = make_float2(__fadd_rn(p1x.h, p1x.l), __fadd_rn(p1y.h, p1y.l));
+        const float2 f2 = make_float2(r2.x.h, r2.y.h);
+        r32[q1] = f1;
+        r32[q2] = f2;
+        // norms only decide convergence: accumulated from FP32-rounded values
+        accf[2 * j] = fmaf(f1.x, f1.x, fmaf(f1.y, f1.y, fmaf(f2.x, f2.x, fmaf(f2.y, f2.y, accf[2 * j]))));
+      }
       accf[2 * j + 1] = fmaf(bn.x.h, bn.x.h, fmaf(bn.y.h, bn.y.h, accf[2 * j + 1]));
     }
   }
