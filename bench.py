@@ -450,6 +450,7 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         if sampler:
             sampler.start()
+        it0 = ctx.stats()["iters_total"]
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -459,11 +460,13 @@ def run_ours(args):
         clocks = sampler.stop() if sampler else None
         barrier(world)
         ms = e0.elapsed_time(e1)
-        return allmax(world, ms, dev), clocks
+        # Krylov iterations per timed step (of each solve, the slowest amplitude's)
+        iters = (ctx.stats()["iters_total"] - it0) / max(nsteps, 1)
+        return allmax(world, ms, dev), clocks, iters
 
     # --- headline: FP32 Krylov + FP64 refinement --------------------------------
     sampler = ClockSampler(local)
-    ms, clocks = timed_steps(args.steps, sampler, args.timed_kernel)
+    ms, clocks, iters_mean = timed_steps(args.steps, sampler, args.timed_kernel)
     st = ctx.stats()
     prof = ctx.profile_read(args.timed_kernel)
     ctx.profile_stop()
@@ -520,7 +523,7 @@ def run_ours(args):
     opts64 = A.apfc_default_opts(precision=A.APFC_FP64, tol=TOL, cheb_degree=args.cheb, tile_rows=args.rows,
                                  picard_iters=args.picard, jacobian=int(args.jacobian))
     ctx.set_opts(opts64)
-    ms64, _ = timed_steps(args.fp64_steps)
+    ms64, _, _ = timed_steps(args.fp64_steps)
     st64 = ctx.stats()
     value64 = world * dof * args.fp64_steps / (ms64 * 1e-3)
 
@@ -654,6 +657,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": dict(workload_config(n), **({"parallelism": f"replicas x{world}"} if world > 1 else {})),
         "iters_per_step_last": st["iters_last"],
+        "iters_per_step_mean": iters_mean,
         "refine_sweeps_last": st["refine_last"],
         "resid_last": st["resid_last"],
         "fp64": {

@@ -128,7 +128,8 @@ enum { APFC_GUESS_PREV = 0, APFC_GUESS_EXTRAP = 1 };
 
 typedef struct {
   long long steps;           /* steps taken since apfc_set_amplitudes             */
-  long long iters_total;     /* Krylov iterations summed over steps and amplitudes */
+  long long iters_total;     /* Krylov iterations summed over steps (of each solve,
+                                the iterations of its slowest amplitude)           */
   int iters_last;            /* max over amplitudes of iterations in the last step */
   int refine_last;           /* refinement sweeps in the last step (FP32_REFINED)  */
   double resid_last;         /* max over amplitudes of ||b-Ax||/||b|| after the last step */

@@ -897,7 +897,12 @@ apfc_status step_refined(apfc_ctx* ctx) {
   ctx->have_prev = false;
   bool ex = false;
   if ((st = guess_prepare(ctx, &ex)) != APFC_OK) return st;
-  if (ex) resid_ready = false;  // the pointwise r0 belongs to the guess x^n: take a stencil residual
+  if (ex && resid_ready) {
+    // the pointwise r0 belongs to x^n, not to the guess: take a stencil residual; the RHS
+    // kernel's ||b||^2 (slot 1 of its partial sums) still holds
+    resid_ready = false;
+    bnorm_ready = true;
+  }
   int total_it = 0, sweeps = 0, worst = KS_CONVERGED;
   bool stencil_last = false;
   st = refine_solve(ctx, ctx->b64, ctx->x64, ctx->r64_prev, resid_ready, &total_it, &sweeps, &worst, &stencil_last,

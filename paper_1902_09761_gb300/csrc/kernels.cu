@@ -1304,10 +1304,7 @@ void launch_zeta(double2* x, const OpCoef& c, cudaStream_t s) {
     return;
   }
   ProfScope ps_(KID_ZETA, s);
-  if (c.dim == 3)
-    k_zeta<3><<<grid_pts3(c), kThreads, 0, s>>>(x, c);
-  else
-    k_zeta<2><<<grid_pts3(c), kThreads, 0, s>>>(x, c);
+  k_zeta<2><<<grid_pts3(c), kThreads, 0, s>>>(x, c);
 }
 void launch_residual_refine(const double2* b, const double2* x, float2* r32, double* partials, const OpCoef& c,
                             cudaStream_t s) {
