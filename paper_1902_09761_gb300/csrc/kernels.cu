@@ -630,9 +630,10 @@ __global__ void __launch_bounds__(256, 3) k_residual_refine2d(const double2* __r
 // kap_j N_j(eta) and r0 are formed in double-float arithmetic (about 2^-44
 // relative per operation, dfloat.cuh).
 // 384 threads per block: the kernel keeps one partial-sum slot per block (kDotBlocks blocks),
-// and 12 warps per block give each SM 24 resident warps to overlap its loads.
+// and 12 warps per block, with registers capped for two blocks per SM (80; uncapped it took
+// 95 and ran 16% slower at one block), give each SM 24 resident warps to overlap its loads.
 constexpr int kRhsThreads = 384;
-__global__ void __launch_bounds__(kRhsThreads) k_rhs_resid_hex(const double2* __restrict__ x, double2* __restrict__ b,
+__global__ void __launch_bounds__(kRhsThreads, 2) k_rhs_resid_hex(const double2* __restrict__ x, double2* __restrict__ b,
                                                        const double2* __restrict__ b_prev,
                                                        const double2* __restrict__ r_prev, float2* __restrict__ r32,
                                                        double2* __restrict__ partials, const __grid_constant__ OpCoef c,
