@@ -214,9 +214,6 @@ struct apfc_ctx {
   float2* jd32 = nullptr;
   // contiguous device copy of host amplitudes (one full-bandwidth host-to-device copy)
   double2* stage = nullptr;
-  // second stream and events of the split host copies (copy_split), made on first use
-  cudaStream_t cstream = nullptr;
-  cudaEvent_t cev[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -940,31 +937,6 @@ apfc_status copy_out_block(apfc_ctx* ctx, void* dst, const double2* src_dev, int
 }
 
 // Copy one part (0 = zeta, 1 = eta) of the state block to/from [J][pts].
-// A host <-> device copy of one contiguous range, in two halves on the context's stream and
-// a second stream so that two copy engines share it (ordered after the context's earlier
-// work; the context's stream waits for both halves).
-apfc_status copy_split(apfc_ctx* ctx, void* dst, const void* src, size_t bytes, cudaMemcpyKind k) {
-  constexpr size_t kMin = 64ull << 20;  // smaller copies go whole
-  if (bytes < kMin) {
-    CK(cudaMemcpyAsync(dst, src, bytes, k, ctx->stream));
-    return APFC_OK;
-  }
-  if (!ctx->cstream) {
-    CK(cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&ctx->cev[0], cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&ctx->cev[1], cudaEventDisableTiming));
-  }
-  const size_t half = (bytes / 2 + 255) & ~static_cast<size_t>(255);
-  CK(cudaEventRecord(ctx->cev[0], ctx->stream));
-  CK(cudaStreamWaitEvent(ctx->cstream, ctx->cev[0], 0));
-  CK(cudaMemcpyAsync(dst, src, half, k, ctx->stream));
-  CK(cudaMemcpyAsync(static_cast<char*>(dst) + half, static_cast<const char*>(src) + half, bytes - half, k,
-                     ctx->cstream));
-  CK(cudaEventRecord(ctx->cev[1], ctx->cstream));
-  CK(cudaStreamWaitEvent(ctx->stream, ctx->cev[1], 0));
-  return APFC_OK;
-}
-
 apfc_status copy_part(apfc_ctx* ctx, void* plain, int where, int part, bool to_state, int dtype = APFC_C128) {
   const size_t row = sizeof(double2) * (size_t)ctx->pts;
   double2* base = ctx->x64 + (size_t)part * ctx->pts;
@@ -974,15 +946,14 @@ apfc_status copy_part(apfc_ctx* ctx, void* plain, int where, int part, bool to_s
     const bool host = where == APFC_HOST;
     if (host && !ctx->stage) CK(cudaMalloc(&ctx->stage, row * ctx->J));
     float2* dev = host ? reinterpret_cast<float2*>(ctx->stage) : static_cast<float2*>(plain);
-    apfc_status st = APFC_OK;
     if (to_state) {
-      if (host && (st = copy_split(ctx, dev, plain, bytes, cudaMemcpyHostToDevice)) != APFC_OK) return st;
+      if (host) CK(cudaMemcpyAsync(dev, plain, bytes, cudaMemcpyHostToDevice, ctx->stream));
       launch_c64_to_part(dev, ctx->x64, ctx->pts, ctx->J, part, ctx->stream);
       CK(cudaGetLastError());
     } else {
       launch_part_to_c64(ctx->x64, dev, ctx->pts, ctx->J, part, ctx->stream);
       CK(cudaGetLastError());
-      if (host && (st = copy_split(ctx, plain, dev, bytes, cudaMemcpyDeviceToHost)) != APFC_OK) return st;
+      if (host) CK(cudaMemcpyAsync(plain, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return APFC_OK;
@@ -996,8 +967,7 @@ apfc_status copy_part(apfc_ctx* ctx, void* plain, int where, int part, bool to_s
     // a strided copy from host memory runs at a fraction of the link's bandwidth:
     // one contiguous copy to the device, then the strided copy on the device
     if (!ctx->stage) CK(cudaMalloc(&ctx->stage, row * ctx->J));
-    const apfc_status st = copy_split(ctx, ctx->stage, plain, row * ctx->J, cudaMemcpyHostToDevice);
-    if (st != APFC_OK) return st;
+    CK(cudaMemcpyAsync(ctx->stage, plain, row * ctx->J, cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpy2DAsync(base, 2 * row, ctx->stage, row, row, ctx->J, cudaMemcpyDeviceToDevice, ctx->stream));
   } else if (to_state) {
     CK(cudaMemcpy2DAsync(base, 2 * row, plain, row, row, ctx->J, k, ctx->stream));
@@ -1005,8 +975,7 @@ apfc_status copy_part(apfc_ctx* ctx, void* plain, int where, int part, bool to_s
     // the same on the way out: the strided copy on the device, then one contiguous copy
     if (!ctx->stage) CK(cudaMalloc(&ctx->stage, row * ctx->J));
     CK(cudaMemcpy2DAsync(ctx->stage, row, base, 2 * row, row, ctx->J, cudaMemcpyDeviceToDevice, ctx->stream));
-    const apfc_status st = copy_split(ctx, plain, ctx->stage, row * ctx->J, cudaMemcpyDeviceToHost);
-    if (st != APFC_OK) return st;
+    CK(cudaMemcpyAsync(plain, ctx->stage, row * ctx->J, cudaMemcpyDeviceToHost, ctx->stream));
   } else {
     CK(cudaMemcpy2DAsync(plain, row, base, 2 * row, row, ctx->J, k, ctx->stream));
   }
@@ -1519,12 +1488,6 @@ void apfc_destroy(apfc_ctx* ctx) {
   cudaFree(ctx->jd);
   cudaFree(ctx->jd32);
   cudaFree(ctx->stage);
-  if (ctx->cstream) {
-    cudaStreamSynchronize(ctx->cstream);
-    cudaStreamDestroy(ctx->cstream);
-  }
-  for (auto& e : ctx->cev)
-    if (e) cudaEventDestroy(e);
   delete ctx;
 }
 
