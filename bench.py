@@ -1085,6 +1085,12 @@ def run_adjoint(args, world=None, rank=None, local=None, sub=False):
                  device=dev)
     e0_dev = torch.from_numpy(eta0).to(dev)
     tg = torch.from_numpy(target).to(dev)
+    # segment height and t-kernel variant for this grid, timed on a few steps from eta0
+    tuned = None
+    if args.rows == 0 and not args.no_autotune:
+        ro.ctx.set_amplitudes(e0_dev)
+        ro.ctx.step(1.0, 3)
+        tuned = ro.ctx.autotune(1.0)
 
     def grad_once():
         e0 = e0_dev.clone().requires_grad_(True)
@@ -1165,6 +1171,7 @@ def run_adjoint(args, world=None, rank=None, local=None, sub=False):
         "vs_baseline": None, "dtype": "f32 Krylov + f64 refinement", "data": "synthetic",
         "config": dict(adjoint_config(args), **({"parallelism": f"replicas x{world}"} if world > 1 else {})),
         "ms_per_gradient": ms,
+        "autotune": tuned,
         "forward_ms_per_step": fwd_ms / K,
         "backward_ms_per_step": bwd_ms / K,
         "backward_over_forward": bwd_ms / fwd_ms,

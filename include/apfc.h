@@ -187,9 +187,9 @@ apfc_status apfc_step(apfc_ctx* ctx, double dt, int n);
 /* Choose the rows per segment of the fused 2D kernels (opts.tile_rows) and the
  * variant of the merged iteration's t-kernel (opts.tile_t) by timing: from the
  * current state, one step of size dt per candidate, each from the same state,
- * after one untimed step; first every height ceil(ny / s) between 96 and 256 rows
- * and the automatic one (t-kernel variant as set), then every t-kernel variant at
- * the best height.  Keeps the fastest in the context's options.  The state and the
+ * after one untimed step; first the automatic height, 32, 48 and 64 rows and every
+ * height ceil(ny / s) between 96 and 256 rows (t-kernel variant as set), then every
+ * t-kernel variant at the best height.  Keeps the fastest in the context's options.  The state and the
  * statistics are restored (the next step takes a stencil initial residual).  Only
  * the FP32-refined fused path on 2D grids has a choice to make: other
  * configurations return APFC_OK with their options unchanged and ms_per_step 0.

@@ -1370,12 +1370,15 @@ apfc_status apfc_autotune(apfc_ctx* ctx, double dt, int* tile_rows, int* tile_t,
     if (ms_per_step) *ms_per_step = 0.0;
     return APFC_OK;
   }
-  // candidate heights: every ceil(ny / s) from 96 to 256 rows, and the automatic one
+  // candidate heights: the automatic one, 32, 48 and 64 rows (small grids want many blocks),
+  // and every ceil(ny / s) from 96 to 256 rows
   const int ny = ctx->grid.n[1];
   const int saved_rows = ctx->opts.tile_rows, saved_tt = ctx->opts.tile_t;
   std::vector<int> cand;
   ctx->opts.tile_rows = 0;
   cand.push_back(fused_rows(ctx));
+  for (int rows : {32, 48, 64})
+    if (rows < ny && std::find(cand.begin(), cand.end(), rows) == cand.end()) cand.push_back(rows);
   for (int s = std::max(1, (ny + 255) / 256); s <= std::max(1, ny / 96); ++s) {
     const int rows = (ny + s - 1) / s;
     if (rows >= 32 && rows <= ny && std::find(cand.begin(), cand.end(), rows) == cand.end()) cand.push_back(rows);

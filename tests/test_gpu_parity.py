@@ -413,7 +413,7 @@ def test_extrapolated_initial_guess_same_trajectory(prec, kind, shape, h):
 def test_autotune_keeps_state_and_continues_the_trajectory():
     # apfc_autotune times one step per candidate segment height from the same state and
     # restores it: amplitudes, zeta and statistics unchanged, the chosen height one of the
-    # candidates (ceil(ny / s) within 96..256 rows, or the automatic one), and the next
+    # candidates (ceil(ny / s) within 96..256 rows, 32, 48, 64, or the automatic one), and the next
     # steps still the oracle's
     shape, h, dt = (300, 530), (1.2, 0.8), 0.5
     eta0 = inputs.random_amplitudes(3, shape, seed=21, scale=0.1)
@@ -426,7 +426,7 @@ def test_autotune_keeps_state_and_continues_the_trajectory():
     assert ctx.stats() == st1
     ny = shape[1]
     allowed = {-(-ny // s) for s in range(max(1, -(-ny // 256)), max(1, ny // 96) + 1)}
-    assert tuned["tile_rows"] in allowed | {128, 64, 32} and tuned["ms_per_step"] > 0
+    assert tuned["tile_rows"] in allowed | {128, 64, 48, 32} and tuned["ms_per_step"] > 0
     assert 0 <= tuned["tile_t"] < 6
     eta_o = eta1.copy()
     for _ in range(2):
