@@ -424,8 +424,9 @@ apfc_status apfc_batch_stats(const apfc_batch* b, int run, apfc_stats_t* out);
 /* Tile autotuner: from the first refinement residual of a step of the current
  * state (the state itself is not changed), time a fixed number of merged
  * BiCGStab iterations over all runs, first for every tile variant (0..5) and
- * segment height (64, 128, 256 rows) shared by both fused kernels, then for every
- * variant of the t-kernel alone with the rest fixed; keep the fastest in the
+ * segment height (32, 48, 64, 96, 128, 192, 256 rows) shared by both fused
+ * kernels, then for every variant of the t-kernel alone with the rest fixed;
+ * keep the fastest in the
  * batch's options (tile, tile_rows, tile_t; see apfc_batch_get_opts) and return
  * tile, rows and ms per iteration (null pointers skipped). */
 apfc_status apfc_batch_autotune(apfc_batch* b, double dt, int* tile, int* tile_rows, double* ms_per_iter);

@@ -25,7 +25,7 @@ constexpr int kBlocks = 10;        // r, rhat, p, v, u, t, r32, p', v', r'
 constexpr int kDefaultRows = 128;  // rows per block segment of the fused pipeline
 constexpr int kMaxRuns = 65536;
 constexpr int kTuneIters = 6;      // merged iterations timed per autotuner candidate
-constexpr int kTuneRows[] = {64, 128, 256};
+constexpr int kTuneRows[] = {32, 48, 64, 96, 128, 192, 256};
 
 }  // namespace
 

@@ -129,7 +129,8 @@ def test_autotune_keeps_state_and_parity():
     with _batch(states, shapes, opts) as b:
         before = [b.get_amplitudes(r) for r in range(len(shapes))]
         best = b.autotune(1.0)
-        assert 0 <= best["tile"] < 6 and best["tile_rows"] in (64, 128, 256) and best["ms_per_iter"] > 0
+        assert 0 <= best["tile"] < 6 and best["tile_rows"] in (32, 48, 64, 96, 128, 192, 256)
+        assert best["ms_per_iter"] > 0
         o = b.opts
         assert o.tile == best["tile"] and o.tile_rows == best["tile_rows"] and 0 <= o.tile_t < 6
         for r in range(len(shapes)):
