@@ -147,11 +147,12 @@ __device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isf
 // amplitude per block.  d[q] are the finished inner products of this op.
 __device__ __forceinline__ void scalar_update(KScal& k, int op, const double2* d) {
   switch (op) {
-    case OP_INIT: {  // d0 = (r, r), d1 = (b, b); rhat = r
+    case OP_INIT:     // d0 = (r, r), d1 = (b, b); rhat = r
+    case OP_INIT3: {  // the same and d2 = (rhat, r) for a shadow residual rhat != r
       k.rnorm2 = d[0].x;
       k.bnorm2 = d[1].x;
       k.tol2 = k.tolrel2 * (k.bnorm2 > 0.0 ? k.bnorm2 : k.rnorm2);
-      k.rho = d[0];
+      k.rho = op == OP_INIT3 ? d[2] : d[0];
       k.alpha = make_double2(0.0, 0.0);
       k.omega = make_double2(0.0, 0.0);
       k.beta = make_double2(0.0, 0.0);

@@ -202,7 +202,7 @@ struct KScal {
 };
 
 enum KStatus { KS_RUNNING = 0, KS_CONVERGED = 1, KS_NOCONV = 2, KS_BREAKDOWN = 3, KS_NAN = 4 };
-enum KOp { OP_INIT = 0, OP_ALPHA = 1, OP_SNORM = 2, OP_OMEGA = 3, OP_RHO = 4, OP_NORMS = 5, OP_OMEGA3 = 6, OP_RNORM = 7, OP_BNORM = 8, OP_OMEGA5 = 9 };
+enum KOp { OP_INIT = 0, OP_ALPHA = 1, OP_SNORM = 2, OP_OMEGA = 3, OP_RHO = 4, OP_NORMS = 5, OP_OMEGA3 = 6, OP_RNORM = 7, OP_BNORM = 8, OP_OMEGA5 = 9, OP_INIT3 = 10 };
 
 // Up to three (u, v) pairs of block vectors for conj(u).v per amplitude.
 template <typename T>
@@ -305,6 +305,10 @@ bool launch_residual_refine_tma(const double2* b, const double2* x, float2* r32,
 // (stream3d_timeouts: those of the 3D passes alone)
 unsigned long long tma_timeouts();
 unsigned long long stream3d_timeouts();
+// Start of an FP32 solve from x0 = 0: r = b, rhat = b rounded to bf16 with its packed copy
+// rh16 [J][pts] (bf16pair.cuh), partials of (r, r), (b, b), (rhat, r) in slots 0-2 (k_dots' layout)
+void launch_init32(const float2* b, float2* r, float2* rhat, uint2* rh16, void* partials, const OpCoef& c,
+                   cudaStream_t s, const BatchLaunch* bl = nullptr);
 // new RHS and initial residual r0 = b - b_prev + r_prev (pointwise); b_prev = r_prev = null:
 // the RHS and the ||b||^2 partials only (the ||r0||^2 slot holds 0, r32 is not written)
 void launch_rhs_resid(const double2* x, double2* b, const double2* b_prev, const double2* r_prev, float2* r32,
@@ -349,8 +353,8 @@ int fused2d_tiles();  // number of tile variants
 // p_new = r + beta (p_old - omega v_old); v_new = A P^{-1} p_new; partial (rhat, v_new)
 template <typename T>
 bool launch_fused_v(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* p_old,
-                    const cplx<T>* v_old, cplx<T>* p_new, cplx<T>* v_new, const cplx<T>* rhat, const KScal* act,
-                    void* partials, cudaStream_t s);
+                    const cplx<T>* v_old, cplx<T>* p_new, cplx<T>* v_new, const cplx<T>* rhat, const uint2* rh16,
+                    const KScal* act, void* partials, cudaStream_t s);
 // t = A P^{-1} (r - alpha v); partials (t, s), (t, t), (s, s)
 template <typename T>
 bool launch_fused_t(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
@@ -371,8 +375,8 @@ bool launch_fused_pinv_store(int m, int Ly, int tile, const OpCoef& c, const Che
 template <typename T>
 bool launch_fused_merged_v(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,
                            const cplx<T>* t, const cplx<T>* p, cplx<T>* u, cplx<T>* r_new, cplx<T>* p_new,
-                           cplx<T>* v_new, const cplx<T>* rhat, const KScal* act, void* partials, cudaStream_t s,
-                           const BatchLaunch* bl = nullptr);
+                           cplx<T>* v_new, const cplx<T>* rhat, const uint2* rh16, const KScal* act, void* partials,
+                           cudaStream_t s, const BatchLaunch* bl = nullptr);
 // t = A P^{-1} s, s = r - alpha v; partials (t, s), (t, t), (s, s), (rhat, s), (rhat, t)
 template <typename T>
 bool launch_fused_merged_t(int m, int Ly, int tile, const OpCoef& c, const ChebStep* w, const cplx<T>* r, const cplx<T>* v,

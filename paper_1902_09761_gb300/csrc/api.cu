@@ -28,6 +28,7 @@ struct Work {
   int npart_cap = 0;
   KScal* ks = nullptr;       // device
   KScal* ks_host = nullptr;  // pinned
+  uint2* rh16 = nullptr;     // FP32: rhat as packed bf16 pairs [J][pts] (bf16pair.cuh)
   bool ready = false;
 };
 
@@ -272,6 +273,7 @@ apfc_status alloc_work(apfc_ctx* ctx, Work<T>& w) {
   w.npart_cap = cap;
   CK(cudaMalloc(&w.partials, 16ull * kDotSlots * cap * ctx->J));
   CK(cudaMalloc(&w.ks, sizeof(KScal) * ctx->J));
+  if (sizeof(T) == 4) CK(cudaMalloc(&w.rh16, sizeof(uint2) * (size_t)ctx->J * (size_t)ctx->pts));
   CK(cudaMallocHost(&w.ks_host, sizeof(KScal) * ctx->J));
   std::memset(w.ks_host, 0, sizeof(KScal) * ctx->J);
   CK(cudaMemsetAsync(w.blk[7], 0, block_bytes<T>(ctx), ctx->stream));
@@ -285,6 +287,8 @@ void free_work(Work<T>& w) {
   for (auto& f : w.fld) cudaFree(f), f = nullptr;
   cudaFree(w.partials);
   cudaFree(w.ks);
+  cudaFree(w.rh16);
+  w.rh16 = nullptr;
   if (w.ks_host) cudaFreeHost(w.ks_host);
   w.partials = nullptr;
   w.ks = nullptr;
@@ -600,17 +604,18 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
       w.ks_host[j].max_iter = max_iter;
     }
     CK(cudaMemcpyAsync(w.ks, w.ks_host, sizeof(KScal) * ctx->J, cudaMemcpyHostToDevice, s));
-    if (fp64) {
-      launch_residual<T>(b, reinterpret_cast<const cplx<T>*>(x64), r, rhat, c, s);
-    } else {
-      CK(cudaMemcpyAsync(r, b, bb, cudaMemcpyDeviceToDevice, s));
-      CK(cudaMemcpyAsync(rhat, b, bb, cudaMemcpyDeviceToDevice, s));
-    }
     CK(cudaMemsetAsync(p, 0, bb, s));
     CK(cudaMemsetAsync(v, 0, bb, s));
     CK(cudaMemsetAsync(u, 0, bb, s));
     if (use_fused(ctx, (int)sizeof(cplx<T>))) CK(cudaMemsetAsync(t, 0, bb, s));
-    {
+    if constexpr (sizeof(T) == 4) {
+      // r = b (x0 = 0) and the shadow residual rhat = b rounded to bf16 (bf16pair.cuh),
+      // rho0 = (rhat, r0), in one pass
+      launch_init32(reinterpret_cast<const float2*>(b), reinterpret_cast<float2*>(r), reinterpret_cast<float2*>(rhat),
+                    w.rh16, w.partials, c, s);
+      launch_finalize<T>(3, w.partials, w.ks, OP_INIT3, ctx->J, s);
+    } else {
+      launch_residual<T>(b, reinterpret_cast<const cplx<T>*>(x64), r, rhat, c, s);
       DotPairs<T> d{{r, b, nullptr}, {r, b, nullptr}};
       launch_dots<T>(2, d, w.partials, c, nullptr, s);
       launch_finalize<T>(2, w.partials, w.ks, OP_INIT, ctx->J, s);
@@ -654,8 +659,9 @@ apfc_status krylov(apfc_ctx* ctx, Work<T>& w, const cplx<T>* b, double2* x64, do
         if (fused) {
           // merged iteration: r' = r - alpha v - omega t, p' = r' + beta (p - omega v),
           // u += alpha p + omega s (the previous iteration's update), v' = A P^{-1} p'
-          launch_fused_merged_v<T>(m, rows, tile, c, cw.data(), rr[cur], vv[cur], t, pp[cur], u, rr[1 - cur],
-                                   pp[1 - cur], vv[1 - cur], rhat, w.ks, w.partials, s);
+          if (!launch_fused_merged_v<T>(m, rows, tile, c, cw.data(), rr[cur], vv[cur], t, pp[cur], u, rr[1 - cur],
+                                        pp[1 - cur], vv[1 - cur], rhat, w.rh16, w.ks, w.partials, s))
+            return fail(ctx, APFC_EINVAL, "the fused pipeline cannot run these options");
           launch_finalize<T>(1, w.partials, w.ks, OP_ALPHA, ctx->J, s, npart);  // alpha = rho / (rhat, v')
           // t = A P^{-1} s, s = r' - alpha v'; omega, rho', beta and ||r''||^2 from five inner products
           launch_fused_merged_t<T>(m, rows, tile_t, c, cw.data(), rr[1 - cur], vv[1 - cur], t, rhat, w.ks,

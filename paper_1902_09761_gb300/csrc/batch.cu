@@ -53,6 +53,7 @@ struct apfc_batch {
   double2* b64_prev = nullptr;
   double2* r64_prev = nullptr;
   float2* blk[kBlocks] = {};
+  uint2* rh16 = nullptr;  // rhat as packed bf16 pairs, [run][J][pts] (bf16pair.cuh)
   void* part_pipe = nullptr;  // fused-pipeline partials (run table layout)
   long long part_pipe_cap = 0;
   void* part_fix = nullptr;  // k_dots / FP64 residual partials: R J kDotSlots kDotBlocks slots
@@ -193,7 +194,8 @@ bool issue_block(apfc_batch* b, int cur, int every, int tile, int rows, int tile
   cudaStream_t s = b->stream;
   for (int q = 0; q < every; ++q) {
     if (!launch_fused_merged_v<float>(m, rows, tile, b->coef, b->cw.data(), x.r[cur], x.v[cur], x.t, x.p[cur], x.u,
-                                      x.r[1 - cur], x.p[1 - cur], x.v[1 - cur], x.rhat, b->ks, b->part_pipe, s, &b->bl))
+                                      x.r[1 - cur], x.p[1 - cur], x.v[1 - cur], x.rhat, b->rh16, b->ks, b->part_pipe, s,
+                                      &b->bl))
       return false;
     launch_finalize_batch<float>(1, b->part_pipe, 0, b->bl, b->J, b->ks, OP_ALPHA, s);
     if (!launch_fused_merged_t<float>(m, rows, tile_t, b->coef, b->cw.data(), x.r[1 - cur], x.v[1 - cur], x.t,
@@ -235,15 +237,13 @@ apfc_status krylov_init(apfc_batch* b, const std::vector<char>& skip, int max_it
       k.max_iter = max_iter;
     }
   BK(cudaMemcpyAsync(b->ks, b->ks_host, sizeof(KScal) * b->R * b->J, cudaMemcpyHostToDevice, s));
-  BK(cudaMemcpyAsync(x.r[0], x.r32, bytes, cudaMemcpyDeviceToDevice, s));
-  BK(cudaMemcpyAsync(x.rhat, x.r32, bytes, cudaMemcpyDeviceToDevice, s));
   BK(cudaMemsetAsync(x.p[0], 0, bytes, s));
   BK(cudaMemsetAsync(x.v[0], 0, bytes, s));
   BK(cudaMemsetAsync(x.u, 0, bytes, s));
   BK(cudaMemsetAsync(x.t, 0, bytes, s));
-  DotPairs<float> d{{x.r[0], x.r32, nullptr}, {x.r[0], x.r32, nullptr}};
-  launch_dots<float>(2, d, b->part_fix, b->coef, nullptr, s, &b->bl);
-  launch_finalize_batch<float>(2, b->part_fix, kDotBlocks, b->bl, b->J, b->ks, OP_INIT, s);
+  // r = r32 and the shadow residual rounded to bf16, as in a context alone: rho0 = (rhat, r0)
+  launch_init32(x.r32, x.r[0], x.rhat, b->rh16, b->part_fix, b->coef, s, &b->bl);
+  launch_finalize_batch<float>(3, b->part_fix, kDotBlocks, b->bl, b->J, b->ks, OP_INIT3, s);
   apfc_status st = sync_ks(b, b->ks, b->ks_host);
   if (st != APFC_OK) return st;
   *any = false;
@@ -416,6 +416,7 @@ void free_batch(apfc_batch* b) {
   cudaFree(b->b64_prev);
   cudaFree(b->r64_prev);
   for (auto& p : b->blk) cudaFree(p);
+  cudaFree(b->rh16);
   cudaFree(b->part_pipe);
   cudaFree(b->part_fix);
   cudaFree(b->ks);
@@ -536,6 +537,7 @@ apfc_status apfc_batch_init(apfc_batch** out, const apfc_lattice* lat, const apf
     if (cudaMalloc(q, blk64) != cudaSuccess) return cleanup(APFC_ENOMEM);
   for (auto& q : b->blk)
     if (cudaMalloc(&q, blk32) != cudaSuccess) return cleanup(APFC_ENOMEM);
+  if (cudaMalloc(&b->rh16, sizeof(uint2) * (size_t)(b->elems / 2)) != cudaSuccess) return cleanup(APFC_ENOMEM);
   if (cudaMalloc(&b->part_pipe, 16ull * (size_t)cap) != cudaSuccess) return cleanup(APFC_ENOMEM);
   if (cudaMalloc(&b->part_fix, 16ull * kDotSlots * kDotBlocks * (size_t)nruns * b->J) != cudaSuccess)
     return cleanup(APFC_ENOMEM);

@@ -32,6 +32,7 @@
 #pragma once
 #include "acc.cuh"
 #include "apfc_internal.cuh"
+#include "bf16pair.cuh"
 #include "dfloat.cuh"
 
 #include <algorithm>
@@ -436,25 +437,42 @@ struct EpAddX {  // x64 += y (the Krylov correction P^{-1} u)
 
 template <typename T>
 struct EpV {  // v = y; (rhat, v)
-  static constexpr int NDOT = 1, NEP = 2;
+  // FP32: rhat staged as one 8-byte value per point, the bf16 pairs of its two parts
+  // (rh16 [J][pts], bf16pair.cuh); FP64: both complex parts of rhat
+  static constexpr bool H16 = sizeof(T) == 4;
+  static constexpr int NDOT = 1, NEP = H16 ? 1 : 2;
   cplx<T>* v;
   const cplx<T>* rhat;
+  const uint2* rh16;
   long long pts;
   long long off;
   Acc<T> acc[1];
   // batched runs: move every array to this run's block vectors
   __device__ void rebase(long long e, long long n) {
     v += e;
-    rhat += e;
+    if constexpr (H16) {
+      rh16 += e / 2;
+    } else {
+      rhat += e;
+    }
     pts = n;
   }
   __device__ void setup(int j, const KScal*) { off = 2LL * j * pts; }
-  __device__ const cplx<T>* ep(int i) const { return rhat + off + i * pts; }
+  __device__ const cplx<T>* ep(int i) const {
+    if constexpr (H16) return reinterpret_cast<const cplx<T>*>(rh16 + off / 2);
+    return rhat + off + i * pts;
+  }
   __device__ void put(const cplx<T>* raw, int st, long long p, cplx<T> y1, cplx<T> y2, cplx<T>, cplx<T>) {
     v[off + p] = y1;
     v[off + pts + p] = y2;
-    acc[0].add_run(raw[0], y1);
-    acc[0].add_run(raw[st], y2);
+    if constexpr (H16) {
+      const cplx<T> w = raw[0];  // the bits of the two bf16 pairs
+      acc[0].add_run(bf16_unpack(__float_as_uint(w.x)), y1);
+      acc[0].add_run(bf16_unpack(__float_as_uint(w.y)), y2);
+    } else {
+      acc[0].add_run(raw[0], y1);
+      acc[0].add_run(raw[st], y2);
+    }
   }
 };
 

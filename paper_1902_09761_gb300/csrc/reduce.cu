@@ -8,6 +8,7 @@
 // every result deterministic.
 #include "acc.cuh"
 #include "apfc_internal.cuh"
+#include "bf16pair.cuh"
 
 namespace apfc {
 
@@ -59,7 +60,7 @@ template <typename T, int NP>
 __device__ void finalize_one(const void* partials, long long base, int npart, int j, KScal& k, int op) {
   // a pending final update was applied after the previous OP_OMEGA5: clear the flag
   if (op == OP_ALPHA && threadIdx.x == 0) k.just_done = 0;
-  if (op != OP_INIT && op != OP_NORMS && op != OP_RNORM && op != OP_BNORM && k.active == 0) return;
+  if (op != OP_INIT && op != OP_INIT3 && op != OP_NORMS && op != OP_RNORM && op != OP_BNORM && k.active == 0) return;
   __shared__ double2 res[kDotSlots];
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
@@ -74,6 +75,48 @@ __device__ void finalize_one(const void* partials, long long base, int npart, in
     if (threadIdx.x == 0) res[q] = a.value();
   }
   if (threadIdx.x == 0) scalar_update(k, op, res);
+}
+
+// Start of an FP32 solve from x0 = 0, in one pass: r = b, rhat = b rounded to bf16 with its
+// packed copy rh16 (bf16pair.cuh), and the partial sums of (r, r), (b, b) and (rhat, r) in
+// slots 0-2, laid out as k_dots' (batched runs: blockIdx.z selects the run).
+__global__ void __launch_bounds__(kThreads) k_init32(const float2* __restrict__ b, float2* __restrict__ r,
+                                                     float2* __restrict__ rhat, uint2* __restrict__ rh16,
+                                                     void* partials, OpCoef c, const RunGeom* rg) {
+  const int j = blockIdx.y;
+  long long o = 0, pbase = 0;
+  if (rg != nullptr) {
+    o = select_run(rg, blockIdx.z, c);
+    pbase = (long long)blockIdx.z * c.J * kDotSlots * kDotBlocks;
+  }
+  const long long pts = c.pts, o1 = o + 2LL * j * pts, o2 = o1 + pts;
+  uint2* q = rh16 + o / 2 + (long long)j * pts;
+  if (c.prof != nullptr && blockIdx.x == 0 && threadIdx.x == 0)
+    atomicAdd(c.prof + kid_of<float>(KID_DOTS), (unsigned long long)pts * (6 * sizeof(float2) + sizeof(uint2)));
+  Acc<float> a0, a2;
+  a0.zero();
+  a2.zero();
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < pts; p += (long long)gridDim.x * blockDim.x) {
+    const float2 b1 = b[o1 + p], b2 = b[o2 + p];
+    r[o1 + p] = b1;
+    r[o2 + p] = b2;
+    const unsigned h1 = bf16_pack(b1), h2 = bf16_pack(b2);
+    const float2 s1 = bf16_unpack(h1), s2 = bf16_unpack(h2);
+    rhat[o1 + p] = s1;
+    rhat[o2 + p] = s2;
+    q[p] = make_uint2(h1, h2);
+    a0.add(b1, b1);
+    a0.add(b2, b2);
+    a2.add(s1, b1);
+    a2.add(s2, b2);
+  }
+  block_reduce<float>(a0);
+  if (threadIdx.x == 0) {
+    a0.store(partials, pbase + (long long)(j * kDotSlots + 0) * kDotBlocks + blockIdx.x);
+    a0.store(partials, pbase + (long long)(j * kDotSlots + 1) * kDotBlocks + blockIdx.x);  // (b, b) = (r, r)
+  }
+  block_reduce<float>(a2);
+  if (threadIdx.x == 0) a2.store(partials, pbase + (long long)(j * kDotSlots + 2) * kDotBlocks + blockIdx.x);
 }
 
 template <typename T, int NP>
@@ -101,6 +144,13 @@ __global__ void k_finalize_batch(const void* partials, int npart_fixed, const Ru
 }
 
 }  // namespace
+
+void launch_init32(const float2* b, float2* r, float2* rhat, uint2* rh16, void* partials, const OpCoef& c,
+                   cudaStream_t s, const BatchLaunch* bl) {
+  ProfScope ps_(kid_of<float>(KID_DOTS), s);
+  k_init32<<<dim3(kDotBlocks, c.J, bl ? bl->R : 1), kThreads, 0, s>>>(b, r, rhat, rh16, partials, c,
+                                                                        bl ? bl->dev : nullptr);
+}
 
 template <typename T>
 void launch_dots(int npair, const DotPairs<T>& pr, void* partials, const OpCoef& c, const KScal* act, cudaStream_t s,
@@ -138,6 +188,8 @@ void launch_finalize_batch(int npair, const void* partials, int npart_fixed, con
     k_finalize_batch<T, 1><<<nb, kThreads, 0, s>>>(partials, npart_fixed, bl.dev, J, k, op, bl.tlay);
   else if (npair == 2)
     k_finalize_batch<T, 2><<<nb, kThreads, 0, s>>>(partials, npart_fixed, bl.dev, J, k, op, bl.tlay);
+  else if (npair == 3)
+    k_finalize_batch<T, 3><<<nb, kThreads, 0, s>>>(partials, npart_fixed, bl.dev, J, k, op, bl.tlay);
   else
     k_finalize_batch<T, 5><<<nb, kThreads, 0, s>>>(partials, npart_fixed, bl.dev, J, k, op, bl.tlay);
 }
